@@ -1,0 +1,404 @@
+"""Plain FP64 geometric multigrid with the kappa-cycle (Section 2.1, Algorithm 3).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Problem (Section 4): 2D rotated anisotropic diffusion on the unit square with
+homogeneous Dirichlet boundary, discretised by the nine-point stencil printed in
+Section 4, on an n x n interior grid (n = 2^k - 1, h = 1/(n+1)).
+
+Grid convention used by every function here:
+  * a grid function is a float64 array of shape (n, n) holding interior points only;
+  * index [j, i]: i is the x index, j is the y index, j+1 is "north";
+  * Dirichlet boundary values are zero and are never stored.
+A stencil is a 3x3 array ``st`` with ``st[1+dy, 1+dx]`` the coefficient that multiplies
+v(i+dx, j+dy) in (A v)(i, j).
+
+Readings of the paper taken here (each also listed in the design doc):
+  * The operator is A = S / h^2 with S the printed table (the table omits h^2).
+  * The top row of the printed table is north (j+1); then the corner entries are
+    NW = SE = +(1-eps)CS/2 and NE = SW = -(1-eps)CS/2, which is the standard
+    second-difference discretisation of -div(K grad u), K = R(theta) diag(1, eps) R^T.
+  * Coarse operators are Galerkin, A^{l+1} = R A^l P, with full weighting R and
+    bilinear P (named in Section 4 for the zebra solvers; used here for all solvers).
+  * Relaxation is damped Jacobi, v <- v + (omega / a0) (f - A v), a0 the stencil centre.
+  * The coarsest level is solved exactly (Algorithm 3, first step): v = f / a0 for a
+    1x1 grid, a dense Cholesky solve otherwise.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg
+
+__all__ = [
+    "fine_stencil", "fine_stencil_derivatives", "apply_stencil", "restrict_fw",
+    "prolong_bilinear", "galerkin_stencil", "jacobi", "Hierarchy", "CallRecorder",
+    "kcycle", "gamma_cycle", "f_cycle", "kcycle_adjoint", "cycle", "cycle_adjoint",
+    "residual", "relres", "solve", "pcg", "param_grads", "level_sizes",
+]
+
+
+# ----------------------------------------------------------------------------------------
+# Discretisation (Section 4)
+# ----------------------------------------------------------------------------------------
+
+def fine_stencil(theta: float, eps: float, n: int) -> np.ndarray:
+    """Nine-point stencil of Section 4 for angle theta and anisotropy eps, scaled by 1/h^2.
+
+    Centre 2(1+eps); west/east -(C^2 + eps S^2); south/north -(eps C^2 + S^2);
+    NW and SE +(1-eps)CS/2; NE and SW -(1-eps)CS/2; C = cos(theta), S = sin(theta).
+    """
+    h = 1.0 / (n + 1)
+    C, S = math.cos(theta), math.sin(theta)
+    cross = 0.5 * (1.0 - eps) * C * S
+    st = np.zeros((3, 3))
+    st[1, 1] = 2.0 * (1.0 + eps)                 # centre
+    st[1, 0] = st[1, 2] = -(C * C + eps * S * S)  # west, east
+    st[0, 1] = st[2, 1] = -(eps * C * C + S * S)  # south, north
+    st[2, 0] = cross                              # north-west
+    st[0, 2] = cross                              # south-east
+    st[2, 2] = -cross                             # north-east
+    st[0, 0] = -cross                             # south-west
+    return st / (h * h)
+
+
+def fine_stencil_derivatives(theta: float, eps: float, n: int):
+    """Derivatives d(stencil)/d(theta) and d(stencil)/d(eps) of ``fine_stencil``.
+
+    Differentiating the Section 4 entries term by term:
+      d/dtheta: centre 0; W/E +(1-eps) sin 2theta; S/N -(1-eps) sin 2theta;
+                NW/SE +(1-eps) cos 2theta / 2; NE/SW -(1-eps) cos 2theta / 2.
+      d/deps:   centre 2; W/E -S^2; S/N -C^2; NW/SE -CS/2; NE/SW +CS/2.
+    Both scaled by 1/h^2. Pinned by central differences of ``fine_stencil``.
+    """
+    h2 = (1.0 / (n + 1)) ** 2
+    C, S = math.cos(theta), math.sin(theta)
+    s2, c2 = math.sin(2 * theta), math.cos(2 * theta)
+    dth = np.zeros((3, 3))
+    dth[1, 0] = dth[1, 2] = (1.0 - eps) * s2
+    dth[0, 1] = dth[2, 1] = -(1.0 - eps) * s2
+    dth[2, 0] = dth[0, 2] = 0.5 * (1.0 - eps) * c2
+    dth[2, 2] = dth[0, 0] = -0.5 * (1.0 - eps) * c2
+    dep = np.zeros((3, 3))
+    dep[1, 1] = 2.0
+    dep[1, 0] = dep[1, 2] = -S * S
+    dep[0, 1] = dep[2, 1] = -C * C
+    dep[2, 0] = dep[0, 2] = -0.5 * C * S
+    dep[2, 2] = dep[0, 0] = 0.5 * C * S
+    return dth / h2, dep / h2
+
+
+def apply_stencil(st: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """(A v) for a constant 9-point stencil with zero Dirichlet values outside the grid."""
+    ny, nx = v.shape
+    padded = np.zeros((ny + 2, nx + 2))
+    padded[1:-1, 1:-1] = v
+    out = np.zeros_like(v)
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            out += st[1 + dy, 1 + dx] * padded[1 + dy:1 + dy + ny, 1 + dx:1 + dx + nx]
+    return out
+
+
+def residual(st: np.ndarray, v: np.ndarray, f: np.ndarray) -> np.ndarray:
+    """r = f - A v."""
+    return f - apply_stencil(st, v)
+
+
+# ----------------------------------------------------------------------------------------
+# Inter-grid transfers (full weighting and bilinear interpolation, Section 4)
+# ----------------------------------------------------------------------------------------
+
+def restrict_fw(r: np.ndarray) -> np.ndarray:
+    """Full-weighting restriction (1/16)[1 2 1; 2 4 2; 1 2 1].
+
+    Fine grid (2m+1)^2 -> coarse grid m^2; coarse point (J, I) sits on fine point
+    (2J+1, 2I+1), so all nine fine points it reads are interior.
+    """
+    nf = r.shape[0]
+    m = (nf - 1) // 2
+    weights = {-1: 1.0, 0: 2.0, 1: 1.0}
+    rows = 2 * np.arange(m) + 1
+    out = np.zeros((m, m))
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            out += (weights[dy] * weights[dx] / 16.0) * r[np.ix_(rows + dy, rows + dx)]
+    return out
+
+
+def prolong_bilinear(vc: np.ndarray) -> np.ndarray:
+    """Bilinear interpolation from an m x m coarse grid to the (2m+1)^2 fine grid.
+
+    Coarse values are injected at fine points with both indices odd; fine points with
+    one even index average their two coarse neighbours along that axis; fine points
+    with both indices even average their four diagonal coarse neighbours. Coarse
+    neighbours outside the grid are the zero Dirichlet values.
+    """
+    m = vc.shape[0]
+    nf = 2 * m + 1
+    pc = np.zeros((m + 2, m + 2))      # coarse grid with its zero boundary ring
+    pc[1:-1, 1:-1] = vc                # pc[J+1, I+1] = vc[J, I]
+    out = np.zeros((nf, nf))
+    out[1::2, 1::2] = vc
+    out[1::2, 0::2] = 0.5 * (pc[1:-1, :-1] + pc[1:-1, 1:])
+    out[0::2, 1::2] = 0.5 * (pc[:-1, 1:-1] + pc[1:, 1:-1])
+    out[0::2, 0::2] = 0.25 * (pc[:-1, :-1] + pc[:-1, 1:] + pc[1:, :-1] + pc[1:, 1:])
+    return out
+
+
+def galerkin_stencil(st: np.ndarray) -> np.ndarray:
+    """Coarse stencil of A_c = R A P (Section 4, Galerkin coarse-grid operator).
+
+    Written as the definition: apply P, then A, then R to a coarse unit vector e_c far
+    from the boundary. R A P e_c is column c of A_c; for a constant-coefficient operator
+    the row entry for offset d is A_c[c, c+d] = (R A P e_c)[c - d].
+    """
+    m = 5
+    c = 2
+    e = np.zeros((m, m))
+    e[c, c] = 1.0
+    col = restrict_fw(apply_stencil(st, prolong_bilinear(e)))
+    out = np.zeros((3, 3))
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            out[1 + dy, 1 + dx] = col[c - dy, c - dx]
+    return out
+
+
+def jacobi(st: np.ndarray, v: np.ndarray, f: np.ndarray, omega: float, sweeps: int) -> np.ndarray:
+    """Damped Jacobi: repeat ``sweeps`` times v <- v + (omega / a0)(f - A v)."""
+    w = omega / st[1, 1]
+    for _ in range(sweeps):
+        v = v + w * (f - apply_stencil(st, v))
+    return v
+
+
+def level_sizes(n: int, levels: int):
+    """Grid side per level, finest first: n, (n-1)/2, ... (Table 3: N = (2^n - 1)^2)."""
+    sizes = [n]
+    for _ in range(levels - 1):
+        sizes.append((sizes[-1] - 1) // 2)
+    return sizes
+
+
+# ----------------------------------------------------------------------------------------
+# Hierarchy
+# ----------------------------------------------------------------------------------------
+
+@dataclass
+class Hierarchy:
+    """Multigrid hierarchy: per-level stencils (level 1 finest) and cycle parameters."""
+    n: int
+    levels: int
+    theta: float
+    eps: float
+    nu1: int = 2
+    nu2: int = 2
+    omega: float = 0.8
+    stencils: list = field(default_factory=list)
+    sizes: list = field(default_factory=list)
+    _chol: object = None
+
+    def __post_init__(self):
+        k = int(round(math.log2(self.n + 1)))
+        if self.n < 1 or (1 << k) - 1 != self.n or not (1 <= self.levels <= k):
+            raise ValueError("n must be 2^k - 1 and 1 <= levels <= k")
+        self.sizes = level_sizes(self.n, self.levels)
+        st = fine_stencil(self.theta, self.eps, self.n)
+        self.stencils = [st]
+        for _ in range(self.levels - 1):
+            st = galerkin_stencil(st)
+            self.stencils.append(st)
+        # coarsest-level operator as a dense SPD matrix, factorised once
+        nc = self.sizes[-1]
+        dense = np.zeros((nc * nc, nc * nc))
+        for col in range(nc * nc):
+            e = np.zeros(nc * nc)
+            e[col] = 1.0
+            dense[:, col] = apply_stencil(self.stencils[-1], e.reshape(nc, nc)).ravel()
+        self._chol = scipy.linalg.cho_factor(dense, lower=True)
+
+    def stencil(self, level: int) -> np.ndarray:
+        return self.stencils[level - 1]
+
+    def coarsest_solve(self, f: np.ndarray) -> np.ndarray:
+        """Exact solve on the coarsest level: division for 1x1, dense Cholesky otherwise."""
+        nc = self.sizes[-1]
+        if nc == 1:
+            return f / self.stencils[-1][1, 1]
+        return scipy.linalg.cho_solve(self._chol, f.ravel()).reshape(nc, nc)
+
+
+class CallRecorder:
+    """Counts cycle-routine calls per level and the counters seen on the coarsest level."""
+
+    def __init__(self, levels: int):
+        self.per_level = [0] * (levels + 1)   # index by level 1..levels
+        self.coarsest_counters = []
+
+    def record(self, level: int, counter: int, coarsest: bool):
+        self.per_level[level] += 1
+        if coarsest:
+            self.coarsest_counters.append(counter)
+
+
+# ----------------------------------------------------------------------------------------
+# Cycles: Algorithm 3 (kappa), Algorithm 1 (gamma), Algorithm 2 (F), and the adjoint
+# ----------------------------------------------------------------------------------------
+
+def kcycle(h: Hierarchy, level: int, v: np.ndarray, f: np.ndarray, kappa: int,
+           rec: CallRecorder | None = None) -> np.ndarray:
+    """Algorithm 3: v <- kappa-cycle(v, f, A, level, n, kappa)."""
+    last = level == h.levels
+    if rec is not None:
+        rec.record(level, kappa, last)
+    if last:                                              # coarsest: solve and return
+        return h.coarsest_solve(f)
+    st = h.stencil(level)
+    v = jacobi(st, v, f, h.omega, h.nu1)                  # relax nu1 times
+    fc = restrict_fw(f - apply_stencil(st, v))            # restrict the residual
+    vc = np.zeros_like(fc)                                # v^{l+1} <- 0
+    vc = kcycle(h, level + 1, vc, fc, kappa, rec)         # call with counter kappa
+    if kappa > 1:
+        vc = kcycle(h, level + 1, vc, fc, kappa - 1, rec)  # then with kappa - 1
+    v = v + prolong_bilinear(vc)                           # coarse-grid correction
+    v = jacobi(st, v, f, h.omega, h.nu2)                   # relax nu2 times
+    return v
+
+
+def gamma_cycle(h: Hierarchy, level: int, v: np.ndarray, f: np.ndarray, gamma: int) -> np.ndarray:
+    """Algorithm 1: the classical gamma-cycle (gamma=1 V, gamma=2 W)."""
+    if level == h.levels:
+        return h.coarsest_solve(f)
+    st = h.stencil(level)
+    v = jacobi(st, v, f, h.omega, h.nu1)
+    fc = restrict_fw(f - apply_stencil(st, v))
+    vc = np.zeros_like(fc)
+    for _ in range(gamma):
+        vc = gamma_cycle(h, level + 1, vc, fc, gamma)
+    v = v + prolong_bilinear(vc)
+    return jacobi(st, v, f, h.omega, h.nu2)
+
+
+def f_cycle(h: Hierarchy, level: int, v: np.ndarray, f: np.ndarray) -> np.ndarray:
+    """Algorithm 2: the F-cycle (one recursive F-cycle, then one V-cycle)."""
+    if level == h.levels:
+        return h.coarsest_solve(f)
+    st = h.stencil(level)
+    v = jacobi(st, v, f, h.omega, h.nu1)
+    fc = restrict_fw(f - apply_stencil(st, v))
+    vc = np.zeros_like(fc)
+    vc = f_cycle(h, level + 1, vc, fc)
+    vc = gamma_cycle(h, level + 1, vc, fc, 1)
+    v = v + prolong_bilinear(vc)
+    return jacobi(st, v, f, h.omega, h.nu2)
+
+
+def kcycle_adjoint(h: Hierarchy, level: int, v: np.ndarray, f: np.ndarray, kappa: int) -> np.ndarray:
+    """Adjoint of Algorithm 3 (the cycle whose zero-start map is B^T).
+
+    With A symmetric, a constant Jacobi diagonal and R = P^T / 4, transposing the cycle's
+    error propagator swaps the pre- and post-smoothing counts and reverses the order of
+    the two coarse calls: the call with counter kappa-1 runs first (from zero), then the
+    call with counter kappa. Pinned by the dot-product test <x, B y> = <B^T x, y>.
+    """
+    if level == h.levels:
+        return h.coarsest_solve(f)
+    st = h.stencil(level)
+    v = jacobi(st, v, f, h.omega, h.nu2)
+    fc = restrict_fw(f - apply_stencil(st, v))
+    vc = np.zeros_like(fc)
+    if kappa > 1:
+        vc = kcycle_adjoint(h, level + 1, vc, fc, kappa - 1)
+    vc = kcycle_adjoint(h, level + 1, vc, fc, kappa)
+    v = v + prolong_bilinear(vc)
+    return jacobi(st, v, f, h.omega, h.nu1)
+
+
+def cycle(h: Hierarchy, v: np.ndarray, f: np.ndarray, kappa: int, rec: CallRecorder | None = None):
+    """One finest-level kappa-cycle."""
+    return kcycle(h, 1, v, f, kappa, rec)
+
+
+def cycle_adjoint(h: Hierarchy, v: np.ndarray, f: np.ndarray, kappa: int):
+    """One finest-level adjoint kappa-cycle."""
+    return kcycle_adjoint(h, 1, v, f, kappa)
+
+
+# ----------------------------------------------------------------------------------------
+# Solvers (Section 4: stand-alone cycles and CG preconditioned by one cycle)
+# ----------------------------------------------------------------------------------------
+
+def relres(h: Hierarchy, v: np.ndarray, f: np.ndarray) -> float:
+    """||f - A v||_2 / ||f||_2 over the finest interior points."""
+    return float(np.linalg.norm(residual(h.stencil(1), v, f)) / np.linalg.norm(f))
+
+
+def solve(h: Hierarchy, f: np.ndarray, kappa: int, tol: float, max_cycles: int,
+          v0: np.ndarray | None = None, adjoint: bool = False):
+    """Stand-alone solver: repeat finest-level cycles until ||f-Av|| / ||f|| <= tol.
+
+    Returns (v, history) with history[k-1] the relative residual after cycle k.
+    """
+    v = np.zeros_like(f) if v0 is None else v0.copy()
+    fnorm = np.linalg.norm(f)
+    hist = []
+    step = cycle_adjoint if adjoint else cycle
+    for _ in range(max_cycles):
+        v = step(h, v, f, kappa)
+        rho = float(np.linalg.norm(residual(h.stencil(1), v, f)) / fnorm)
+        hist.append(rho)
+        if rho <= tol:
+            break
+    return v, hist
+
+
+def pcg(h: Hierarchy, b: np.ndarray, kappa: int, tol: float, max_iters: int, flexible: bool = False):
+    """Conjugate gradients preconditioned by one kappa-cycle from a zero start (MGCG).
+
+    x0 = 0, r = b, z = B r, p = z; each iteration: q = A p, alpha = (r.z)/(p.q),
+    x += alpha p, r -= alpha q, stop when ||r||/||b|| <= tol, z = B r,
+    beta = (r_new.z_new)/(r.z) (or (r_new.(z_new - z_old))/(r.z) when ``flexible``),
+    p = z + beta p. Returns (x, history) with history[k-1] = ||r_k|| / ||b||.
+    """
+    st = h.stencil(1)
+    x = np.zeros_like(b)
+    r = b.copy()
+    bnorm = np.linalg.norm(b)
+    z = cycle(h, np.zeros_like(b), r, kappa)
+    p = z.copy()
+    rz = float(np.sum(r * z))
+    hist = []
+    for _ in range(max_iters):
+        q = apply_stencil(st, p)
+        alpha = rz / float(np.sum(p * q))
+        x = x + alpha * p
+        r = r - alpha * q
+        rho = float(np.linalg.norm(r) / bnorm)
+        hist.append(rho)
+        if rho <= tol:
+            break
+        z_new = cycle(h, np.zeros_like(b), r, kappa)
+        if flexible:
+            rz_new = float(np.sum(r * z_new))
+            beta = float(np.sum(r * (z_new - z))) / rz
+        else:
+            rz_new = float(np.sum(r * z_new))
+            beta = rz_new / rz
+        p = z_new + beta * p
+        z = z_new
+        rz = rz_new
+    return x, hist
+
+
+def param_grads(theta: float, eps: float, n: int, lam: np.ndarray, u: np.ndarray):
+    """dL/dtheta and dL/deps for u = A(theta, eps)^{-1} f and lam = A^{-T} dL/du.
+
+    Differentiating A u = f gives du/dp = -A^{-1} (dA/dp) u, hence
+    dL/dp = -lam^T (dA/dp) u with dA/dp the stencil derivative applied to u.
+    """
+    dth, dep = fine_stencil_derivatives(theta, eps, n)
+    return (-float(np.sum(lam * apply_stencil(dth, u))),
+            -float(np.sum(lam * apply_stencil(dep, u))))

@@ -1,0 +1,197 @@
+"""Pins of the oracle's cycles (CPU only).
+
+* recursion counts against the closed forms of Proposition 2.2, Proposition 2.4 and
+  Lemma 2.9 (coarsest calls carry counter kappa - j, C(n-1, j) times);
+* Proposition 2.1: kappa=1 is the V-cycle, kappa=2 the F-cycle, kappa>=n the W-cycle,
+  iterate for iterate against separately written Algorithms 1 and 2;
+* convergence to the dense direct solution;
+* the symmetry statement of Section 4 (V and W symmetric from a zero start, 1<kappa<n not)
+  and the adjoint cycle by the dot-product test.
+"""
+import math
+from collections import Counter
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+from paper_2010_00626_b300.inputs import rhs_uniform
+
+
+def level_calls_closed(kappa, level):
+    """Proposition 2.2."""
+    return sum(math.comb(level - 1, j) for j in range(0, min(kappa - 1, level - 1) + 1))
+
+
+def total_calls_closed(kappa, n):
+    """Proposition 2.4."""
+    return sum(math.comb(n, j) for j in range(1, min(kappa, n) + 1))
+
+
+def small_hierarchy(n=31, levels=None, theta=math.pi / 6, eps=1e-2, nu1=2, nu2=2):
+    levels = levels or int(round(math.log2(n + 1)))
+    return oracle.Hierarchy(n, levels, theta, eps, nu1=nu1, nu2=nu2)
+
+
+@pytest.mark.parametrize("levels", [1, 2, 3, 4, 5, 6])
+def test_recursion_counts_match_closed_forms(levels):
+    h = small_hierarchy(63, levels)
+    f = rhs_uniform(63, 0)
+    for kappa in range(1, levels + 3):
+        rec = oracle.CallRecorder(levels)
+        oracle.cycle(h, np.zeros_like(f), f, kappa, rec)
+        for lvl in range(1, levels + 1):
+            assert rec.per_level[lvl] == level_calls_closed(kappa, lvl)
+        assert sum(rec.per_level) == total_calls_closed(kappa, levels)
+        # Lemma 2.9: C(n-1, j) coarsest calls with counter kappa - j
+        seen = Counter(rec.coarsest_counters)
+        expect = {kappa - j: math.comb(levels - 1, j) for j in range(0, min(kappa - 1, levels - 1) + 1)}
+        assert dict(seen) == expect
+
+
+def test_total_calls_examples():
+    """Section 1: a W-cycle with ten levels makes 2^10 - 1 calls; Corollary 2.5."""
+    assert total_calls_closed(10, 10) == 1023
+    assert total_calls_closed(1, 12) == 12
+    assert [total_calls_closed(k, 12) for k in (1, 2, 3, 4, 5, 12)] == [12, 78, 298, 793, 1585, 4095]
+
+
+@pytest.mark.parametrize("n", [31, 63])
+def test_kappa_one_is_v_cycle_bitwise(n):
+    h = small_hierarchy(n)
+    f = rhs_uniform(n, 1)
+    v1 = v2 = np.zeros_like(f)
+    for _ in range(3):
+        v1 = oracle.cycle(h, v1, f, 1)
+        v2 = oracle.gamma_cycle(h, 1, v2, f, 1)
+        assert np.array_equal(v1, v2)
+
+
+@pytest.mark.parametrize("n", [31, 63])
+def test_kappa_two_is_f_cycle_bitwise(n):
+    h = small_hierarchy(n)
+    f = rhs_uniform(n, 2)
+    v1 = v2 = np.zeros_like(f)
+    for _ in range(3):
+        v1 = oracle.cycle(h, v1, f, 2)
+        v2 = oracle.f_cycle(h, 1, v2, f)
+        assert np.array_equal(v1, v2)
+
+
+@pytest.mark.parametrize("n", [31, 63])
+def test_kappa_at_least_levels_is_w_cycle_bitwise(n):
+    h = small_hierarchy(n)
+    f = rhs_uniform(n, 3)
+    for kappa in (h.levels, h.levels + 3):
+        v1 = v2 = np.zeros_like(f)
+        for _ in range(2):
+            v1 = oracle.cycle(h, v1, f, kappa)
+            v2 = oracle.gamma_cycle(h, 1, v2, f, 2)
+            assert np.array_equal(v1, v2)
+
+
+def test_kappa_between_is_neither_v_nor_w():
+    h = small_hierarchy(63)
+    f = rhs_uniform(63, 4)
+    z = np.zeros_like(f)
+    v3 = oracle.cycle(h, z, f, 3)
+    assert not np.allclose(v3, oracle.gamma_cycle(h, 1, z, f, 1))
+    assert not np.allclose(v3, oracle.gamma_cycle(h, 1, z, f, 2))
+
+
+def dense_matrix_of(h):
+    n = h.n
+    cols = []
+    for k in range(n * n):
+        e = np.zeros(n * n)
+        e[k] = 1.0
+        cols.append(oracle.apply_stencil(h.stencil(1), e.reshape(n, n)).ravel())
+    return np.stack(cols, axis=1)
+
+
+@pytest.mark.parametrize("n,levels", [(3, 2), (7, 3), (15, 4), (31, 5), (15, 3), (31, 3)])
+def test_solve_reaches_dense_direct_solution(n, levels):
+    h = small_hierarchy(n, levels, theta=math.pi / 3, eps=1e-2)
+    f = rhs_uniform(n, 5)
+    A = dense_matrix_of(h)
+    exact = scipy.linalg.solve(A, f.ravel(), assume_a="pos").reshape(n, n)
+    v, hist = oracle.solve(h, f, 3, 1e-14, 500)
+    assert hist[-1] <= 1e-14
+    assert np.linalg.norm(v - exact) <= 1e-12 * np.linalg.norm(exact)
+    # history entries are the residuals of the iterates
+    assert hist == sorted(hist, reverse=True) or hist[-1] < hist[0]
+
+
+def test_one_level_is_exact_in_one_cycle():
+    h = small_hierarchy(7, 1)
+    f = rhs_uniform(7, 6)
+    A = dense_matrix_of(h)
+    v = oracle.cycle(h, np.zeros_like(f), f, 1)
+    assert np.allclose(A @ v.ravel(), f.ravel(), rtol=0, atol=1e-13 * np.abs(f).max())
+
+
+def cycle_matrix(h, kappa, adjoint=False):
+    n = h.n
+    step = oracle.cycle_adjoint if adjoint else oracle.cycle
+    cols = []
+    for k in range(n * n):
+        e = np.zeros(n * n)
+        e[k] = 1.0
+        cols.append(step(h, np.zeros((n, n)), e.reshape(n, n), kappa).ravel())
+    return np.stack(cols, axis=1)
+
+
+def test_v_and_w_cycles_symmetric_others_not():
+    """Section 4: with symmetric Jacobi, nu1 = nu2 and R the adjoint of P, the V- and
+    W-cycle matrices from a zero start are symmetric; for 1 < kappa < n they are not."""
+    h = small_hierarchy(15, 4, theta=math.pi / 3, eps=1e-3)
+    # kappa = n-1 is symmetric too: its only difference from W is a second call at level
+    # n-1 that repeats an exact coarsest solve and so changes nothing (Section 1 remark).
+    for kappa in (1, 3, 4, 7):
+        B = cycle_matrix(h, kappa)
+        assert np.max(np.abs(B - B.T)) <= 1e-13 * np.abs(B).max()
+        assert np.all(np.linalg.eigvalsh(0.5 * (B + B.T)) > 0)
+    for kappa in (2,):
+        B = cycle_matrix(h, kappa)
+        assert np.max(np.abs(B - B.T)) > 1e-6 * np.abs(B).max()
+
+
+@pytest.mark.parametrize("nu", [(2, 2), (1, 3), (0, 2)])
+def test_adjoint_cycle_is_transpose(nu):
+    h = small_hierarchy(15, 4, theta=0.7, eps=1e-3, nu1=nu[0], nu2=nu[1])
+    for kappa in (1, 2, 3, 4):
+        B = cycle_matrix(h, kappa)
+        Bt = cycle_matrix(h, kappa, adjoint=True)
+        assert np.max(np.abs(Bt - B.T)) <= 1e-13 * np.abs(B).max()
+
+
+def test_adjoint_dot_product_large():
+    h = small_hierarchy(63, 6, theta=0.7, eps=1e-3)
+    rng = np.random.default_rng(9)
+    x, y = rng.standard_normal((2, 63, 63))
+    z = np.zeros((63, 63))
+    for kappa in (2, 3, 5):
+        lhs = np.sum(x * oracle.cycle(h, z, y, kappa))
+        rhs = np.sum(oracle.cycle_adjoint(h, z, x, kappa) * y)
+        assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+
+
+def test_cycle_from_nonzero_start_is_affine():
+    """v_out = v + B (f - A v): the cycle is the stationary iteration of its zero-start map."""
+    h = small_hierarchy(31, 5)
+    rng = np.random.default_rng(10)
+    v, f = rng.standard_normal((2, 31, 31))
+    for kappa in (1, 3):
+        lhs = oracle.cycle(h, v, f, kappa)
+        rhs = v + oracle.cycle(h, np.zeros_like(v), oracle.residual(h.stencil(1), v, f), kappa)
+        assert np.allclose(lhs, rhs, rtol=0, atol=1e-12 * np.abs(lhs).max())
+
+
+def test_coarsest_dense_when_levels_short():
+    """levels < k: the coarsest grid is larger than 1x1 and solved exactly (3x3 here)."""
+    h = small_hierarchy(127, 6, theta=math.pi / 6, eps=1e-2)
+    assert h.sizes[-1] == 3
+    f = rhs_uniform(3, 7)
+    v = h.coarsest_solve(f)
+    assert np.allclose(oracle.apply_stencil(h.stencils[-1], v), f, rtol=0, atol=1e-13 * np.abs(f).max())

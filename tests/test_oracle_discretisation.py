@@ -1,0 +1,167 @@
+"""Pins of the oracle's discretisation, transfers and Galerkin operator (CPU only).
+
+Each pin checks the oracle against something other than itself: the continuous operator
+-div(K grad u) on quadratics (the nine-point formula is exact there), the textbook Galerkin
+stencil of the 5-point Laplacian, dense matrix products, and exactness of the transfers
+on polynomials.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+CASES = [(0.0, 1.0), (math.pi / 6, 1e-2), (math.pi / 3, 1e-4), (0.7, 1e-3), (2.5, 0.3)]
+
+
+def diffusion_tensor(theta, eps):
+    """K = R(theta) diag(1, eps) R(theta)^T: strong diffusion along angle theta."""
+    c, s = math.cos(theta), math.sin(theta)
+    rot = np.array([[c, -s], [s, c]])
+    return rot @ np.diag([1.0, eps]) @ rot.T
+
+
+def grid(n):
+    h = 1.0 / (n + 1)
+    x = (np.arange(n) + 1) * h
+    return np.meshgrid(x, x)  # X[j, i] = x_i, Y[j, i] = y_j
+
+
+@pytest.mark.parametrize("theta,eps", CASES)
+@pytest.mark.parametrize("abc", [(1, 0, 0), (0, 1, 0), (0, 0, 1), (0.3, -0.7, 1.1)])
+def test_fine_stencil_exact_on_quadratics(theta, eps, abc):
+    """Section 4 stencil (top row = north, A = S/h^2) reproduces -div(K grad u) exactly
+    for u = a x^2 + b xy + c y^2, with K built from the rotation, not from the table."""
+    n = 31
+    a, b, c = abc
+    X, Y = grid(n)
+    u = a * X * X + b * X * Y + c * Y * Y
+    K = diffusion_tensor(theta, eps)
+    expected = -(2 * a * K[0, 0] + 2 * b * K[0, 1] + 2 * c * K[1, 1])
+    Au = oracle.apply_stencil(oracle.fine_stencil(theta, eps, n), u)[1:-1, 1:-1]
+    scale = 8.0 * (n + 1) ** 2 * np.max(np.abs(u))  # size of the cancelling terms
+    assert np.max(np.abs(Au - expected)) <= 1e-13 * scale
+
+
+def test_fine_stencil_symmetric_and_zero_row_sum():
+    for theta, eps in CASES:
+        st = oracle.fine_stencil(theta, eps, 15)
+        assert np.allclose(st, st[::-1, ::-1], rtol=0, atol=1e-12 * np.abs(st).max())
+        assert abs(st.sum()) <= 1e-13 * np.abs(st).max()
+
+
+def test_apply_dirichlet_is_dense_matrix_of_stencil_neighbours():
+    """Brute force: A as an explicit double loop over grid points and their neighbours."""
+    n = 7
+    st = oracle.fine_stencil(0.7, 1e-3, n)
+    v = np.random.default_rng(3).standard_normal((n, n))
+    out = np.zeros((n, n))
+    for j in range(n):
+        for i in range(n):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    jj, ii = j + dy, i + dx
+                    if 0 <= jj < n and 0 <= ii < n:
+                        out[j, i] += st[1 + dy, 1 + dx] * v[jj, ii]
+    assert np.allclose(oracle.apply_stencil(st, v), out, rtol=1e-14, atol=1e-12)
+
+
+def dense(op, shape_in):
+    """Dense matrix of a linear grid operator, by columns on unit vectors."""
+    size = shape_in[0] * shape_in[1]
+    cols = []
+    for k in range(size):
+        e = np.zeros(size)
+        e[k] = 1.0
+        cols.append(op(e.reshape(shape_in)).ravel())
+    return np.stack(cols, axis=1)
+
+
+def test_restriction_is_quarter_prolongation_transpose():
+    """Full weighting = P^T / 4 (the adjoint pair named in Section 4)."""
+    P = dense(oracle.prolong_bilinear, (7, 7))
+    R = dense(oracle.restrict_fw, (15, 15))
+    assert P.shape == (225, 49) and R.shape == (49, 225)
+    assert np.array_equal(R, P.T / 4.0)
+
+
+def test_prolongation_exact_on_bilinear_functions():
+    m = 7
+    n = 2 * m + 1
+    Xc, Yc = grid(m)
+    Xf, Yf = grid(n)
+    g = lambda X, Y: 0.4 + 1.3 * X - 0.8 * Y + 2.1 * X * Y
+    # a bilinear function does not vanish on the boundary; compare only where no
+    # boundary value enters: fine points whose coarse neighbours are all interior
+    pf = oracle.prolong_bilinear(g(Xc, Yc))
+    assert np.allclose(pf[1:-1, 1:-1], g(Xf, Yf)[1:-1, 1:-1], rtol=0, atol=1e-14)
+
+
+def test_restriction_exact_on_linear_functions():
+    n = 15
+    Xf, Yf = grid(n)
+    Xc, Yc = grid(7)
+    g = lambda X, Y: 0.4 + 1.3 * X - 0.8 * Y
+    assert np.allclose(oracle.restrict_fw(g(Xf, Yf)), g(Xc, Yc), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("theta,eps", CASES)
+def test_galerkin_equals_dense_rap_including_boundary_rows(theta, eps):
+    """Dense R A P on 15^2 -> 7^2 equals the constant coarse stencil on every row."""
+    nf, nc = 15, 7
+    st = oracle.fine_stencil(theta, eps, nf)
+    A = dense(lambda v: oracle.apply_stencil(st, v), (nf, nf))
+    P = dense(oracle.prolong_bilinear, (nc, nc))
+    R = dense(oracle.restrict_fw, (nf, nf))
+    Ac = R @ A @ P
+    stc = oracle.galerkin_stencil(st)
+    Ac_st = dense(lambda v: oracle.apply_stencil(stc, v), (nc, nc))
+    assert np.max(np.abs(Ac - Ac_st)) <= 1e-14 * np.abs(Ac).max()
+    assert np.allclose(Ac, Ac.T, rtol=0, atol=1e-14 * np.abs(Ac).max())
+
+
+def test_galerkin_of_laplacian_is_textbook_stencil():
+    """eps=1, theta=0 is the 5-point Laplacian; its Galerkin coarse operator with full
+    weighting and bilinear interpolation is (1/H^2)[-1/4 -1/2 -1/4; -1/2 3 -1/2; ...]."""
+    n = 31
+    H = 2.0 / (n + 1)
+    stc = oracle.galerkin_stencil(oracle.fine_stencil(0.0, 1.0, n))
+    expect = np.array([[-0.25, -0.5, -0.25], [-0.5, 3.0, -0.5], [-0.25, -0.5, -0.25]]) / H ** 2
+    assert np.allclose(stc, expect, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("theta,eps", CASES)
+def test_galerkin_consistent_on_quadratics(theta, eps):
+    """Two Galerkin steps stay consistent with -div(K grad u) at the coarse spacing."""
+    n = 63
+    st = oracle.fine_stencil(theta, eps, n)
+    for m in (31, 15):
+        st = oracle.galerkin_stencil(st)
+        X, Y = grid(m)
+        K = diffusion_tensor(theta, eps)
+        u = 0.3 * X * X - 0.7 * X * Y + 1.1 * Y * Y
+        expected = -(2 * 0.3 * K[0, 0] - 2 * 0.7 * K[0, 1] + 2 * 1.1 * K[1, 1])
+        Au = oracle.apply_stencil(st, u)[1:-1, 1:-1]
+        assert np.max(np.abs(Au - expected)) <= 1e-12 * np.abs(st).sum() * np.abs(u).max()
+
+
+def test_stencil_derivatives_match_central_differences():
+    n, d = 31, 1e-6
+    for theta, eps in CASES:
+        dth, dep = oracle.fine_stencil_derivatives(theta, eps, n)
+        fd_th = (oracle.fine_stencil(theta + d, eps, n) - oracle.fine_stencil(theta - d, eps, n)) / (2 * d)
+        fd_ep = (oracle.fine_stencil(theta, eps + d, n) - oracle.fine_stencil(theta, eps - d, n)) / (2 * d)
+        scale = (n + 1) ** 2
+        assert np.max(np.abs(dth - fd_th)) <= 1e-7 * scale
+        assert np.max(np.abs(dep - fd_ep)) <= 1e-7 * scale
+
+
+def test_level_sizes():
+    assert oracle.level_sizes(127, 7) == [127, 63, 31, 15, 7, 3, 1]
+    assert oracle.level_sizes(4095, 12)[-1] == 1
+    assert oracle.level_sizes(127, 6)[-1] == 3
+    with pytest.raises(ValueError):
+        oracle.Hierarchy(100, 3, 0.1, 0.1)
+    with pytest.raises(ValueError):
+        oracle.Hierarchy(127, 8, 0.1, 0.1)
