@@ -1,0 +1,151 @@
+/* kcycle.h -- C ABI of the B300 kappa-cycle multigrid library (libkcycle.so).
+ *
+ * Method: Avnat & Yavneh, "On the recursive structure of multigrid cycles" (arXiv 2010.00626).
+ * The cycle is Algorithm 3 (Section 2.1): relax nu1 times, restrict the residual, solve the
+ * coarse problem by one recursive call with cycle counter kappa and, if kappa > 1, a second
+ * call with kappa - 1, interpolate and correct, relax nu2 times. kappa = 1 is the V-cycle,
+ * kappa = 2 the F-cycle, kappa >= levels the W-cycle (Proposition 2.1).
+ *
+ * Problem (Section 4): rotated anisotropic diffusion on the unit square, homogeneous Dirichlet
+ * boundary, nine-point stencil of Section 4 scaled by 1/h^2 (h = 1/(n+1)); Galerkin coarse
+ * operators A^{l+1} = R A^l P with full weighting R and bilinear P; damped Jacobi relaxation;
+ * exact coarsest solve.
+ *
+ * Conventions shared by every entry point
+ *   Grid layout   A grid function on the finest level is n*n doubles, row-major, interior points
+ *                 only: element (i, j) (i = x index, j = y index, j+1 = north) is at [j*n + i].
+ *                 Boundary values are zero and never stored.
+ *   Pointers      Arguments documented "device" are CUDA device pointers to memory the caller
+ *                 owns (for example torch CUDA tensors); "host" arguments are ordinary host
+ *                 memory. The library keeps no reference to caller memory after a call returns.
+ *                 Every device pointer must be 8-byte aligned.
+ *   Streams       Work is queued on the handle's stream (mg_set_stream; default: a stream the
+ *                 handle creates). Entry points that return results on the host synchronise that
+ *                 stream; mg_kcycle, mg_kcycle_adjoint and mg_apply do not.
+ *   Errors        Every entry point returns an mg_status code; nothing is thrown across the ABI.
+ *                 Asynchronous CUDA errors surface at the next synchronising call as MG_ERR_CUDA.
+ *                 mg_last_error() gives a text for the last failure on the calling thread.
+ *   Threads       A handle must not be used from two host threads at once.
+ */
+#ifndef KCYCLE_H
+#define KCYCLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_ctx* mg_handle;
+
+typedef enum {
+  MG_OK = 0,
+  MG_NOT_CONVERGED = 1,   /* iteration limit reached before the tolerance           */
+  MG_ERR_ARG = -1,        /* invalid argument (sizes, kappa <= 0, tol <= 0, ...)    */
+  MG_ERR_NOMEM = -2,      /* device allocation failed                               */
+  MG_ERR_CUDA = -3,       /* a CUDA call or kernel failed                           */
+  MG_ERR_TIMEOUT = -4,    /* a device-side wait gave up                             */
+  MG_ERR_STATE = -5       /* handle not usable (NULL, destroyed, or failed setup)   */
+} mg_status;
+
+/* Any counter >= the number of levels is the W-cycle (Proposition 2.1). */
+#define MG_KAPPA_W 0x7fffffff
+
+/* Options for mg_set_option / mg_get_option. */
+typedef enum {
+  MG_OPT_OMEGA = 1,        /* Jacobi damping (Section 4: between 0.8 and 0.87); default 0.8     */
+  MG_OPT_COARSE_N = 2,     /* largest grid side handled by the single-CTA coarse-level kernel,
+                              which walks the kappa recursion on the device; one of 1, 3, 7,
+                              15, 31, 63                                                          */
+  MG_OPT_LEVELS = 3,       /* read-only: number of levels                                          */
+  MG_OPT_N = 4,            /* read-only: finest grid side                                          */
+  MG_OPT_LAUNCHES = 5      /* read-only: kernel launches in the last cycle graph built              */
+} mg_option;
+
+/* Set up the hierarchy for the Section 4 problem on an n x n interior grid.
+ *   n       grid side, n = 2^k - 1 with 1 <= k <= 14
+ *   eps     anisotropy, 0 < eps <= 1 (Section 4)
+ *   theta   angle of strong diffusion in radians (the paper's phi; K = R(theta) diag(1,eps) R^T)
+ *   levels  1 <= levels <= k; the coarsest grid side 2^(k-levels+1) - 1 must be <= 15
+ *   nu1,nu2 pre- and post-relaxation sweeps, 0..8
+ * The fine stencil, the Galerkin coarse stencils and the coarsest-level inverse are computed by
+ * device kernels. Allocates the coarse-level arrays (about n*n/3 doubles per vector kind) and one
+ * n*n temporary. On success *out owns them; release with mg_destroy.
+ * Errors: MG_ERR_ARG for invalid sizes/parameters, MG_ERR_NOMEM, MG_ERR_CUDA. */
+int mg_setup(int n, double eps, double theta, int levels, int nu1, int nu2, mg_handle* out);
+
+/* Free everything the handle owns. Safe on NULL. */
+int mg_destroy(mg_handle h);
+
+int mg_set_option(mg_handle h, int key, double value);
+int mg_get_option(mg_handle h, int key, double* value);
+
+/* Queue all further work of this handle on the given cudaStream_t (NULL = the handle's own). */
+int mg_set_stream(mg_handle h, void* cuda_stream);
+
+/* One finest-level kappa-cycle in place (Algorithm 3): v <- kappa-cycle(v, f, A, 1, levels, kappa).
+ *   v  device, n*n, in/out; f device, n*n, read-only; v and f must not overlap.
+ *   kappa >= 1 (MG_KAPPA_W or any value >= levels gives the W-cycle).
+ * Asynchronous on the handle's stream. */
+int mg_kcycle(mg_handle h, double* v, const double* f, int kappa);
+
+/* The adjoint cycle: the cycle whose zero-start map is the transpose B^T of the kappa-cycle's
+ * zero-start map B. It swaps nu1 and nu2 and makes the coarse call with counter kappa-1 before
+ * the call with kappa (transpose of the error propagator of Algorithm 3, with A symmetric,
+ * a constant Jacobi diagonal and R = P^T/4). Same arguments and behaviour as mg_kcycle. */
+int mg_kcycle_adjoint(mg_handle h, double* v, const double* f, int kappa);
+
+/* Stand-alone solver (Section 4, first solver): repeat finest-level kappa-cycles from the initial
+ * guess in v until ||f - A v||_2 / ||f||_2 <= tol or max_cycles cycles ran. The stopping test runs
+ * on the device after every cycle (one graph launch for the whole solve).
+ *   v device in/out (initial guess, then the solution); f device.
+ *   tol > 0; max_cycles >= 1.
+ *   cycles, final_relres  host, nullable: cycles run and the last relative residual.
+ *   history               host, nullable, max_cycles doubles: relative residual after each cycle.
+ * Returns MG_OK, or MG_NOT_CONVERGED if max_cycles ran without reaching tol. Synchronises. */
+int mg_solve(mg_handle h, double* v, const double* f, int kappa, double tol, int max_cycles,
+             int* cycles, double* final_relres, double* history);
+
+/* mg_solve on HOST buffers: copies f and the initial guess v to the device, solves, copies v
+ * back. v, f: host, n*n doubles (page-locked memory gives the fastest copies). */
+int mg_solve_host(mg_handle h, double* v, const double* f, int kappa, double tol, int max_cycles,
+                  int* cycles, double* final_relres, double* history);
+
+/* Conjugate gradients preconditioned by one kappa-cycle from a zero start per iteration (MGCG,
+ * Section 4, second solver). x0 = 0; stops when ||r||_2/||b||_2 <= tol or after max_iters.
+ *   x device out; b device. flexible != 0 uses beta = r_new.(z_new - z_old) / (r_old.z_old).
+ *   iters, final_relres, history: as for mg_solve (history: max_iters doubles).
+ * FP64 throughout. Allocates five n*n work vectors on first use. Synchronises. */
+int mg_pcg(mg_handle h, double* x, const double* b, int kappa, double tol, int max_iters,
+           int flexible, int* iters, double* final_relres, double* history);
+
+/* out = A v on the finest level (device pointers, n*n each). Asynchronous. */
+int mg_apply(mg_handle h, const double* v, double* out);
+
+/* ||f - A v||_2 on the finest level; result to host *norm. Synchronises. */
+int mg_residual_norm(mg_handle h, const double* v, const double* f, double* norm);
+
+/* Parameter gradients of a loss L through u = A(theta, eps)^{-1} f: with lambda = A^{-T} dL/du,
+ * dL/dtheta = -lambda^T (dA/dtheta) u and dL/deps = -lambda^T (dA/deps) u, dA/dp being the
+ * derivative of the Section 4 stencil. lambda, u: device n*n. dtheta, deps: host. Synchronises. */
+int mg_param_grads(mg_handle h, const double* lambda, const double* u, double* dtheta, double* deps);
+
+/* Copy the per-level stencils computed on the device to host memory: out[l*9 + (dy+1)*3 + (dx+1)]
+ * is the coefficient of v(i+dx, j+dy) in (A^l v)(i, j), l = 0 finest. out: host, max_levels*9.
+ * The number of levels written goes to *written (nullable). Synchronises. */
+int mg_stencils(mg_handle h, double* out, int max_levels, int* written);
+
+/* Call counts of one kappa-cycle of this handle's hierarchy: calls_per_level[l] for l = 0..levels-1
+ * (Proposition 2.2), the kernel launches of its cycle graph and the calls served by the coarse-level
+ * kernel. All host, nullable; calls_per_level holds levels entries. No device work. */
+int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* launches,
+                long long* coarse_calls);
+
+/* Static string for a status code. */
+const char* mg_status_string(int status);
+
+/* Text of the last failure seen on the calling host thread ("" if none). */
+const char* mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KCYCLE_H */

@@ -1,0 +1,824 @@
+// Host runtime and C ABI of the kappa-cycle multigrid (declared in include/kcycle.h).
+//
+// The handle owns the level hierarchy (per level: current estimate, right-hand side and a
+// temporary, Section 3.1), the per-level Galerkin stencils computed on the device, and a cache of
+// CUDA graphs. A cycle is Algorithm 3 unrolled on the host into kernel launches for the fine
+// levels -- pass A before the recursive calls, pass B after -- while every call at or below the
+// coarse threshold is one launch of the single-CTA coarse kernel, which walks the rest of the
+// recursion on the device. The launch sequence of a cycle is captured once into a graph and
+// replayed; stand-alone solves and MGCG put one cycle (or one PCG iteration) in the body of a
+// WHILE conditional node whose last kernel evaluates the stopping test on the device, so a whole
+// solve is a single graph launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/kcycle.h"
+#include "kernels.cuh"
+
+using namespace kc;
+
+namespace {
+
+thread_local char g_err[256] = "";
+
+#define KC_CUDA(call)                                                                       \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      snprintf(g_err, sizeof(g_err), "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),       \
+               __FILE__, __LINE__);                                                         \
+      return e_ == cudaErrorMemoryAllocation ? MG_ERR_NOMEM : MG_ERR_CUDA;                  \
+    }                                                                                       \
+  } while (0)
+
+#define KC_TRY(expr)          \
+  do {                        \
+    int s_ = (expr);          \
+    if (s_ < 0) return s_;    \
+  } while (0)
+
+constexpr int NT_SMALL = 256;
+constexpr int NT_BIG = 512;
+constexpr int NT_COARSE = 256;
+constexpr int NT_VEC = 256;
+constexpr int MAX_NU = 8;
+constexpr int VEC_BLOCKS = 148 * 8;
+constexpr int MAX_COARSE_N = 63;
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+struct Level {
+  int n = 0, ld = 0;
+  double* v = nullptr;    // current estimate (level 0: the caller's array)
+  double* tmp = nullptr;  // relaxed v between pass A and pass B
+  double* f = nullptr;    // right-hand side (level 0: the caller's array)
+};
+
+enum GraphKind { G_CYCLE = 1, G_SOLVE = 2, G_PCG = 3 };
+
+struct GraphEntry {
+  int kind = 0, kappa = 0, flag = 0;
+  const void* p0 = nullptr;
+  const void* p1 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int launches = 0;
+};
+
+// Per-call pointer binding of level 0 (caller memory) over the handle's own levels.
+struct Binding {
+  double* v0;
+  const double* f0;
+  int ld0;
+};
+
+}  // namespace
+
+struct mg_ctx {
+  int n = 0, k = 0, levels = 0, nu1 = 2, nu2 = 2;
+  double eps = 0, theta = 0, omega = 0.8;
+  int coarse_n = 15;  // largest side handled by the coarse kernel
+  int lc = 0;         // first level handled by the coarse kernel
+  Level lv[MAXL];
+  double* coef = nullptr;
+  float* coef32 = nullptr;
+  double* stencils = nullptr;   // MAXL*9
+  double* dstencil = nullptr;   // 18: d/dtheta, d/deps of the fine stencil
+  double* cinv = nullptr;
+  float* cinv32 = nullptr;
+  double* work = nullptr;
+  double* partial = nullptr;
+  double* partial2 = nullptr;
+  size_t npartial = 0;
+  double* scal = nullptr;
+  int* ints = nullptr;
+  double* hist = nullptr;
+  int hist_cap = 0;
+  double *pr = nullptr, *pp = nullptr, *pq = nullptr, *pz = nullptr, *pzold = nullptr;  // PCG vectors
+  double *hv = nullptr, *hf = nullptr;  // device copies for mg_solve_host
+  cudaStream_t own = nullptr;
+  cudaStream_t ext = nullptr;
+  bool has_ext = false;
+  std::vector<GraphEntry> graphs;
+  int last_launches = 0;
+  int launch_count = 0;  // counter while emitting
+  bool ok = false;
+
+  cudaStream_t stream() const { return has_ext ? ext : own; }
+};
+
+namespace {
+
+// ------------------------------------------------------------------------------------------
+// Tile configurations per level size
+// ------------------------------------------------------------------------------------------
+template <int BX, int BY, int NT>
+struct TileCfg {
+  static constexpr int bx = BX, by = BY, nt = NT;
+};
+using BigTile = TileCfg<64, 64, NT_BIG>;
+using MidTile = TileCfg<32, 32, NT_SMALL>;
+using SmallTile = TileCfg<16, 16, NT_SMALL>;
+
+int tile_class(int n) { return n >= 512 ? 2 : (n >= 64 ? 1 : 0); }
+
+template <typename Cfg>
+int launch_pass_a(const PassAArgs<double>& a, cudaStream_t s) {
+  dim3 grid((a.n + Cfg::bx - 1) / Cfg::bx, (a.n + Cfg::by - 1) / Cfg::by);
+  const size_t sm = pass_a_smem<double, Cfg::bx, Cfg::by>(a.nu);
+  pass_a_kernel<double, Cfg::bx, Cfg::by, Cfg::nt><<<grid, Cfg::nt, sm, s>>>(a);
+  KC_CUDA(cudaGetLastError());
+  return MG_OK;
+}
+template <typename Cfg>
+int launch_pass_b(const PassBArgs<double>& a, cudaStream_t s) {
+  dim3 grid((a.n + Cfg::bx - 1) / Cfg::bx, (a.n + Cfg::by - 1) / Cfg::by);
+  const size_t sm = pass_b_smem<double, Cfg::bx, Cfg::by>(a.nu, a.partial != nullptr);
+  pass_b_kernel<double, Cfg::bx, Cfg::by, Cfg::nt><<<grid, Cfg::nt, sm, s>>>(a);
+  KC_CUDA(cudaGetLastError());
+  return MG_OK;
+}
+
+template <typename Cfg>
+int set_smem_attrs() {
+  KC_CUDA(cudaFuncSetAttribute(pass_a_kernel<double, Cfg::bx, Cfg::by, Cfg::nt>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)pass_a_smem<double, Cfg::bx, Cfg::by>(MAX_NU)));
+  KC_CUDA(cudaFuncSetAttribute(pass_b_kernel<double, Cfg::bx, Cfg::by, Cfg::nt>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)pass_b_smem<double, Cfg::bx, Cfg::by>(MAX_NU, true)));
+  return MG_OK;
+}
+
+size_t pass_grid_blocks(int n) {
+  const int c = tile_class(n);
+  const int b = c == 2 ? 64 : (c == 1 ? 32 : 16);
+  const size_t g = (n + b - 1) / b;
+  return g * g;
+}
+
+size_t apply_grid_blocks(int n) {
+  return size_t((n + 31) / 32) * size_t((n + NT_VEC / 32 - 1) / (NT_VEC / 32));
+}
+
+// ------------------------------------------------------------------------------------------
+// Cycle emission (Algorithm 3 unrolled over the fine levels)
+// ------------------------------------------------------------------------------------------
+double* lv_v(mg_ctx* h, const Binding& b, int l) { return l == 0 ? b.v0 : h->lv[l].v; }
+const double* lv_f(mg_ctx* h, const Binding& b, int l) { return l == 0 ? b.f0 : h->lv[l].f; }
+int lv_ld(mg_ctx* h, const Binding& b, int l) { return l == 0 ? b.ld0 : h->lv[l].ld; }
+
+int emit_coarse(mg_ctx* h, const Binding& b, int k1, int k2, int zero1, bool adjoint, const int* skip,
+                cudaStream_t s) {
+  CoarseArgs<double> a;
+  a.v = lv_v(h, b, h->lc);
+  a.f = lv_f(h, b, h->lc);
+  a.coef = h->coef;
+  a.cinv = h->cinv;
+  a.skip = skip;
+  a.ldv = lv_ld(h, b, h->lc);
+  a.ldf = lv_ld(h, b, h->lc);
+  a.n_lc = h->lv[h->lc].n;
+  a.lc = h->lc;
+  a.L = h->levels;
+  a.nu1 = h->nu1;
+  a.nu2 = h->nu2;
+  a.k1 = k1;
+  a.k2 = k2;
+  a.zero1 = zero1;
+  a.adjoint = adjoint ? 1 : 0;
+  const size_t sm = coarse_smem<double>(a.n_lc, a.L - a.lc);
+  coarse_kernel<double, NT_COARSE><<<1, NT_COARSE, sm, s>>>(a);
+  KC_CUDA(cudaGetLastError());
+  ++h->launch_count;
+  return MG_OK;
+}
+
+int emit_pass_a(mg_ctx* h, const Binding& b, int l, bool zero, int nu, const int* skip, cudaStream_t s) {
+  PassAArgs<double> a;
+  a.vin = zero ? nullptr : lv_v(h, b, l);
+  a.vout = h->lv[l].tmp;
+  a.f = lv_f(h, b, l);
+  a.fc = h->lv[l + 1].f;
+  a.coef = h->coef;
+  a.skip = skip;
+  a.ldvin = lv_ld(h, b, l);
+  a.ldvout = h->lv[l].ld;
+  a.ldf = lv_ld(h, b, l);
+  a.ldc = h->lv[l + 1].ld;
+  a.n = h->lv[l].n;
+  a.nu = nu;
+  a.level = l;
+  ++h->launch_count;
+  switch (tile_class(a.n)) {
+    case 2: return launch_pass_a<BigTile>(a, s);
+    case 1: return launch_pass_a<MidTile>(a, s);
+    default: return launch_pass_a<SmallTile>(a, s);
+  }
+}
+
+int emit_pass_b(mg_ctx* h, const Binding& b, int l, int nu, double* partial, const int* skip, cudaStream_t s) {
+  PassBArgs<double> a;
+  a.vin = h->lv[l].tmp;
+  a.vout = lv_v(h, b, l);
+  a.f = lv_f(h, b, l);
+  a.vc = h->lv[l + 1].v;
+  a.coef = h->coef;
+  a.skip = skip;
+  a.partial = partial;
+  a.ldvin = h->lv[l].ld;
+  a.ldvout = lv_ld(h, b, l);
+  a.ldf = lv_ld(h, b, l);
+  a.ldc = h->lv[l + 1].ld;
+  a.n = h->lv[l].n;
+  a.nu = nu;
+  a.level = l;
+  ++h->launch_count;
+  switch (tile_class(a.n)) {
+    case 2: return launch_pass_b<BigTile>(a, s);
+    case 1: return launch_pass_b<MidTile>(a, s);
+    default: return launch_pass_b<SmallTile>(a, s);
+  }
+}
+
+// Counters of the two coarse calls made by a call with counter kappa (Algorithm 3); the adjoint
+// cycle makes them in the opposite order.
+void child_counters(int kappa, bool adjoint, int* first, int* second) {
+  if (!adjoint) {
+    *first = kappa;
+    *second = kappa > 1 ? kappa - 1 : 0;
+  } else {
+    *first = kappa > 1 ? kappa - 1 : kappa;
+    *second = kappa > 1 ? kappa : 0;
+  }
+}
+
+// emit call(l, kappa) for a fine level l < lc; `norm` adds residual partial sums at level 0
+int emit_call(mg_ctx* h, const Binding& b, int l, int kappa, bool zero, bool adjoint, bool norm,
+              const int* skip, cudaStream_t s) {
+  const int nu_pre = adjoint ? h->nu2 : h->nu1;
+  const int nu_post = adjoint ? h->nu1 : h->nu2;
+  KC_TRY(emit_pass_a(h, b, l, zero, nu_pre, skip, s));
+  int k1, k2;
+  child_counters(kappa, adjoint, &k1, &k2);
+  if (l + 1 >= h->lc) {
+    KC_TRY(emit_coarse(h, b, k1, k2, 1, adjoint, skip, s));
+  } else {
+    KC_TRY(emit_call(h, b, l + 1, k1, true, adjoint, false, skip, s));
+    if (k2 > 0) KC_TRY(emit_call(h, b, l + 1, k2, false, adjoint, false, skip, s));
+  }
+  return emit_pass_b(h, b, l, nu_post, norm && l == 0 ? h->partial : nullptr, skip, s);
+}
+
+int emit_apply(mg_ctx* h, const double* v, const double* f, double* out, double* partial, const int* skip,
+               cudaStream_t s) {
+  const int n = h->n;
+  dim3 grid((n + 31) / 32, (n + NT_VEC / 32 - 1) / (NT_VEC / 32));
+  apply_kernel<double, NT_VEC><<<grid, NT_VEC, 0, s>>>(v, f, out, h->coef, 0, n, n, partial, skip);
+  KC_CUDA(cudaGetLastError());
+  ++h->launch_count;
+  return MG_OK;
+}
+
+// One finest-level cycle. With norm, the last pass writes residual partial sums (or, when the
+// coarse kernel handles level 0, a separate residual pass does).
+int emit_cycle(mg_ctx* h, const Binding& b, int kappa, bool zero, bool adjoint, bool norm, const int* skip,
+               cudaStream_t s) {
+  if (h->lc == 0) {
+    KC_TRY(emit_coarse(h, b, kappa, 0, zero ? 1 : 0, adjoint, skip, s));
+    if (norm) KC_TRY(emit_apply(h, b.v0, b.f0, nullptr, h->partial, skip, s));
+    return MG_OK;
+  }
+  return emit_call(h, b, 0, kappa, zero, adjoint, norm, skip, s);
+}
+
+int norm_partials(mg_ctx* h) { return (int)(h->lc == 0 ? apply_grid_blocks(h->n) : pass_grid_blocks(h->n)); }
+
+// ------------------------------------------------------------------------------------------
+// Graph cache
+// ------------------------------------------------------------------------------------------
+GraphEntry* find_graph(mg_ctx* h, int kind, int kappa, int flag, const void* p0, const void* p1) {
+  for (auto& g : h->graphs)
+    if (g.kind == kind && g.kappa == kappa && g.flag == flag && g.p0 == p0 && g.p1 == p1) return &g;
+  return nullptr;
+}
+
+void drop_graphs(mg_ctx* h) {
+  for (auto& g : h->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+  }
+  h->graphs.clear();
+}
+
+GraphEntry* add_graph(mg_ctx* h, const GraphEntry& e) {
+  if (h->graphs.size() >= 16) {  // bounded cache: forget the oldest
+    auto& g = h->graphs.front();
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    h->graphs.erase(h->graphs.begin());
+  }
+  h->graphs.push_back(e);
+  return &h->graphs.back();
+}
+
+// Plain cycle graph: flag bit0 = zero start, bit1 = adjoint.
+int get_cycle_graph(mg_ctx* h, double* v, const double* f, int kappa, int flag, GraphEntry** out) {
+  if ((*out = find_graph(h, G_CYCLE, kappa, flag, v, f))) return MG_OK;
+  Binding b{v, f, h->n};
+  cudaGraph_t g;
+  h->launch_count = 0;
+  KC_CUDA(cudaStreamBeginCapture(h->own, cudaStreamCaptureModeThreadLocal));
+  const int st = emit_cycle(h, b, kappa, flag & 1, (flag & 2) != 0, false, nullptr, h->own);
+  const cudaError_t ce = cudaStreamEndCapture(h->own, &g);
+  if (st < 0) {
+    if (ce == cudaSuccess) cudaGraphDestroy(g);
+    return st;
+  }
+  KC_CUDA(ce);
+  GraphEntry e;
+  e.kind = G_CYCLE; e.kappa = kappa; e.flag = flag; e.p0 = v; e.p1 = f; e.graph = g;
+  e.launches = h->launch_count;
+  const cudaError_t ie = cudaGraphInstantiate(&e.exec, g, 0);
+  if (ie != cudaSuccess) {
+    cudaGraphDestroy(g);
+    KC_CUDA(ie);
+  }
+  h->last_launches = e.launches;
+  *out = add_graph(h, e);
+  return MG_OK;
+}
+
+// WHILE-loop graph whose body is captured from `body(handle)`.
+template <typename Body>
+int build_while_graph(mg_ctx* h, Body body, cudaGraph_t* g_out, cudaGraphExec_t* e_out) {
+  cudaGraph_t g;
+  KC_CUDA(cudaGraphCreate(&g, 0));
+  auto fail = [&](cudaError_t e) {
+    cudaGraphDestroy(g);
+    snprintf(g_err, sizeof(g_err), "while-graph: %s", cudaGetErrorString(e));
+    return MG_ERR_CUDA;
+  };
+  cudaGraphConditionalHandle ch;
+  cudaError_t e1 = cudaGraphConditionalHandleCreate(&ch, g, 1, cudaGraphCondAssignDefault);
+  if (e1 != cudaSuccess) return fail(e1);
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = ch;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  e1 = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+  if (e1 != cudaSuccess) return fail(e1);
+  cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+  e1 = cudaStreamBeginCaptureToGraph(h->own, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e1 != cudaSuccess) return fail(e1);
+  h->launch_count = 0;
+  const int st = body(ch);
+  cudaGraph_t captured;
+  const cudaError_t ce = cudaStreamEndCapture(h->own, &captured);
+  if (st < 0) {
+    cudaGraphDestroy(g);
+    return st;
+  }
+  if (ce != cudaSuccess) return fail(ce);
+  cudaGraphExec_t ex;
+  const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+  if (ie != cudaSuccess) return fail(ie);
+  *g_out = g;
+  *e_out = ex;
+  return MG_OK;
+}
+
+int ensure_hist(mg_ctx* h, int count) {
+  if (count <= h->hist_cap) return MG_OK;
+  if (h->hist) KC_CUDA(cudaFree(h->hist));
+  h->hist = nullptr;
+  h->hist_cap = 0;
+  KC_CUDA(cudaMalloc(&h->hist, sizeof(double) * (size_t)count));
+  h->hist_cap = count;
+  // history buffer moved: graphs that write it are stale
+  drop_graphs(h);
+  return MG_OK;
+}
+
+int launch_norm2(mg_ctx* h, const double* x, double* out_scalar, cudaStream_t s) {
+  const size_t len = (size_t)h->n * h->n;
+  dot_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, s>>>(x, x, nullptr, len, h->partial2, nullptr, nullptr);
+  KC_CUDA(cudaGetLastError());
+  sum_to_scalar_kernel<NT_VEC><<<1, NT_VEC, 0, s>>>(h->partial2, VEC_BLOCKS, out_scalar);
+  KC_CUDA(cudaGetLastError());
+  return MG_OK;
+}
+
+bool valid_handle(mg_handle h) { return h && h->ok; }
+
+int read_result(mg_ctx* h, cudaStream_t s, double tol, int* count_out, double* final_relres, double* history) {
+  int ints[NINT];
+  double scal[NSCAL];
+  KC_CUDA(cudaMemcpyAsync(ints, h->ints, sizeof(ints), cudaMemcpyDeviceToHost, s));
+  KC_CUDA(cudaMemcpyAsync(scal, h->scal, sizeof(scal), cudaMemcpyDeviceToHost, s));
+  KC_CUDA(cudaStreamSynchronize(s));
+  const int count = ints[I_COUNT];
+  if (history && count > 0) KC_CUDA(cudaMemcpy(history, h->hist, sizeof(double) * count, cudaMemcpyDeviceToHost));
+  if (count_out) *count_out = count;
+  if (final_relres) *final_relres = scal[S_LAST];
+  return scal[S_LAST] <= tol ? MG_OK : MG_NOT_CONVERGED;
+}
+
+int solve_impl(mg_handle h, double* v, const double* f, int kappa, double tol, int max_cycles, int* cycles,
+               double* final_relres, double* history) {
+  if (!valid_handle(h)) return MG_ERR_STATE;
+  if (!v || !f || kappa < 1 || !(tol > 0) || max_cycles < 1) return MG_ERR_ARG;
+  KC_TRY(ensure_hist(h, max_cycles));
+  cudaStream_t s = h->stream();
+  GraphEntry* ge = find_graph(h, G_SOLVE, kappa, 0, v, f);
+  if (!ge) {
+    GraphEntry e;
+    e.kind = G_SOLVE; e.kappa = kappa; e.flag = 0; e.p0 = v; e.p1 = f;
+    Binding b{v, f, h->n};
+    const int np = norm_partials(h);
+    KC_TRY(build_while_graph(h, [&](cudaGraphConditionalHandle ch) -> int {
+      KC_TRY(emit_cycle(h, b, kappa, false, false, true, h->ints + I_DONE, h->own));
+      finish_step_kernel<NT_VEC><<<1, NT_VEC, 0, h->own>>>(h->partial, np, h->scal, h->ints, h->hist, ch, 1);
+      KC_CUDA(cudaGetLastError());
+      ++h->launch_count;
+      return MG_OK;
+    }, &e.graph, &e.exec));
+    e.launches = h->launch_count;
+    ge = add_graph(h, e);
+  }
+  KC_TRY(launch_norm2(h, f, h->scal + S_FNORM2, s));
+  reset_state_kernel<<<1, 1, 0, s>>>(h->ints, max_cycles, h->scal, tol);
+  KC_CUDA(cudaGetLastError());
+  KC_CUDA(cudaGraphLaunch(ge->exec, s));
+  return read_result(h, s, tol, cycles, final_relres, history);
+}
+
+int alloc_levels(mg_ctx* h) {
+  // coarse-kernel levels: the first level whose side is <= coarse_n (at least the coarsest)
+  h->lc = h->levels - 1;
+  for (int l = 0; l < h->levels; ++l)
+    if (h->lv[l].n <= h->coarse_n) {
+      h->lc = l;
+      break;
+    }
+  for (int l = 0; l < h->levels; ++l) {
+    Level& L = h->lv[l];
+    const size_t bytes = sizeof(double) * (size_t)L.ld * L.n;
+    if (l < h->lc) KC_CUDA(cudaMalloc(&L.tmp, bytes));
+    if (l > 0 && l <= h->lc) {
+      KC_CUDA(cudaMalloc(&L.v, bytes));
+      KC_CUDA(cudaMalloc(&L.f, bytes));
+      KC_CUDA(cudaMemsetAsync(L.v, 0, bytes, h->own));
+      KC_CUDA(cudaMemsetAsync(L.f, 0, bytes, h->own));
+    }
+  }
+  return MG_OK;
+}
+
+int free_levels(mg_ctx* h) {
+  for (int l = 0; l < MAXL; ++l) {
+    if (l > 0) {
+      if (h->lv[l].v) KC_CUDA(cudaFree(h->lv[l].v));
+      if (h->lv[l].f) KC_CUDA(cudaFree(h->lv[l].f));
+      h->lv[l].v = h->lv[l].f = nullptr;
+    }
+    if (h->lv[l].tmp) KC_CUDA(cudaFree(h->lv[l].tmp));
+    h->lv[l].tmp = nullptr;
+  }
+  return MG_OK;
+}
+
+int run_setup_kernels(mg_ctx* h) {
+  setup_stencils_kernel<<<1, 32, 0, h->own>>>(h->theta, h->eps, h->n, h->levels, h->omega, h->coef, h->coef32,
+                                             h->stencils, h->dstencil);
+  KC_CUDA(cudaGetLastError());
+  const int nc = h->lv[h->levels - 1].n;
+  if (nc > 1) {
+    coarsest_inverse_kernel<<<1, 256, 0, h->own>>>(h->stencils, h->levels - 1, nc, h->work, h->cinv, h->cinv32);
+    KC_CUDA(cudaGetLastError());
+  }
+  KC_CUDA(cudaStreamSynchronize(h->own));
+  return MG_OK;
+}
+
+}  // namespace
+
+// ============================================================================================
+// C ABI
+// ============================================================================================
+extern "C" {
+
+const char* mg_status_string(int status) {
+  switch (status) {
+    case MG_OK: return "ok";
+    case MG_NOT_CONVERGED: return "not converged within the iteration limit";
+    case MG_ERR_ARG: return "invalid argument";
+    case MG_ERR_NOMEM: return "device allocation failed";
+    case MG_ERR_CUDA: return "CUDA error";
+    case MG_ERR_TIMEOUT: return "device-side wait timed out";
+    case MG_ERR_STATE: return "invalid handle";
+    default: return "unknown status";
+  }
+}
+
+const char* mg_last_error(void) { return g_err; }
+
+int mg_destroy(mg_handle h) {
+  if (!h) return MG_OK;
+  if (h->own) cudaStreamSynchronize(h->own);
+  drop_graphs(h);
+  free_levels(h);
+  void* ptrs[] = {h->coef, h->coef32, h->stencils, h->dstencil, h->cinv, h->cinv32, h->work, h->partial,
+                  h->partial2, h->scal, h->ints, h->hist, h->pr, h->pp, h->pq, h->pz, h->pzold, h->hv, h->hf};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->own) cudaStreamDestroy(h->own);
+  h->ok = false;
+  delete h;
+  return MG_OK;
+}
+
+int mg_setup(int n, double eps, double theta, int levels, int nu1, int nu2, mg_handle* out) {
+  if (!out) return MG_ERR_ARG;
+  *out = nullptr;
+  int k = 0;
+  while (k < 15 && ((1 << k) - 1) < n) ++k;
+  if (n < 1 || ((1 << k) - 1) != n || k > 14) return MG_ERR_ARG;
+  if (levels < 1 || levels > k || (k - levels + 1) > 4) return MG_ERR_ARG;
+  if (!(eps > 0.0) || !(eps <= 1.0) || !std::isfinite(theta)) return MG_ERR_ARG;
+  if (nu1 < 0 || nu2 < 0 || nu1 > MAX_NU || nu2 > MAX_NU) return MG_ERR_ARG;
+  mg_ctx* h = new (std::nothrow) mg_ctx();
+  if (!h) return MG_ERR_NOMEM;
+  h->n = n; h->k = k; h->levels = levels; h->nu1 = nu1; h->nu2 = nu2; h->eps = eps; h->theta = theta;
+  for (int l = 0; l < levels; ++l) {
+    h->lv[l].n = (1 << (k - l)) - 1;
+    h->lv[l].ld = l == 0 ? n : round_up(h->lv[l].n, 32);
+  }
+  auto fail = [&](int st) {
+    mg_destroy(h);
+    return st;
+  };
+  if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) return fail(MG_ERR_CUDA);
+  int st = alloc_levels(h);
+  if (st < 0) return fail(st);
+  const int nc = h->lv[levels - 1].n, N = nc * nc;
+  const size_t np = std::max(pass_grid_blocks(n), apply_grid_blocks(n)) + VEC_BLOCKS;
+  h->npartial = np;
+#define ALLOC(ptr, bytes) \
+  if (cudaMalloc(&(ptr), (bytes)) != cudaSuccess) return fail(MG_ERR_NOMEM)
+  ALLOC(h->coef, sizeof(double) * MAXL * NCOEF);
+  ALLOC(h->coef32, sizeof(float) * MAXL * NCOEF);
+  ALLOC(h->stencils, sizeof(double) * MAXL * 9);
+  ALLOC(h->dstencil, sizeof(double) * 18);
+  ALLOC(h->partial, sizeof(double) * np);
+  ALLOC(h->partial2, sizeof(double) * np);
+  ALLOC(h->scal, sizeof(double) * NSCAL);
+  ALLOC(h->ints, sizeof(int) * NINT);
+  if (N > 1) {
+    ALLOC(h->cinv, sizeof(double) * N * N);
+    ALLOC(h->cinv32, sizeof(float) * N * N);
+    ALLOC(h->work, sizeof(double) * N * N);
+  }
+#undef ALLOC
+  if (cudaMemsetAsync(h->ints, 0, sizeof(int) * NINT, h->own) != cudaSuccess) return fail(MG_ERR_CUDA);
+  if (cudaMemsetAsync(h->scal, 0, sizeof(double) * NSCAL, h->own) != cudaSuccess) return fail(MG_ERR_CUDA);
+  if ((st = run_setup_kernels(h)) < 0) return fail(st);
+  if ((st = set_smem_attrs<BigTile>()) < 0 || (st = set_smem_attrs<MidTile>()) < 0 ||
+      (st = set_smem_attrs<SmallTile>()) < 0)
+    return fail(st);
+  if (cudaFuncSetAttribute(coarse_kernel<double, NT_COARSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)coarse_smem<double>(MAX_COARSE_N, 6)) != cudaSuccess)
+    return fail(MG_ERR_CUDA);
+  h->ok = true;
+  *out = h;
+  return MG_OK;
+}
+
+int mg_set_option(mg_handle h, int key, double value) {
+  if (!valid_handle(h)) return MG_ERR_STATE;
+  switch (key) {
+    case MG_OPT_OMEGA: {
+      if (!(value > 0.0) || !(value < 2.0)) return MG_ERR_ARG;
+      KC_CUDA(cudaStreamSynchronize(h->stream()));
+      h->omega = value;
+      drop_graphs(h);
+      return run_setup_kernels(h);
+    }
+    case MG_OPT_COARSE_N: {
+      const int c = (int)value;
+      if (value != (double)c || !(c == 1 || c == 3 || c == 7 || c == 15 || c == 31 || c == 63)) return MG_ERR_ARG;
+      KC_CUDA(cudaStreamSynchronize(h->stream()));
+      drop_graphs(h);
+      KC_TRY(free_levels(h));
+      h->coarse_n = c;
+      KC_TRY(alloc_levels(h));
+      KC_CUDA(cudaStreamSynchronize(h->own));
+      return MG_OK;
+    }
+    default: return MG_ERR_ARG;
+  }
+}
+
+int mg_get_option(mg_handle h, int key, double* value) {
+  if (!value) return MG_ERR_ARG;
+  if (!valid_handle(h)) return MG_ERR_STATE;
+  switch (key) {
+    case MG_OPT_OMEGA: *value = h->omega; return MG_OK;
+    case MG_OPT_COARSE_N: *value = h->coarse_n; return MG_OK;
+    case MG_OPT_LEVELS: *value = h->levels; return MG_OK;
+    case MG_OPT_N: *value = h->n; return MG_OK;
+    case MG_OPT_LAUNCHES: *value = h->last_launches; return MG_OK;
+    default: return MG_ERR_ARG;
+  }
+}
+
+int mg_set_stream(mg_handle h, void* stream) {
+  if (!valid_handle(h)) return MG_ERR_STATE;
+  h->ext = (cudaStream_t)stream;
+  h->has_ext = stream != nullptr;
+  return MG_OK;
+}
+
+static int kcycle_common(mg_handle h, double* v, const double* f, int kappa, bool adjoint) {
+  if (!valid_handle(h)) return MG_ERR_STATE;
+  if (!v || !f || kappa < 1) return MG_ERR_ARG;
+  GraphEntry* ge;
+  KC_TRY(get_cycle_graph(h, v, f, kappa, adjoint ? 2 : 0, &ge));
+  KC_CUDA(cudaGraphLaunch(ge->exec, h->stream()));
+  return MG_OK;
+}
+
+int mg_kcycle(mg_handle h, double* v, const double* f, int kappa) { return kcycle_common(h, v, f, kappa, false); }
+
+int mg_kcycle_adjoint(mg_handle h, double* v, const double* f, int kappa) {
+  return kcycle_common(h, v, f, kappa, true);
+}
+
+int mg_solve(mg_handle h, double* v, const double* f, int kappa, double tol, int max_cycles, int* cycles,
+             double* final_relres, double* history) {
+  return solve_impl(h, v, f, kappa, tol, max_cycles, cycles, final_relres, history);
+}
+
+int mg_solve_host(mg_handle h, double* v, const double* f, int kappa, double tol, int max_cycles, int* cycles,
+                  double* final_relres, double* history) {
+  if (!valid_handle(h)) return MG_ERR_STATE;
+  if (!v || !f) return MG_ERR_ARG;
+  const size_t bytes = sizeof(double) * (size_t)h->n * h->n;
+  if (!h->hv) KC_CUDA(cudaMalloc(&h->hv, bytes));
+  if (!h->hf) KC_CUDA(cudaMalloc(&h->hf, bytes));
+  cudaStream_t s = h->stream();
+  KC_CUDA(cudaMemcpyAsync(h->hf, f, bytes, cudaMemcpyHostToDevice, s));
+  KC_CUDA(cudaMemcpyAsync(h->hv, v, bytes, cudaMemcpyHostToDevice, s));
+  const int st = solve_impl(h, h->hv, h->hf, kappa, tol, max_cycles, cycles, final_relres, history);
+  if (st < 0) return st;
+  KC_CUDA(cudaMemcpyAsync(v, h->hv, bytes, cudaMemcpyDeviceToHost, s));
+  KC_CUDA(cudaStreamSynchronize(s));
+  return st;
+}
+
+int mg_pcg(mg_handle h, double* x, const double* b, int kappa, double tol, int max_iters, int flexible, int* iters,
+           double* final_relres, double* history) {
+  if (!valid_handle(h)) return MG_ERR_STATE;
+  if (!x || !b || kappa < 1 || !(tol > 0) || max_iters < 1) return MG_ERR_ARG;
+  const size_t len = (size_t)h->n * h->n, bytes = sizeof(double) * len;
+  double** vecs[] = {&h->pr, &h->pp, &h->pq, &h->pz, &h->pzold};
+  for (double** p : vecs)
+    if (!*p) KC_CUDA(cudaMalloc(p, bytes));
+  KC_TRY(ensure_hist(h, max_iters));
+  cudaStream_t s = h->stream();
+  const int* done = h->ints + I_DONE;
+  GraphEntry* zc;  // z = B r from a zero start, as its own cached cycle graph
+  KC_TRY(get_cycle_graph(h, h->pz, h->pr, kappa, 1, &zc));
+  const int fl = flexible ? 1 : 0;
+  GraphEntry* ge = find_graph(h, G_PCG, kappa, fl, x, b);
+  if (!ge) {
+    GraphEntry e;
+    e.kind = G_PCG; e.kappa = kappa; e.flag = fl; e.p0 = x; e.p1 = b;
+    Binding bz{h->pz, h->pr, h->n};
+    const int napply = (int)apply_grid_blocks(h->n);
+    KC_TRY(build_while_graph(h, [&](cudaGraphConditionalHandle ch) -> int {
+      cudaStream_t o = h->own;
+      const int n = h->n;
+      dim3 grid((n + 31) / 32, (n + NT_VEC / 32 - 1) / (NT_VEC / 32));
+      apply_dot_kernel<NT_VEC><<<grid, NT_VEC, 0, o>>>(h->pp, h->pq, h->coef, n, h->partial, done);
+      pcg_alpha_kernel<NT_VEC><<<1, NT_VEC, 0, o>>>(h->partial, napply, h->scal, h->ints);
+      pcg_update_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, o>>>(x, h->pr, h->pp, h->pq, len, h->scal, h->partial,
+                                                             h->ints);
+      finish_step_kernel<NT_VEC><<<1, NT_VEC, 0, o>>>(h->partial, VEC_BLOCKS, h->scal, h->ints, h->hist, ch, 1);
+      KC_CUDA(cudaGetLastError());
+      KC_TRY(emit_cycle(h, bz, kappa, true, false, false, done, o));
+      dot_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, o>>>(h->pr, h->pz, fl ? h->pzold : nullptr, len, h->partial,
+                                                       h->partial2, done);
+      pcg_beta_kernel<NT_VEC><<<1, NT_VEC, 0, o>>>(h->partial, h->partial2, VEC_BLOCKS, fl, h->scal, h->ints);
+      pcg_p_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, o>>>(h->pp, h->pz, fl ? h->pzold : nullptr, len, h->scal, 1,
+                                                         h->ints);
+      KC_CUDA(cudaGetLastError());
+      h->launch_count += 7;
+      return MG_OK;
+    }, &e.graph, &e.exec));
+    e.launches = h->launch_count;
+    ge = add_graph(h, e);
+  }
+  // initialisation: x = 0, r = b, z = B r, p = z, rz = r.z
+  KC_CUDA(cudaMemsetAsync(x, 0, bytes, s));
+  KC_CUDA(cudaMemcpyAsync(h->pr, b, bytes, cudaMemcpyDeviceToDevice, s));
+  KC_TRY(launch_norm2(h, b, h->scal + S_FNORM2, s));
+  reset_state_kernel<<<1, 1, 0, s>>>(h->ints, max_iters, h->scal, tol);
+  KC_CUDA(cudaGetLastError());
+  KC_CUDA(cudaGraphLaunch(zc->exec, s));
+  pcg_p_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, s>>>(h->pp, h->pz, fl ? h->pzold : nullptr, len, h->scal, 0,
+                                                     h->ints);
+  dot_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, s>>>(h->pr, h->pz, nullptr, len, h->partial, nullptr, nullptr);
+  sum_to_scalar_kernel<NT_VEC><<<1, NT_VEC, 0, s>>>(h->partial, VEC_BLOCKS, h->scal + S_RZ);
+  KC_CUDA(cudaGetLastError());
+  KC_CUDA(cudaGraphLaunch(ge->exec, s));
+  return read_result(h, s, tol, iters, final_relres, history);
+}
+
+int mg_apply(mg_handle h, const double* v, double* out) {
+  if (!valid_handle(h)) return MG_ERR_STATE;
+  if (!v || !out) return MG_ERR_ARG;
+  return emit_apply(h, v, nullptr, out, nullptr, nullptr, h->stream());
+}
+
+int mg_residual_norm(mg_handle h, const double* v, const double* f, double* norm) {
+  if (!valid_handle(h)) return MG_ERR_STATE;
+  if (!v || !f || !norm) return MG_ERR_ARG;
+  cudaStream_t s = h->stream();
+  KC_TRY(emit_apply(h, v, f, nullptr, h->partial, nullptr, s));
+  sum_to_scalar_kernel<NT_VEC><<<1, NT_VEC, 0, s>>>(h->partial, (int)apply_grid_blocks(h->n), h->scal + S_LAST);
+  KC_CUDA(cudaGetLastError());
+  double r2;
+  KC_CUDA(cudaMemcpyAsync(&r2, h->scal + S_LAST, sizeof(double), cudaMemcpyDeviceToHost, s));
+  KC_CUDA(cudaStreamSynchronize(s));
+  *norm = std::sqrt(r2);
+  return MG_OK;
+}
+
+int mg_param_grads(mg_handle h, const double* lambda, const double* u, double* dtheta, double* deps) {
+  if (!valid_handle(h)) return MG_ERR_STATE;
+  if (!lambda || !u || !dtheta || !deps) return MG_ERR_ARG;
+  cudaStream_t s = h->stream();
+  const int n = h->n;
+  dim3 grid((n + 31) / 32, (n + NT_VEC / 32 - 1) / (NT_VEC / 32));
+  grad_kernel<NT_VEC><<<grid, NT_VEC, 0, s>>>(lambda, u, n, h->dstencil, h->partial, h->partial2);
+  const int np = (int)apply_grid_blocks(n);
+  sum_to_scalar_kernel<NT_VEC><<<1, NT_VEC, 0, s>>>(h->partial, np, h->scal + S_ALPHA);
+  sum_to_scalar_kernel<NT_VEC><<<1, NT_VEC, 0, s>>>(h->partial2, np, h->scal + S_BETA);
+  KC_CUDA(cudaGetLastError());
+  double r[NSCAL];
+  KC_CUDA(cudaMemcpyAsync(r, h->scal, sizeof(r), cudaMemcpyDeviceToHost, s));
+  KC_CUDA(cudaStreamSynchronize(s));
+  *dtheta = -r[S_ALPHA];
+  *deps = -r[S_BETA];
+  return MG_OK;
+}
+
+int mg_stencils(mg_handle h, double* out, int max_levels, int* written) {
+  if (!valid_handle(h)) return MG_ERR_STATE;
+  if (!out || max_levels < 1) return MG_ERR_ARG;
+  const int nl = std::min(max_levels, h->levels);
+  KC_CUDA(cudaStreamSynchronize(h->stream()));
+  KC_CUDA(cudaMemcpy(out, h->stencils, sizeof(double) * 9 * nl, cudaMemcpyDeviceToHost));
+  if (written) *written = nl;
+  return MG_OK;
+}
+
+int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* launches, long long* coarse_calls) {
+  if (!valid_handle(h)) return MG_ERR_STATE;
+  if (kappa < 1) return MG_ERR_ARG;
+  // walk Algorithm 3's recursion, counting only
+  std::vector<long long> calls(h->levels, 0);
+  long long fine_launches = 0, coarse = 0;
+  struct Walk {
+    mg_ctx* h;
+    std::vector<long long>& calls;
+    long long& fine_launches;
+    long long& coarse;
+    void call(int l, int kap) {
+      calls[l] += 1;
+      if (l >= h->lc) ++coarse;
+      if (l == h->levels - 1) return;
+      if (l < h->lc) fine_launches += 2;  // pass A + pass B
+      call(l + 1, kap);
+      if (kap > 1) call(l + 1, kap - 1);
+    }
+  } w{h, calls, fine_launches, coarse};
+  w.call(0, std::min(kappa, h->levels + 1));
+  // one coarse-kernel launch serves both calls of a fine parent (or the whole cycle when lc == 0)
+  const long long coarse_launches = h->lc == 0 ? 1 : calls[h->lc - 1];
+  if (calls_per_level)
+    for (int l = 0; l < h->levels; ++l) calls_per_level[l] = calls[l];
+  if (launches) *launches = fine_launches + coarse_launches;
+  if (coarse_calls) *coarse_calls = coarse;
+  return MG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,909 @@
+// Device kernels of the kappa-cycle multigrid (Avnat & Yavneh, arXiv 2010.00626) for sm_103a.
+//
+// Grid functions are row-major n x n arrays of interior points with a pitch (ld); element
+// (i, j) -- i the x index, j the y index, j+1 north -- is at [j*ld + i]. Dirichlet boundary
+// values are zero and never stored; every kernel treats points outside [0,n)^2 as zero.
+//
+// Level kernels (one launch per level visit, Section 2.1 / Algorithm 3):
+//   pass_a_kernel   relax nu1 times + residual + full-weighting restriction, fused in one
+//                   shared-memory tile (temporal blocking: the tile carries a halo of nu1+1
+//                   points and recomputes the shrinking halo, so v and f are read once and the
+//                   relaxed v and the coarse right-hand side are written once).
+//   pass_b_kernel   bilinear interpolation + correction + relax nu2 times (+ optional partial
+//                   sums of ||f - A v||^2 for the stopping test), fused the same way.
+//   coarse_kernel   one CTA that keeps every level at or below a small grid side in shared
+//                   memory and walks the kappa recursion itself (an explicit stack), so the
+//                   many sequential coarse-level calls cost no kernel launches.
+// All level arithmetic is done in T (double on the FP64 path); norms and dot products always
+// accumulate in double.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kc {
+
+constexpr int MAXL = 16;
+
+// Per-level coefficient table (NCOEF entries of type T per level).
+// A constant symmetric nine-point stencil has five distinct values: centre c0, west/east cwe,
+// south/north cns, north-west/south-east cnw and north-east/south-west cne.
+// Damped Jacobi v <- v + w (f - A v), w = omega/c0, is evaluated as
+//   b0 v + w f + bwe (vW+vE) + bns (vS+vN) + bnw (vNW+vSE) + bne (vNE+vSW)
+// with b0 = 1 - w c0 and b* = -w c*: 4 additions, 1 multiply and 5 multiply-adds per point.
+enum {
+  C_C0 = 0, C_WE, C_NS, C_NW, C_NE, C_W, C_B0, C_BWE, C_BNS, C_BNW, C_BNE,
+  C_ST = 12,  // 9 entries: full stencil st[(dy+1)*3 + (dx+1)] as computed
+  NCOEF = 24
+};
+
+template <typename T>
+struct Coef {
+  T c0, cwe, cns, cnw, cne, w, b0, bwe, bns, bnw, bne;
+};
+
+template <typename T>
+__device__ __forceinline__ Coef<T> load_coef(const T* __restrict__ tab, int level) {
+  const T* p = tab + level * NCOEF;
+  Coef<T> c;
+  c.c0 = p[C_C0]; c.cwe = p[C_WE]; c.cns = p[C_NS]; c.cnw = p[C_NW]; c.cne = p[C_NE];
+  c.w = p[C_W]; c.b0 = p[C_B0]; c.bwe = p[C_BWE]; c.bns = p[C_BNS]; c.bnw = p[C_BNW]; c.bne = p[C_BNE];
+  return c;
+}
+
+// Neighbour sums at position k of a row-major buffer with row stride W (k+W is north).
+template <typename T>
+struct Nb {
+  T c, we, ns, d1, d2;
+};
+template <typename T>
+__device__ __forceinline__ Nb<T> neighbours(const T* s, int k, int W) {
+  Nb<T> r;
+  r.c = s[k];
+  r.we = s[k - 1] + s[k + 1];
+  r.ns = s[k - W] + s[k + W];
+  r.d1 = s[k + W - 1] + s[k - W + 1];  // NW + SE
+  r.d2 = s[k + W + 1] + s[k - W - 1];  // NE + SW
+  return r;
+}
+
+// One damped-Jacobi update of the point with neighbourhood nb and right-hand side fv.
+template <typename T>
+__device__ __forceinline__ T jacobi_update(const Nb<T>& nb, T fv, const Coef<T>& c) {
+  T t = c.b0 * nb.c;
+  t = fma(c.w, fv, t);
+  t = fma(c.bwe, nb.we, t);
+  t = fma(c.bns, nb.ns, t);
+  t = fma(c.bnw, nb.d1, t);
+  t = fma(c.bne, nb.d2, t);
+  return t;
+}
+
+// Residual f - A v at the point.
+template <typename T>
+__device__ __forceinline__ T residual_at(const Nb<T>& nb, T fv, const Coef<T>& c) {
+  T t = fma(-c.c0, nb.c, fv);
+  t = fma(-c.cwe, nb.we, t);
+  t = fma(-c.cns, nb.ns, t);
+  t = fma(-c.cnw, nb.d1, t);
+  t = fma(-c.cne, nb.d2, t);
+  return t;
+}
+
+// (A v) at the point.
+template <typename T>
+__device__ __forceinline__ T apply_at(const Nb<T>& nb, const Coef<T>& c) {
+  T t = c.c0 * nb.c;
+  t = fma(c.cwe, nb.we, t);
+  t = fma(c.cns, nb.ns, t);
+  t = fma(c.cnw, nb.d1, t);
+  t = fma(c.cne, nb.d2, t);
+  return t;
+}
+
+// Full weighting (1/16)[1 2 1; 2 4 2; 1 2 1] of r around position k (row stride W).
+template <typename T>
+__device__ __forceinline__ T full_weight(const T* r, int k, int W) {
+  T e = (r[k - 1] + r[k + 1]) + (r[k - W] + r[k + W]);
+  T d = (r[k - W - 1] + r[k - W + 1]) + (r[k + W - 1] + r[k + W + 1]);
+  T t = T(0.25) * r[k];
+  t = fma(T(0.125), e, t);
+  return fma(T(0.0625), d, t);
+}
+
+// Visit every point of an Rw x Rh region with NT threads, lanes on consecutive x.
+template <int NT, typename F>
+__device__ __forceinline__ void for_region(int Rw, int Rh, F fn) {
+  const int q = NT / Rw, r = NT - q * Rw;
+  int ly = threadIdx.x / Rw, lx = threadIdx.x - ly * Rw;
+  while (ly < Rh) {
+    fn(lx, ly);
+    lx += r;
+    ly += q;
+    if (lx >= Rw) { lx -= Rw; ++ly; }
+  }
+}
+
+__device__ __forceinline__ bool inside(int gx, int gy, int n) {
+  return (unsigned)gx < (unsigned)n && (unsigned)gy < (unsigned)n;
+}
+
+// Deterministic block sum of one double per thread (fixed order); result valid in thread 0.
+// Callers that use `red` again must __syncthreads() first.
+template <int NT>
+__device__ __forceinline__ double block_sum(double x, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pass A: relax nu times from v (or from zero), then f_c = R (f - A v) (Algorithm 3, steps 2-4)
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct PassAArgs {
+  const T* vin;   // nullptr: zero initial guess (the v^{l+1} <- 0 of Algorithm 3)
+  T* vout;        // relaxed v (must not alias vin)
+  const T* f;
+  T* fc;          // coarse right-hand side, (n-1)/2 square
+  const T* coef;
+  const int* skip;  // nullable; kernel returns at once when *skip != 0
+  int ldvin, ldvout, ldf, ldc;
+  int n, nu, level;
+};
+
+// Shared memory: two v buffers and f, each (BX+2H+1) x (BY+2H+1), H = nu + 1.
+template <typename T, int BX, int BY>
+__host__ __device__ constexpr size_t pass_a_smem(int nu) {
+  return size_t(3) * (BX + 2 * (nu + 1) + 1) * (BY + 2 * (nu + 1) + 1) * sizeof(T);
+}
+
+template <typename T, int BX, int BY, int NT>
+__global__ void __launch_bounds__(NT) pass_a_kernel(const PassAArgs<T> a) {
+  if (a.skip && *a.skip) return;
+  static_assert(BX % 2 == 0 && BY % 2 == 0, "tiles start on even fine indices");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int H = a.nu + 1;
+  const int W = BX + 2 * H + 1, Hh = BY + 2 * H + 1;
+  T* s0 = reinterpret_cast<T*>(smem_raw);
+  T* s1 = s0 + W * Hh;
+  T* fs = s1 + W * Hh;
+  const int n = a.n;
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+  const int gx0 = x0 - H, gy0 = y0 - H;
+  const Coef<T> c = load_coef(a.coef, a.level);
+
+  // local (lx, ly) <-> global (gx0 + lx, gy0 + ly)
+  for_region<NT>(W, Hh, [&](int lx, int ly) {
+    const int gx = gx0 + lx, gy = gy0 + ly, k = ly * W + lx;
+    const bool in = inside(gx, gy, n);
+    s0[k] = (in && a.vin) ? a.vin[(size_t)gy * a.ldvin + gx] : T(0);
+    fs[k] = in ? a.f[(size_t)gy * a.ldf + gx] : T(0);
+  });
+  __syncthreads();
+
+  T* src = s0;
+  T* dst = s1;
+  for (int s = 1; s <= a.nu; ++s) {
+    const int g = a.nu - s + 1;  // sweep s is needed on the tile grown by g
+    const int lo = H - g, R = BX + 2 * g + 1, Ry = BY + 2 * g + 1;
+    for_region<NT>(R, Ry, [&](int rx, int ry) {
+      const int lx = lo + rx, ly = lo + ry, k = ly * W + lx;
+      dst[k] = inside(gx0 + lx, gy0 + ly, n) ? jacobi_update(neighbours(src, k, W), fs[k], c) : T(0);
+    });
+    __syncthreads();
+    T* t = src; src = dst; dst = t;
+  }
+
+  // relaxed v on the tile
+  for_region<NT>(BX, BY, [&](int tx, int ty) {
+    const int gx = x0 + tx, gy = y0 + ty;
+    if (inside(gx, gy, n)) a.vout[(size_t)gy * a.ldvout + gx] = src[(ty + H) * W + tx + H];
+  });
+  // residual on the tile plus one column/row beyond it (full weighting reads it)
+  for_region<NT>(BX + 1, BY + 1, [&](int tx, int ty) {
+    const int lx = H + tx, ly = H + ty, k = ly * W + lx;
+    dst[k] = inside(gx0 + lx, gy0 + ly, n) ? residual_at(neighbours(src, k, W), fs[k], c) : T(0);
+  });
+  __syncthreads();
+  // coarse point (I, J) sits on fine (2I+1, 2J+1); this tile owns I in [x0/2, x0/2 + BX/2)
+  const int nc = (n - 1) / 2;
+  for_region<NT>(BX / 2, BY / 2, [&](int ci, int cj) {
+    const int I = x0 / 2 + ci, J = y0 / 2 + cj;
+    if (I < nc && J < nc) {
+      const int k = (2 * cj + 1 + H) * W + (2 * ci + 1 + H);
+      a.fc[(size_t)J * a.ldc + I] = full_weight(dst, k, W);
+    }
+  });
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pass B: v <- v + P v_c, relax nu times (Algorithm 3, steps 7-8); optionally partial sums of
+// ||f - A v||^2 over the tile (one double per block) for the stopping test.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct PassBArgs {
+  const T* vin;   // v before correction
+  T* vout;        // corrected and relaxed v (must not alias vin)
+  const T* f;
+  const T* vc;    // coarse-level correction, (n-1)/2 square
+  const T* coef;
+  const int* skip;
+  double* partial;  // nullable: per-block sum of squared residuals of the result
+  int ldvin, ldvout, ldf, ldc;
+  int n, nu, level;
+};
+
+template <typename T, int BX, int BY>
+__host__ __device__ constexpr size_t pass_b_smem(int nu, bool norm) {
+  // block-sum scratch + two v buffers + f, (BX+2H) x (BY+2H) with H = nu + norm; coarse tile
+  return 64 * sizeof(double) +
+         size_t(3) * (BX + 2 * (nu + (norm ? 1 : 0))) * (BY + 2 * (nu + (norm ? 1 : 0))) * sizeof(T) +
+         size_t(BX / 2 + nu + (norm ? 1 : 0) + 3) * (BY / 2 + nu + (norm ? 1 : 0) + 3) * sizeof(T);
+}
+
+template <typename T, int BX, int BY, int NT>
+__global__ void __launch_bounds__(NT) pass_b_kernel(const PassBArgs<T> a) {
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int E = a.partial ? 1 : 0;
+  const int H = a.nu + E;
+  const int W = BX + 2 * H, Hh = BY + 2 * H;
+  const int n = a.n, nc = (n - 1) / 2;
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+  const int gx0 = x0 - H, gy0 = y0 - H;
+  // coarse indices that bilinear interpolation reads for fine x in [gx0, gx0 + W)
+  const int cx0 = (gx0 >> 1) - 1, cy0 = (gy0 >> 1) - 1;
+  const int CW = ((gx0 + W - 1) >> 1) - cx0 + 1, CH = ((gy0 + Hh - 1) >> 1) - cy0 + 1;
+  double* red = reinterpret_cast<double*>(smem_raw);  // NT/32 doubles for block_sum
+  T* s0 = reinterpret_cast<T*>(smem_raw + 64 * sizeof(double));
+  T* s1 = s0 + W * Hh;
+  T* fs = s1 + W * Hh;
+  T* cs = fs + W * Hh;
+  const Coef<T> c = load_coef(a.coef, a.level);
+
+  for_region<NT>(CW, CH, [&](int lx, int ly) {
+    const int cx = cx0 + lx, cy = cy0 + ly;
+    cs[ly * CW + lx] = inside(cx, cy, nc) ? a.vc[(size_t)cy * a.ldc + cx] : T(0);
+  });
+  __syncthreads();
+  auto cv = [&](int cx, int cy) { return cs[(cy - cy0) * CW + (cx - cx0)]; };
+  for_region<NT>(W, Hh, [&](int lx, int ly) {
+    const int gx = gx0 + lx, gy = gy0 + ly, k = ly * W + lx;
+    T v = T(0), fv = T(0);
+    if (inside(gx, gy, n)) {
+      fv = a.f[(size_t)gy * a.ldf + gx];
+      // fine (gx, gy): odd index = coarse point (gx-1)/2; even index between gx/2-1 and gx/2
+      T p;
+      const bool xo = gx & 1, yo = gy & 1;
+      const int hx = gx >> 1, hy = gy >> 1;
+      if (xo && yo) {
+        p = cv(hx, hy);
+      } else if (yo) {
+        p = T(0.5) * (cv(hx - 1, hy) + cv(hx, hy));
+      } else if (xo) {
+        p = T(0.5) * (cv(hx, hy - 1) + cv(hx, hy));
+      } else {
+        p = T(0.25) * ((cv(hx - 1, hy - 1) + cv(hx, hy - 1)) + (cv(hx - 1, hy) + cv(hx, hy)));
+      }
+      v = a.vin[(size_t)gy * a.ldvin + gx] + p;
+    }
+    s0[k] = v;
+    fs[k] = fv;
+  });
+  __syncthreads();
+
+  T* src = s0;
+  T* dst = s1;
+  for (int s = 1; s <= a.nu; ++s) {
+    const int g = a.nu - s + E;
+    const int lo = H - g, R = BX + 2 * g, Ry = BY + 2 * g;
+    for_region<NT>(R, Ry, [&](int rx, int ry) {
+      const int lx = lo + rx, ly = lo + ry, k = ly * W + lx;
+      dst[k] = inside(gx0 + lx, gy0 + ly, n) ? jacobi_update(neighbours(src, k, W), fs[k], c) : T(0);
+    });
+    __syncthreads();
+    T* t = src; src = dst; dst = t;
+  }
+  double ss = 0.0;
+  for_region<NT>(BX, BY, [&](int tx, int ty) {
+    const int gx = x0 + tx, gy = y0 + ty;
+    if (inside(gx, gy, n)) {
+      const int k = (ty + H) * W + tx + H;
+      a.vout[(size_t)gy * a.ldvout + gx] = src[k];
+      if (E) {
+        const double r = (double)residual_at(neighbours(src, k, W), fs[k], c);
+        ss = fma(r, r, ss);
+      }
+    }
+  });
+  if (E) {
+    const double tot = block_sum<NT>(ss, red);
+    if (threadIdx.x == 0) a.partial[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Coarse levels: one CTA walks Algorithm 3 for levels lc..L-1 entirely in shared memory.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct CoarseArgs {
+  T* v;            // global v at level lc (read when the first call is not zero-start; written back)
+  const T* f;      // global f at level lc
+  const T* coef;   // coefficient table of all levels
+  const T* cinv;   // dense inverse of the coarsest operator when its grid is larger than 1x1
+  const int* skip;
+  int ldv, ldf;
+  int n_lc;        // grid side of level lc
+  int lc, L;       // first coarse level and number of levels
+  int nu1, nu2;
+  int k1, k2;      // counters of the (up to) two calls made at level lc; k2 = 0: one call
+  int zero1;       // first call starts from zero
+  int adjoint;     // adjoint cycle: nu1 <-> nu2 and the kappa-1 call first
+};
+
+__host__ __device__ inline int coarse_side(int n_lc, int d) {
+  int s = n_lc;
+  for (int i = 0; i < d; ++i) s = (s - 1) / 2;
+  return s;
+}
+
+// Shared memory: per level v and f with a zero border ((n_l+2)^2 each), plus one temporary of
+// the largest level.
+template <typename T>
+__host__ __device__ inline size_t coarse_smem(int n_lc, int nlev) {
+  size_t tot = 0;
+  for (int d = 0; d < nlev; ++d) {
+    const int s = coarse_side(n_lc, d) + 2;
+    tot += 2 * size_t(s) * s;
+  }
+  tot += size_t(n_lc + 2) * (n_lc + 2);
+  return tot * sizeof(T);
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nlev = a.L - a.lc;
+  const int top_n = a.n_lc;
+  int side[MAXL], off_v[MAXL], off_f[MAXL];
+  T* base = reinterpret_cast<T*>(smem_raw);
+  int off = 0;
+  for (int d = 0; d < nlev; ++d) {
+    side[d] = coarse_side(top_n, d);
+    const int pp = (side[d] + 2) * (side[d] + 2);
+    off_v[d] = off; off += pp;
+    off_f[d] = off; off += pp;
+  }
+  T* tmp = base + off;
+  const int total = off + (top_n + 2) * (top_n + 2);
+  for (int k = threadIdx.x; k < total; k += NT) base[k] = T(0);  // borders must be zero
+  __syncthreads();
+  {
+    const int s = top_n, P = s + 2;
+    T* fv = base + off_f[0];
+    T* vv = base + off_v[0];
+    for (int k = threadIdx.x; k < s * s; k += NT) {
+      const int j = k / s, i = k - j * s;
+      fv[(j + 1) * P + i + 1] = a.f[(size_t)j * a.ldf + i];
+      if (!a.zero1) vv[(j + 1) * P + i + 1] = a.v[(size_t)j * a.ldv + i];
+    }
+  }
+  __syncthreads();
+
+  const int nu_pre = a.adjoint ? a.nu2 : a.nu1;
+  const int nu_post = a.adjoint ? a.nu1 : a.nu2;
+
+  // relax `sweeps` times on level d (in place: new values held in registers across a barrier)
+  constexpr int MAXP = (63 * 63 + NT - 1) / NT;
+  auto relax = [&](int d, int sweeps, bool zero) {
+    const int s = side[d], P = s + 2;
+    T* v = base + off_v[d];
+    const T* f = base + off_f[d];
+    const Coef<T> c = load_coef(a.coef, a.lc + d);
+    if (zero) {
+      for (int k = threadIdx.x; k < s * s; k += NT) {
+        const int j = k / s, i = k - j * s;
+        v[(j + 1) * P + i + 1] = T(0);
+      }
+      __syncthreads();
+    }
+    for (int it = 0; it < sweeps; ++it) {
+      T nv[MAXP];
+#pragma unroll
+      for (int q = 0; q < MAXP; ++q) {
+        const int k = threadIdx.x + q * NT;
+        if (k < s * s) {
+          const int j = k / s, i = k - j * s, kk = (j + 1) * P + i + 1;
+          nv[q] = jacobi_update(neighbours(v, kk, P), f[kk], c);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < MAXP; ++q) {
+        const int k = threadIdx.x + q * NT;
+        if (k < s * s) {
+          const int j = k / s, i = k - j * s;
+          v[(j + 1) * P + i + 1] = nv[q];
+        }
+      }
+      __syncthreads();
+    }
+  };
+  // f_{d+1} = R (f_d - A v_d)
+  auto restrict_residual = [&](int d) {
+    const int s = side[d], P = s + 2;
+    const T* v = base + off_v[d];
+    const T* f = base + off_f[d];
+    const Coef<T> c = load_coef(a.coef, a.lc + d);
+    for (int k = threadIdx.x; k < s * s; k += NT) {
+      const int j = k / s, i = k - j * s, kk = (j + 1) * P + i + 1;
+      tmp[kk] = residual_at(neighbours(v, kk, P), f[kk], c);
+    }
+    __syncthreads();
+    const int sc = side[d + 1], Pc = sc + 2;
+    T* fc = base + off_f[d + 1];
+    for (int k = threadIdx.x; k < sc * sc; k += NT) {
+      const int J = k / sc, I = k - J * sc;
+      // coarse (I, J) sits on fine (2I+1, 2J+1), padded position (2J+2, 2I+2)
+      fc[(J + 1) * Pc + I + 1] = full_weight(tmp, (2 * J + 2) * P + (2 * I + 2), P);
+    }
+    __syncthreads();
+  };
+  // v_d += P v_{d+1}; padded coarse index of (I, J) is (J+1)*Pc + I+1, borders are zero
+  auto prolong_add = [&](int d) {
+    const int s = side[d], P = s + 2, Pc = side[d + 1] + 2;
+    T* v = base + off_v[d];
+    const T* vc = base + off_v[d + 1];
+    for (int k = threadIdx.x; k < s * s; k += NT) {
+      const int j = k / s, i = k - j * s;
+      const int hx = i >> 1, hy = j >> 1;  // padded coarse column of coarse hx-1 is hx
+      T p;
+      const bool xo = i & 1, yo = j & 1;
+      if (xo && yo) {
+        p = vc[(hy + 1) * Pc + hx + 1];
+      } else if (yo) {
+        p = T(0.5) * (vc[(hy + 1) * Pc + hx] + vc[(hy + 1) * Pc + hx + 1]);
+      } else if (xo) {
+        p = T(0.5) * (vc[hy * Pc + hx + 1] + vc[(hy + 1) * Pc + hx + 1]);
+      } else {
+        p = T(0.25) * ((vc[hy * Pc + hx] + vc[hy * Pc + hx + 1]) + (vc[(hy + 1) * Pc + hx] + vc[(hy + 1) * Pc + hx + 1]));
+      }
+      v[(j + 1) * P + i + 1] += p;
+    }
+    __syncthreads();
+  };
+  auto coarsest = [&]() {
+    const int d = nlev - 1, s = side[d], P = s + 2;
+    T* v = base + off_v[d];
+    const T* f = base + off_f[d];
+    if (s == 1) {
+      if (threadIdx.x == 0) v[P + 1] = f[P + 1] / a.coef[(a.L - 1) * NCOEF + C_C0];
+    } else {
+      const int N = s * s;
+      for (int r = threadIdx.x; r < N; r += NT) {
+        T acc = T(0);
+        for (int q = 0; q < N; ++q) {
+          const int jq = q / s, iq = q - jq * s;
+          acc = fma(a.cinv[(size_t)r * N + q], f[(jq + 1) * P + iq + 1], acc);
+        }
+        tmp[r] = acc;
+      }
+      __syncthreads();
+      for (int r = threadIdx.x; r < N; r += NT) {
+        const int j = r / s, i = r - j * s;
+        v[(j + 1) * P + i + 1] = tmp[r];
+      }
+    }
+    __syncthreads();
+  };
+
+  struct Frame { int d, k, state, zero; };
+  Frame st[MAXL];
+  const int ncalls = a.k2 > 0 ? 2 : 1;
+  for (int call = 0; call < ncalls; ++call) {
+    int sp = 0;
+    st[sp++] = Frame{0, call == 0 ? a.k1 : a.k2, 0, call == 0 ? a.zero1 : 0};
+    while (sp > 0) {
+      Frame& fr = st[sp - 1];
+      if (fr.d == nlev - 1) {  // coarsest level: exact solve (ignores the incoming v)
+        coarsest();
+        --sp;
+        continue;
+      }
+      if (fr.state == 0) {
+        relax(fr.d, nu_pre, fr.zero != 0);
+        restrict_residual(fr.d);
+        fr.state = 1;
+        const int kf = a.adjoint ? (fr.k > 1 ? fr.k - 1 : fr.k) : fr.k;
+        st[sp++] = Frame{fr.d + 1, kf, 0, 1};
+        continue;
+      }
+      if (fr.state == 1) {
+        fr.state = 2;
+        const int ks = a.adjoint ? (fr.k > 1 ? fr.k : 0) : (fr.k > 1 ? fr.k - 1 : 0);
+        if (ks > 0) {
+          st[sp++] = Frame{fr.d + 1, ks, 0, 0};
+          continue;
+        }
+      }
+      prolong_add(fr.d);
+      relax(fr.d, nu_post, false);
+      --sp;
+    }
+  }
+  {
+    const int s = top_n, P = s + 2;
+    const T* vv = base + off_v[0];
+    for (int k = threadIdx.x; k < s * s; k += NT) {
+      const int j = k / s, i = k - j * s;
+      a.v[(size_t)j * a.ldv + i] = vv[(j + 1) * P + i + 1];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Setup: fine stencil (Section 4), Galerkin coarse stencils A^{l+1} = R A^l P, coefficient
+// tables in double and float, stencil derivatives, and the dense inverse of the coarsest operator.
+// ---------------------------------------------------------------------------------------------
+__device__ inline double hat1(int d) { return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.5 : 0.0); }
+
+__device__ inline void fill_coef(const double st[9], double omega, double* out, float* out32) {
+  const double c0 = st[4];
+  const double w = omega / c0;
+  double c[NCOEF];
+  for (int q = 0; q < NCOEF; ++q) c[q] = 0.0;
+  c[C_C0] = c0;
+  c[C_WE] = st[3];  // west (dy=0, dx=-1); east st[5] equal by symmetry
+  c[C_NS] = st[1];  // south (dy=-1, dx=0); north st[7]
+  c[C_NW] = st[6];  // north-west (dy=+1, dx=-1); south-east st[2]
+  c[C_NE] = st[8];  // north-east (dy=+1, dx=+1); south-west st[0]
+  c[C_W] = w;
+  c[C_B0] = 1.0 - w * c0;
+  c[C_BWE] = -w * c[C_WE];
+  c[C_BNS] = -w * c[C_NS];
+  c[C_BNW] = -w * c[C_NW];
+  c[C_BNE] = -w * c[C_NE];
+  for (int q = 0; q < 9; ++q) c[C_ST + q] = st[q];
+  for (int q = 0; q < NCOEF; ++q) {
+    out[q] = c[q];
+    out32[q] = (float)c[q];
+  }
+}
+
+// One thread builds all stencils; st index (dy+1)*3 + (dx+1).
+__global__ void setup_stencils_kernel(double theta, double eps, int n, int levels, double omega,
+                                      double* coef, float* coef32, double* stencils, double* dstencil) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double h = 1.0 / (n + 1);
+  const double h2 = h * h;
+  const double C = cos(theta), S = sin(theta);
+  const double cross = 0.5 * (1.0 - eps) * C * S;
+  double st[9];
+  st[4] = 2.0 * (1.0 + eps);
+  st[3] = st[5] = -(C * C + eps * S * S);
+  st[1] = st[7] = -(eps * C * C + S * S);
+  st[6] = cross;   // NW
+  st[2] = cross;   // SE
+  st[8] = -cross;  // NE
+  st[0] = -cross;  // SW
+  for (int q = 0; q < 9; ++q) st[q] /= h2;
+  // derivatives of the Section 4 entries with respect to theta and eps, scaled by 1/h^2
+  {
+    const double s2 = sin(2.0 * theta), c2 = cos(2.0 * theta);
+    double* dt = dstencil;
+    double* de = dstencil + 9;
+    dt[4] = 0.0;
+    dt[3] = dt[5] = (1.0 - eps) * s2;
+    dt[1] = dt[7] = -(1.0 - eps) * s2;
+    dt[6] = dt[2] = 0.5 * (1.0 - eps) * c2;
+    dt[8] = dt[0] = -0.5 * (1.0 - eps) * c2;
+    de[4] = 2.0;
+    de[3] = de[5] = -S * S;
+    de[1] = de[7] = -C * C;
+    de[6] = de[2] = -0.5 * C * S;
+    de[8] = de[0] = 0.5 * C * S;
+    for (int q = 0; q < 18; ++q) dstencil[q] /= h2;
+  }
+  for (int l = 0; l < levels; ++l) {
+    for (int q = 0; q < 9; ++q) stencils[l * 9 + q] = st[q];
+    fill_coef(st, omega, coef + l * NCOEF, coef32 + l * NCOEF);
+    // A_c(D) = sum_{a,b} r(a) S(b) p(a + b - 2D) with r = p/4, p the bilinear hat (separable):
+    // (A P e_J)(y) = sum_b S(b) p(y + b - 2J) and (R g)(I) = sum_a r(a) g(2I + a).
+    double sc[9];
+    for (int Dy = -1; Dy <= 1; ++Dy)
+      for (int Dx = -1; Dx <= 1; ++Dx) {
+        double acc = 0.0;
+        for (int ay = -1; ay <= 1; ++ay)
+          for (int ax = -1; ax <= 1; ++ax) {
+            const double r = 0.25 * hat1(ay) * hat1(ax);
+            for (int by = -1; by <= 1; ++by)
+              for (int bx = -1; bx <= 1; ++bx) {
+                const double pv = hat1(ay + by - 2 * Dy) * hat1(ax + bx - 2 * Dx);
+                if (pv != 0.0) acc += r * st[(by + 1) * 3 + (bx + 1)] * pv;
+              }
+          }
+        sc[(Dy + 1) * 3 + (Dx + 1)] = acc;
+      }
+    for (int q = 0; q < 9; ++q) st[q] = sc[q];
+  }
+}
+
+// Dense inverse of the coarsest operator (N = s*s <= 225) by Gauss-Jordan elimination without
+// pivoting (the matrix is symmetric positive definite). One block; work[N*N] is scratch.
+__global__ void coarsest_inverse_kernel(const double* stencils, int level, int s, double* work, double* inv,
+                                        float* inv32) {
+  const int N = s * s;
+  const double* st = stencils + level * 9;
+  for (int k = threadIdx.x; k < N * N; k += blockDim.x) {
+    const int r = k / N, q = k - r * N;
+    const int jr = r / s, ir = r - jr * s, jq = q / s, iq = q - jq * s;
+    const int dy = jq - jr, dx = iq - ir;
+    double v = 0.0;
+    if (dy >= -1 && dy <= 1 && dx >= -1 && dx <= 1) v = st[(dy + 1) * 3 + (dx + 1)];
+    work[k] = v;
+    inv[k] = (r == q) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  __shared__ double piv;
+  for (int p = 0; p < N; ++p) {
+    if (threadIdx.x == 0) piv = work[p * N + p];
+    __syncthreads();
+    const double ip = 1.0 / piv;
+    for (int q = threadIdx.x; q < N; q += blockDim.x) {
+      work[p * N + q] *= ip;
+      inv[p * N + q] *= ip;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < N * N; k += blockDim.x) {
+      const int r = k / N, q = k - r * N;
+      if (r != p) {
+        const double m = work[r * N + p];
+        if (q != p) work[k] -= m * work[p * N + q];
+        inv[k] -= m * inv[p * N + q];
+      }
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < N; r += blockDim.x)
+      if (r != p) work[r * N + p] = 0.0;
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < N * N; k += blockDim.x) inv32[k] = (float)inv[k];
+}
+
+// ---------------------------------------------------------------------------------------------
+// Whole-grid helpers (one point per thread): apply / residual with partial sums, dot products,
+// vector updates for PCG, finalisation of reductions.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ Nb<T> neighbours_global(const T* v, int i, int j, int n, int ld) {
+  auto at = [&](int ii, int jj) { return inside(ii, jj, n) ? v[(size_t)jj * ld + ii] : T(0); };
+  Nb<T> nb;
+  nb.c = v[(size_t)j * ld + i];
+  nb.we = at(i - 1, j) + at(i + 1, j);
+  nb.ns = at(i, j - 1) + at(i, j + 1);
+  nb.d1 = at(i - 1, j + 1) + at(i + 1, j - 1);
+  nb.d2 = at(i + 1, j + 1) + at(i - 1, j - 1);
+  return nb;
+}
+
+// out = A v (f == nullptr) or out = f - A v; partial sums of out^2 when partial != nullptr.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) apply_kernel(const T* __restrict__ v, const T* __restrict__ f, T* out,
+                                                   const T* coef, int level, int n, int ld, double* partial,
+                                                   const int* skip) {
+  if (skip && *skip) return;
+  __shared__ double red[NT / 32];
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int j = blockIdx.y * (NT / 32) + (threadIdx.x >> 5);
+  const Coef<T> c = load_coef(coef, level);
+  double ss = 0.0;
+  if (i < n && j < n) {
+    const Nb<T> nb = neighbours_global(v, i, j, n, ld);
+    const T r = f ? residual_at(nb, f[(size_t)j * ld + i], c) : apply_at(nb, c);
+    if (out) out[(size_t)j * ld + i] = r;
+    ss = (double)r * (double)r;
+  }
+  if (partial) {
+    const double t = block_sum<NT>(ss, red);
+    if (threadIdx.x == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// q = A p with partial sums of p.q (PCG).
+template <int NT>
+__global__ void __launch_bounds__(NT) apply_dot_kernel(const double* __restrict__ p, double* q, const double* coef,
+                                                       int n, double* partial, const int* skip) {
+  if (skip && *skip) return;
+  __shared__ double red[NT / 32];
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int j = blockIdx.y * (NT / 32) + (threadIdx.x >> 5);
+  const Coef<double> c = load_coef(coef, 0);
+  double ss = 0.0;
+  if (i < n && j < n) {
+    const Nb<double> nb = neighbours_global(p, i, j, n, n);
+    const double r = apply_at(nb, c);
+    q[(size_t)j * n + i] = r;
+    ss = nb.c * r;
+  }
+  const double t = block_sum<NT>(ss, red);
+  if (threadIdx.x == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+// partial sums of x.y (and of x.z into partial2 when z != nullptr) over a flat array of len
+template <int NT>
+__global__ void __launch_bounds__(NT) dot_kernel(const double* x, const double* y, const double* z, size_t len,
+                                                 double* partial, double* partial2, const int* skip) {
+  if (skip && *skip) return;
+  __shared__ double red[NT / 32];
+  double s1 = 0.0, s2 = 0.0;
+  for (size_t k = blockIdx.x * (size_t)NT + threadIdx.x; k < len; k += (size_t)gridDim.x * NT) {
+    s1 = fma(x[k], y[k], s1);
+    if (z) s2 = fma(x[k], z[k], s2);
+  }
+  double t = block_sum<NT>(s1, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+  if (z) {
+    __syncthreads();
+    t = block_sum<NT>(s2, red);
+    if (threadIdx.x == 0) partial2[blockIdx.x] = t;
+  }
+}
+
+// Deterministic sum of np partials (fixed order), valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double sum_partials(const double* partial, int np, double* red) {
+  double s = 0.0;
+  for (int k = threadIdx.x; k < np; k += NT) s += partial[k];
+  return block_sum<NT>(s, red);
+}
+
+// Scalar slots of the solver state on the device.
+enum {
+  S_FNORM2 = 0,   // ||f||^2 (or ||b||^2)
+  S_RZ,           // r.z of the previous PCG iteration
+  S_ALPHA,
+  S_BETA,
+  S_TOL,
+  S_LAST,         // last relative residual
+  NSCAL = 8
+};
+// Integer slots
+enum { I_DONE = 0, I_COUNT, I_MAX, NINT = 4 };
+
+template <int NT>
+__global__ void __launch_bounds__(NT) sum_to_scalar_kernel(const double* partial, int np, double* out) {
+  __shared__ double red[NT / 32];
+  const double s = sum_partials<NT>(partial, np, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// After a cycle (or a PCG update): rho = sqrt(sum) / ||f||; record it; decide whether to go on.
+// cond: conditional-node handle of the enclosing WHILE loop (used when use_cond != 0).
+template <int NT>
+__global__ void __launch_bounds__(NT) finish_step_kernel(const double* partial, int np, double* scal, int* ints,
+                                                         double* hist, cudaGraphConditionalHandle cond,
+                                                         int use_cond) {
+  __shared__ double red[NT / 32];
+  if (ints[I_DONE]) {
+    if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(cond, 0);
+    return;
+  }
+  const double s = sum_partials<NT>(partial, np, red);
+  if (threadIdx.x == 0) {
+    const double fn = sqrt(scal[S_FNORM2]);
+    const double rho = fn > 0.0 ? sqrt(s) / fn : sqrt(s);
+    const int k = ints[I_COUNT];
+    hist[k] = rho;
+    ints[I_COUNT] = k + 1;
+    scal[S_LAST] = rho;
+    const bool stop = (rho <= scal[S_TOL]) || (k + 1 >= ints[I_MAX]);
+    if (stop) ints[I_DONE] = 1;
+    if (use_cond) cudaGraphSetConditional(cond, stop ? 0 : 1);
+  }
+}
+
+// PCG: alpha = rz / (p.q) from the p.q partials.
+template <int NT>
+__global__ void __launch_bounds__(NT) pcg_alpha_kernel(const double* partial, int np, double* scal, const int* ints) {
+  __shared__ double red[NT / 32];
+  if (ints[I_DONE]) return;
+  const double pq = sum_partials<NT>(partial, np, red);
+  if (threadIdx.x == 0) scal[S_ALPHA] = scal[S_RZ] / pq;
+}
+
+// PCG: beta = (r.z_new [- r.z_old]) / rz_old; rz <- r.z_new.
+template <int NT>
+__global__ void __launch_bounds__(NT) pcg_beta_kernel(const double* partial, const double* partial2, int np,
+                                                      int flexible, double* scal, const int* ints) {
+  __shared__ double red[NT / 32];
+  if (ints[I_DONE]) return;
+  const double rz_new = sum_partials<NT>(partial, np, red);
+  __syncthreads();
+  double rz_old_new = 0.0;
+  if (flexible) rz_old_new = sum_partials<NT>(partial2, np, red);
+  if (threadIdx.x == 0) {
+    scal[S_BETA] = (flexible ? (rz_new - rz_old_new) : rz_new) / scal[S_RZ];
+    scal[S_RZ] = rz_new;
+  }
+}
+
+// x += alpha p; r -= alpha q; partial sums of r.r
+template <int NT>
+__global__ void __launch_bounds__(NT) pcg_update_kernel(double* x, double* r, const double* p, const double* q,
+                                                        size_t len, const double* scal, double* partial,
+                                                        const int* ints) {
+  if (ints[I_DONE]) return;
+  __shared__ double red[NT / 32];
+  const double alpha = scal[S_ALPHA];
+  double s = 0.0;
+  for (size_t k = blockIdx.x * (size_t)NT + threadIdx.x; k < len; k += (size_t)gridDim.x * NT) {
+    x[k] = fma(alpha, p[k], x[k]);
+    const double rk = fma(-alpha, q[k], r[k]);
+    r[k] = rk;
+    s = fma(rk, rk, s);
+  }
+  const double t = block_sum<NT>(s, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+// p = z + beta p (use_beta) or p = z; optional copy z -> zold
+template <int NT>
+__global__ void __launch_bounds__(NT) pcg_p_kernel(double* p, const double* z, double* zold, size_t len,
+                                                   const double* scal, int use_beta, const int* ints) {
+  if (ints[I_DONE]) return;
+  const double beta = use_beta ? scal[S_BETA] : 0.0;
+  for (size_t k = blockIdx.x * (size_t)NT + threadIdx.x; k < len; k += (size_t)gridDim.x * NT) {
+    const double zk = z[k];
+    p[k] = use_beta ? fma(beta, p[k], zk) : zk;
+    if (zold) zold[k] = zk;
+  }
+}
+
+// Parameter gradients: partial sums of lambda . (dA/dtheta u) and lambda . (dA/deps u).
+template <int NT>
+__global__ void __launch_bounds__(NT) grad_kernel(const double* lam, const double* u, int n, const double* dst,
+                                                  double* partial_th, double* partial_ep) {
+  __shared__ double red[NT / 32];
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int j = blockIdx.y * (NT / 32) + (threadIdx.x >> 5);
+  double s_th = 0.0, s_ep = 0.0;
+  if (i < n && j < n) {
+    double a_th = 0.0, a_ep = 0.0;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int ii = i + dx, jj = j + dy;
+        if (inside(ii, jj, n)) {
+          const double uv = u[(size_t)jj * n + ii];
+          a_th = fma(dst[(dy + 1) * 3 + (dx + 1)], uv, a_th);
+          a_ep = fma(dst[9 + (dy + 1) * 3 + (dx + 1)], uv, a_ep);
+        }
+      }
+    const double l = lam[(size_t)j * n + i];
+    s_th = l * a_th;
+    s_ep = l * a_ep;
+  }
+  double t = block_sum<NT>(s_th, red);
+  if (threadIdx.x == 0) partial_th[blockIdx.y * gridDim.x + blockIdx.x] = t;
+  __syncthreads();
+  t = block_sum<NT>(s_ep, red);
+  if (threadIdx.x == 0) partial_ep[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void reset_state_kernel(int* ints, int max_iters, double* scal, double tol) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    ints[I_DONE] = 0;
+    ints[I_COUNT] = 0;
+    ints[I_MAX] = max_iters;
+    scal[S_TOL] = tol;
+  }
+}
+
+}  // namespace kc
