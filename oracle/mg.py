@@ -19,7 +19,9 @@ Readings of the paper taken here (each also listed in the design doc):
     NW = SE = +(1-eps)CS/2 and NE = SW = -(1-eps)CS/2, which is the standard
     second-difference discretisation of -div(K grad u), K = R(theta) diag(1, eps) R^T.
   * Coarse operators are Galerkin, A^{l+1} = R A^l P, with full weighting R and
-    bilinear P (named in Section 4 for the zebra solvers; used here for all solvers).
+    bilinear P (named in Section 4 for the zebra solvers; used here for all solvers); the
+    centre of each coarse stencil is evaluated from the exact zero-row-sum identity
+    (``zero_row_sum_centre``).
   * Relaxation is damped Jacobi, v <- v + (omega / a0) (f - A v), a0 the stencil centre.
   * The coarsest level is solved exactly (Algorithm 3, first step): v = f / a0 for a
     1x1 grid, a dense Cholesky solve otherwise.
@@ -34,7 +36,7 @@ import scipy.linalg
 
 __all__ = [
     "fine_stencil", "fine_stencil_derivatives", "apply_stencil", "restrict_fw",
-    "prolong_bilinear", "galerkin_stencil", "jacobi", "Hierarchy", "CallRecorder",
+    "prolong_bilinear", "galerkin_stencil", "zero_row_sum_centre", "jacobi", "Hierarchy", "CallRecorder",
     "kcycle", "gamma_cycle", "f_cycle", "kcycle_adjoint", "cycle", "cycle_adjoint",
     "residual", "relres", "solve", "pcg", "param_grads", "level_sizes",
 ]
@@ -167,6 +169,27 @@ def galerkin_stencil(st: np.ndarray) -> np.ndarray:
     return out
 
 
+def zero_row_sum_centre(st: np.ndarray) -> np.ndarray:
+    """Coarse stencil with its centre evaluated from the zero-row-sum identity.
+
+    The Section 4 stencil annihilates constants (its entries sum to 2(1+eps)(1 - C^2 - S^2) = 0),
+    and the Galerkin map keeps the entry sum of a stencil (sum_D p(x - 2D) = 1 and sum_a r(a) = 1)
+    while scaling the entries by about 1/4 per level, so every exact coarse stencil sums to zero.
+    In FP64 the rounding of that sum would grow fourfold per level relative to the stencil
+    (about 1e-10 at level 11); setting centre = -(sum of the eight off-centre entries, summed in
+    row-major order) keeps each coarse stencil within a few ulp of the exact Galerkin stencil.
+    Pinned against exact rational arithmetic in the tests.
+    """
+    out = st.copy()
+    off = 0.0
+    for dy in (0, 1, 2):
+        for dx in (0, 1, 2):
+            if (dy, dx) != (1, 1):
+                off += float(st[dy, dx])
+    out[1, 1] = -off
+    return out
+
+
 def jacobi(st: np.ndarray, v: np.ndarray, f: np.ndarray, omega: float, sweeps: int) -> np.ndarray:
     """Damped Jacobi: repeat ``sweeps`` times v <- v + (omega / a0)(f - A v)."""
     w = omega / st[1, 1]
@@ -209,7 +232,7 @@ class Hierarchy:
         st = fine_stencil(self.theta, self.eps, self.n)
         self.stencils = [st]
         for _ in range(self.levels - 1):
-            st = galerkin_stencil(st)
+            st = zero_row_sum_centre(galerkin_stencil(st))
             self.stencils.append(st)
         # coarsest-level operator as a dense SPD matrix, factorised once
         nc = self.sizes[-1]

@@ -165,3 +165,42 @@ def test_level_sizes():
         oracle.Hierarchy(100, 3, 0.1, 0.1)
     with pytest.raises(ValueError):
         oracle.Hierarchy(127, 8, 0.1, 0.1)
+
+
+def _galerkin_exact(S):
+    """R A P of a 3x3 stencil in exact rational arithmetic (independent of the oracle)."""
+    from fractions import Fraction as Fr
+    hat = {-1: Fr(1, 2), 0: Fr(1), 1: Fr(1, 2)}
+    out = [[Fr(0)] * 3 for _ in range(3)]
+    for Dy in (-1, 0, 1):
+        for Dx in (-1, 0, 1):
+            acc = Fr(0)
+            for ay in (-1, 0, 1):
+                for ax in (-1, 0, 1):
+                    r = Fr(1, 4) * hat[ay] * hat[ax]
+                    for by in (-1, 0, 1):
+                        for bx in (-1, 0, 1):
+                            y, x = ay + by - 2 * Dy, ax + bx - 2 * Dx
+                            if abs(y) <= 1 and abs(x) <= 1:
+                                acc += r * S[by + 1][bx + 1] * hat[y] * hat[x]
+            out[Dy + 1][Dx + 1] = acc
+    return out
+
+
+@pytest.mark.parametrize("theta,eps", [(math.pi / 3, 1e-4), (math.pi / 6, 1e-2), (0.7, 1e-3)])
+def test_hierarchy_stencils_match_exact_galerkin(theta, eps):
+    """12 levels: the oracle's coarse stencils equal the exact rational Galerkin chain of the
+    fine stencil with its centre set to -(sum of the others) to a few ulp per level."""
+    from fractions import Fraction as Fr
+    n, levels = 4095, 12
+    h = oracle.Hierarchy(n, levels, theta, eps)
+    fine = [[Fr(float(v)) for v in row] for row in h.stencils[0]]
+    zs = [row[:] for row in fine]
+    zs[1][1] = -(sum(sum(r) for r in zs) - zs[1][1])
+    for l in range(1, levels):
+        zs = _galerkin_exact(zs)
+        exact = np.array([[float(v) for v in r] for r in zs])
+        scale = np.abs(exact).max()
+        # each level adds a few ulp in components the Galerkin map does not amplify
+        assert np.max(np.abs(h.stencils[l] - exact)) <= 16 * (l + 1) * np.finfo(float).eps * scale, l
+        assert abs(h.stencils[l].sum()) <= 16 * np.finfo(float).eps * scale
