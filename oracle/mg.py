@@ -30,12 +30,13 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field
+from fractions import Fraction
 
 import numpy as np
 import scipy.linalg
 
 __all__ = [
-    "fine_stencil", "fine_stencil_derivatives", "apply_stencil", "restrict_fw",
+    "cos_sin", "fine_stencil", "fine_stencil_derivatives", "apply_stencil", "restrict_fw",
     "prolong_bilinear", "galerkin_stencil", "zero_row_sum_centre", "jacobi", "Hierarchy", "CallRecorder",
     "kcycle", "gamma_cycle", "f_cycle", "kcycle_adjoint", "cycle", "cycle_adjoint",
     "residual", "relres", "solve", "pcg", "param_grads", "level_sizes",
@@ -46,14 +47,44 @@ __all__ = [
 # Discretisation (Section 4)
 # ----------------------------------------------------------------------------------------
 
+def cos_sin(theta: float):
+    """cos(theta) and sin(theta) correctly rounded to FP64.
+
+    Taylor series of cos and sin evaluated in 60-digit decimal arithmetic on the exact value of
+    the FP64 argument (|theta| <= 8), then rounded once. Correct rounding makes the result
+    independent of any math library, so every implementation that rounds correctly gets the
+    same bits. Pinned against math.cos / math.sin (within 1 ulp) in the tests.
+    """
+    from decimal import Decimal, localcontext
+    if not abs(theta) <= 8.0:
+        raise ValueError("theta must satisfy |theta| <= 8")
+    fr = Fraction(theta)
+    with localcontext() as ctx:
+        ctx.prec = 60
+        x = Decimal(fr.numerator) / Decimal(fr.denominator)
+        term, c, s = Decimal(1), Decimal(0), Decimal(0)
+        for k in range(160):      # x^k / k!, signs of cos (k even) and sin (k odd)
+            if k % 4 == 0:
+                c += term
+            elif k % 4 == 1:
+                s += term
+            elif k % 4 == 2:
+                c -= term
+            else:
+                s -= term
+            term = term * x / (k + 1)
+        return float(Fraction(c)), float(Fraction(s))
+
+
 def fine_stencil(theta: float, eps: float, n: int) -> np.ndarray:
     """Nine-point stencil of Section 4 for angle theta and anisotropy eps, scaled by 1/h^2.
 
     Centre 2(1+eps); west/east -(C^2 + eps S^2); south/north -(eps C^2 + S^2);
-    NW and SE +(1-eps)CS/2; NE and SW -(1-eps)CS/2; C = cos(theta), S = sin(theta).
+    NW and SE +(1-eps)CS/2; NE and SW -(1-eps)CS/2; C = cos(theta), S = sin(theta),
+    each correctly rounded (``cos_sin``); entries evaluated left to right, then divided by h*h.
     """
     h = 1.0 / (n + 1)
-    C, S = math.cos(theta), math.sin(theta)
+    C, S = cos_sin(theta)
     cross = 0.5 * (1.0 - eps) * C * S
     st = np.zeros((3, 3))
     st[1, 1] = 2.0 * (1.0 + eps)                 # centre
@@ -156,16 +187,32 @@ def galerkin_stencil(st: np.ndarray) -> np.ndarray:
     Written as the definition: apply P, then A, then R to a coarse unit vector e_c far
     from the boundary. R A P e_c is column c of A_c; for a constant-coefficient operator
     the row entry for offset d is A_c[c, c+d] = (R A P e_c)[c - d].
+    Evaluated in exact rational arithmetic on the FP64 entries of ``st`` and rounded once to
+    FP64 (correct rounding), with plain loops on an 11 x 11 fine / 5 x 5 coarse grid that
+    follow ``prolong_bilinear``, ``apply_stencil`` and ``restrict_fw`` rule by rule.
     """
-    m = 5
-    c = 2
-    e = np.zeros((m, m))
-    e[c, c] = 1.0
-    col = restrict_fw(apply_stencil(st, prolong_bilinear(e)))
+    m, c = 5, 2
+    nf = 2 * m + 1
+    S = [[Fraction(float(st[a, b])) for b in range(3)] for a in range(3)]
+    half = Fraction(1, 2)
+
+    def hat(fine, coarse):  # bilinear weight of coarse point `coarse` at fine index `fine`
+        d = abs(fine - (2 * coarse + 1))
+        return Fraction(1) if d == 0 else (half if d == 1 else Fraction(0))
+
+    pe = [[hat(j, c) * hat(i, c) for i in range(nf)] for j in range(nf)]          # P e_c
+    ape = [[sum((S[1 + dy][1 + dx] * pe[j + dy][i + dx]
+                 for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+                 if 0 <= j + dy < nf and 0 <= i + dx < nf), Fraction(0))
+            for i in range(nf)] for j in range(nf)]                                 # A P e_c
+    fw = {-1: 1, 0: 2, 1: 1}
+    col = [[sum((Fraction(fw[dy] * fw[dx], 16) * ape[2 * J + 1 + dy][2 * I + 1 + dx]
+                 for dy in (-1, 0, 1) for dx in (-1, 0, 1)), Fraction(0))
+            for I in range(m)] for J in range(m)]                                   # R A P e_c
     out = np.zeros((3, 3))
     for dy in (-1, 0, 1):
         for dx in (-1, 0, 1):
-            out[1 + dy, 1 + dx] = col[c - dy, c - dx]
+            out[1 + dy, 1 + dx] = float(col[c - dy][c - dx])
     return out
 
 

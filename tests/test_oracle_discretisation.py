@@ -204,3 +204,27 @@ def test_hierarchy_stencils_match_exact_galerkin(theta, eps):
         # each level adds a few ulp in components the Galerkin map does not amplify
         assert np.max(np.abs(h.stencils[l] - exact)) <= 16 * (l + 1) * np.finfo(float).eps * scale, l
         assert abs(h.stencils[l].sum()) <= 16 * np.finfo(float).eps * scale
+
+
+def test_cos_sin_correctly_rounded_against_libm():
+    """The oracle's cos/sin are within 1 ulp of libm and equal to it almost always."""
+    rng = np.random.default_rng(0)
+    angles = [math.pi / 6, math.pi / 3, 0.7, 0.0, math.pi / 4, 2.5] + list(rng.uniform(0, math.pi, 100))
+    same = 0
+    for a in angles:
+        c, s = oracle.cos_sin(float(a))
+        assert abs(c - math.cos(a)) <= np.spacing(abs(math.cos(a))) and abs(s - math.sin(a)) <= np.spacing(abs(math.sin(a)))
+        same += (c == math.cos(a)) and (s == math.sin(a))
+    assert same >= len(angles) - 3
+    assert oracle.cos_sin(0.0) == (1.0, 0.0)
+
+
+def test_galerkin_exact_matches_float_probing():
+    """The exactly rounded Galerkin stencil equals R A P applied in FP64 up to rounding."""
+    for theta, eps in CASES:
+        st = oracle.fine_stencil(theta, eps, 63)
+        e = np.zeros((5, 5))
+        e[2, 2] = 1.0
+        col = oracle.restrict_fw(oracle.apply_stencil(st, oracle.prolong_bilinear(e)))
+        probe = np.array([[col[2 - dy, 2 - dx] for dx in (-1, 0, 1)] for dy in (-1, 0, 1)])
+        assert np.max(np.abs(oracle.galerkin_stencil(st) - probe)) <= 16 * np.finfo(float).eps * np.abs(st).max()
