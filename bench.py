@@ -1,0 +1,336 @@
+"""Benchmark: milliseconds to a 1e-8 relative residual for the kappa-cycle stand-alone solver.
+
+Workload (synthetic, shaped like the paper's Section 4 tests): 4095^2 interior grid, 12 levels,
+theta = pi/3, eps = 1e-4, f ~ N(0,1) (seed = rank), v0 = 0, nu1 = nu2 = 2, omega = 0.8, Galerkin
+coarse operators, FP64 throughout. One step = one solve to 1e-8 with the step's kappa (default
+4) through the C ABI (one CUDA-graph launch with an on-device stopping test).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--kappa K] [--impl reference]
+
+Prints one JSON line. Under torchrun (N > 1) each rank solves its own problem (replicas); the
+step time is the maximum over ranks and rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2010_00626_b300.inputs import KAPPA_W, LARGE, rhs_normal  # noqa: E402
+
+METRIC = "ms to 1e-8 rel. residual per kappa (FP64 vs mixed/batched) and % of HBM peak"
+WORKLOAD = "large standalone 4095^2 (12 levels, theta=pi/3, eps=1e-4, FP64)"
+NOMINAL_FP64_TFLOPS = 1.25  # recipe's nominal B300 FP64 rate
+
+
+def kname(k):
+    return "W" if k >= 1000 else str(k)
+
+
+# ------------------------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------ oracle CPU arm
+def oracle_cycles_to_tol(kappa):
+    """Cycles the oracle needs to reach 1e-8 on this workload, from the golden file written by
+    oracle/full_size_cycles.py (calls only the oracle); None when not recorded."""
+    path = os.path.join(ROOT, "tests", "golden", f"large_standalone_cycles_k{kappa}.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh)["cycles"]
+    return None
+
+
+def time_oracle_cycles(kappa, ncycles):
+    """Wall ms per oracle cycle on the host cores, timed over `ncycles` cycles from v0 = 0."""
+    import oracle
+    cfg = LARGE
+    h = oracle.Hierarchy(cfg["n"], cfg["levels"], cfg["theta"], cfg["eps"])
+    f = rhs_normal(cfg["n"], 0)
+    v = np.zeros_like(f)
+    t0 = time.perf_counter()
+    for _ in range(ncycles):
+        v = oracle.cycle(h, v, f, kappa)
+    return 1e3 * (time.perf_counter() - t0) / ncycles
+
+
+def cpu_cores_used():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([1] + [int(i.get("num_threads", 1)) for i in info if i.get("internal_api") != "openmp"])
+    except Exception:
+        return 1
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    kappa = args.kappa
+    cycles = oracle_cycles_to_tol(kappa)
+    samples = []
+    for _ in range(args.warmup):
+        time_oracle_cycles(kappa, 1)
+    for _ in range(args.steps):
+        samples.append(time_oracle_cycles(kappa, 1))
+    ms_cycle = statistics.mean(samples)
+    value = ms_cycle * cycles if cycles else None
+    sample = (f"each step one kappa={kname(kappa)} oracle cycle on the 4095^2 problem from v0=0; value = mean ms per "
+              f"cycle x {cycles} cycles, the oracle's own count to 1e-8 (tests/golden)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_cycle, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "kappa": kname(kappa), "tol": 1e-8},
+            "cpu_baseline": {"value": value, "unit": "ms", "cores": cpu_cores_used(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------ GPU arm
+def dp_ops_per_point(kind, nu, norm):
+    """FP64 operations per fine point the method needs in one launch (no halo recomputation):
+    Jacobi 10 (4 adds, 1 mul, 5 fma), residual 9, full weighting 9 per coarse point (2.25 per fine),
+    bilinear interpolation + correction 3 on average; flops count an fma as 2."""
+    jac_ops, jac_flops = 10, 15
+    res_ops, res_flops = 9, 14
+    fw_ops, fw_flops = 9 / 4, 11 / 4
+    pr_ops, pr_flops = 3, 3
+    if kind == 0:
+        return nu * jac_ops + res_ops + fw_ops, nu * jac_flops + res_flops + fw_flops
+    ops = pr_ops + nu * jac_ops + (res_ops + 1 if norm else 0)
+    flops = pr_flops + nu * jac_flops + (res_flops + 2 if norm else 0)
+    return ops, flops
+
+
+def bytes_per_point(kind, norm):
+    """Algorithmic HBM bytes per fine point of one fused pass (each field read or written once)."""
+    return 8 + 8 + 8 + 2 if kind == 0 else 8 + 8 + 2 + 8
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--kappa", type=int, default=4)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-sweep", action="store_true", help="skip the per-kappa sweep")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_2010_00626_b300 import build
+    build.build()
+    from paper_2010_00626_b300 import kcycle
+
+    cfg = LARGE
+    n, levels, tol, kappa = cfg["n"], cfg["levels"], 1e-8, args.kappa
+    mg = kcycle.Multigrid(n, cfg["eps"], cfg["theta"], levels, cfg["nu1"], cfg["nu2"])
+    f_host = rhs_normal(n, rank)
+    f = torch.tensor(f_host, device="cuda")
+    v = torch.zeros_like(f)
+    max_cycles = 20000
+
+    def step():
+        v.zero_()
+        return mg.solve(v, f, kappa, tol, max_cycles, history=False)
+
+    for _ in range(args.warmup):
+        st, cycles, rel, _ = step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        barrier()
+        e0.record()
+        for _ in range(args.steps):
+            st, cycles, rel, _ = step()
+        e1.record()
+        barrier()
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    assert st == 0 and rel <= tol, (st, rel)
+    launches_cycle = mg.counters(kappa)[1]
+    gpu_launches = args.steps * (2 + 1 + cycles * (launches_cycle + 1))
+
+    # ---------------------------------------------------------------- per-launch profile
+    prof_ms, prof_kind, prof_level = None, None, None
+    for _ in range(3):
+        prof_ms, prof_kind, prof_level = mg.profile_cycle(v, f, kappa, with_norm=True)
+    share = {}
+    for t, k, l in zip(prof_ms, prof_kind, prof_level):
+        key = (int(k), int(l))
+        share[key] = share.get(key, 0.0) + float(t)
+    total = sum(share.values())
+    top = max(share, key=share.get)
+    kinds = {0: "pass_a", 1: "pass_b", 2: "coarse", 3: "residual"}
+    # the finest-level pass A: the dominant fused kernel of the FP64 path
+    dom = (0, 0)
+    dom_ms = [float(t) for t, k, l in zip(prof_ms, prof_kind, prof_level) if (k, l) == dom]
+    dom_avg = sum(dom_ms) / len(dom_ms)
+    ops, flops = dp_ops_per_point(0, cfg["nu1"], False)
+    pts = n * n
+    achieved_tflops = flops * pts / (dom_avg * 1e-3) / 1e12
+    bytes_alg = bytes_per_point(0, False) * pts
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    hbm_achieved = bytes_alg / (dom_avg * 1e-3) / 1e9
+    roofline = {"bound": "alu", "kernel": "pass_a level 0 (4095^2, FP64)", "achieved": achieved_tflops,
+                "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tflops / NOMINAL_FP64_TFLOPS,
+                "peak_source": "nominal FP64 rate (no FP64 figure in MEASURED_PEAKS.json)",
+                "fp64_instr_per_s": ops * pts / (dom_avg * 1e-3), "ms_per_launch": dom_avg,
+                "traffic": None,
+                "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
+                        "algorithmic_bytes": bytes_alg}}
+    cycle_share = {f"{kinds[k]}@L{l}": round(t / total, 4) for (k, l), t in sorted(share.items(), key=lambda x: -x[1])[:8]}
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    e2e = None
+    if rank == 0 or world > 1:
+        fh_pin = torch.tensor(f_host).pin_memory()
+        vh_pin = torch.zeros_like(fh_pin).pin_memory()
+        vh_np, fh_np = vh_pin.numpy(), fh_pin.numpy()
+        mg.solve_host(vh_np, fh_np, kappa, tol, max_cycles)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            vh_np[:] = 0.0
+            st2, c2, r2 = mg.solve_host(vh_np, fh_np, kappa, tol, max_cycles)
+        e2e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0) / args.steps)
+        e2e = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": 2 * 8 * n * n, "d2h_bytes_per_step": 8 * n * n}
+
+    # ---------------------------------------------------------------- per-kappa sweep
+    per_kappa = {}
+    if not args.no_sweep:
+        for k in (1, 2, 3, 4, 5, KAPPA_W):
+            v.zero_()
+            mg.solve(v, f, k, tol, 1, history=False)  # builds the graph
+            v.zero_()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            st_k, cyc_k, rel_k, _ = mg.solve(v, f, k, tol, max_cycles, history=False)
+            b.record()
+            torch.cuda.synchronize()
+            ms_k = a.elapsed_time(b)
+            per_kappa[kname(k)] = {"ms": round(ms_k, 3), "cycles": cyc_k, "ms_per_cycle": round(ms_k / cyc_k, 4),
+                                   "relres": rel_k, "status": st_k}
+
+    # ---------------------------------------------------------------- oracle on the host cores
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        ms_cycle_cpu = time_oracle_cycles(kappa, 2)
+        cyc_or = oracle_cycles_to_tol(kappa)
+        cyc_used = cyc_or if cyc_or else cycles
+        cpu = {"value": ms_cycle_cpu * cyc_used, "unit": "ms", "cores": cpu_cores_used(), "kind": "oracle",
+               "sample": (f"2 kappa={kname(kappa)} oracle cycles on the 4095^2 problem from v0=0 "
+                          f"({ms_cycle_cpu:.0f} ms/cycle) x {cyc_used} cycles to 1e-8 "
+                          f"({'oracle count, tests/golden' if cyc_or else 'GPU count'})")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": n, "levels": levels, "theta": cfg["theta"], "eps": cfg["eps"],
+                           "kappa": kname(kappa), "tol": tol, "nu1": cfg["nu1"], "nu2": cfg["nu2"],
+                           "omega": cfg["omega"], "cycles": cycles, "ms_per_cycle": ms_step / cycles,
+                           "l2": "inputs larger than L2 (each 4095^2 FP64 array is 134 MB)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "roofline": roofline, "cycle_share": cycle_share, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": gpu_launches, "clocks": clocks.summary(), "per_kappa": per_kappa}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

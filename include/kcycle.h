@@ -63,11 +63,13 @@ typedef enum {
 /* Set up the hierarchy for the Section 4 problem on an n x n interior grid.
  *   n       grid side, n = 2^k - 1 with 1 <= k <= 14
  *   eps     anisotropy, 0 < eps <= 1 (Section 4)
- *   theta   angle of strong diffusion in radians (the paper's phi; K = R(theta) diag(1,eps) R^T)
+ *   theta   angle of strong diffusion in radians, |theta| <= 1e4 (the paper's phi;
+ *           K = R(theta) diag(1,eps) R^T)
  *   levels  1 <= levels <= k; the coarsest grid side 2^(k-levels+1) - 1 must be <= 15
  *   nu1,nu2 pre- and post-relaxation sweeps, 0..8
  * The fine stencil, the Galerkin coarse stencils and the coarsest-level inverse are computed by
- * device kernels. Allocates the coarse-level arrays (about n*n/3 doubles per vector kind) and one
+ * device kernels; every stencil entry is rounded once from its exact value (correctly rounded
+ * cos/sin, exact Galerkin sums, zero-row-sum coarse centres), so it is reproducible bit for bit. Allocates the coarse-level arrays (about n*n/3 doubles per vector kind) and one
  * n*n temporary. On success *out owns them; release with mg_destroy.
  * Errors: MG_ERR_ARG for invalid sizes/parameters, MG_ERR_NOMEM, MG_ERR_CUDA. */
 int mg_setup(int n, double eps, double theta, int levels, int nu1, int nu2, mg_handle* out);
@@ -78,7 +80,8 @@ int mg_destroy(mg_handle h);
 int mg_set_option(mg_handle h, int key, double value);
 int mg_get_option(mg_handle h, int key, double* value);
 
-/* Queue all further work of this handle on the given cudaStream_t (NULL = the handle's own). */
+/* Queue all further work of this handle on the given cudaStream_t (NULL = the handle's own, a
+ * non-blocking stream; pass cudaStreamLegacy to order work with the legacy default stream). */
 int mg_set_stream(mg_handle h, void* cuda_stream);
 
 /* One finest-level kappa-cycle in place (Algorithm 3): v <- kappa-cycle(v, f, A, 1, levels, kappa).
@@ -138,6 +141,16 @@ int mg_stencils(mg_handle h, double* out, int max_levels, int* written);
  * kernel. All host, nullable; calls_per_level holds levels entries. No device work. */
 int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* launches,
                 long long* coarse_calls);
+
+/* Run one finest-level kappa-cycle like mg_kcycle (from the initial guess in v), but launch by
+ * launch with a CUDA event pair around every kernel instead of through a graph, and report each
+ * launch: ms[r] its duration in milliseconds, kind[r] 0 = pass A (relax + residual + restrict),
+ * 1 = pass B (interpolate + correct + relax), 2 = coarse-level kernel, 3 = whole-grid residual;
+ * level[r] its level (0 finest). with_norm adds the residual partial sums of a solve cycle.
+ * ms, kind, level: host, nullable, max_records entries; *count: number of launches (may exceed
+ * max_records). Measurement hook with no counterpart in the paper. Synchronises. */
+int mg_profile_cycle(mg_handle h, double* v, const double* f, int kappa, int with_norm, int max_records,
+                     double* ms, int* kind, int* level, int* count);
 
 /* Static string for a status code. */
 const char* mg_status_string(int status);

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <list>
 #include <new>
 #include <vector>
 
@@ -44,6 +45,7 @@ thread_local char g_err[256] = "";
   } while (0)
 
 constexpr int NT_SMALL = 256;
+constexpr int NT_TINY = 128;
 constexpr int NT_BIG = 512;
 constexpr int NT_COARSE = 256;
 constexpr int NT_VEC = 256;
@@ -105,10 +107,14 @@ struct mg_ctx {
   cudaStream_t own = nullptr;
   cudaStream_t ext = nullptr;
   bool has_ext = false;
-  std::vector<GraphEntry> graphs;
+  std::list<GraphEntry> graphs;  // stable addresses; trimmed only at the start of a public call
   int last_launches = 0;
   int launch_count = 0;  // counter while emitting
   bool ok = false;
+  // per-launch timing (mg_profile_cycle): an event pair around each launch while `prof` is set
+  bool prof = false;
+  std::vector<cudaEvent_t> pev;
+  std::vector<int> pkind, plevel;
 
   cudaStream_t stream() const { return has_ext ? ext : own; }
 };
@@ -122,11 +128,20 @@ template <int BX, int BY, int NT>
 struct TileCfg {
   static constexpr int bx = BX, by = BY, nt = NT;
 };
-using BigTile = TileCfg<64, 64, NT_BIG>;
-using MidTile = TileCfg<32, 32, NT_SMALL>;
-using SmallTile = TileCfg<16, 16, NT_SMALL>;
+using Tile64 = TileCfg<64, 64, NT_BIG>;
+using Tile32 = TileCfg<32, 32, NT_SMALL>;
+using Tile16 = TileCfg<16, 16, NT_TINY>;
+using Tile8 = TileCfg<8, 8, NT_TINY>;
 
-int tile_class(int n) { return n >= 512 ? 2 : (n >= 64 ? 1 : 0); }
+// FP64 level passes are bound by the FP64 pipe of each SM, so a launch must spread over all SMs:
+// take the largest tile that still gives about two waves of CTAs (tile edge 64, 32, 16 or 8).
+int tile_edge(int n) {
+  for (int b : {64, 32, 16}) {
+    const int g = (n + b - 1) / b;
+    if (g * g >= 2 * 148) return b;
+  }
+  return 8;
+}
 
 template <typename Cfg>
 int launch_pass_a(const PassAArgs<double>& a, cudaStream_t s) {
@@ -157,9 +172,7 @@ int set_smem_attrs() {
 }
 
 size_t pass_grid_blocks(int n) {
-  const int c = tile_class(n);
-  const int b = c == 2 ? 64 : (c == 1 ? 32 : 16);
-  const size_t g = (n + b - 1) / b;
+  const size_t g = (n + tile_edge(n) - 1) / tile_edge(n);
   return g * g;
 }
 
@@ -173,6 +186,25 @@ size_t apply_grid_blocks(int n) {
 double* lv_v(mg_ctx* h, const Binding& b, int l) { return l == 0 ? b.v0 : h->lv[l].v; }
 const double* lv_f(mg_ctx* h, const Binding& b, int l) { return l == 0 ? b.f0 : h->lv[l].f; }
 int lv_ld(mg_ctx* h, const Binding& b, int l) { return l == 0 ? b.ld0 : h->lv[l].ld; }
+
+enum { K_PASS_A = 0, K_PASS_B = 1, K_COARSE = 2, K_APPLY = 3 };
+
+void prof_begin(mg_ctx* h, int kind, int level, cudaStream_t s) {
+  if (!h->prof) return;
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  cudaEventRecord(e, s);
+  h->pev.push_back(e);
+  h->pkind.push_back(kind);
+  h->plevel.push_back(level);
+}
+void prof_end(mg_ctx* h, cudaStream_t s) {
+  if (!h->prof) return;
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  cudaEventRecord(e, s);
+  h->pev.push_back(e);
+}
 
 int emit_coarse(mg_ctx* h, const Binding& b, int k1, int k2, int zero1, bool adjoint, const int* skip,
                 cudaStream_t s) {
@@ -194,7 +226,9 @@ int emit_coarse(mg_ctx* h, const Binding& b, int k1, int k2, int zero1, bool adj
   a.zero1 = zero1;
   a.adjoint = adjoint ? 1 : 0;
   const size_t sm = coarse_smem<double>(a.n_lc, a.L - a.lc);
+  prof_begin(h, K_COARSE, h->lc, s);
   coarse_kernel<double, NT_COARSE><<<1, NT_COARSE, sm, s>>>(a);
+  prof_end(h, s);
   KC_CUDA(cudaGetLastError());
   ++h->launch_count;
   return MG_OK;
@@ -216,11 +250,16 @@ int emit_pass_a(mg_ctx* h, const Binding& b, int l, bool zero, int nu, const int
   a.nu = nu;
   a.level = l;
   ++h->launch_count;
-  switch (tile_class(a.n)) {
-    case 2: return launch_pass_a<BigTile>(a, s);
-    case 1: return launch_pass_a<MidTile>(a, s);
-    default: return launch_pass_a<SmallTile>(a, s);
+  prof_begin(h, K_PASS_A, l, s);
+  int st;
+  switch (tile_edge(a.n)) {
+    case 64: st = launch_pass_a<Tile64>(a, s); break;
+    case 32: st = launch_pass_a<Tile32>(a, s); break;
+    case 16: st = launch_pass_a<Tile16>(a, s); break;
+    default: st = launch_pass_a<Tile8>(a, s); break;
   }
+  prof_end(h, s);
+  return st;
 }
 
 int emit_pass_b(mg_ctx* h, const Binding& b, int l, int nu, double* partial, const int* skip, cudaStream_t s) {
@@ -240,11 +279,16 @@ int emit_pass_b(mg_ctx* h, const Binding& b, int l, int nu, double* partial, con
   a.nu = nu;
   a.level = l;
   ++h->launch_count;
-  switch (tile_class(a.n)) {
-    case 2: return launch_pass_b<BigTile>(a, s);
-    case 1: return launch_pass_b<MidTile>(a, s);
-    default: return launch_pass_b<SmallTile>(a, s);
+  prof_begin(h, K_PASS_B, l, s);
+  int st;
+  switch (tile_edge(a.n)) {
+    case 64: st = launch_pass_b<Tile64>(a, s); break;
+    case 32: st = launch_pass_b<Tile32>(a, s); break;
+    case 16: st = launch_pass_b<Tile16>(a, s); break;
+    default: st = launch_pass_b<Tile8>(a, s); break;
   }
+  prof_end(h, s);
+  return st;
 }
 
 // Counters of the two coarse calls made by a call with counter kappa (Algorithm 3); the adjoint
@@ -280,7 +324,9 @@ int emit_apply(mg_ctx* h, const double* v, const double* f, double* out, double*
                cudaStream_t s) {
   const int n = h->n;
   dim3 grid((n + 31) / 32, (n + NT_VEC / 32 - 1) / (NT_VEC / 32));
+  prof_begin(h, K_APPLY, 0, s);
   apply_kernel<double, NT_VEC><<<grid, NT_VEC, 0, s>>>(v, f, out, h->coef, 0, n, n, partial, skip);
+  prof_end(h, s);
   KC_CUDA(cudaGetLastError());
   ++h->launch_count;
   return MG_OK;
@@ -318,14 +364,19 @@ void drop_graphs(mg_ctx* h) {
 }
 
 GraphEntry* add_graph(mg_ctx* h, const GraphEntry& e) {
-  if (h->graphs.size() >= 16) {  // bounded cache: forget the oldest
+  h->graphs.push_back(e);
+  return &h->graphs.back();
+}
+
+// Bounded cache: forget the oldest graphs. Called only at the start of a public entry point, so
+// no GraphEntry pointer held by a caller inside the library is invalidated.
+void trim_graphs(mg_ctx* h) {
+  while (h->graphs.size() > 24) {
     auto& g = h->graphs.front();
     if (g.exec) cudaGraphExecDestroy(g.exec);
     if (g.graph) cudaGraphDestroy(g.graph);
-    h->graphs.erase(h->graphs.begin());
+    h->graphs.pop_front();
   }
-  h->graphs.push_back(e);
-  return &h->graphs.back();
 }
 
 // Plain cycle graph: flag bit0 = zero start, bit1 = adjoint.
@@ -435,6 +486,7 @@ int solve_impl(mg_handle h, double* v, const double* f, int kappa, double tol, i
                double* final_relres, double* history) {
   if (!valid_handle(h)) return MG_ERR_STATE;
   if (!v || !f || kappa < 1 || !(tol > 0) || max_cycles < 1) return MG_ERR_ARG;
+  trim_graphs(h);
   KC_TRY(ensure_hist(h, max_cycles));
   cudaStream_t s = h->stream();
   GraphEntry* ge = find_graph(h, G_SOLVE, kappa, 0, v, f);
@@ -552,7 +604,7 @@ int mg_setup(int n, double eps, double theta, int levels, int nu1, int nu2, mg_h
   while (k < 15 && ((1 << k) - 1) < n) ++k;
   if (n < 1 || ((1 << k) - 1) != n || k > 14) return MG_ERR_ARG;
   if (levels < 1 || levels > k || (k - levels + 1) > 4) return MG_ERR_ARG;
-  if (!(eps > 0.0) || !(eps <= 1.0) || !std::isfinite(theta)) return MG_ERR_ARG;
+  if (!(eps > 0.0) || !(eps <= 1.0) || !(std::fabs(theta) <= 1e4)) return MG_ERR_ARG;
   if (nu1 < 0 || nu2 < 0 || nu1 > MAX_NU || nu2 > MAX_NU) return MG_ERR_ARG;
   mg_ctx* h = new (std::nothrow) mg_ctx();
   if (!h) return MG_ERR_NOMEM;
@@ -590,8 +642,8 @@ int mg_setup(int n, double eps, double theta, int levels, int nu1, int nu2, mg_h
   if (cudaMemsetAsync(h->ints, 0, sizeof(int) * NINT, h->own) != cudaSuccess) return fail(MG_ERR_CUDA);
   if (cudaMemsetAsync(h->scal, 0, sizeof(double) * NSCAL, h->own) != cudaSuccess) return fail(MG_ERR_CUDA);
   if ((st = run_setup_kernels(h)) < 0) return fail(st);
-  if ((st = set_smem_attrs<BigTile>()) < 0 || (st = set_smem_attrs<MidTile>()) < 0 ||
-      (st = set_smem_attrs<SmallTile>()) < 0)
+  if ((st = set_smem_attrs<Tile64>()) < 0 || (st = set_smem_attrs<Tile32>()) < 0 ||
+      (st = set_smem_attrs<Tile16>()) < 0 || (st = set_smem_attrs<Tile8>()) < 0)
     return fail(st);
   if (cudaFuncSetAttribute(coarse_kernel<double, NT_COARSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)coarse_smem<double>(MAX_COARSE_N, 6)) != cudaSuccess)
@@ -649,6 +701,7 @@ int mg_set_stream(mg_handle h, void* stream) {
 static int kcycle_common(mg_handle h, double* v, const double* f, int kappa, bool adjoint) {
   if (!valid_handle(h)) return MG_ERR_STATE;
   if (!v || !f || kappa < 1) return MG_ERR_ARG;
+  trim_graphs(h);
   GraphEntry* ge;
   KC_TRY(get_cycle_graph(h, v, f, kappa, adjoint ? 2 : 0, &ge));
   KC_CUDA(cudaGraphLaunch(ge->exec, h->stream()));
@@ -687,6 +740,7 @@ int mg_pcg(mg_handle h, double* x, const double* b, int kappa, double tol, int m
            double* final_relres, double* history) {
   if (!valid_handle(h)) return MG_ERR_STATE;
   if (!x || !b || kappa < 1 || !(tol > 0) || max_iters < 1) return MG_ERR_ARG;
+  trim_graphs(h);
   const size_t len = (size_t)h->n * h->n, bytes = sizeof(double) * len;
   double** vecs[] = {&h->pr, &h->pp, &h->pq, &h->pz, &h->pzold};
   for (double** p : vecs)
@@ -819,6 +873,42 @@ int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* l
   if (launches) *launches = fine_launches + coarse_launches;
   if (coarse_calls) *coarse_calls = coarse;
   return MG_OK;
+}
+
+int mg_profile_cycle(mg_handle h, double* v, const double* f, int kappa, int with_norm, int max_records,
+                     double* ms, int* kind, int* level, int* count) {
+  if (!valid_handle(h)) return MG_ERR_STATE;
+  if (!v || !f || kappa < 1 || max_records < 0) return MG_ERR_ARG;
+  cudaStream_t s = h->stream();
+  Binding b{v, f, h->n};
+  h->pev.clear();
+  h->pkind.clear();
+  h->plevel.clear();
+  h->prof = true;
+  const int st = emit_cycle(h, b, kappa, false, false, with_norm != 0, nullptr, s);
+  h->prof = false;
+  int result = st;
+  if (st >= 0) {
+    const cudaError_t se = cudaStreamSynchronize(s);
+    if (se != cudaSuccess) {
+      snprintf(g_err, sizeof(g_err), "mg_profile_cycle: %s", cudaGetErrorString(se));
+      result = MG_ERR_CUDA;
+    }
+  }
+  const int nrec = (int)h->pkind.size();
+  if (result >= 0) {
+    for (int r = 0; r < nrec && r < max_records; ++r) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, h->pev[2 * r], h->pev[2 * r + 1]);
+      if (ms) ms[r] = t;
+      if (kind) kind[r] = h->pkind[r];
+      if (level) level[r] = h->plevel[r];
+    }
+    if (count) *count = nrec;
+  }
+  for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
+  h->pev.clear();
+  return result;
 }
 
 }  // extern "C"

@@ -354,14 +354,24 @@ __host__ __device__ inline int coarse_side(int n_lc, int d) {
   return s;
 }
 
-// Shared memory: per level v and f with a zero border ((n_l+2)^2 each), plus one temporary of
-// the largest level.
+// Jacobi update written as a shallow tree (depth 4 instead of 6) for the latency-bound coarse
+// levels: two more FP64 operations per point, more independent work per thread.
+template <typename T>
+__device__ __forceinline__ T jacobi_update_tree(const Nb<T>& nb, T fv, const Coef<T>& c) {
+  const T t1 = fma(c.w, fv, c.b0 * nb.c);
+  const T t2 = fma(c.bns, nb.ns, c.bwe * nb.we);
+  const T t3 = fma(c.bne, nb.d2, c.bnw * nb.d1);
+  return (t1 + t2) + t3;
+}
+
+// Shared memory of the coarse kernel: per level two v buffers and f, each (side+2)^2 with a zero
+// border, plus one temporary of the largest level.
 template <typename T>
 __host__ __device__ inline size_t coarse_smem(int n_lc, int nlev) {
   size_t tot = 0;
   for (int d = 0; d < nlev; ++d) {
     const int s = coarse_side(n_lc, d) + 2;
-    tot += 2 * size_t(s) * s;
+    tot += 3 * size_t(s) * s;
   }
   tot += size_t(n_lc + 2) * (n_lc + 2);
   return tot * sizeof(T);
@@ -371,29 +381,45 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ Coef<T> cf[MAXL];
+  __shared__ int g_side[MAXL], g_off[MAXL + 1], g_magic[MAXL];
   const int nlev = a.L - a.lc;
-  const int top_n = a.n_lc;
-  int side[MAXL], off_v[MAXL], off_f[MAXL];
   T* base = reinterpret_cast<T*>(smem_raw);
-  int off = 0;
-  for (int d = 0; d < nlev; ++d) {
-    side[d] = coarse_side(top_n, d);
-    const int pp = (side[d] + 2) * (side[d] + 2);
-    off_v[d] = off; off += pp;
-    off_f[d] = off; off += pp;
+  if (threadIdx.x < nlev) cf[threadIdx.x] = load_coef(a.coef, a.lc + threadIdx.x);
+  if (threadIdx.x == 0) {
+    int off = 0;
+    for (int d = 0; d < nlev; ++d) {
+      const int sd = coarse_side(a.n_lc, d);
+      g_side[d] = sd;
+      g_off[d] = off;  // v0 at off, v1 at off + P^2, f at off + 2 P^2
+      g_magic[d] = (int)((0x100000000ull + sd - 1) / sd);  // k / sd == umulhi(k, magic) for k < 4096
+      off += 3 * (sd + 2) * (sd + 2);
+    }
+    g_off[nlev] = off;
   }
-  T* tmp = base + off;
-  const int total = off + (top_n + 2) * (top_n + 2);
-  for (int k = threadIdx.x; k < total; k += NT) base[k] = T(0);  // borders must be zero
   __syncthreads();
+  T* tmp = base + g_off[nlev];
+  const int total = g_off[nlev] + (a.n_lc + 2) * (a.n_lc + 2);
+  for (int k = threadIdx.x; k < total; k += NT) base[k] = T(0);  // borders stay zero
+  __syncthreads();
+
+  unsigned cur = 0;  // bit d: which of the two v buffers of level d holds the current iterate
+  auto vbuf = [&](int d, int which) { const int P = g_side[d] + 2; return base + g_off[d] + which * P * P; };
+  auto fbuf = [&](int d) { const int P = g_side[d] + 2; return base + g_off[d] + 2 * P * P; };
+  auto vcur = [&](int d) { return vbuf(d, (cur >> d) & 1u); };
+  auto pos = [&](int d, int k) {  // padded position of interior point k of level d
+    const int s = g_side[d];
+    const int j = (int)__umulhi((unsigned)k, (unsigned)g_magic[d]);
+    return (j + 1) * (s + 2) + (k - j * s) + 1;
+  };
   {
-    const int s = top_n, P = s + 2;
-    T* fv = base + off_f[0];
-    T* vv = base + off_v[0];
+    const int s = a.n_lc;
+    T* fv = fbuf(0);
+    T* vv = vbuf(0, 0);
     for (int k = threadIdx.x; k < s * s; k += NT) {
-      const int j = k / s, i = k - j * s;
-      fv[(j + 1) * P + i + 1] = a.f[(size_t)j * a.ldf + i];
-      if (!a.zero1) vv[(j + 1) * P + i + 1] = a.v[(size_t)j * a.ldv + i];
+      const int j = (int)__umulhi((unsigned)k, (unsigned)g_magic[0]), i = k - j * s;
+      fv[pos(0, k)] = a.f[(size_t)j * a.ldf + i];
+      if (!a.zero1) vv[pos(0, k)] = a.v[(size_t)j * a.ldv + i];
     }
   }
   __syncthreads();
@@ -401,70 +427,59 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
   const int nu_pre = a.adjoint ? a.nu2 : a.nu1;
   const int nu_post = a.adjoint ? a.nu1 : a.nu2;
 
-  // relax `sweeps` times on level d (in place: new values held in registers across a barrier)
-  constexpr int MAXP = (63 * 63 + NT - 1) / NT;
+  // `sweeps` damped-Jacobi sweeps on level d, ping-ponging between its two v buffers; a zero
+  // start makes the first sweep v = w f (the update of v = 0)
   auto relax = [&](int d, int sweeps, bool zero) {
-    const int s = side[d], P = s + 2;
-    T* v = base + off_v[d];
-    const T* f = base + off_f[d];
-    const Coef<T> c = load_coef(a.coef, a.lc + d);
-    if (zero) {
-      for (int k = threadIdx.x; k < s * s; k += NT) {
-        const int j = k / s, i = k - j * s;
-        v[(j + 1) * P + i + 1] = T(0);
-      }
+    const int s = g_side[d], P = s + 2;
+    const T* f = fbuf(d);
+    const Coef<T> c = cf[d];
+    if (zero && sweeps == 0) {
+      T* v = vcur(d);
+      for (int k = threadIdx.x; k < s * s; k += NT) v[pos(d, k)] = T(0);
       __syncthreads();
+      return;
     }
     for (int it = 0; it < sweeps; ++it) {
-      T nv[MAXP];
-#pragma unroll
-      for (int q = 0; q < MAXP; ++q) {
-        const int k = threadIdx.x + q * NT;
-        if (k < s * s) {
-          const int j = k / s, i = k - j * s, kk = (j + 1) * P + i + 1;
-          nv[q] = jacobi_update(neighbours(v, kk, P), f[kk], c);
-        }
+      const unsigned b = (cur >> d) & 1u;
+      const T* src = vbuf(d, b);
+      T* dst = vbuf(d, b ^ 1u);
+      const bool from_zero = zero && it == 0;
+      for (int k = threadIdx.x; k < s * s; k += NT) {
+        const int kk = pos(d, k);
+        dst[kk] = from_zero ? c.w * f[kk] : jacobi_update_tree(neighbours(src, kk, P), f[kk], c);
       }
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < MAXP; ++q) {
-        const int k = threadIdx.x + q * NT;
-        if (k < s * s) {
-          const int j = k / s, i = k - j * s;
-          v[(j + 1) * P + i + 1] = nv[q];
-        }
-      }
+      cur ^= 1u << d;
       __syncthreads();
     }
   };
   // f_{d+1} = R (f_d - A v_d)
   auto restrict_residual = [&](int d) {
-    const int s = side[d], P = s + 2;
-    const T* v = base + off_v[d];
-    const T* f = base + off_f[d];
-    const Coef<T> c = load_coef(a.coef, a.lc + d);
+    const int s = g_side[d], P = s + 2;
+    const T* v = vcur(d);
+    const T* f = fbuf(d);
+    const Coef<T> c = cf[d];
     for (int k = threadIdx.x; k < s * s; k += NT) {
-      const int j = k / s, i = k - j * s, kk = (j + 1) * P + i + 1;
+      const int kk = pos(d, k);
       tmp[kk] = residual_at(neighbours(v, kk, P), f[kk], c);
     }
     __syncthreads();
-    const int sc = side[d + 1], Pc = sc + 2;
-    T* fc = base + off_f[d + 1];
+    const int sc = g_side[d + 1];
+    T* fc = fbuf(d + 1);
     for (int k = threadIdx.x; k < sc * sc; k += NT) {
-      const int J = k / sc, I = k - J * sc;
+      const int J = (int)__umulhi((unsigned)k, (unsigned)g_magic[d + 1]), I = k - J * sc;
       // coarse (I, J) sits on fine (2I+1, 2J+1), padded position (2J+2, 2I+2)
-      fc[(J + 1) * Pc + I + 1] = full_weight(tmp, (2 * J + 2) * P + (2 * I + 2), P);
+      fc[pos(d + 1, k)] = full_weight(tmp, (2 * J + 2) * P + (2 * I + 2), P);
     }
     __syncthreads();
   };
-  // v_d += P v_{d+1}; padded coarse index of (I, J) is (J+1)*Pc + I+1, borders are zero
+  // v_d += P v_{d+1}; the padded coarse index of coarse (I, J) is (J+1)*Pc + I+1
   auto prolong_add = [&](int d) {
-    const int s = side[d], P = s + 2, Pc = side[d + 1] + 2;
-    T* v = base + off_v[d];
-    const T* vc = base + off_v[d + 1];
+    const int s = g_side[d], Pc = g_side[d + 1] + 2;
+    T* v = vcur(d);
+    const T* vc = vcur(d + 1);
     for (int k = threadIdx.x; k < s * s; k += NT) {
-      const int j = k / s, i = k - j * s;
-      const int hx = i >> 1, hy = j >> 1;  // padded coarse column of coarse hx-1 is hx
+      const int j = (int)__umulhi((unsigned)k, (unsigned)g_magic[d]), i = k - j * s;
+      const int hx = i >> 1, hy = j >> 1;
       T p;
       const bool xo = i & 1, yo = j & 1;
       if (xo && yo) {
@@ -476,32 +491,27 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
       } else {
         p = T(0.25) * ((vc[hy * Pc + hx] + vc[hy * Pc + hx + 1]) + (vc[(hy + 1) * Pc + hx] + vc[(hy + 1) * Pc + hx + 1]));
       }
-      v[(j + 1) * P + i + 1] += p;
+      v[(j + 1) * (s + 2) + i + 1] += p;
     }
     __syncthreads();
   };
+  // exact coarsest solve: division for 1x1, dense inverse otherwise (into the other buffer)
   auto coarsest = [&]() {
-    const int d = nlev - 1, s = side[d], P = s + 2;
-    T* v = base + off_v[d];
-    const T* f = base + off_f[d];
+    const int d = nlev - 1, s = g_side[d];
+    const T* f = fbuf(d);
+    const unsigned b = (cur >> d) & 1u;
+    T* dst = vbuf(d, b ^ 1u);
     if (s == 1) {
-      if (threadIdx.x == 0) v[P + 1] = f[P + 1] / a.coef[(a.L - 1) * NCOEF + C_C0];
+      if (threadIdx.x == 0) dst[4] = f[4] / cf[d].c0;  // padded 3x3, interior at 4
     } else {
       const int N = s * s;
       for (int r = threadIdx.x; r < N; r += NT) {
         T acc = T(0);
-        for (int q = 0; q < N; ++q) {
-          const int jq = q / s, iq = q - jq * s;
-          acc = fma(a.cinv[(size_t)r * N + q], f[(jq + 1) * P + iq + 1], acc);
-        }
-        tmp[r] = acc;
-      }
-      __syncthreads();
-      for (int r = threadIdx.x; r < N; r += NT) {
-        const int j = r / s, i = r - j * s;
-        v[(j + 1) * P + i + 1] = tmp[r];
+        for (int q = 0; q < N; ++q) acc = fma(a.cinv[(size_t)r * N + q], f[pos(d, q)], acc);
+        dst[pos(d, r)] = acc;
       }
     }
+    cur ^= 1u << d;
     __syncthreads();
   };
 
@@ -540,11 +550,11 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
     }
   }
   {
-    const int s = top_n, P = s + 2;
-    const T* vv = base + off_v[0];
+    const int s = a.n_lc;
+    const T* vv = vcur(0);
     for (int k = threadIdx.x; k < s * s; k += NT) {
-      const int j = k / s, i = k - j * s;
-      a.v[(size_t)j * a.ldv + i] = vv[(j + 1) * P + i + 1];
+      const int j = (int)__umulhi((unsigned)k, (unsigned)g_magic[0]), i = k - j * s;
+      a.v[(size_t)j * a.ldv + i] = vv[pos(0, k)];
     }
   }
 }
@@ -578,23 +588,97 @@ __device__ inline void fill_coef(const double st[9], double omega, double* out, 
   }
 }
 
+// ---- double-double arithmetic (Dekker 1971; Knuth, TAOCP vol. 2, 4.2.2): a value hi + lo with
+// |lo| <= ulp(hi)/2, about 106 significant bits. Used only at setup, to round results once.
+struct DD {
+  double hi, lo;
+};
+__device__ inline DD dd_two_sum(double a, double b) {
+  const double s = __dadd_rn(a, b);
+  const double bb = __dsub_rn(s, a);
+  const double e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+  return DD{s, e};
+}
+__device__ inline DD dd_fast_two_sum(double a, double b) {  // requires |a| >= |b|
+  const double s = __dadd_rn(a, b);
+  return DD{s, __dsub_rn(b, __dsub_rn(s, a))};
+}
+__device__ inline DD dd_two_prod(double a, double b) {  // exact product via a fused multiply-add
+  const double p = __dmul_rn(a, b);
+  return DD{p, __fma_rn(a, b, -p)};
+}
+__device__ inline DD dd_add(DD a, DD b) {
+  DD s = dd_two_sum(a.hi, b.hi);
+  const DD t = dd_two_sum(a.lo, b.lo);
+  s = dd_fast_two_sum(s.hi, __dadd_rn(s.lo, t.hi));
+  return dd_fast_two_sum(s.hi, __dadd_rn(s.lo, t.lo));
+}
+__device__ inline DD dd_mul(DD a, DD b) {
+  const DD p = dd_two_prod(a.hi, b.hi);
+  return dd_fast_two_sum(p.hi, __dadd_rn(p.lo, __fma_rn(a.hi, b.lo, __dmul_rn(a.lo, b.hi))));
+}
+__device__ inline DD dd_div_small_int(DD a, double m) {  // a / m for a small positive integer m
+  const double q1 = __ddiv_rn(a.hi, m);
+  const DD p = dd_two_prod(q1, m);
+  const double r = __dadd_rn(__dsub_rn(__dsub_rn(a.hi, p.hi), p.lo), a.lo);
+  return dd_fast_two_sum(q1, __ddiv_rn(r, m));
+}
+__device__ inline DD dd_neg(DD a) { return DD{-a.hi, -a.lo}; }
+
+// cos(theta), sin(theta) correctly rounded to double (up to arguments within ~1e-30 of a rounding
+// boundary): Cody-Waite reduction by pi/2 = P1 + P2 + P3 (the binary expansion of pi/2 split into
+// three doubles), then the Taylor series of cos and sin on |r| <= pi/4 in double-double, rounded
+// once. Valid for |theta| <= 1e4.
+__device__ inline void dd_cos_sin(double theta, double* c_out, double* s_out) {
+  const double P1 = 0x1.921fb54442d18p+0, P2 = 0x1.1a62633145c07p-54, P3 = -0x1.f1976b7ed8fbcp-110;
+  const double kd = rint(__ddiv_rn(theta, P1));
+  DD r{theta, 0.0};
+  r = dd_add(r, dd_neg(dd_two_prod(kd, P1)));
+  r = dd_add(r, dd_neg(dd_two_prod(kd, P2)));
+  r = dd_add(r, dd_neg(dd_two_prod(kd, P3)));
+  const DD r2 = dd_mul(r, r);
+  DD cs{1.0, 0.0}, sn = r, tc{1.0, 0.0}, ts = r;
+  for (int m = 1; m <= 16; ++m) {  // terms r^(2m)/(2m)! and r^(2m+1)/(2m+1)!
+    tc = dd_div_small_int(dd_div_small_int(dd_mul(tc, r2), 2.0 * m - 1.0), 2.0 * m);
+    ts = dd_div_small_int(dd_div_small_int(dd_mul(ts, r2), 2.0 * m), 2.0 * m + 1.0);
+    cs = dd_add(cs, (m & 1) ? dd_neg(tc) : tc);
+    sn = dd_add(sn, (m & 1) ? dd_neg(ts) : ts);
+  }
+  const int q = ((int)fmod(kd, 4.0) + 4) & 3;
+  DD c, s;
+  if (q == 0) { c = cs; s = sn; }
+  else if (q == 1) { c = dd_neg(sn); s = cs; }
+  else if (q == 2) { c = dd_neg(cs); s = dd_neg(sn); }
+  else { c = sn; s = dd_neg(cs); }
+  *c_out = __dadd_rn(c.hi, c.lo);
+  *s_out = __dadd_rn(s.hi, s.lo);
+}
+
 // One thread builds all stencils; st index (dy+1)*3 + (dx+1).
+// Every stencil is rounded from an exactly known value, so any correctly rounding evaluation
+// gives the same bits: the fine entries are evaluated in a fixed order of correctly rounded
+// operations (no contraction into fused multiply-adds) from correctly rounded cos and sin; each
+// Galerkin entry is a sum of exact products (the transfer weights are powers of two) accumulated
+// in double-double and rounded once; the coarse centre follows from the zero-row-sum identity.
 __global__ void setup_stencils_kernel(double theta, double eps, int n, int levels, double omega,
                                       double* coef, float* coef32, double* stencils, double* dstencil) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double h = 1.0 / (n + 1);
-  const double h2 = h * h;
-  const double C = cos(theta), S = sin(theta);
-  const double cross = 0.5 * (1.0 - eps) * C * S;
+  const double h = __ddiv_rn(1.0, (double)(n + 1));
+  const double h2 = __dmul_rn(h, h);
+  double C, S;
+  dd_cos_sin(theta, &C, &S);
+  const double cross = __dmul_rn(__dmul_rn(__dmul_rn(0.5, __dsub_rn(1.0, eps)), C), S);  // ((0.5(1-eps))C)S
+  const double we = -__dadd_rn(__dmul_rn(C, C), __dmul_rn(__dmul_rn(eps, S), S));       // -(CC + (eps S)S)
+  const double ns = -__dadd_rn(__dmul_rn(__dmul_rn(eps, C), C), __dmul_rn(S, S));       // -((eps C)C + SS)
   double st[9];
-  st[4] = 2.0 * (1.0 + eps);
-  st[3] = st[5] = -(C * C + eps * S * S);
-  st[1] = st[7] = -(eps * C * C + S * S);
+  st[4] = __dmul_rn(2.0, __dadd_rn(1.0, eps));
+  st[3] = st[5] = we;
+  st[1] = st[7] = ns;
   st[6] = cross;   // NW
   st[2] = cross;   // SE
   st[8] = -cross;  // NE
   st[0] = -cross;  // SW
-  for (int q = 0; q < 9; ++q) st[q] /= h2;
+  for (int q = 0; q < 9; ++q) st[q] = __ddiv_rn(st[q], h2);
   // derivatives of the Section 4 entries with respect to theta and eps, scaled by 1/h^2
   {
     const double s2 = sin(2.0 * theta), c2 = cos(2.0 * theta);
@@ -620,18 +704,25 @@ __global__ void setup_stencils_kernel(double theta, double eps, int n, int level
     double sc[9];
     for (int Dy = -1; Dy <= 1; ++Dy)
       for (int Dx = -1; Dx <= 1; ++Dx) {
-        double acc = 0.0;
+        DD acc{0.0, 0.0};
         for (int ay = -1; ay <= 1; ++ay)
           for (int ax = -1; ax <= 1; ++ax) {
             const double r = 0.25 * hat1(ay) * hat1(ax);
             for (int by = -1; by <= 1; ++by)
               for (int bx = -1; bx <= 1; ++bx) {
                 const double pv = hat1(ay + by - 2 * Dy) * hat1(ax + bx - 2 * Dx);
-                if (pv != 0.0) acc += r * st[(by + 1) * 3 + (bx + 1)] * pv;
+                if (pv != 0.0) acc = dd_add(acc, DD{__dmul_rn(__dmul_rn(r, st[(by + 1) * 3 + (bx + 1)]), pv), 0.0});
               }
           }
-        sc[(Dy + 1) * 3 + (Dx + 1)] = acc;
+        sc[(Dy + 1) * 3 + (Dx + 1)] = __dadd_rn(acc.hi, acc.lo);
       }
+    // exact coarse stencils sum to zero (the fine stencil annihilates constants and the Galerkin
+    // map keeps the entry sum); evaluating the centre from that identity, off-centre entries
+    // summed in row-major order, stops FP64 rounding of the sum from growing 4x per level
+    double off = 0.0;
+    for (int q = 0; q < 9; ++q)
+      if (q != 4) off = __dadd_rn(off, sc[q]);
+    sc[4] = -off;
     for (int q = 0; q < 9; ++q) st[q] = sc[q];
   }
 }

@@ -1,0 +1,215 @@
+"""Thin Python binding of libkcycle.so (the C ABI declared in include/kcycle.h).
+
+Argument marshalling only: every step of the multigrid runs in the library's CUDA kernels.
+Device arrays are torch CUDA tensors of dtype float64, shape (n, n), contiguous; torch is used
+for device memory and streams only. The library must have been built (``build()`` in
+``__graft_entry__`` or ``python -m paper_2010_00626_b300.build``); importing this module without
+it raises, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libkcycle.so")
+
+MG_OK, MG_NOT_CONVERGED = 0, 1
+MG_KAPPA_W = 0x7FFFFFFF
+CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
+MG_OPT_OMEGA, MG_OPT_COARSE_N, MG_OPT_LEVELS, MG_OPT_N, MG_OPT_LAUNCHES = 1, 2, 3, 4, 5
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libkcycle.so is not built ({LIB_PATH}); run python -m paper_2010_00626_b300.build")
+_lib = ctypes.CDLL(LIB_PATH)
+
+_h = ctypes.c_void_p
+_d = ctypes.c_double
+_i = ctypes.c_int
+_p = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_llp = ctypes.POINTER(ctypes.c_longlong)
+
+# every symbol declared in include/kcycle.h, with its signature
+SIGNATURES = {
+    "mg_setup": (_i, [_i, _d, _d, _i, _i, _i, ctypes.POINTER(_h)]),
+    "mg_destroy": (_i, [_h]),
+    "mg_set_option": (_i, [_h, _i, _d]),
+    "mg_get_option": (_i, [_h, _i, _dp]),
+    "mg_set_stream": (_i, [_h, _p]),
+    "mg_kcycle": (_i, [_h, _p, _p, _i]),
+    "mg_kcycle_adjoint": (_i, [_h, _p, _p, _i]),
+    "mg_solve": (_i, [_h, _p, _p, _i, _d, _i, _ip, _dp, _dp]),
+    "mg_solve_host": (_i, [_h, _p, _p, _i, _d, _i, _ip, _dp, _dp]),
+    "mg_pcg": (_i, [_h, _p, _p, _i, _d, _i, _i, _ip, _dp, _dp]),
+    "mg_apply": (_i, [_h, _p, _p]),
+    "mg_residual_norm": (_i, [_h, _p, _p, _dp]),
+    "mg_param_grads": (_i, [_h, _p, _p, _dp, _dp]),
+    "mg_stencils": (_i, [_h, _dp, _i, _ip]),
+    "mg_counters": (_i, [_h, _i, _llp, _llp, _llp]),
+    "mg_profile_cycle": (_i, [_h, _p, _p, _i, _i, _i, _dp, _ip, _ip, _ip]),
+    "mg_status_string": (ctypes.c_char_p, [_i]),
+    "mg_last_error": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in SIGNATURES.items():
+    _fn = getattr(_lib, _name)
+    _fn.restype = _res
+    _fn.argtypes = _args
+
+
+class MultigridError(RuntimeError):
+    pass
+
+
+def _check(status: int, what: str) -> int:
+    if status < 0:
+        msg = _lib.mg_status_string(status).decode()
+        detail = _lib.mg_last_error().decode()
+        raise MultigridError(f"{what}: {msg} ({status}) {detail}")
+    return status
+
+
+def _dev(t, n):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+            and tuple(t.shape) == (n, n)):
+        raise ValueError(f"expected a contiguous float64 CUDA tensor of shape ({n}, {n})")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(a, n, writable=False):
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.shape == (n, n)):
+        raise ValueError(f"expected a C-contiguous float64 array of shape ({n}, {n})")
+    if writable and not a.flags.writeable:
+        raise ValueError("array must be writable")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Multigrid:
+    """One hierarchy for the Section 4 problem: ``mg_setup(n, eps, theta, levels, nu1, nu2)``."""
+
+    def __init__(self, n, eps, theta, levels, nu1=2, nu2=2, omega=None, coarse_n=None):
+        h = _h()
+        _check(_lib.mg_setup(int(n), float(eps), float(theta), int(levels), int(nu1), int(nu2), ctypes.byref(h)),
+               "mg_setup")
+        self._h = h
+        self.n, self.levels, self.eps, self.theta, self.nu1, self.nu2 = int(n), int(levels), eps, theta, nu1, nu2
+        if omega is not None:
+            self.set_option(MG_OPT_OMEGA, omega)
+        if coarse_n is not None:
+            self.set_option(MG_OPT_COARSE_N, coarse_n)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.mg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # --------------------------------------------------------------------- options / streams
+    def set_option(self, key, value):
+        _check(_lib.mg_set_option(self._h, int(key), float(value)), "mg_set_option")
+
+    def get_option(self, key):
+        out = _d()
+        _check(_lib.mg_get_option(self._h, int(key), ctypes.byref(out)), "mg_get_option")
+        return out.value
+
+    def _stream(self):
+        """Order the library's work on torch's current stream (the legacy default stream when
+        torch reports handle 0, passed as cudaStreamLegacy)."""
+        import torch
+        s = torch.cuda.current_stream().cuda_stream or CUDA_STREAM_LEGACY
+        _check(_lib.mg_set_stream(self._h, ctypes.c_void_p(s)), "mg_set_stream")
+
+    # --------------------------------------------------------------------- cycles and solvers
+    def kcycle(self, v, f, kappa):
+        self._stream()
+        _check(_lib.mg_kcycle(self._h, _dev(v, self.n), _dev(f, self.n), int(kappa)), "mg_kcycle")
+
+    def kcycle_adjoint(self, v, f, kappa):
+        self._stream()
+        _check(_lib.mg_kcycle_adjoint(self._h, _dev(v, self.n), _dev(f, self.n), int(kappa)), "mg_kcycle_adjoint")
+
+    def solve(self, v, f, kappa, tol, max_cycles, history=True):
+        """Returns (status, cycles, final_relres, history list)."""
+        self._stream()
+        cyc, rel = _i(), _d()
+        hist = np.zeros(max_cycles) if history else None
+        st = _check(_lib.mg_solve(self._h, _dev(v, self.n), _dev(f, self.n), int(kappa), float(tol), int(max_cycles),
+                                  ctypes.byref(cyc), ctypes.byref(rel),
+                                  hist.ctypes.data_as(_dp) if history else None), "mg_solve")
+        return st, cyc.value, rel.value, (list(hist[:cyc.value]) if history else None)
+
+    def solve_host(self, v, f, kappa, tol, max_cycles):
+        """mg_solve_host on numpy arrays (v is updated in place). Returns (status, cycles, final_relres)."""
+        cyc, rel = _i(), _d()
+        st = _check(_lib.mg_solve_host(self._h, _host(v, self.n, True), _host(f, self.n), int(kappa), float(tol),
+                                       int(max_cycles), ctypes.byref(cyc), ctypes.byref(rel), None),
+                    "mg_solve_host")
+        return st, cyc.value, rel.value
+
+    def pcg(self, x, b, kappa, tol, max_iters, flexible=False, history=True):
+        self._stream()
+        it, rel = _i(), _d()
+        hist = np.zeros(max_iters) if history else None
+        st = _check(_lib.mg_pcg(self._h, _dev(x, self.n), _dev(b, self.n), int(kappa), float(tol), int(max_iters),
+                                int(bool(flexible)), ctypes.byref(it), ctypes.byref(rel),
+                                hist.ctypes.data_as(_dp) if history else None), "mg_pcg")
+        return st, it.value, rel.value, (list(hist[:it.value]) if history else None)
+
+    def apply(self, v, out):
+        self._stream()
+        _check(_lib.mg_apply(self._h, _dev(v, self.n), _dev(out, self.n)), "mg_apply")
+
+    def residual_norm(self, v, f):
+        self._stream()
+        out = _d()
+        _check(_lib.mg_residual_norm(self._h, _dev(v, self.n), _dev(f, self.n), ctypes.byref(out)),
+               "mg_residual_norm")
+        return out.value
+
+    def param_grads(self, lam, u):
+        self._stream()
+        a, b = _d(), _d()
+        _check(_lib.mg_param_grads(self._h, _dev(lam, self.n), _dev(u, self.n), ctypes.byref(a), ctypes.byref(b)),
+               "mg_param_grads")
+        return a.value, b.value
+
+    def stencils(self):
+        out = np.zeros(self.levels * 9)
+        w = _i()
+        _check(_lib.mg_stencils(self._h, out.ctypes.data_as(_dp), self.levels, ctypes.byref(w)), "mg_stencils")
+        return out[: w.value * 9].reshape(w.value, 3, 3)
+
+    def profile_cycle(self, v, f, kappa, with_norm=False, max_records=8192):
+        """Per-launch (ms, kind, level) of one cycle run launch by launch with CUDA events."""
+        self._stream()
+        ms = np.zeros(max_records)
+        kind = np.zeros(max_records, dtype=np.int32)
+        level = np.zeros(max_records, dtype=np.int32)
+        cnt = _i()
+        _check(_lib.mg_profile_cycle(self._h, _dev(v, self.n), _dev(f, self.n), int(kappa), int(bool(with_norm)),
+                                     max_records, ms.ctypes.data_as(_dp), kind.ctypes.data_as(_ip),
+                                     level.ctypes.data_as(_ip), ctypes.byref(cnt)), "mg_profile_cycle")
+        k = min(cnt.value, max_records)
+        return ms[:k], kind[:k], level[:k]
+
+    def counters(self, kappa):
+        calls = (ctypes.c_longlong * self.levels)()
+        lau, coarse = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(_lib.mg_counters(self._h, int(kappa), calls, ctypes.byref(lau), ctypes.byref(coarse)), "mg_counters")
+        return list(calls), lau.value, coarse.value

@@ -19,5 +19,7 @@ def lib():
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+    from paper_2010_00626_b300 import build
+    build.build()
     from paper_2010_00626_b300 import kcycle
     return kcycle
