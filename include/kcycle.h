@@ -152,6 +152,26 @@ int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* l
 int mg_profile_cycle(mg_handle h, double* v, const double* f, int kappa, int with_norm, int max_records,
                      double* ms, int* kind, int* level, int* count);
 
+/* ||f - A v||_2 on the finest grid of the Section 4 operator for (n, eps, theta), computed WITHOUT
+ * allocating anything. The paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc at the point where they need the number -- for example code running while another
+ * framework owns the whole device memory pool, a plug-in whose host application forbids device
+ * allocation, or a timing loop that cannot afford the device-wide synchronisation an allocation
+ * may cause. It needs no handle.
+ *   n      grid side, n = 2^k - 1, at most 16383 (larger sizes return MG_ERR_ARG with a message)
+ *   eps, theta as for mg_setup
+ *   v, f   device, n*n doubles, row-major (caller-owned; only read)
+ *   cuda_stream  cudaStream_t to queue on; NULL means the legacy default stream
+ *   norm   host, receives the result
+ * Scratch: one 5760-byte static device array in libkcycle.so, which every GPU that loads the
+ * library holds until the process exits. The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first call before any stream
+ * capture. Each call rewrites every scratch slot it reads, so nothing needs clearing between
+ * calls, but all calls share the array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller. Synchronises the stream. */
+int mg_residual_norm_noalloc(int n, double eps, double theta, const double* v, const double* f,
+                             void* cuda_stream, double* norm);
+
 /* Static string for a status code. */
 const char* mg_status_string(int status);
 

@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <list>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -912,3 +913,97 @@ int mg_profile_cycle(mg_handle h, double* v, const double* f, int kappa, int wit
 }
 
 }  // extern "C"
+
+// ============================================================================================
+// ||f - A v|| without allocating: the whole-grid residual-norm kernel, variant whose scratch
+// (stencil coefficients, per-block partial sums, result) lives in one static device array.
+// ============================================================================================
+namespace {
+constexpr int NA_MAX_N = 16383;     // largest grid side accepted
+constexpr int NA_BLOCKS = 148 * 4;  // fixed grid of the partial-sum kernel: one partial per block
+constexpr int NA_OFF_COEF = 0, NA_OFF_COEF32 = 32, NA_OFF_ST = 48, NA_OFF_DST = 64, NA_OFF_RESULT = 96,
+              NA_OFF_PART = 128;
+constexpr int NA_DOUBLES = NA_OFF_PART + NA_BLOCKS;  // 720 doubles = 5760 bytes
+constexpr int NA_MAX_DEVICES = 64;
+}  // namespace
+
+// Every GPU that loads this library holds this array until the process exits. In host code its
+// name is only a host-side stand-in; kernels get the device address from cudaGetSymbolAddress.
+static __device__ __align__(256) double g_noalloc_scratch[NA_DOUBLES];
+
+namespace {
+std::mutex g_na_mutex;
+double* g_na_ptr[NA_MAX_DEVICES] = {};
+
+template <int NT>
+__global__ void __launch_bounds__(NT) residual_partials_fixed_grid_kernel(const double* __restrict__ v,
+                                                                          const double* __restrict__ f, int n,
+                                                                          const double* coef, double* partial) {
+  __shared__ double red[NT / 32];
+  const Coef<double> c = load_coef(coef, 0);
+  const size_t len = (size_t)n * n;
+  double ss = 0.0;
+  for (size_t k = blockIdx.x * (size_t)NT + threadIdx.x; k < len; k += (size_t)gridDim.x * NT) {
+    const int j = (int)(k / (size_t)n), i = (int)(k - (size_t)j * n);
+    const double r = residual_at(neighbours_global(v, i, j, n, n), f[k], c);
+    ss = fma(r, r, ss);
+  }
+  const double t = block_sum<NT>(ss, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;  // every block writes its slot on every call
+}
+
+// Device address of the static scratch on the current device, looked up once per device.
+int noalloc_scratch(double** out) {
+  int dev = -1;
+  KC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NA_MAX_DEVICES) {
+    snprintf(g_err, sizeof(g_err), "mg_residual_norm_noalloc: device %d out of range", dev);
+    return MG_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_na_mutex);
+  if (!g_na_ptr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      snprintf(g_err, sizeof(g_err), "mg_residual_norm_noalloc: cudaGetSymbolAddress failed: %s",
+               cudaGetErrorString(e));
+      return MG_ERR_CUDA;
+    }
+    g_na_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_na_ptr[dev];
+  return MG_OK;
+}
+}  // namespace
+
+extern "C" int mg_residual_norm_noalloc(int n, double eps, double theta, const double* v, const double* f,
+                                        void* cuda_stream, double* norm) {
+  if (!v || !f || !norm) return MG_ERR_ARG;
+  int k = 0;
+  while (k < 15 && ((1 << k) - 1) < n) ++k;
+  if (n < 1 || ((1 << k) - 1) != n) {
+    snprintf(g_err, sizeof(g_err), "mg_residual_norm_noalloc: n=%d is not 2^k - 1", n);
+    return MG_ERR_ARG;
+  }
+  if (n > NA_MAX_N) {
+    snprintf(g_err, sizeof(g_err), "mg_residual_norm_noalloc: n=%d exceeds the maximum grid side %d", n, NA_MAX_N);
+    return MG_ERR_ARG;
+  }
+  if (!(eps > 0.0) || !(eps <= 1.0) || !(std::fabs(theta) <= 1e4)) return MG_ERR_ARG;
+  double* sc = nullptr;
+  KC_TRY(noalloc_scratch(&sc));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  // the fine-level stencil of (n, eps, theta) into the scratch (the same setup kernel as mg_setup)
+  setup_stencils_kernel<<<1, 32, 0, s>>>(theta, eps, n, 1, 0.8, sc + NA_OFF_COEF,
+                                         reinterpret_cast<float*>(sc + NA_OFF_COEF32), sc + NA_OFF_ST,
+                                         sc + NA_OFF_DST);
+  residual_partials_fixed_grid_kernel<NT_VEC><<<NA_BLOCKS, NT_VEC, 0, s>>>(v, f, n, sc + NA_OFF_COEF,
+                                                                          sc + NA_OFF_PART);
+  sum_to_scalar_kernel<NT_VEC><<<1, NT_VEC, 0, s>>>(sc + NA_OFF_PART, NA_BLOCKS, sc + NA_OFF_RESULT);
+  KC_CUDA(cudaGetLastError());
+  double r2 = 0.0;
+  KC_CUDA(cudaMemcpyAsync(&r2, sc + NA_OFF_RESULT, sizeof(double), cudaMemcpyDeviceToHost, s));
+  KC_CUDA(cudaStreamSynchronize(s));
+  *norm = std::sqrt(r2);
+  return MG_OK;
+}

@@ -51,6 +51,7 @@ SIGNATURES = {
     "mg_stencils": (_i, [_h, _dp, _i, _ip]),
     "mg_counters": (_i, [_h, _i, _llp, _llp, _llp]),
     "mg_profile_cycle": (_i, [_h, _p, _p, _i, _i, _i, _dp, _ip, _ip, _ip]),
+    "mg_residual_norm_noalloc": (_i, [_i, _d, _d, _p, _p, _p, _dp]),
     "mg_status_string": (ctypes.c_char_p, [_i]),
     "mg_last_error": (ctypes.c_char_p, []),
 }
