@@ -305,6 +305,23 @@ def main():
             per_kappa[kname(k)] = {"ms": round(ms_k, 3), "cycles": cyc_k, "ms_per_cycle": round(ms_k / cyc_k, 4),
                                    "relres": rel_k, "status": st_k}
 
+    # ---------------------------------------------------------------- mixed precision (FP32 cycles + FP64 IR)
+    per_kappa_mixed = {}
+    if not args.no_sweep:
+        for k in (1, 2, 3, 4, 5, KAPPA_W):
+            v.zero_()
+            mg.solve_mixed(v, f, k, tol, 1, history=False)  # builds the graph and the FP32 levels
+            v.zero_()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            st_k, it_k, rel_k, _ = mg.solve_mixed(v, f, k, tol, max_cycles, history=False)
+            b.record()
+            torch.cuda.synchronize()
+            ms_k = a.elapsed_time(b)
+            per_kappa_mixed[kname(k)] = {"ms": round(ms_k, 3), "iterations": it_k,
+                                         "ms_per_iteration": round(ms_k / it_k, 4), "relres": rel_k, "status": st_k}
+
     # ---------------------------------------------------------------- oracle on the host cores
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -326,7 +343,8 @@ def main():
                            "l2": "inputs larger than L2 (each 4095^2 FP64 array is 134 MB)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roofline, "cycle_share": cycle_share, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": gpu_launches, "clocks": clocks.summary(), "per_kappa": per_kappa}
+                "gpu_launches": gpu_launches, "clocks": clocks.summary(), "per_kappa": per_kappa,
+                "per_kappa_mixed": per_kappa_mixed}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -120,6 +120,21 @@ int mg_solve_host(mg_handle h, double* v, const double* f, int kappa, double tol
 int mg_pcg(mg_handle h, double* x, const double* b, int kappa, double tol, int max_iters,
            int flexible, int* iters, double* final_relres, double* history);
 
+/* Mixed precision (an extension of the paper's FP64 method): iterative refinement in FP64 around
+ * FP32 kappa-cycles. Each iteration runs one FP32 kappa-cycle from zero on the FP32-rounded
+ * residual, d = B32 r (relaxation, restriction and interpolation in FP32; the coarsest solve in
+ * FP64), then x += d and r = f - A x in FP64, and tests ||r||_2/||f||_2 <= tol on the device.
+ *   x device in/out (initial guess, then the solution, FP64); f device (FP64).
+ *   iters, final_relres, history: as for mg_solve (history: max_iters doubles).
+ * Allocates the FP32 level arrays (about 4n^2/3 floats per vector kind) on first use.
+ * Returns MG_OK or MG_NOT_CONVERGED. Synchronises. */
+int mg_solve_mixed(mg_handle h, double* x, const double* f, int kappa, double tol, int max_iters,
+                   int* iters, double* final_relres, double* history);
+
+/* One kappa-cycle in FP32 arithmetic in place (the inner cycle of mg_solve_mixed; coarsest solve
+ * in FP64): v, f device float arrays, n*n, row-major. Asynchronous. */
+int mg_kcycle_f32(mg_handle h, float* v, const float* f, int kappa);
+
 /* out = A v on the finest level (device pointers, n*n each). Asynchronous. */
 int mg_apply(mg_handle h, const double* v, double* out);
 

@@ -18,6 +18,7 @@
 #include <list>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/kcycle.h"
@@ -61,9 +62,14 @@ struct Level {
   double* v = nullptr;    // current estimate (level 0: the caller's array)
   double* tmp = nullptr;  // relaxed v between pass A and pass B
   double* f = nullptr;    // right-hand side (level 0: the caller's array)
+  // FP32 hierarchy of the mixed-precision cycle, allocated on first use; level 0 holds the
+  // FP32 correction d (v32) and the rounded FP64 residual (f32)
+  float* v32 = nullptr;
+  float* tmp32 = nullptr;
+  float* f32 = nullptr;
 };
 
-enum GraphKind { G_CYCLE = 1, G_SOLVE = 2, G_PCG = 3 };
+enum GraphKind { G_CYCLE = 1, G_SOLVE = 2, G_PCG = 3, G_CYCLE32 = 4, G_MIXED = 5 };
 
 struct GraphEntry {
   int kind = 0, kappa = 0, flag = 0;
@@ -75,19 +81,23 @@ struct GraphEntry {
 };
 
 // Per-call pointer binding of level 0 (caller memory) over the handle's own levels.
-struct Binding {
-  double* v0;
-  const double* f0;
+template <typename T>
+struct BindingT {
+  T* v0;
+  const T* f0;
   int ld0;
 };
+using Binding = BindingT<double>;
 
 }  // namespace
 
 struct mg_ctx {
   int n = 0, k = 0, levels = 0, nu1 = 2, nu2 = 2;
   double eps = 0, theta = 0, omega = 0.8;
-  int coarse_n = 15;  // largest side handled by the coarse kernel
-  int lc = 0;         // first level handled by the coarse kernel
+  int coarse_n = 15;  // largest side handled by the coarse kernel (FP64 cycles)
+  int lc = 0;         // first level handled by the coarse kernel (FP64 cycles)
+  int lc32 = 0;       // same for the FP32 cycles of the mixed path: sides <= 63 (one SM does
+                      // FP32 at 64x the FP64 rate, so the single-CTA kernel takes more levels)
   Level lv[MAXL];
   double* coef = nullptr;
   float* coef32 = nullptr;
@@ -103,6 +113,7 @@ struct mg_ctx {
   int* ints = nullptr;
   double* hist = nullptr;
   int hist_cap = 0;
+  bool have32 = false;  // FP32 hierarchy allocated
   double *pr = nullptr, *pp = nullptr, *pq = nullptr, *pz = nullptr, *pzold = nullptr;  // PCG vectors
   double *hv = nullptr, *hf = nullptr;  // device copies for mg_solve_host
   cudaStream_t own = nullptr;
@@ -144,31 +155,42 @@ int tile_edge(int n) {
   return 8;
 }
 
-template <typename Cfg>
-int launch_pass_a(const PassAArgs<double>& a, cudaStream_t s) {
+template <typename Cfg, typename T>
+int launch_pass_a(const PassAArgs<T>& a, cudaStream_t s) {
   dim3 grid((a.n + Cfg::bx - 1) / Cfg::bx, (a.n + Cfg::by - 1) / Cfg::by);
-  const size_t sm = pass_a_smem<double, Cfg::bx, Cfg::by>(a.nu);
-  pass_a_kernel<double, Cfg::bx, Cfg::by, Cfg::nt><<<grid, Cfg::nt, sm, s>>>(a);
+  const size_t sm = pass_a_smem<T, Cfg::bx, Cfg::by>(a.nu);
+  pass_a_kernel<T, Cfg::bx, Cfg::by, Cfg::nt><<<grid, Cfg::nt, sm, s>>>(a);
   KC_CUDA(cudaGetLastError());
   return MG_OK;
 }
-template <typename Cfg>
-int launch_pass_b(const PassBArgs<double>& a, cudaStream_t s) {
+template <typename Cfg, typename T>
+int launch_pass_b(const PassBArgs<T>& a, cudaStream_t s) {
   dim3 grid((a.n + Cfg::bx - 1) / Cfg::bx, (a.n + Cfg::by - 1) / Cfg::by);
-  const size_t sm = pass_b_smem<double, Cfg::bx, Cfg::by>(a.nu, a.partial != nullptr);
-  pass_b_kernel<double, Cfg::bx, Cfg::by, Cfg::nt><<<grid, Cfg::nt, sm, s>>>(a);
+  const size_t sm = pass_b_smem<T, Cfg::bx, Cfg::by>(a.nu, a.partial != nullptr);
+  pass_b_kernel<T, Cfg::bx, Cfg::by, Cfg::nt><<<grid, Cfg::nt, sm, s>>>(a);
   KC_CUDA(cudaGetLastError());
   return MG_OK;
 }
 
-template <typename Cfg>
+template <typename Cfg, typename T>
 int set_smem_attrs() {
-  KC_CUDA(cudaFuncSetAttribute(pass_a_kernel<double, Cfg::bx, Cfg::by, Cfg::nt>,
+  KC_CUDA(cudaFuncSetAttribute(pass_a_kernel<T, Cfg::bx, Cfg::by, Cfg::nt>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)pass_a_smem<double, Cfg::bx, Cfg::by>(MAX_NU)));
-  KC_CUDA(cudaFuncSetAttribute(pass_b_kernel<double, Cfg::bx, Cfg::by, Cfg::nt>,
+                               (int)pass_a_smem<T, Cfg::bx, Cfg::by>(MAX_NU)));
+  KC_CUDA(cudaFuncSetAttribute(pass_b_kernel<T, Cfg::bx, Cfg::by, Cfg::nt>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)pass_b_smem<double, Cfg::bx, Cfg::by>(MAX_NU, true)));
+                               (int)pass_b_smem<T, Cfg::bx, Cfg::by>(MAX_NU, true)));
+  return MG_OK;
+}
+
+template <typename T>
+int set_all_smem_attrs() {
+  KC_TRY((set_smem_attrs<Tile64, T>()));
+  KC_TRY((set_smem_attrs<Tile32, T>()));
+  KC_TRY((set_smem_attrs<Tile16, T>()));
+  KC_TRY((set_smem_attrs<Tile8, T>()));
+  KC_CUDA(cudaFuncSetAttribute(coarse_kernel<T, NT_COARSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)coarse_smem<T>(MAX_COARSE_N, 6)));
   return MG_OK;
 }
 
@@ -184,9 +206,33 @@ size_t apply_grid_blocks(int n) {
 // ------------------------------------------------------------------------------------------
 // Cycle emission (Algorithm 3 unrolled over the fine levels)
 // ------------------------------------------------------------------------------------------
-double* lv_v(mg_ctx* h, const Binding& b, int l) { return l == 0 ? b.v0 : h->lv[l].v; }
-const double* lv_f(mg_ctx* h, const Binding& b, int l) { return l == 0 ? b.f0 : h->lv[l].f; }
-int lv_ld(mg_ctx* h, const Binding& b, int l) { return l == 0 ? b.ld0 : h->lv[l].ld; }
+// Level arrays of one precision: the FP64 hierarchy or the FP32 one of the mixed cycle.
+template <typename T>
+struct Arr;
+template <>
+struct Arr<double> {
+  static double* v(mg_ctx* h, int l) { return h->lv[l].v; }
+  static double* tmp(mg_ctx* h, int l) { return h->lv[l].tmp; }
+  static double* f(mg_ctx* h, int l) { return h->lv[l].f; }
+  static const double* coef(mg_ctx* h) { return h->coef; }
+};
+template <>
+struct Arr<float> {
+  static float* v(mg_ctx* h, int l) { return h->lv[l].v32; }
+  static float* tmp(mg_ctx* h, int l) { return h->lv[l].tmp32; }
+  static float* f(mg_ctx* h, int l) { return h->lv[l].f32; }
+  static const float* coef(mg_ctx* h) { return h->coef32; }
+};
+
+template <typename T>
+int lc_of(const mg_ctx* h) { return std::is_same<T, double>::value ? h->lc : h->lc32; }
+
+template <typename T>
+T* lv_v(mg_ctx* h, const BindingT<T>& b, int l) { return l == 0 ? b.v0 : Arr<T>::v(h, l); }
+template <typename T>
+const T* lv_f(mg_ctx* h, const BindingT<T>& b, int l) { return l == 0 ? b.f0 : Arr<T>::f(h, l); }
+template <typename T>
+int lv_ld(mg_ctx* h, const BindingT<T>& b, int l) { return l == 0 ? b.ld0 : h->lv[l].ld; }
 
 enum { K_PASS_A = 0, K_PASS_B = 1, K_COARSE = 2, K_APPLY = 3 };
 
@@ -207,18 +253,21 @@ void prof_end(mg_ctx* h, cudaStream_t s) {
   h->pev.push_back(e);
 }
 
-int emit_coarse(mg_ctx* h, const Binding& b, int k1, int k2, int zero1, bool adjoint, const int* skip,
+template <typename T>
+int emit_coarse(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int zero1, bool adjoint, const int* skip,
                 cudaStream_t s) {
-  CoarseArgs<double> a;
-  a.v = lv_v(h, b, h->lc);
-  a.f = lv_f(h, b, h->lc);
-  a.coef = h->coef;
+  const int lc = lc_of<T>(h);
+  CoarseArgs<T> a;
+  a.v = lv_v(h, b, lc);
+  a.f = lv_f(h, b, lc);
+  a.coef = Arr<T>::coef(h);
+  a.coef64 = h->coef;
   a.cinv = h->cinv;
   a.skip = skip;
-  a.ldv = lv_ld(h, b, h->lc);
-  a.ldf = lv_ld(h, b, h->lc);
-  a.n_lc = h->lv[h->lc].n;
-  a.lc = h->lc;
+  a.ldv = lv_ld(h, b, lc);
+  a.ldf = lv_ld(h, b, lc);
+  a.n_lc = h->lv[lc].n;
+  a.lc = lc;
   a.L = h->levels;
   a.nu1 = h->nu1;
   a.nu2 = h->nu2;
@@ -226,22 +275,23 @@ int emit_coarse(mg_ctx* h, const Binding& b, int k1, int k2, int zero1, bool adj
   a.k2 = k2;
   a.zero1 = zero1;
   a.adjoint = adjoint ? 1 : 0;
-  const size_t sm = coarse_smem<double>(a.n_lc, a.L - a.lc);
-  prof_begin(h, K_COARSE, h->lc, s);
-  coarse_kernel<double, NT_COARSE><<<1, NT_COARSE, sm, s>>>(a);
+  const size_t sm = coarse_smem<T>(a.n_lc, a.L - a.lc);
+  prof_begin(h, K_COARSE, lc, s);
+  coarse_kernel<T, NT_COARSE><<<1, NT_COARSE, sm, s>>>(a);
   prof_end(h, s);
   KC_CUDA(cudaGetLastError());
   ++h->launch_count;
   return MG_OK;
 }
 
-int emit_pass_a(mg_ctx* h, const Binding& b, int l, bool zero, int nu, const int* skip, cudaStream_t s) {
-  PassAArgs<double> a;
+template <typename T>
+int emit_pass_a(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const int* skip, cudaStream_t s) {
+  PassAArgs<T> a;
   a.vin = zero ? nullptr : lv_v(h, b, l);
-  a.vout = h->lv[l].tmp;
+  a.vout = Arr<T>::tmp(h, l);
   a.f = lv_f(h, b, l);
-  a.fc = h->lv[l + 1].f;
-  a.coef = h->coef;
+  a.fc = Arr<T>::f(h, l + 1);
+  a.coef = Arr<T>::coef(h);
   a.skip = skip;
   a.ldvin = lv_ld(h, b, l);
   a.ldvout = h->lv[l].ld;
@@ -263,13 +313,14 @@ int emit_pass_a(mg_ctx* h, const Binding& b, int l, bool zero, int nu, const int
   return st;
 }
 
-int emit_pass_b(mg_ctx* h, const Binding& b, int l, int nu, double* partial, const int* skip, cudaStream_t s) {
-  PassBArgs<double> a;
-  a.vin = h->lv[l].tmp;
+template <typename T>
+int emit_pass_b(mg_ctx* h, const BindingT<T>& b, int l, int nu, double* partial, const int* skip, cudaStream_t s) {
+  PassBArgs<T> a;
+  a.vin = Arr<T>::tmp(h, l);
   a.vout = lv_v(h, b, l);
   a.f = lv_f(h, b, l);
-  a.vc = h->lv[l + 1].v;
-  a.coef = h->coef;
+  a.vc = Arr<T>::v(h, l + 1);
+  a.coef = Arr<T>::coef(h);
   a.skip = skip;
   a.partial = partial;
   a.ldvin = h->lv[l].ld;
@@ -305,14 +356,15 @@ void child_counters(int kappa, bool adjoint, int* first, int* second) {
 }
 
 // emit call(l, kappa) for a fine level l < lc; `norm` adds residual partial sums at level 0
-int emit_call(mg_ctx* h, const Binding& b, int l, int kappa, bool zero, bool adjoint, bool norm,
+template <typename T>
+int emit_call(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero, bool adjoint, bool norm,
               const int* skip, cudaStream_t s) {
   const int nu_pre = adjoint ? h->nu2 : h->nu1;
   const int nu_post = adjoint ? h->nu1 : h->nu2;
   KC_TRY(emit_pass_a(h, b, l, zero, nu_pre, skip, s));
   int k1, k2;
   child_counters(kappa, adjoint, &k1, &k2);
-  if (l + 1 >= h->lc) {
+  if (l + 1 >= lc_of<T>(h)) {
     KC_TRY(emit_coarse(h, b, k1, k2, 1, adjoint, skip, s));
   } else {
     KC_TRY(emit_call(h, b, l + 1, k1, true, adjoint, false, skip, s));
@@ -333,13 +385,20 @@ int emit_apply(mg_ctx* h, const double* v, const double* f, double* out, double*
   return MG_OK;
 }
 
-// One finest-level cycle. With norm, the last pass writes residual partial sums (or, when the
-// coarse kernel handles level 0, a separate residual pass does).
-int emit_cycle(mg_ctx* h, const Binding& b, int kappa, bool zero, bool adjoint, bool norm, const int* skip,
+// One finest-level cycle. With norm (FP64 only), the last pass writes residual partial sums (or,
+// when the coarse kernel handles level 0, a separate residual pass does).
+template <typename T>
+int emit_cycle(mg_ctx* h, const BindingT<T>& b, int kappa, bool zero, bool adjoint, bool norm, const int* skip,
                cudaStream_t s) {
-  if (h->lc == 0) {
+  if (lc_of<T>(h) == 0) {
     KC_TRY(emit_coarse(h, b, kappa, 0, zero ? 1 : 0, adjoint, skip, s));
-    if (norm) KC_TRY(emit_apply(h, b.v0, b.f0, nullptr, h->partial, skip, s));
+    if (norm) {
+      if constexpr (std::is_same<T, double>::value) {
+        KC_TRY(emit_apply(h, b.v0, b.f0, nullptr, h->partial, skip, s));
+      } else {
+        return MG_ERR_ARG;
+      }
+    }
     return MG_OK;
   }
   return emit_call(h, b, 0, kappa, zero, adjoint, norm, skip, s);
@@ -535,8 +594,38 @@ int alloc_levels(mg_ctx* h) {
   return MG_OK;
 }
 
+// FP32 hierarchy of the mixed cycle: same shapes as the FP64 one, plus level 0 (d and r32).
+int ensure_levels32(mg_ctx* h) {
+  if (h->have32) return MG_OK;
+  h->lc32 = h->levels - 1;
+  for (int l = 0; l < h->levels; ++l)
+    if (h->lv[l].n <= MAX_COARSE_N) {
+      h->lc32 = l;
+      break;
+    }
+  for (int l = 0; l < h->levels; ++l) {
+    Level& L = h->lv[l];
+    const size_t bytes = sizeof(float) * (size_t)L.ld * L.n;
+    if (l < h->lc32) KC_CUDA(cudaMalloc(&L.tmp32, bytes));
+    if (l <= h->lc32) {
+      KC_CUDA(cudaMalloc(&L.v32, bytes));
+      KC_CUDA(cudaMalloc(&L.f32, bytes));
+      KC_CUDA(cudaMemsetAsync(L.v32, 0, bytes, h->own));
+      KC_CUDA(cudaMemsetAsync(L.f32, 0, bytes, h->own));
+    }
+  }
+  KC_CUDA(cudaStreamSynchronize(h->own));
+  h->have32 = true;
+  return MG_OK;
+}
+
 int free_levels(mg_ctx* h) {
   for (int l = 0; l < MAXL; ++l) {
+    float** f32s[] = {&h->lv[l].v32, &h->lv[l].tmp32, &h->lv[l].f32};
+    for (float** p : f32s) {
+      if (*p) KC_CUDA(cudaFree(*p));
+      *p = nullptr;
+    }
     if (l > 0) {
       if (h->lv[l].v) KC_CUDA(cudaFree(h->lv[l].v));
       if (h->lv[l].f) KC_CUDA(cudaFree(h->lv[l].f));
@@ -545,6 +634,7 @@ int free_levels(mg_ctx* h) {
     if (h->lv[l].tmp) KC_CUDA(cudaFree(h->lv[l].tmp));
     h->lv[l].tmp = nullptr;
   }
+  h->have32 = false;
   return MG_OK;
 }
 
@@ -643,12 +733,7 @@ int mg_setup(int n, double eps, double theta, int levels, int nu1, int nu2, mg_h
   if (cudaMemsetAsync(h->ints, 0, sizeof(int) * NINT, h->own) != cudaSuccess) return fail(MG_ERR_CUDA);
   if (cudaMemsetAsync(h->scal, 0, sizeof(double) * NSCAL, h->own) != cudaSuccess) return fail(MG_ERR_CUDA);
   if ((st = run_setup_kernels(h)) < 0) return fail(st);
-  if ((st = set_smem_attrs<Tile64>()) < 0 || (st = set_smem_attrs<Tile32>()) < 0 ||
-      (st = set_smem_attrs<Tile16>()) < 0 || (st = set_smem_attrs<Tile8>()) < 0)
-    return fail(st);
-  if (cudaFuncSetAttribute(coarse_kernel<double, NT_COARSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)coarse_smem<double>(MAX_COARSE_N, 6)) != cudaSuccess)
-    return fail(MG_ERR_CUDA);
+  if ((st = set_all_smem_attrs<double>()) < 0 || (st = set_all_smem_attrs<float>()) < 0) return fail(st);
   h->ok = true;
   *out = h;
   return MG_OK;
@@ -792,6 +877,79 @@ int mg_pcg(mg_handle h, double* x, const double* b, int kappa, double tol, int m
                                                      h->ints);
   dot_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, s>>>(h->pr, h->pz, nullptr, len, h->partial, nullptr, nullptr);
   sum_to_scalar_kernel<NT_VEC><<<1, NT_VEC, 0, s>>>(h->partial, VEC_BLOCKS, h->scal + S_RZ);
+  KC_CUDA(cudaGetLastError());
+  KC_CUDA(cudaGraphLaunch(ge->exec, s));
+  return read_result(h, s, tol, iters, final_relres, history);
+}
+
+int mg_kcycle_f32(mg_handle h, float* v, const float* f, int kappa) {
+  if (!valid_handle(h)) return MG_ERR_STATE;
+  if (!v || !f || kappa < 1) return MG_ERR_ARG;
+  trim_graphs(h);
+  KC_TRY(ensure_levels32(h));
+  GraphEntry* ge = find_graph(h, G_CYCLE32, kappa, 0, v, f);
+  if (!ge) {
+    BindingT<float> b{v, f, h->n};
+    cudaGraph_t g;
+    h->launch_count = 0;
+    KC_CUDA(cudaStreamBeginCapture(h->own, cudaStreamCaptureModeThreadLocal));
+    const int st = emit_cycle(h, b, kappa, false, false, false, nullptr, h->own);
+    const cudaError_t ce = cudaStreamEndCapture(h->own, &g);
+    if (st < 0) {
+      if (ce == cudaSuccess) cudaGraphDestroy(g);
+      return st;
+    }
+    KC_CUDA(ce);
+    GraphEntry e;
+    e.kind = G_CYCLE32; e.kappa = kappa; e.p0 = v; e.p1 = f; e.graph = g; e.launches = h->launch_count;
+    const cudaError_t ie = cudaGraphInstantiate(&e.exec, g, 0);
+    if (ie != cudaSuccess) {
+      cudaGraphDestroy(g);
+      KC_CUDA(ie);
+    }
+    ge = add_graph(h, e);
+  }
+  KC_CUDA(cudaGraphLaunch(ge->exec, h->stream()));
+  return MG_OK;
+}
+
+int mg_solve_mixed(mg_handle h, double* x, const double* f, int kappa, double tol, int max_iters, int* iters,
+                   double* final_relres, double* history) {
+  if (!valid_handle(h)) return MG_ERR_STATE;
+  if (!x || !f || kappa < 1 || !(tol > 0) || max_iters < 1) return MG_ERR_ARG;
+  trim_graphs(h);
+  KC_TRY(ensure_levels32(h));
+  KC_TRY(ensure_hist(h, max_iters));
+  cudaStream_t s = h->stream();
+  const int n = h->n;
+  const size_t len = (size_t)n * n;
+  float* d = h->lv[0].v32;
+  float* r32 = h->lv[0].f32;
+  const int napply = (int)apply_grid_blocks(n);
+  dim3 agrid((n + 31) / 32, (n + NT_VEC / 32 - 1) / (NT_VEC / 32));
+  GraphEntry* ge = find_graph(h, G_MIXED, kappa, 0, x, f);
+  if (!ge) {
+    GraphEntry e;
+    e.kind = G_MIXED; e.kappa = kappa; e.p0 = x; e.p1 = f;
+    BindingT<float> b{d, r32, n};
+    const int* done = h->ints + I_DONE;
+    KC_TRY(build_while_graph(h, [&](cudaGraphConditionalHandle ch) -> int {
+      cudaStream_t o = h->own;
+      // d = B r (FP32 kappa-cycle from zero), x += d, r = f - A x (FP64), stopping test
+      KC_TRY(emit_cycle(h, b, kappa, true, false, false, done, o));
+      ir_add_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, o>>>(x, d, len, done);
+      ir_residual_kernel<NT_VEC><<<agrid, NT_VEC, 0, o>>>(x, f, r32, h->coef, n, h->partial, done);
+      finish_step_kernel<NT_VEC><<<1, NT_VEC, 0, o>>>(h->partial, napply, h->scal, h->ints, h->hist, ch, 1);
+      KC_CUDA(cudaGetLastError());
+      h->launch_count += 3;
+      return MG_OK;
+    }, &e.graph, &e.exec));
+    e.launches = h->launch_count;
+    ge = add_graph(h, e);
+  }
+  KC_TRY(launch_norm2(h, f, h->scal + S_FNORM2, s));
+  reset_state_kernel<<<1, 1, 0, s>>>(h->ints, max_iters, h->scal, tol);
+  ir_residual_kernel<NT_VEC><<<agrid, NT_VEC, 0, s>>>(x, f, r32, h->coef, n, h->partial, nullptr);
   KC_CUDA(cudaGetLastError());
   KC_CUDA(cudaGraphLaunch(ge->exec, s));
   return read_result(h, s, tol, iters, final_relres, history);

@@ -336,8 +336,9 @@ template <typename T>
 struct CoarseArgs {
   T* v;            // global v at level lc (read when the first call is not zero-start; written back)
   const T* f;      // global f at level lc
-  const T* coef;   // coefficient table of all levels
-  const T* cinv;   // dense inverse of the coarsest operator when its grid is larger than 1x1
+  const T* coef;   // coefficient table of all levels (precision T)
+  const double* coef64;  // FP64 coefficient table: the coarsest solve is always FP64
+  const double* cinv;    // FP64 dense inverse of the coarsest operator when its grid is larger than 1x1
   const int* skip;
   int ldv, ldf;
   int n_lc;        // grid side of level lc
@@ -495,20 +496,21 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
     }
     __syncthreads();
   };
-  // exact coarsest solve: division for 1x1, dense inverse otherwise (into the other buffer)
+  // exact coarsest solve in FP64 whatever T is: division for 1x1, dense inverse otherwise (into the
+// other buffer)
   auto coarsest = [&]() {
     const int d = nlev - 1, s = g_side[d];
     const T* f = fbuf(d);
     const unsigned b = (cur >> d) & 1u;
     T* dst = vbuf(d, b ^ 1u);
-    if (s == 1) {
-      if (threadIdx.x == 0) dst[4] = f[4] / cf[d].c0;  // padded 3x3, interior at 4
+    if (s == 1) {  // padded 3x3, interior at 4
+      if (threadIdx.x == 0) dst[4] = (T)((double)f[4] / a.coef64[(a.L - 1) * NCOEF + C_C0]);
     } else {
       const int N = s * s;
       for (int r = threadIdx.x; r < N; r += NT) {
-        T acc = T(0);
-        for (int q = 0; q < N; ++q) acc = fma(a.cinv[(size_t)r * N + q], f[pos(d, q)], acc);
-        dst[pos(d, r)] = acc;
+        double acc = 0.0;
+        for (int q = 0; q < N; ++q) acc = fma(a.cinv[(size_t)r * N + q], (double)f[pos(d, q)], acc);
+        dst[pos(d, r)] = (T)acc;
       }
     }
     cur ^= 1u << d;
@@ -986,6 +988,38 @@ __global__ void __launch_bounds__(NT) grad_kernel(const double* lam, const doubl
   __syncthreads();
   t = block_sum<NT>(s_ep, red);
   if (threadIdx.x == 0) partial_ep[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Mixed precision: FP32 cycles inside FP64 iterative refinement.
+// ---------------------------------------------------------------------------------------------
+// x += d (FP64 += FP32 correction), pointwise
+template <int NT>
+__global__ void __launch_bounds__(NT) ir_add_kernel(double* x, const float* d, size_t len, const int* skip) {
+  if (skip && *skip) return;
+  for (size_t k = blockIdx.x * (size_t)NT + threadIdx.x; k < len; k += (size_t)gridDim.x * NT)
+    x[k] += (double)d[k];
+}
+
+// r = f - A x in FP64, stored rounded to FP32 as the right-hand side of the next FP32 cycle, with
+// partial sums of r^2 (FP64) for the stopping test
+template <int NT>
+__global__ void __launch_bounds__(NT) ir_residual_kernel(const double* __restrict__ x, const double* __restrict__ f,
+                                                         float* r32, const double* coef, int n, double* partial,
+                                                         const int* skip) {
+  if (skip && *skip) return;
+  __shared__ double red[NT / 32];
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int j = blockIdx.y * (NT / 32) + (threadIdx.x >> 5);
+  const Coef<double> c = load_coef(coef, 0);
+  double ss = 0.0;
+  if (i < n && j < n) {
+    const double r = residual_at(neighbours_global(x, i, j, n, n), f[(size_t)j * n + i], c);
+    r32[(size_t)j * n + i] = (float)r;
+    ss = r * r;
+  }
+  const double t = block_sum<NT>(ss, red);
+  if (threadIdx.x == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
 __global__ void reset_state_kernel(int* ints, int max_iters, double* scal, double tol) {

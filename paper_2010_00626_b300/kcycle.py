@@ -52,6 +52,8 @@ SIGNATURES = {
     "mg_counters": (_i, [_h, _i, _llp, _llp, _llp]),
     "mg_profile_cycle": (_i, [_h, _p, _p, _i, _i, _i, _dp, _ip, _ip, _ip]),
     "mg_residual_norm_noalloc": (_i, [_i, _d, _d, _p, _p, _p, _dp]),
+    "mg_solve_mixed": (_i, [_h, _p, _p, _i, _d, _i, _ip, _dp, _dp]),
+    "mg_kcycle_f32": (_i, [_h, _p, _p, _i]),
     "mg_status_string": (ctypes.c_char_p, [_i]),
     "mg_last_error": (ctypes.c_char_p, []),
 }
@@ -73,11 +75,12 @@ def _check(status: int, what: str) -> int:
     return status
 
 
-def _dev(t, n):
+def _dev(t, n, dtype="float64"):
     import torch
-    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    want = getattr(torch, dtype)
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == want and t.is_contiguous()
             and tuple(t.shape) == (n, n)):
-        raise ValueError(f"expected a contiguous float64 CUDA tensor of shape ({n}, {n})")
+        raise ValueError(f"expected a contiguous {dtype} CUDA tensor of shape ({n}, {n})")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -171,6 +174,21 @@ class Multigrid:
                                 int(bool(flexible)), ctypes.byref(it), ctypes.byref(rel),
                                 hist.ctypes.data_as(_dp) if history else None), "mg_pcg")
         return st, it.value, rel.value, (list(hist[:it.value]) if history else None)
+
+    def solve_mixed(self, x, f, kappa, tol, max_iters, history=True):
+        """FP64 iterative refinement around FP32 kappa-cycles. Returns (status, iters, relres, history)."""
+        self._stream()
+        it, rel = _i(), _d()
+        hist = np.zeros(max_iters) if history else None
+        st = _check(_lib.mg_solve_mixed(self._h, _dev(x, self.n), _dev(f, self.n), int(kappa), float(tol),
+                                        int(max_iters), ctypes.byref(it), ctypes.byref(rel),
+                                        hist.ctypes.data_as(_dp) if history else None), "mg_solve_mixed")
+        return st, it.value, rel.value, (list(hist[:it.value]) if history else None)
+
+    def kcycle_f32(self, v, f, kappa):
+        self._stream()
+        _check(_lib.mg_kcycle_f32(self._h, _dev(v, self.n, "float32"), _dev(f, self.n, "float32"), int(kappa)),
+               "mg_kcycle_f32")
 
     def apply(self, v, out):
         self._stream()
