@@ -107,6 +107,11 @@ int mg_kcycle_adjoint(mg_handle h, double* v, const double* f, int kappa);
 int mg_solve(mg_handle h, double* v, const double* f, int kappa, double tol, int max_cycles,
              int* cycles, double* final_relres, double* history);
 
+/* mg_solve iterating the adjoint cycle (mg_kcycle_adjoint): solves A^T v = f, the adjoint problem
+ * of a differentiable solve (lambda = A^-T dL/du). Same arguments and behaviour as mg_solve. */
+int mg_solve_adjoint(mg_handle h, double* v, const double* f, int kappa, double tol, int max_cycles,
+                     int* cycles, double* final_relres, double* history);
+
 /* mg_solve on HOST buffers: copies f and the initial guess v to the device, solves, copies v
  * back. v, f: host, n*n doubles (page-locked memory gives the fastest copies). */
 int mg_solve_host(mg_handle h, double* v, const double* f, int kappa, double tol, int max_cycles,
@@ -161,7 +166,9 @@ int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* l
  * launch with a CUDA event pair around every kernel instead of through a graph, and report each
  * launch: ms[r] its duration in milliseconds, kind[r] 0 = pass A (relax + residual + restrict),
  * 1 = pass B (interpolate + correct + relax), 2 = coarse-level kernel, 3 = whole-grid residual;
- * level[r] its level (0 finest). with_norm adds the residual partial sums of a solve cycle.
+ * level[r] its level (0 finest). Flags in with_norm: bit 0 adds the residual partial sums of a
+ * solve cycle; bit 1 profiles instead the FP32 cycle of mg_solve_mixed (zero start on the handle's
+ * FP32 level-0 arrays; v and f are then not used).
  * ms, kind, level: host, nullable, max_records entries; *count: number of launches (may exceed
  * max_records). Measurement hook with no counterpart in the paper. Synchronises. */
 int mg_profile_cycle(mg_handle h, double* v, const double* f, int kappa, int with_norm, int max_records,

@@ -49,7 +49,10 @@ thread_local char g_err[256] = "";
 constexpr int NT_SMALL = 256;
 constexpr int NT_TINY = 128;
 constexpr int NT_BIG = 512;
-constexpr int NT_COARSE = 256;
+constexpr int NT_COARSE = 256;     // coarse kernel, FP64 (bound by the SM's FP64 pipe)
+constexpr int NT_COARSE32 = 512;   // coarse kernel, FP32 (more independent points per phase)
+template <typename T>
+constexpr int nt_coarse() { return std::is_same<T, double>::value ? NT_COARSE : NT_COARSE32; }
 constexpr int NT_VEC = 256;
 constexpr int MAX_NU = 8;
 constexpr int VEC_BLOCKS = 148 * 8;
@@ -189,7 +192,7 @@ int set_all_smem_attrs() {
   KC_TRY((set_smem_attrs<Tile32, T>()));
   KC_TRY((set_smem_attrs<Tile16, T>()));
   KC_TRY((set_smem_attrs<Tile8, T>()));
-  KC_CUDA(cudaFuncSetAttribute(coarse_kernel<T, NT_COARSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  KC_CUDA(cudaFuncSetAttribute(coarse_kernel<T, nt_coarse<T>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)coarse_smem<T>(MAX_COARSE_N, 6)));
   return MG_OK;
 }
@@ -277,7 +280,7 @@ int emit_coarse(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int zero1, bool
   a.adjoint = adjoint ? 1 : 0;
   const size_t sm = coarse_smem<T>(a.n_lc, a.L - a.lc);
   prof_begin(h, K_COARSE, lc, s);
-  coarse_kernel<T, NT_COARSE><<<1, NT_COARSE, sm, s>>>(a);
+  coarse_kernel<T, nt_coarse<T>()><<<1, nt_coarse<T>(), sm, s>>>(a);
   prof_end(h, s);
   KC_CUDA(cudaGetLastError());
   ++h->launch_count;
@@ -543,20 +546,20 @@ int read_result(mg_ctx* h, cudaStream_t s, double tol, int* count_out, double* f
 }
 
 int solve_impl(mg_handle h, double* v, const double* f, int kappa, double tol, int max_cycles, int* cycles,
-               double* final_relres, double* history) {
+               double* final_relres, double* history, bool adjoint = false) {
   if (!valid_handle(h)) return MG_ERR_STATE;
   if (!v || !f || kappa < 1 || !(tol > 0) || max_cycles < 1) return MG_ERR_ARG;
   trim_graphs(h);
   KC_TRY(ensure_hist(h, max_cycles));
   cudaStream_t s = h->stream();
-  GraphEntry* ge = find_graph(h, G_SOLVE, kappa, 0, v, f);
+  GraphEntry* ge = find_graph(h, G_SOLVE, kappa, adjoint ? 1 : 0, v, f);
   if (!ge) {
     GraphEntry e;
-    e.kind = G_SOLVE; e.kappa = kappa; e.flag = 0; e.p0 = v; e.p1 = f;
+    e.kind = G_SOLVE; e.kappa = kappa; e.flag = adjoint ? 1 : 0; e.p0 = v; e.p1 = f;
     Binding b{v, f, h->n};
     const int np = norm_partials(h);
     KC_TRY(build_while_graph(h, [&](cudaGraphConditionalHandle ch) -> int {
-      KC_TRY(emit_cycle(h, b, kappa, false, false, true, h->ints + I_DONE, h->own));
+      KC_TRY(emit_cycle(h, b, kappa, false, adjoint, true, h->ints + I_DONE, h->own));
       finish_step_kernel<NT_VEC><<<1, NT_VEC, 0, h->own>>>(h->partial, np, h->scal, h->ints, h->hist, ch, 1);
       KC_CUDA(cudaGetLastError());
       ++h->launch_count;
@@ -805,6 +808,11 @@ int mg_solve(mg_handle h, double* v, const double* f, int kappa, double tol, int
   return solve_impl(h, v, f, kappa, tol, max_cycles, cycles, final_relres, history);
 }
 
+int mg_solve_adjoint(mg_handle h, double* v, const double* f, int kappa, double tol, int max_cycles, int* cycles,
+                     double* final_relres, double* history) {
+  return solve_impl(h, v, f, kappa, tol, max_cycles, cycles, final_relres, history, true);
+}
+
 int mg_solve_host(mg_handle h, double* v, const double* f, int kappa, double tol, int max_cycles, int* cycles,
                   double* final_relres, double* history) {
   if (!valid_handle(h)) return MG_ERR_STATE;
@@ -1040,11 +1048,19 @@ int mg_profile_cycle(mg_handle h, double* v, const double* f, int kappa, int wit
   if (!v || !f || kappa < 1 || max_records < 0) return MG_ERR_ARG;
   cudaStream_t s = h->stream();
   Binding b{v, f, h->n};
+  const bool fp32 = (with_norm & 2) != 0;
+  if (fp32) KC_TRY(ensure_levels32(h));
   h->pev.clear();
   h->pkind.clear();
   h->plevel.clear();
   h->prof = true;
-  const int st = emit_cycle(h, b, kappa, false, false, with_norm != 0, nullptr, s);
+  int st;
+  if (fp32) {  // the FP32 cycle of the mixed path: d = B32 r from zero on the handle's FP32 arrays
+    BindingT<float> b32{h->lv[0].v32, h->lv[0].f32, h->n};
+    st = emit_cycle(h, b32, kappa, true, false, false, nullptr, s);
+  } else {
+    st = emit_cycle(h, b, kappa, false, false, (with_norm & 1) != 0, nullptr, s);
+  }
   h->prof = false;
   int result = st;
   if (st >= 0) {

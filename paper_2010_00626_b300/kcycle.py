@@ -44,6 +44,7 @@ SIGNATURES = {
     "mg_kcycle_adjoint": (_i, [_h, _p, _p, _i]),
     "mg_solve": (_i, [_h, _p, _p, _i, _d, _i, _ip, _dp, _dp]),
     "mg_solve_host": (_i, [_h, _p, _p, _i, _d, _i, _ip, _dp, _dp]),
+    "mg_solve_adjoint": (_i, [_h, _p, _p, _i, _d, _i, _ip, _dp, _dp]),
     "mg_pcg": (_i, [_h, _p, _p, _i, _d, _i, _i, _ip, _dp, _dp]),
     "mg_apply": (_i, [_h, _p, _p]),
     "mg_residual_norm": (_i, [_h, _p, _p, _dp]),
@@ -148,12 +149,13 @@ class Multigrid:
         self._stream()
         _check(_lib.mg_kcycle_adjoint(self._h, _dev(v, self.n), _dev(f, self.n), int(kappa)), "mg_kcycle_adjoint")
 
-    def solve(self, v, f, kappa, tol, max_cycles, history=True):
-        """Returns (status, cycles, final_relres, history list)."""
+    def solve(self, v, f, kappa, tol, max_cycles, history=True, adjoint=False):
+        """Returns (status, cycles, final_relres, history list); adjoint iterates the adjoint cycle."""
         self._stream()
         cyc, rel = _i(), _d()
         hist = np.zeros(max_cycles) if history else None
-        st = _check(_lib.mg_solve(self._h, _dev(v, self.n), _dev(f, self.n), int(kappa), float(tol), int(max_cycles),
+        fn = _lib.mg_solve_adjoint if adjoint else _lib.mg_solve
+        st = _check(fn(self._h, _dev(v, self.n), _dev(f, self.n), int(kappa), float(tol), int(max_cycles),
                                   ctypes.byref(cyc), ctypes.byref(rel),
                                   hist.ctypes.data_as(_dp) if history else None), "mg_solve")
         return st, cyc.value, rel.value, (list(hist[:cyc.value]) if history else None)
@@ -214,14 +216,16 @@ class Multigrid:
         _check(_lib.mg_stencils(self._h, out.ctypes.data_as(_dp), self.levels, ctypes.byref(w)), "mg_stencils")
         return out[: w.value * 9].reshape(w.value, 3, 3)
 
-    def profile_cycle(self, v, f, kappa, with_norm=False, max_records=8192):
-        """Per-launch (ms, kind, level) of one cycle run launch by launch with CUDA events."""
+    def profile_cycle(self, v, f, kappa, with_norm=False, max_records=8192, fp32=False):
+        """Per-launch (ms, kind, level) of one cycle run launch by launch with CUDA events
+        (fp32: the FP32 cycle of the mixed solve)."""
         self._stream()
+        with_norm = int(bool(with_norm)) | (2 if fp32 else 0)
         ms = np.zeros(max_records)
         kind = np.zeros(max_records, dtype=np.int32)
         level = np.zeros(max_records, dtype=np.int32)
         cnt = _i()
-        _check(_lib.mg_profile_cycle(self._h, _dev(v, self.n), _dev(f, self.n), int(kappa), int(bool(with_norm)),
+        _check(_lib.mg_profile_cycle(self._h, _dev(v, self.n), _dev(f, self.n), int(kappa), with_norm,
                                      max_records, ms.ctypes.data_as(_dp), kind.ctypes.data_as(_ip),
                                      level.ctypes.data_as(_ip), ctypes.byref(cnt)), "mg_profile_cycle")
         k = min(cnt.value, max_records)
