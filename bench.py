@@ -322,6 +322,68 @@ def main():
             per_kappa_mixed[kname(k)] = {"ms": round(ms_k, 3), "iterations": it_k,
                                          "ms_per_iteration": round(ms_k / it_k, 4), "relres": rel_k, "status": st_k}
 
+    # ---------------------------------------------------------------- run-time model (Section 3) and kappa pre-selection
+    model_report = None
+    if not args.no_sweep and world == 1:
+        from paper_2010_00626_b300 import fit_model, model
+        samples = fit_model.measure(max_levels=12, reps=2)
+        fitted = fit_model.fit(samples)
+        bf = fitted["b300_form"]
+        params = (bf["alpha_fine_launch_ms"], bf["alpha_coarse_call_ms"], bf["beta_ms"])
+        lc = next(l for l in range(levels) if (n + 1) // (2 ** l) - 1 <= mg.get_option(kcycle.MG_OPT_COARSE_N))
+        pred_cycle, rho = {}, {}
+        for k in (1, 2, 3, 4, 5, KAPPA_W):
+            kk = model.W_COUNTER if k == KAPPA_W else k
+            pred_cycle[kname(k)] = model.predict_b300(params, kk, levels, lc, n)
+            v.zero_()
+            _, _, _, hist10 = mg.solve(v, f, k, 1e-300, 10)
+            rho[kname(k)] = model.contraction(hist10)
+        best_pred, table = model.preselect_kappa(pred_cycle, rho, tol)
+        measured = {k: d["ms"] for k, d in per_kappa.items()}
+        model_report = {"fit": {"paper_alpha_ms": fitted["paper_form"]["alpha_ms"],
+                                "paper_beta_ms": fitted["paper_form"]["beta_ms"],
+                                "turning_point_levels": fitted["paper_form"]["turning_point_levels"],
+                                "alpha_fine_launch_ms": params[0], "alpha_coarse_call_ms": params[1],
+                                "beta_ms": params[2]},
+                        "predicted_ms_per_cycle": {k: round(t, 4) for k, t in pred_cycle.items()},
+                        "rho_first_10_cycles": {k: round(r, 5) for k, r in rho.items()},
+                        "predicted_ms_to_tol": {k: round(t, 1) for k, t in table.items()},
+                        "predicted_best_kappa": best_pred,
+                        "measured_best_kappa": min(measured, key=measured.get) if measured else None}
+
+    # ---------------------------------------------------------------- batched (256 ragged instances, one launch each)
+    batched = None
+    if not args.no_sweep and world == 1:
+        from paper_2010_00626_b300.inputs import batched_instances, rhs_uniform
+        inst = batched_instances(count=256, seed=0)
+        ns = [d["n"] for d in inst]
+        fs_b = [torch.tensor(rhs_uniform(d["n"], d["seed"]), device="cuda") for d in inst]
+        xs_b = [torch.zeros_like(fb) for fb in fs_b]
+        batched = {"workload": "256 instances, n uniform over {127,255,511,1023}, theta~U[0,pi), "
+                               "log10 eps~U[-5,-1], f~U(-1,1), kappa=3, tol 1e-8, cap 3000 iterations",
+                   "dof": int(sum(n * n for n in ns))}
+        for mixed in (True, False):
+            bt = kcycle.Batch(ns, [d["eps"] for d in inst], [d["theta"] for d in inst])
+            chosen = bt.autotune(3, mixed=mixed)
+            for xb in xs_b:
+                xb.zero_()
+            bt.solve(xs_b, fs_b, 3, tol, 1)  # builds the graph
+            for xb in xs_b:
+                xb.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st_b, it_b, rel_b = bt.solve(xs_b, fs_b, 3, tol, 3000, mixed=mixed)
+            ms_b = 1e3 * (time.perf_counter() - t0)
+            conv = [i for i in range(len(ns)) if rel_b[i] <= tol]
+            q = sorted(it_b)
+            batched["mixed" if mixed else "fp64"] = {
+                "ms_one_launch": round(ms_b, 1), "converged": len(conv), "of": len(ns),
+                "iterations_quartiles": [q[0], q[len(q) // 4], q[len(q) // 2], q[3 * len(q) // 4], q[-1]],
+                "autotuned_coarse_n": {str(k): v for k, v in chosen.items()}}
+            bt.close()
+        batched["note"] = ("instances that miss tol are near-grid-aligned with small eps, where damped point "
+                           "Jacobi does not smooth (Section 4 uses line relaxation there)")
+
     # ---------------------------------------------------------------- oracle on the host cores
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -344,7 +406,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roofline, "cycle_share": cycle_share, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clocks.summary(), "per_kappa": per_kappa,
-                "per_kappa_mixed": per_kappa_mixed}
+                "per_kappa_mixed": per_kappa_mixed, "batched": batched, "model": model_report}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

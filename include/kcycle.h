@@ -57,7 +57,8 @@ typedef enum {
                               15, 31, 63                                                          */
   MG_OPT_LEVELS = 3,       /* read-only: number of levels                                          */
   MG_OPT_N = 4,            /* read-only: finest grid side                                          */
-  MG_OPT_LAUNCHES = 5      /* read-only: kernel launches in the last cycle graph built              */
+  MG_OPT_LAUNCHES = 5,     /* read-only: kernel launches in the last cycle graph built              */
+  MG_OPT_COARSE_N32 = 6    /* as MG_OPT_COARSE_N for the FP32 cycles of the mixed forms; default 63  */
 } mg_option;
 
 /* Set up the hierarchy for the Section 4 problem on an n x n interior grid.
@@ -140,6 +141,14 @@ int mg_solve_mixed(mg_handle h, double* x, const double* f, int kappa, double to
  * in FP64): v, f device float arrays, n*n, row-major. Asynchronous. */
 int mg_kcycle_f32(mg_handle h, float* v, const float* f, int kappa);
 
+/* MGCG with a mixed-precision preconditioner (an extension of the paper's FP64 method): the PCG
+ * vectors, A p, the inner products and alpha/beta are FP64; each preconditioner application rounds
+ * r to FP32, runs one FP32 kappa-cycle from zero (coarsest solve FP64) and widens z back to FP64.
+ * Same arguments and behaviour as mg_pcg; the flexible beta (flexible != 0) suits this inexact
+ * preconditioner. Allocates the FP32 level arrays on first use. Synchronises. */
+int mg_pcg_mixed(mg_handle h, double* x, const double* b, int kappa, double tol, int max_iters,
+                 int flexible, int* iters, double* final_relres, double* history);
+
 /* out = A v on the finest level (device pointers, n*n each). Asynchronous. */
 int mg_apply(mg_handle h, const double* v, double* out);
 
@@ -193,6 +202,35 @@ int mg_profile_cycle(mg_handle h, double* v, const double* f, int kappa, int wit
  * threads) race and must be serialised by the caller. Synchronises the stream. */
 int mg_residual_norm_noalloc(int n, double eps, double theta, const double* v, const double* f,
                              void* cuda_stream, double* norm);
+
+/* Batched solves (an extension beyond the paper): many independent problems -- each with its own
+ * grid side n_i, anisotropy eps_i and angle theta_i, so a ragged set of level hierarchies -- solved
+ * by ONE CUDA-graph launch. The graph holds one branch per instance (its initialisation, then a
+ * WHILE conditional node repeating {cycle, stopping test}); the branches are independent, so the
+ * GPU runs the instances' kernels concurrently. */
+typedef struct mg_batch_ctx* mg_batch;
+
+/* Create `count` instances: n[i], eps[i], theta[i] as for mg_setup, levels[i] (NULL: all levels down
+ * to 1x1), shared nu1, nu2. *out owns every hierarchy; release with mg_batch_destroy. */
+int mg_batch_create(int count, const int* n, const double* eps, const double* theta, const int* levels,
+                    int nu1, int nu2, mg_batch* out);
+
+/* Autotuner: for each distinct grid side in the batch, time kappa-cycles of one instance with the
+ * candidate coarse-kernel thresholds (FP64: 7, 15, 31; FP32 when mixed != 0: 15, 31, 63) and apply
+ * the fastest to every instance of that side. chosen (host, nullable, 2 ints per distinct side):
+ * pairs (n, threshold). Allocates and frees temporary arrays. Synchronises. */
+int mg_batch_autotune(mg_batch b, int kappa, int mixed, int* chosen);
+
+/* Solve every instance to ||f_i - A_i x_i|| / ||f_i|| <= tol from the initial guesses x_i, with
+ * FP64 kappa-cycles (mixed == 0, as mg_solve) or FP32 kappa-cycles inside FP64 iterative refinement
+ * (mixed != 0, as mg_solve_mixed). x, f: host arrays of `count` device pointers (n_i*n_i doubles
+ * each). iters, relres: host, nullable, `count` entries. One graph launch; synchronises. Returns
+ * MG_OK when every instance converged, MG_NOT_CONVERGED otherwise. */
+int mg_batch_solve(mg_batch b, double* const* x, const double* const* f, int kappa, double tol,
+                   int max_iters, int mixed, int* iters, double* relres);
+
+int mg_batch_size(mg_batch b, int* count);
+int mg_batch_destroy(mg_batch b);
 
 /* Static string for a status code. */
 const char* mg_status_string(int status);

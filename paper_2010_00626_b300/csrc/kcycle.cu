@@ -50,7 +50,7 @@ constexpr int NT_SMALL = 256;
 constexpr int NT_TINY = 128;
 constexpr int NT_BIG = 512;
 constexpr int NT_COARSE = 256;     // coarse kernel, FP64 (bound by the SM's FP64 pipe)
-constexpr int NT_COARSE32 = 512;   // coarse kernel, FP32 (more independent points per phase)
+constexpr int NT_COARSE32 = 256;   // coarse kernel, FP32
 template <typename T>
 constexpr int nt_coarse() { return std::is_same<T, double>::value ? NT_COARSE : NT_COARSE32; }
 constexpr int NT_VEC = 256;
@@ -99,8 +99,9 @@ struct mg_ctx {
   double eps = 0, theta = 0, omega = 0.8;
   int coarse_n = 15;  // largest side handled by the coarse kernel (FP64 cycles)
   int lc = 0;         // first level handled by the coarse kernel (FP64 cycles)
-  int lc32 = 0;       // same for the FP32 cycles of the mixed path: sides <= 63 (one SM does
-                      // FP32 at 64x the FP64 rate, so the single-CTA kernel takes more levels)
+  int lc32 = 0;       // same for the FP32 cycles of the mixed path
+  int coarse_n32 = 63;  // FP32 threshold: one SM does FP32 at 64x the FP64 rate, so the single-CTA
+                        // kernel takes more levels
   Level lv[MAXL];
   double* coef = nullptr;
   float* coef32 = nullptr;
@@ -545,6 +546,63 @@ int read_result(mg_ctx* h, cudaStream_t s, double tol, int* count_out, double* f
   return scal[S_LAST] <= tol ? MG_OK : MG_NOT_CONVERGED;
 }
 
+// Add to `parent` one instance's whole solve: a child graph with its initialisation (||f||^2,
+// reset of the device state, and for the mixed form the first FP64 residual), then a WHILE
+// conditional node repeating {cycle, [x += d, r = f - A x,] stopping test}.
+int add_solve_branch(mg_ctx* h, cudaGraph_t parent, double* x, const double* f, int kappa, double tol, int max_iters,
+                     bool mixed) {
+  const int n = h->n;
+  const size_t len = (size_t)n * n;
+  float* d = h->lv[0].v32;
+  float* r32 = h->lv[0].f32;
+  const int napply = (int)apply_grid_blocks(n);
+  dim3 agrid((n + 31) / 32, (n + NT_VEC / 32 - 1) / (NT_VEC / 32));
+  cudaGraph_t init;
+  KC_CUDA(cudaStreamBeginCapture(h->own, cudaStreamCaptureModeThreadLocal));
+  int st = launch_norm2(h, f, h->scal + S_FNORM2, h->own);
+  reset_state_kernel<<<1, 1, 0, h->own>>>(h->ints, max_iters, h->scal, tol);
+  if (mixed) ir_residual_kernel<NT_VEC><<<agrid, NT_VEC, 0, h->own>>>(x, f, r32, h->coef, n, h->partial, nullptr);
+  const cudaError_t le = cudaGetLastError();
+  const cudaError_t ce = cudaStreamEndCapture(h->own, &init);
+  if (st < 0) return st;
+  KC_CUDA(le);
+  KC_CUDA(ce);
+  cudaGraphNode_t init_node;
+  const cudaError_t ae = cudaGraphAddChildGraphNode(&init_node, parent, nullptr, 0, init);
+  cudaGraphDestroy(init);  // the child node holds its own copy
+  KC_CUDA(ae);
+  cudaGraphConditionalHandle ch;
+  KC_CUDA(cudaGraphConditionalHandleCreate(&ch, parent, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+  np.conditional.handle = ch;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  KC_CUDA(cudaGraphAddNode(&node, parent, &init_node, nullptr, 1, &np));
+  KC_CUDA(cudaStreamBeginCaptureToGraph(h->own, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal));
+  const int* done = h->ints + I_DONE;
+  if (mixed) {
+    BindingT<float> b{d, r32, n};
+    st = emit_cycle(h, b, kappa, true, false, false, done, h->own);
+    ir_add_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, h->own>>>(x, d, len, done);
+    ir_residual_kernel<NT_VEC><<<agrid, NT_VEC, 0, h->own>>>(x, f, r32, h->coef, n, h->partial, done);
+    finish_step_kernel<NT_VEC><<<1, NT_VEC, 0, h->own>>>(h->partial, napply, h->scal, h->ints, h->hist, ch, 1);
+  } else {
+    Binding b{x, f, n};
+    st = emit_cycle(h, b, kappa, false, false, true, done, h->own);
+    finish_step_kernel<NT_VEC><<<1, NT_VEC, 0, h->own>>>(h->partial, norm_partials(h), h->scal, h->ints, h->hist,
+                                                         ch, 1);
+  }
+  const cudaError_t le2 = cudaGetLastError();
+  cudaGraph_t captured;
+  const cudaError_t ce2 = cudaStreamEndCapture(h->own, &captured);
+  if (st < 0) return st;
+  KC_CUDA(le2);
+  KC_CUDA(ce2);
+  return MG_OK;
+}
+
 int solve_impl(mg_handle h, double* v, const double* f, int kappa, double tol, int max_cycles, int* cycles,
                double* final_relres, double* history, bool adjoint = false) {
   if (!valid_handle(h)) return MG_ERR_STATE;
@@ -602,7 +660,7 @@ int ensure_levels32(mg_ctx* h) {
   if (h->have32) return MG_OK;
   h->lc32 = h->levels - 1;
   for (int l = 0; l < h->levels; ++l)
-    if (h->lv[l].n <= MAX_COARSE_N) {
+    if (h->lv[l].n <= h->coarse_n32) {
       h->lc32 = l;
       break;
     }
@@ -752,13 +810,14 @@ int mg_set_option(mg_handle h, int key, double value) {
       drop_graphs(h);
       return run_setup_kernels(h);
     }
-    case MG_OPT_COARSE_N: {
+    case MG_OPT_COARSE_N:
+    case MG_OPT_COARSE_N32: {
       const int c = (int)value;
       if (value != (double)c || !(c == 1 || c == 3 || c == 7 || c == 15 || c == 31 || c == 63)) return MG_ERR_ARG;
       KC_CUDA(cudaStreamSynchronize(h->stream()));
       drop_graphs(h);
       KC_TRY(free_levels(h));
-      h->coarse_n = c;
+      if (key == MG_OPT_COARSE_N) h->coarse_n = c; else h->coarse_n32 = c;
       KC_TRY(alloc_levels(h));
       KC_CUDA(cudaStreamSynchronize(h->own));
       return MG_OK;
@@ -773,6 +832,7 @@ int mg_get_option(mg_handle h, int key, double* value) {
   switch (key) {
     case MG_OPT_OMEGA: *value = h->omega; return MG_OK;
     case MG_OPT_COARSE_N: *value = h->coarse_n; return MG_OK;
+    case MG_OPT_COARSE_N32: *value = h->coarse_n32; return MG_OK;
     case MG_OPT_LEVELS: *value = h->levels; return MG_OK;
     case MG_OPT_N: *value = h->n; return MG_OK;
     case MG_OPT_LAUNCHES: *value = h->last_launches; return MG_OK;
@@ -830,8 +890,8 @@ int mg_solve_host(mg_handle h, double* v, const double* f, int kappa, double tol
   return st;
 }
 
-int mg_pcg(mg_handle h, double* x, const double* b, int kappa, double tol, int max_iters, int flexible, int* iters,
-           double* final_relres, double* history) {
+static int pcg_impl(mg_handle h, double* x, const double* b, int kappa, double tol, int max_iters, int flexible,
+                    bool mixed, int* iters, double* final_relres, double* history) {
   if (!valid_handle(h)) return MG_ERR_STATE;
   if (!x || !b || kappa < 1 || !(tol > 0) || max_iters < 1) return MG_ERR_ARG;
   trim_graphs(h);
@@ -839,17 +899,31 @@ int mg_pcg(mg_handle h, double* x, const double* b, int kappa, double tol, int m
   double** vecs[] = {&h->pr, &h->pp, &h->pq, &h->pz, &h->pzold};
   for (double** p : vecs)
     if (!*p) KC_CUDA(cudaMalloc(p, bytes));
+  if (mixed) KC_TRY(ensure_levels32(h));
   KC_TRY(ensure_hist(h, max_iters));
   cudaStream_t s = h->stream();
   const int* done = h->ints + I_DONE;
-  GraphEntry* zc;  // z = B r from a zero start, as its own cached cycle graph
-  KC_TRY(get_cycle_graph(h, h->pz, h->pr, kappa, 1, &zc));
-  const int fl = flexible ? 1 : 0;
+  float* r32 = h->lv[0].f32;
+  float* z32 = h->lv[0].v32;
+  // z = B r from a zero start: FP64 cycle, or r -> FP32, FP32 cycle, z <- FP64
+  auto emit_precond = [&](cudaStream_t o, const int* skip) -> int {
+    if (!mixed) {
+      Binding bz{h->pz, h->pr, h->n};
+      return emit_cycle(h, bz, kappa, true, false, false, skip, o);
+    }
+    convert_kernel<NT_VEC, double, float><<<VEC_BLOCKS, NT_VEC, 0, o>>>(r32, h->pr, len, skip);
+    BindingT<float> b32{z32, r32, h->n};
+    KC_TRY(emit_cycle(h, b32, kappa, true, false, false, skip, o));
+    convert_kernel<NT_VEC, float, double><<<VEC_BLOCKS, NT_VEC, 0, o>>>(h->pz, z32, len, skip);
+    KC_CUDA(cudaGetLastError());
+    h->launch_count += 2;
+    return MG_OK;
+  };
+  const int fl = (flexible ? 1 : 0) | (mixed ? 2 : 0);
   GraphEntry* ge = find_graph(h, G_PCG, kappa, fl, x, b);
   if (!ge) {
     GraphEntry e;
     e.kind = G_PCG; e.kappa = kappa; e.flag = fl; e.p0 = x; e.p1 = b;
-    Binding bz{h->pz, h->pr, h->n};
     const int napply = (int)apply_grid_blocks(h->n);
     KC_TRY(build_while_graph(h, [&](cudaGraphConditionalHandle ch) -> int {
       cudaStream_t o = h->own;
@@ -861,11 +935,11 @@ int mg_pcg(mg_handle h, double* x, const double* b, int kappa, double tol, int m
                                                              h->ints);
       finish_step_kernel<NT_VEC><<<1, NT_VEC, 0, o>>>(h->partial, VEC_BLOCKS, h->scal, h->ints, h->hist, ch, 1);
       KC_CUDA(cudaGetLastError());
-      KC_TRY(emit_cycle(h, bz, kappa, true, false, false, done, o));
-      dot_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, o>>>(h->pr, h->pz, fl ? h->pzold : nullptr, len, h->partial,
+      KC_TRY(emit_precond(o, done));
+      dot_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, o>>>(h->pr, h->pz, (fl & 1) ? h->pzold : nullptr, len, h->partial,
                                                        h->partial2, done);
-      pcg_beta_kernel<NT_VEC><<<1, NT_VEC, 0, o>>>(h->partial, h->partial2, VEC_BLOCKS, fl, h->scal, h->ints);
-      pcg_p_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, o>>>(h->pp, h->pz, fl ? h->pzold : nullptr, len, h->scal, 1,
+      pcg_beta_kernel<NT_VEC><<<1, NT_VEC, 0, o>>>(h->partial, h->partial2, VEC_BLOCKS, fl & 1, h->scal, h->ints);
+      pcg_p_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, o>>>(h->pp, h->pz, (fl & 1) ? h->pzold : nullptr, len, h->scal, 1,
                                                          h->ints);
       KC_CUDA(cudaGetLastError());
       h->launch_count += 7;
@@ -880,14 +954,24 @@ int mg_pcg(mg_handle h, double* x, const double* b, int kappa, double tol, int m
   KC_TRY(launch_norm2(h, b, h->scal + S_FNORM2, s));
   reset_state_kernel<<<1, 1, 0, s>>>(h->ints, max_iters, h->scal, tol);
   KC_CUDA(cudaGetLastError());
-  KC_CUDA(cudaGraphLaunch(zc->exec, s));
-  pcg_p_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, s>>>(h->pp, h->pz, fl ? h->pzold : nullptr, len, h->scal, 0,
+  KC_TRY(emit_precond(s, nullptr));
+  pcg_p_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, s>>>(h->pp, h->pz, (fl & 1) ? h->pzold : nullptr, len, h->scal, 0,
                                                      h->ints);
   dot_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, s>>>(h->pr, h->pz, nullptr, len, h->partial, nullptr, nullptr);
   sum_to_scalar_kernel<NT_VEC><<<1, NT_VEC, 0, s>>>(h->partial, VEC_BLOCKS, h->scal + S_RZ);
   KC_CUDA(cudaGetLastError());
   KC_CUDA(cudaGraphLaunch(ge->exec, s));
   return read_result(h, s, tol, iters, final_relres, history);
+}
+
+int mg_pcg(mg_handle h, double* x, const double* b, int kappa, double tol, int max_iters, int flexible, int* iters,
+           double* final_relres, double* history) {
+  return pcg_impl(h, x, b, kappa, tol, max_iters, flexible, false, iters, final_relres, history);
+}
+
+int mg_pcg_mixed(mg_handle h, double* x, const double* b, int kappa, double tol, int max_iters, int flexible,
+                 int* iters, double* final_relres, double* history) {
+  return pcg_impl(h, x, b, kappa, tol, max_iters, flexible, true, iters, final_relres, history);
 }
 
 int mg_kcycle_f32(mg_handle h, float* v, const float* f, int kappa) {
@@ -1084,6 +1168,190 @@ int mg_profile_cycle(mg_handle h, double* v, const double* f, int kappa, int wit
   for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
   h->pev.clear();
   return result;
+}
+
+}  // extern "C"
+
+// ============================================================================================
+// Batched solves: many independent instances (ragged sizes, own theta and eps) in one graph
+// launch, one branch per instance.
+// ============================================================================================
+struct mg_batch_ctx {
+  std::vector<mg_handle> inst;
+  cudaStream_t stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> key;  // pointers, kappa, tol, max_iters, mixed of the cached graph
+};
+
+namespace {
+void batch_drop_graph(mg_batch_ctx* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  b->key.clear();
+}
+
+// Time `reps` kappa-cycles of handle h in the given precision (ms per cycle) on scratch arrays.
+int time_cycles(mg_handle h, bool mixed, int kappa, int reps, double* v64, double* f64, float* v32, float* f32,
+                float* ms_out) {
+  cudaEvent_t e0, e1;
+  KC_CUDA(cudaEventCreate(&e0));
+  KC_CUDA(cudaEventCreate(&e1));
+  auto one = [&]() -> int { return mixed ? mg_kcycle_f32(h, v32, f32, kappa) : mg_kcycle(h, v64, f64, kappa); };
+  KC_TRY(one());
+  KC_CUDA(cudaEventRecord(e0, h->stream()));
+  for (int r = 0; r < reps; ++r) KC_TRY(one());
+  KC_CUDA(cudaEventRecord(e1, h->stream()));
+  KC_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  KC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_out = ms / reps;
+  return MG_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int mg_batch_destroy(mg_batch b) {
+  if (!b) return MG_OK;
+  batch_drop_graph(b);
+  for (mg_handle h : b->inst) mg_destroy(h);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return MG_OK;
+}
+
+int mg_batch_create(int count, const int* n, const double* eps, const double* theta, const int* levels, int nu1,
+                    int nu2, mg_batch* out) {
+  if (!out || count < 1 || !n || !eps || !theta) return MG_ERR_ARG;
+  *out = nullptr;
+  mg_batch_ctx* b = new (std::nothrow) mg_batch_ctx();
+  if (!b) return MG_ERR_NOMEM;
+  for (int i = 0; i < count; ++i) {
+    int k = 0;
+    while (k < 15 && ((1 << k) - 1) < n[i]) ++k;
+    mg_handle h = nullptr;
+    const int st = mg_setup(n[i], eps[i], theta[i], levels ? levels[i] : k, nu1, nu2, &h);
+    if (st < 0) {
+      mg_batch_destroy(b);
+      return st;
+    }
+    b->inst.push_back(h);
+  }
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    mg_batch_destroy(b);
+    return MG_ERR_CUDA;
+  }
+  *out = b;
+  return MG_OK;
+}
+
+int mg_batch_autotune(mg_batch b, int kappa, int mixed, int* chosen) {
+  if (!b || kappa < 1) return MG_ERR_ARG;
+  // one representative per grid side; candidates for the coarse-kernel threshold
+  std::vector<int> sizes;
+  for (mg_handle h : b->inst)
+    if (std::find(sizes.begin(), sizes.end(), h->n) == sizes.end()) sizes.push_back(h->n);
+  const int cand64[] = {7, 15, 31};
+  const int cand32[] = {15, 31, 63};
+  int pos = 0;
+  for (int n : sizes) {
+    mg_handle rep = nullptr;
+    for (mg_handle h : b->inst)
+      if (h->n == n) { rep = h; break; }
+    const size_t len = (size_t)n * n;
+    double *v64 = nullptr, *f64 = nullptr;
+    float *v32 = nullptr, *f32 = nullptr;
+    KC_CUDA(cudaMalloc(&v64, len * 8));
+    KC_CUDA(cudaMalloc(&f64, len * 8));
+    KC_CUDA(cudaMalloc(&v32, len * 4));
+    KC_CUDA(cudaMalloc(&f32, len * 4));
+    KC_CUDA(cudaMemset(v64, 0, len * 8));
+    KC_CUDA(cudaMemset(f64, 0, len * 8));
+    KC_CUDA(cudaMemset(v32, 0, len * 4));
+    KC_CUDA(cudaMemset(f32, 0, len * 4));
+    const int key = mixed ? MG_OPT_COARSE_N32 : MG_OPT_COARSE_N;
+    int best = -1;
+    float best_ms = 1e30f;
+    for (int c : (mixed ? cand32 : cand64)) {
+      if (mg_set_option(rep, key, c) < 0) continue;
+      float ms;
+      if (time_cycles(rep, mixed != 0, kappa, 3, v64, f64, v32, f32, &ms) < 0) continue;
+      if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+    cudaFree(v64); cudaFree(f64); cudaFree(v32); cudaFree(f32);
+    if (best < 0) return MG_ERR_CUDA;
+    for (mg_handle h : b->inst)
+      if (h->n == n) KC_TRY(mg_set_option(h, key, best));
+    if (chosen) { chosen[2 * pos] = n; chosen[2 * pos + 1] = best; }
+    ++pos;
+  }
+  batch_drop_graph(b);
+  return MG_OK;
+}
+
+int mg_batch_solve(mg_batch b, double* const* x, const double* const* f, int kappa, double tol, int max_iters,
+                   int mixed, int* iters, double* relres) {
+  if (!b || !x || !f || kappa < 1 || !(tol > 0) || max_iters < 1) return MG_ERR_ARG;
+  const size_t cnt = b->inst.size();
+  std::vector<const void*> key;
+  for (size_t i = 0; i < cnt; ++i) {
+    if (!x[i] || !f[i]) return MG_ERR_ARG;
+    key.push_back(x[i]);
+    key.push_back(f[i]);
+  }
+  key.push_back((const void*)(intptr_t)kappa);
+  key.push_back((const void*)(intptr_t)max_iters);
+  key.push_back((const void*)(intptr_t)mixed);
+  double tl = tol;
+  const void* tk;
+  memcpy(&tk, &tl, sizeof(tk));
+  key.push_back(tk);
+  if (!b->exec || key != b->key) {
+    batch_drop_graph(b);
+    for (mg_handle h : b->inst) {
+      KC_TRY(ensure_hist(h, max_iters));
+      if (mixed) KC_TRY(ensure_levels32(h));
+    }
+    KC_CUDA(cudaGraphCreate(&b->graph, 0));
+    for (size_t i = 0; i < cnt; ++i) {
+      const int st = add_solve_branch(b->inst[i], b->graph, x[i], f[i], kappa, tol, max_iters, mixed != 0);
+      if (st < 0) {
+        batch_drop_graph(b);
+        return st;
+      }
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (ie != cudaSuccess) {
+      batch_drop_graph(b);
+      KC_CUDA(ie);
+    }
+    b->key = key;
+  }
+  KC_CUDA(cudaGraphLaunch(b->exec, b->stream));
+  KC_CUDA(cudaStreamSynchronize(b->stream));
+  int worst = MG_OK;
+  for (size_t i = 0; i < cnt; ++i) {
+    mg_handle h = b->inst[i];
+    int ints[NINT];
+    double scal[NSCAL];
+    KC_CUDA(cudaMemcpy(ints, h->ints, sizeof(ints), cudaMemcpyDeviceToHost));
+    KC_CUDA(cudaMemcpy(scal, h->scal, sizeof(scal), cudaMemcpyDeviceToHost));
+    if (iters) iters[i] = ints[I_COUNT];
+    if (relres) relres[i] = scal[S_LAST];
+    if (!(scal[S_LAST] <= tol)) worst = MG_NOT_CONVERGED;
+  }
+  return worst;
+}
+
+int mg_batch_size(mg_batch b, int* count) {
+  if (!b || !count) return MG_ERR_ARG;
+  *count = (int)b->inst.size();
+  return MG_OK;
 }
 
 }  // extern "C"

@@ -127,49 +127,6 @@ __device__ __forceinline__ bool inside(int gx, int gy, int n) {
   return (unsigned)gx < (unsigned)n && (unsigned)gy < (unsigned)n;
 }
 
-// One pass of a nine-point operation over the region [lx0, lx0+Rw) x [ly0, ly0+Rh) of a
-// shared-memory tile with row stride W. Each thread owns one column of the region and a run of
-// consecutive rows, sliding a 3x3 window down the run, so every point costs three shared loads of
-// src (the new row) and one of f instead of nine. Lanes take consecutive columns (no bank
-// conflicts); the run length is chosen so the whole region is one round of the CTA's threads.
-// op(nb, fv, gx, gy) returns the new value (points outside [0,n)^2 get 0).
-template <int NT, typename T, typename Op>
-__device__ __forceinline__ void sweep_columns(const T* __restrict__ src, T* __restrict__ dst, const T* __restrict__ fs,
-                                              int W, int lx0, int ly0, int Rw, int Rh, int gx0, int gy0, int n,
-                                              Op op) {
-  const int per_col = max(1, NT / Rw);            // row runs per column
-  const int run = (Rh + per_col - 1) / per_col;   // rows per run
-  const int items = Rw * ((Rh + run - 1) / run);
-  for (int it = threadIdx.x; it < items; it += NT) {
-    const int cx = it % Rw, seg = it / Rw;
-    const int x = lx0 + cx;
-    const int y_begin = ly0 + seg * run;
-    const int y_end = min(y_begin + run, ly0 + Rh);
-    const int gx = gx0 + x;
-    const bool col_in = (unsigned)gx < (unsigned)n;
-    int k = (y_begin - 1) * W + x;
-    T u0 = src[k - 1], u1 = src[k], u2 = src[k + 1];  // row y-1
-    k += W;
-    T m0 = src[k - 1], m1 = src[k], m2 = src[k + 1];  // row y
-#pragma unroll 2
-    for (int y = y_begin; y < y_end; ++y) {
-      const int kn = k + W;
-      const T a = src[kn - 1], b = src[kn], c = src[kn + 1];  // row y+1 (north)
-      Nb<T> nb;
-      nb.c = m1;
-      nb.we = m0 + m2;
-      nb.ns = u1 + b;
-      nb.d1 = a + u2;  // NW + SE
-      nb.d2 = c + u0;  // NE + SW
-      const bool in = col_in && (unsigned)(gy0 + y) < (unsigned)n;
-      dst[k] = in ? op(nb, fs[k]) : T(0);
-      u0 = m0; u1 = m1; u2 = m2;
-      m0 = a; m1 = b; m2 = c;
-      k = kn;
-    }
-  }
-}
-
 // Deterministic block sum of one double per thread (fixed order); result valid in thread 0.
 // Callers that use `red` again must __syncthreads() first.
 template <int NT>
@@ -233,11 +190,13 @@ __global__ void __launch_bounds__(NT) pass_a_kernel(const PassAArgs<T> a) {
 
   T* src = s0;
   T* dst = s1;
-  auto jac = [&](const Nb<T>& nb, T fv) { return jacobi_update(nb, fv, c); };
   for (int s = 1; s <= a.nu; ++s) {
     const int g = a.nu - s + 1;  // sweep s is needed on the tile grown by g
-    const int lo = H - g;
-    sweep_columns<NT>(src, dst, fs, W, lo, lo, BX + 2 * g + 1, BY + 2 * g + 1, gx0, gy0, n, jac);
+    const int lo = H - g, R = BX + 2 * g + 1, Ry = BY + 2 * g + 1;
+    for_region<NT>(R, Ry, [&](int rx, int ry) {
+      const int lx = lo + rx, ly = lo + ry, k = ly * W + lx;
+      dst[k] = inside(gx0 + lx, gy0 + ly, n) ? jacobi_update(neighbours(src, k, W), fs[k], c) : T(0);
+    });
     __syncthreads();
     T* t = src; src = dst; dst = t;
   }
@@ -248,8 +207,10 @@ __global__ void __launch_bounds__(NT) pass_a_kernel(const PassAArgs<T> a) {
     if (inside(gx, gy, n)) a.vout[(size_t)gy * a.ldvout + gx] = src[(ty + H) * W + tx + H];
   });
   // residual on the tile plus one column/row beyond it (full weighting reads it)
-  sweep_columns<NT>(src, dst, fs, W, H, H, BX + 1, BY + 1, gx0, gy0, n,
-                    [&](const Nb<T>& nb, T fv) { return residual_at(nb, fv, c); });
+  for_region<NT>(BX + 1, BY + 1, [&](int tx, int ty) {
+    const int lx = H + tx, ly = H + ty, k = ly * W + lx;
+    dst[k] = inside(gx0 + lx, gy0 + ly, n) ? residual_at(neighbours(src, k, W), fs[k], c) : T(0);
+  });
   __syncthreads();
   // coarse point (I, J) sits on fine (2I+1, 2J+1); this tile owns I in [x0/2, x0/2 + BX/2)
   const int nc = (n - 1) / 2;
@@ -340,11 +301,13 @@ __global__ void __launch_bounds__(NT) pass_b_kernel(const PassBArgs<T> a) {
 
   T* src = s0;
   T* dst = s1;
-  auto jac = [&](const Nb<T>& nb, T fv) { return jacobi_update(nb, fv, c); };
   for (int s = 1; s <= a.nu; ++s) {
     const int g = a.nu - s + E;
-    const int lo = H - g;
-    sweep_columns<NT>(src, dst, fs, W, lo, lo, BX + 2 * g, BY + 2 * g, gx0, gy0, n, jac);
+    const int lo = H - g, R = BX + 2 * g, Ry = BY + 2 * g;
+    for_region<NT>(R, Ry, [&](int rx, int ry) {
+      const int lx = lo + rx, ly = lo + ry, k = ly * W + lx;
+      dst[k] = inside(gx0 + lx, gy0 + ly, n) ? jacobi_update(neighbours(src, k, W), fs[k], c) : T(0);
+    });
     __syncthreads();
     T* t = src; src = dst; dst = t;
   }
@@ -493,7 +456,6 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
       const T* src = vbuf(d, b);
       T* dst = vbuf(d, b ^ 1u);
       const bool from_zero = zero && it == 0;
-#pragma unroll 4
       for (int k = threadIdx.x; k < s * s; k += NT) {
         const int kk = pos(d, k);
         dst[kk] = from_zero ? c.w * f[kk] : jacobi_update_tree(neighbours(src, kk, P), f[kk], c);
@@ -508,7 +470,6 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
     const T* v = vcur(d);
     const T* f = fbuf(d);
     const Coef<T> c = cf[d];
-#pragma unroll 4
     for (int k = threadIdx.x; k < s * s; k += NT) {
       const int kk = pos(d, k);
       tmp[kk] = residual_at(neighbours(v, kk, P), f[kk], c);
@@ -516,7 +477,6 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
     __syncthreads();
     const int sc = g_side[d + 1];
     T* fc = fbuf(d + 1);
-#pragma unroll 4
     for (int k = threadIdx.x; k < sc * sc; k += NT) {
       const int J = (int)__umulhi((unsigned)k, (unsigned)g_magic[d + 1]), I = k - J * sc;
       // coarse (I, J) sits on fine (2I+1, 2J+1), padded position (2J+2, 2I+2)
@@ -529,7 +489,6 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
     const int s = g_side[d], Pc = g_side[d + 1] + 2;
     T* v = vcur(d);
     const T* vc = vcur(d + 1);
-#pragma unroll 4
     for (int k = threadIdx.x; k < s * s; k += NT) {
       const int j = (int)__umulhi((unsigned)k, (unsigned)g_magic[d]), i = k - j * s;
       const int hx = i >> 1, hy = j >> 1;
@@ -1072,6 +1031,13 @@ __global__ void __launch_bounds__(NT) ir_residual_kernel(const double* __restric
   }
   const double t = block_sum<NT>(ss, red);
   if (threadIdx.x == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+// y = (double) x or y = (float) x, pointwise (mixed-precision preconditioner hand-off)
+template <int NT, typename S, typename D>
+__global__ void __launch_bounds__(NT) convert_kernel(D* y, const S* x, size_t len, const int* skip) {
+  if (skip && *skip) return;
+  for (size_t k = blockIdx.x * (size_t)NT + threadIdx.x; k < len; k += (size_t)gridDim.x * NT) y[k] = (D)x[k];
 }
 
 __global__ void reset_state_kernel(int* ints, int max_iters, double* scal, double tol) {

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libkcycle.so")
 MG_OK, MG_NOT_CONVERGED = 0, 1
 MG_KAPPA_W = 0x7FFFFFFF
 CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
-MG_OPT_OMEGA, MG_OPT_COARSE_N, MG_OPT_LEVELS, MG_OPT_N, MG_OPT_LAUNCHES = 1, 2, 3, 4, 5
+MG_OPT_OMEGA, MG_OPT_COARSE_N, MG_OPT_LEVELS, MG_OPT_N, MG_OPT_LAUNCHES, MG_OPT_COARSE_N32 = 1, 2, 3, 4, 5, 6
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libkcycle.so is not built ({LIB_PATH}); run python -m paper_2010_00626_b300.build")
@@ -46,6 +46,7 @@ SIGNATURES = {
     "mg_solve_host": (_i, [_h, _p, _p, _i, _d, _i, _ip, _dp, _dp]),
     "mg_solve_adjoint": (_i, [_h, _p, _p, _i, _d, _i, _ip, _dp, _dp]),
     "mg_pcg": (_i, [_h, _p, _p, _i, _d, _i, _i, _ip, _dp, _dp]),
+    "mg_pcg_mixed": (_i, [_h, _p, _p, _i, _d, _i, _i, _ip, _dp, _dp]),
     "mg_apply": (_i, [_h, _p, _p]),
     "mg_residual_norm": (_i, [_h, _p, _p, _dp]),
     "mg_param_grads": (_i, [_h, _p, _p, _dp, _dp]),
@@ -55,6 +56,11 @@ SIGNATURES = {
     "mg_residual_norm_noalloc": (_i, [_i, _d, _d, _p, _p, _p, _dp]),
     "mg_solve_mixed": (_i, [_h, _p, _p, _i, _d, _i, _ip, _dp, _dp]),
     "mg_kcycle_f32": (_i, [_h, _p, _p, _i]),
+    "mg_batch_create": (_i, [_i, _ip, _dp, _dp, _ip, _i, _i, ctypes.POINTER(_h)]),
+    "mg_batch_autotune": (_i, [_h, _i, _i, _ip]),
+    "mg_batch_solve": (_i, [_h, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, _d, _i, _i, _ip, _dp]),
+    "mg_batch_size": (_i, [_h, _ip]),
+    "mg_batch_destroy": (_i, [_h]),
     "mg_status_string": (ctypes.c_char_p, [_i]),
     "mg_last_error": (ctypes.c_char_p, []),
 }
@@ -168,11 +174,13 @@ class Multigrid:
                     "mg_solve_host")
         return st, cyc.value, rel.value
 
-    def pcg(self, x, b, kappa, tol, max_iters, flexible=False, history=True):
+    def pcg(self, x, b, kappa, tol, max_iters, flexible=False, history=True, mixed=False):
+        """MGCG (mixed: FP32 preconditioner cycles). Returns (status, iters, relres, history)."""
         self._stream()
         it, rel = _i(), _d()
         hist = np.zeros(max_iters) if history else None
-        st = _check(_lib.mg_pcg(self._h, _dev(x, self.n), _dev(b, self.n), int(kappa), float(tol), int(max_iters),
+        fn = _lib.mg_pcg_mixed if mixed else _lib.mg_pcg
+        st = _check(fn(self._h, _dev(x, self.n), _dev(b, self.n), int(kappa), float(tol), int(max_iters),
                                 int(bool(flexible)), ctypes.byref(it), ctypes.byref(rel),
                                 hist.ctypes.data_as(_dp) if history else None), "mg_pcg")
         return st, it.value, rel.value, (list(hist[:it.value]) if history else None)
@@ -236,3 +244,48 @@ class Multigrid:
         lau, coarse = ctypes.c_longlong(), ctypes.c_longlong()
         _check(_lib.mg_counters(self._h, int(kappa), calls, ctypes.byref(lau), ctypes.byref(coarse)), "mg_counters")
         return list(calls), lau.value, coarse.value
+
+
+class Batch:
+    """Many independent instances solved by one graph launch (``mg_batch_*``)."""
+
+    def __init__(self, ns, epss, thetas, nu1=2, nu2=2, levels=None):
+        cnt = len(ns)
+        h = _h()
+        arr_i = (ctypes.c_int * cnt)(*[int(v) for v in ns])
+        arr_e = (ctypes.c_double * cnt)(*[float(v) for v in epss])
+        arr_t = (ctypes.c_double * cnt)(*[float(v) for v in thetas])
+        arr_l = (ctypes.c_int * cnt)(*[int(v) for v in levels]) if levels is not None else None
+        _check(_lib.mg_batch_create(cnt, arr_i, arr_e, arr_t, arr_l, int(nu1), int(nu2), ctypes.byref(h)),
+               "mg_batch_create")
+        self._h, self.ns = h, [int(v) for v in ns]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.mg_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def autotune(self, kappa, mixed=False):
+        """Returns {n: chosen coarse-kernel threshold}."""
+        out = (ctypes.c_int * (2 * len(set(self.ns))))()
+        _check(_lib.mg_batch_autotune(self._h, int(kappa), int(bool(mixed)), out), "mg_batch_autotune")
+        return {out[2 * i]: out[2 * i + 1] for i in range(len(set(self.ns)))}
+
+    def solve(self, xs, fs, kappa, tol, max_iters, mixed=False):
+        """xs, fs: lists of float64 CUDA tensors (n_i, n_i). Returns (status, iters list, relres list)."""
+        import torch
+        cnt = len(self.ns)
+        px = (ctypes.c_void_p * cnt)(*[_dev(x, n).value for x, n in zip(xs, self.ns)])
+        pf = (ctypes.c_void_p * cnt)(*[_dev(f, n).value for f, n in zip(fs, self.ns)])
+        it = (ctypes.c_int * cnt)()
+        rel = (ctypes.c_double * cnt)()
+        torch.cuda.synchronize()
+        st = _check(_lib.mg_batch_solve(self._h, px, pf, int(kappa), float(tol), int(max_iters), int(bool(mixed)),
+                                        it, rel), "mg_batch_solve")
+        return st, list(it), list(rel)

@@ -1,0 +1,71 @@
+"""Batched solves in one graph launch (ragged sizes, per-instance theta and eps) against the
+oracle and against single-instance solves of the same problems."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2010_00626_b300.inputs import batched_instances, rhs_uniform
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    import torch
+    return torch.tensor(a, dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_small_batch(lib, mixed):
+    import torch
+    inst = batched_instances(count=6, seed=3, sizes=(63, 127, 255))
+    ns = [d["n"] for d in inst]
+    batch = lib.Batch(ns, [d["eps"] for d in inst], [d["theta"] for d in inst])
+    fs = [rhs_uniform(d["n"], d["seed"]) for d in inst]
+    xs = [dev(np.zeros((d["n"], d["n"]))) for d in inst]
+    st, iters, rel = batch.solve(xs, [dev(f) for f in fs], 3, 1e-8, 2000, mixed=mixed)
+    assert st == 0 and all(r <= 1e-8 for r in rel)
+    for d, f, x, it in zip(inst, fs, xs, iters):
+        h = oracle.Hierarchy(d["n"], int(round(math.log2(d["n"] + 1))), d["theta"], d["eps"])
+        torch.cuda.synchronize()
+        assert oracle.relres(h, x.cpu().numpy(), f) <= 1e-8 * (1 + 1e-6)
+        # the same instance solved alone takes the same number of iterations
+        mg = lib.Multigrid(d["n"], d["eps"], d["theta"], int(round(math.log2(d["n"] + 1))))
+        y = dev(np.zeros((d["n"], d["n"])))
+        single = mg.solve_mixed(y, dev(f), 3, 1e-8, 2000) if mixed else mg.solve(y, dev(f), 3, 1e-8, 2000)
+        assert single[1] == it
+
+
+def near_grid_aligned(theta, tol=0.06):
+    """Angle within `tol` radians of 0, pi/2 or pi."""
+    return min(abs(theta - k * math.pi / 2) for k in range(3)) <= tol
+
+
+def test_autotune_and_full_batch(lib):
+    """256 instances, sizes uniform over {127, 255, 511, 1023}, theta ~ U[0, pi), log10 eps ~ U[-5, -1],
+    f ~ U(-1, 1): autotuned thresholds, FP32 cycles with FP64 refinement to 1e-8, one launch.
+
+    Damped point Jacobi cannot smooth strongly anisotropic problems whose strong direction is
+    nearly aligned with the grid (Section 4 makes the same remark and uses line relaxation there);
+    the instances that miss the tolerance within the iteration cap must be exactly such cases."""
+    import torch
+    inst = batched_instances(count=256, seed=0)
+    ns = [d["n"] for d in inst]
+    batch = lib.Batch(ns, [d["eps"] for d in inst], [d["theta"] for d in inst])
+    chosen = batch.autotune(3, mixed=True)
+    assert set(chosen) == set(ns) and all(c in (15, 31, 63) for c in chosen.values())
+    fs = [rhs_uniform(d["n"], d["seed"]) for d in inst]
+    xs = [dev(np.zeros((d["n"], d["n"]))) for d in inst]
+    st, iters, rel = batch.solve(xs, [dev(f) for f in fs], 3, 1e-8, 3000, mixed=True)
+    stalled = [i for i in range(256) if not rel[i] <= 1e-8]
+    assert len(stalled) <= 8
+    for i in stalled:
+        assert near_grid_aligned(inst[i]["theta"]) and inst[i]["eps"] < 1e-3, inst[i]
+    for i in range(0, 256, 37):  # the oracle recomputes a sample of residuals
+        if i in stalled:
+            continue
+        d = inst[i]
+        h = oracle.Hierarchy(d["n"], int(round(math.log2(d["n"] + 1))), d["theta"], d["eps"])
+        torch.cuda.synchronize()
+        assert oracle.relres(h, xs[i].cpu().numpy(), fs[i]) <= 1e-8 * (1 + 1e-6)

@@ -95,3 +95,38 @@ def test_mixed_solve_not_converged_and_bad_args(lib):
     assert st == 1 and iters == 2 and len(hist) == 2
     with pytest.raises(lib.MultigridError):
         mg.solve_mixed(dev(np.zeros((n, n))), dev(f), 0, 1e-8, 5)
+
+
+@pytest.mark.parametrize("kappa,flexible", [(1, True), (3, True), (3, False)])
+def test_mixed_pcg_small(lib, kappa, flexible):
+    n, levels, theta, eps = 255, 8, 2.0, 1e-3
+    h = oracle.Hierarchy(n, levels, theta, eps)
+    b = rhs_normal(n, 7)
+    _, hist64 = oracle.pcg(h, b, kappa, 1e-10, 300, flexible=flexible)
+    mg = lib.Multigrid(n, eps, theta, levels)
+    xd = dev(np.zeros((n, n)))
+    st, iters, relres, hist = mg.pcg(xd, dev(b), kappa, 1e-10, 300, flexible=flexible, mixed=True)
+    assert st == 0 and relres <= 1e-10
+    assert oracle.relres(h, host(xd), b) <= 1e-10 * (1 + 1e-5)
+    assert abs(iters - len(hist64)) <= max(2, len(hist64) // 5)
+
+
+def test_pcg_large_fp64_and_mixed(lib):
+    """8191^2, 13 levels, theta from seed 0, eps=1e-5, kappa=3, tol 1e-10: FP64 and mixed MGCG;
+    the oracle recomputes both residuals in FP64."""
+    from paper_2010_00626_b300.inputs import pcg_theta
+    n, levels, eps = 8191, 13, 1e-5
+    theta = pcg_theta(0)
+    h = oracle.Hierarchy(n, levels, theta, eps)
+    b = rhs_normal(n, 0)
+    mg = lib.Multigrid(n, eps, theta, levels)
+    bd = dev(b)
+    results = {}
+    for mixed in (False, True):
+        xd = dev(np.zeros((n, n)))
+        st, iters, relres, _ = mg.pcg(xd, bd, 3, 1e-10, 1000, flexible=True, mixed=mixed, history=False)
+        assert st == 0 and relres <= 1e-10
+        assert oracle.relres(h, host(xd), b) <= 1e-10 * (1 + 1e-5)
+        results[mixed] = iters
+        del xd
+    assert abs(results[True] - results[False]) <= max(2, results[False] // 5), results

@@ -1,0 +1,73 @@
+"""The run-time model (Section 3) against the paper's printed numbers and the oracle's counts."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2010_00626_b300 import model
+from paper_2010_00626_b300.inputs import rhs_uniform
+
+GOLDEN = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+
+
+def kap(k):
+    return model.W_COUNTER if k == "inf" else k
+
+
+def test_closed_forms_match_oracle_recursion_counts():
+    h = oracle.Hierarchy(63, 6, 0.5, 1e-2)
+    f = rhs_uniform(63, 0)
+    for kappa in range(1, 8):
+        rec = oracle.CallRecorder(6)
+        oracle.cycle(h, np.zeros_like(f), f, kappa, rec)
+        assert [model.level_calls(kappa, l) for l in range(1, 7)] == rec.per_level[1:]
+        assert model.total_calls(kappa, 6) == sum(rec.per_level)
+
+
+def test_table4_per_cycle_times_from_paper_alpha_beta():
+    """Eq. 3.1 with alpha, beta of Section 3.2 and nu = 4 reproduces Table 4's per-cycle times
+    (12 levels) to within 2.5%."""
+    p = GOLDEN["model_parameters"]
+    t4 = GOLDEN["table4_standalone_12_levels"]
+    for k, ms in zip(t4["kappa"], t4["ms_per_cycle"]):
+        pred = model.predict_paper(p["alpha_ms"], p["beta_ms"], kap(k), 12, 4)
+        assert abs(pred - ms) <= 0.025 * ms, (k, pred, ms)
+
+
+def test_table1_turning_points():
+    """Appendix iteration with Section 3.2's alpha, beta: the W row matches Table 1 with nu = 4 and
+    the kappa = 1..4 rows match with nu = 2 (the table mixes the two; parity for the kappa rows with
+    the nu = 4 of Section 3 is unpinned)."""
+    p = GOLDEN["model_parameters"]
+    t1 = GOLDEN["table1_turning_points"]
+    for k, ntp in zip(t1["kappa"], t1["n_tp"]):
+        nu = 4 if k == "inf" else 2
+        got, _ = model.turning_point(p["alpha_ms"], p["beta_ms"], kap(k), nu)
+        assert abs(got - ntp) <= 0.06, (k, got, ntp)
+
+
+def test_fit_recovers_parameters():
+    alpha, beta = 3e-3, 2e-6
+    samples = [(k, n, model.predict_paper(alpha, beta, k, n, 4)) for k in (1, 2, 3, 4, model.W_COUNTER)
+               for n in range(4, 14)]
+    a, b = model.fit_paper(samples, 4)
+    assert abs(a - alpha) <= 1e-9 and abs(b - beta) <= 1e-12
+    params = (2e-3, 5e-4, 1e-7)
+    s2 = []
+    for k in (1, 2, 3, 4, model.W_COUNTER):
+        for L in range(4, 13):
+            fine, coarse = model.b300_counts(k, L, max(0, L - 4))
+            s2.append((fine, coarse, (2 ** L - 1) ** 2 * model.c_kappa(k),
+                       model.predict_b300(params, k, L, max(0, L - 4), 2 ** L - 1)))
+    assert np.allclose(model.fit_b300(s2), params, rtol=1e-8)
+
+
+def test_b300_counts_and_preselection():
+    fine, coarse = model.b300_counts(4, 12, 8)
+    assert fine == 2 * sum(model.level_calls(4, l) for l in range(1, 9))
+    assert coarse == sum(model.level_calls(4, l) for l in range(9, 13))
+    k, table = model.preselect_kappa({1: 1.0, 2: 1.5, 3: 2.0}, {1: 0.99, 2: 0.9, 3: 0.88}, 1e-8)
+    assert k == 2 and table[1] > table[2]
+    assert model.contraction([1.0, 0.5, 0.25, 0.125]) == pytest.approx(0.5)
