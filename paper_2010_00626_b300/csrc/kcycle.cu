@@ -23,6 +23,7 @@
 
 #include "../../include/kcycle.h"
 #include "kernels.cuh"
+#include "stream_f32.cuh"
 
 using namespace kc;
 
@@ -118,6 +119,7 @@ struct mg_ctx {
   double* hist = nullptr;
   int hist_cap = 0;
   bool have32 = false;  // FP32 hierarchy allocated
+  int ld32_0 = 0;       // pitch of the FP32 level-0 arrays (multiple of 32 floats)
   double *pr = nullptr, *pp = nullptr, *pq = nullptr, *pz = nullptr, *pzold = nullptr;  // PCG vectors
   double *hv = nullptr, *hf = nullptr;  // device copies for mg_solve_host
   cudaStream_t own = nullptr;
@@ -219,6 +221,7 @@ struct Arr<double> {
   static double* tmp(mg_ctx* h, int l) { return h->lv[l].tmp; }
   static double* f(mg_ctx* h, int l) { return h->lv[l].f; }
   static const double* coef(mg_ctx* h) { return h->coef; }
+  static int ld(mg_ctx* h, int l) { return h->lv[l].ld; }
 };
 template <>
 struct Arr<float> {
@@ -226,6 +229,7 @@ struct Arr<float> {
   static float* tmp(mg_ctx* h, int l) { return h->lv[l].tmp32; }
   static float* f(mg_ctx* h, int l) { return h->lv[l].f32; }
   static const float* coef(mg_ctx* h) { return h->coef32; }
+  static int ld(mg_ctx* h, int l) { return l == 0 ? h->ld32_0 : h->lv[l].ld; }
 };
 
 template <typename T>
@@ -236,7 +240,7 @@ T* lv_v(mg_ctx* h, const BindingT<T>& b, int l) { return l == 0 ? b.v0 : Arr<T>:
 template <typename T>
 const T* lv_f(mg_ctx* h, const BindingT<T>& b, int l) { return l == 0 ? b.f0 : Arr<T>::f(h, l); }
 template <typename T>
-int lv_ld(mg_ctx* h, const BindingT<T>& b, int l) { return l == 0 ? b.ld0 : h->lv[l].ld; }
+int lv_ld(mg_ctx* h, const BindingT<T>& b, int l) { return l == 0 ? b.ld0 : Arr<T>::ld(h, l); }
 
 enum { K_PASS_A = 0, K_PASS_B = 1, K_COARSE = 2, K_APPLY = 3 };
 
@@ -255,6 +259,35 @@ void prof_end(mg_ctx* h, cudaStream_t s) {
   cudaEventCreate(&e);
   cudaEventRecord(e, s);
   h->pev.push_back(e);
+}
+
+// FP32 streaming passes: large levels, nu <= 2, 16-byte aligned rows with a pitch multiple of 4.
+bool stream_ok(int n, int nu, const void* p, int ld) {
+  return n >= 2047 && nu <= 2 && (p == nullptr || ((uintptr_t)p & 15) == 0) && (ld & 3) == 0;
+}
+int stream_rows(int n) { return n >= 4095 ? 64 : (n >= 2047 ? 32 : 16); }
+
+int launch_pass_a_stream(const PassAArgs<float>& a, cudaStream_t s) {
+  const int strips = (a.n + SF_COLS - 1) / SF_COLS, R = stream_rows(a.n);
+  dim3 grid((strips + SF_WARPS - 1) / SF_WARPS, (a.n + R - 1) / R);
+  switch (a.nu) {
+    case 0: pass_a_stream_f32<0><<<grid, 32 * SF_WARPS, 0, s>>>(a, R); break;
+    case 1: pass_a_stream_f32<1><<<grid, 32 * SF_WARPS, 0, s>>>(a, R); break;
+    default: pass_a_stream_f32<2><<<grid, 32 * SF_WARPS, 0, s>>>(a, R); break;
+  }
+  KC_CUDA(cudaGetLastError());
+  return MG_OK;
+}
+int launch_pass_b_stream(const PassBArgs<float>& a, cudaStream_t s) {
+  const int strips = (a.n + SF_COLS - 1) / SF_COLS, R = stream_rows(a.n);
+  dim3 grid((strips + SF_WARPS - 1) / SF_WARPS, (a.n + R - 1) / R);
+  switch (a.nu) {
+    case 0: pass_b_stream_f32<0, false><<<grid, 32 * SF_WARPS, 0, s>>>(a, R); break;
+    case 1: pass_b_stream_f32<1, false><<<grid, 32 * SF_WARPS, 0, s>>>(a, R); break;
+    default: pass_b_stream_f32<2, false><<<grid, 32 * SF_WARPS, 0, s>>>(a, R); break;
+  }
+  KC_CUDA(cudaGetLastError());
+  return MG_OK;
 }
 
 template <typename T>
@@ -298,15 +331,23 @@ int emit_pass_a(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const
   a.coef = Arr<T>::coef(h);
   a.skip = skip;
   a.ldvin = lv_ld(h, b, l);
-  a.ldvout = h->lv[l].ld;
+  a.ldvout = Arr<T>::ld(h, l);
   a.ldf = lv_ld(h, b, l);
-  a.ldc = h->lv[l + 1].ld;
+  a.ldc = Arr<T>::ld(h, l + 1);
   a.n = h->lv[l].n;
   a.nu = nu;
   a.level = l;
   ++h->launch_count;
   prof_begin(h, K_PASS_A, l, s);
   int st;
+  if constexpr (std::is_same<T, float>::value) {
+    if (stream_ok(a.n, nu, a.vin, a.ldvin) && stream_ok(a.n, nu, a.f, a.ldf) && stream_ok(a.n, nu, a.vout, a.ldvout) &&
+        ((uintptr_t)a.fc & 7) == 0 && (a.ldc & 1) == 0) {
+      st = launch_pass_a_stream(a, s);
+      prof_end(h, s);
+      return st;
+    }
+  }
   switch (tile_edge(a.n)) {
     case 64: st = launch_pass_a<Tile64>(a, s); break;
     case 32: st = launch_pass_a<Tile32>(a, s); break;
@@ -327,16 +368,24 @@ int emit_pass_b(mg_ctx* h, const BindingT<T>& b, int l, int nu, double* partial,
   a.coef = Arr<T>::coef(h);
   a.skip = skip;
   a.partial = partial;
-  a.ldvin = h->lv[l].ld;
+  a.ldvin = Arr<T>::ld(h, l);
   a.ldvout = lv_ld(h, b, l);
   a.ldf = lv_ld(h, b, l);
-  a.ldc = h->lv[l + 1].ld;
+  a.ldc = Arr<T>::ld(h, l + 1);
   a.n = h->lv[l].n;
   a.nu = nu;
   a.level = l;
   ++h->launch_count;
   prof_begin(h, K_PASS_B, l, s);
   int st;
+  if constexpr (std::is_same<T, float>::value) {
+    if (partial == nullptr && stream_ok(a.n, nu, a.vin, a.ldvin) && stream_ok(a.n, nu, a.f, a.ldf) &&
+        stream_ok(a.n, nu, a.vout, a.ldvout) && ((uintptr_t)a.vc & 7) == 0 && (a.ldc & 1) == 0) {
+      st = launch_pass_b_stream(a, s);
+      prof_end(h, s);
+      return st;
+    }
+  }
   switch (tile_edge(a.n)) {
     case 64: st = launch_pass_b<Tile64>(a, s); break;
     case 32: st = launch_pass_b<Tile32>(a, s); break;
@@ -552,7 +601,6 @@ int read_result(mg_ctx* h, cudaStream_t s, double tol, int* count_out, double* f
 int add_solve_branch(mg_ctx* h, cudaGraph_t parent, double* x, const double* f, int kappa, double tol, int max_iters,
                      bool mixed) {
   const int n = h->n;
-  const size_t len = (size_t)n * n;
   float* d = h->lv[0].v32;
   float* r32 = h->lv[0].f32;
   const int napply = (int)apply_grid_blocks(n);
@@ -561,7 +609,8 @@ int add_solve_branch(mg_ctx* h, cudaGraph_t parent, double* x, const double* f, 
   KC_CUDA(cudaStreamBeginCapture(h->own, cudaStreamCaptureModeThreadLocal));
   int st = launch_norm2(h, f, h->scal + S_FNORM2, h->own);
   reset_state_kernel<<<1, 1, 0, h->own>>>(h->ints, max_iters, h->scal, tol);
-  if (mixed) ir_residual_kernel<NT_VEC><<<agrid, NT_VEC, 0, h->own>>>(x, f, r32, h->coef, n, h->partial, nullptr);
+  if (mixed)
+    ir_residual_kernel<NT_VEC><<<agrid, NT_VEC, 0, h->own>>>(x, f, r32, h->ld32_0, h->coef, n, h->partial, nullptr);
   const cudaError_t le = cudaGetLastError();
   const cudaError_t ce = cudaStreamEndCapture(h->own, &init);
   if (st < 0) return st;
@@ -583,10 +632,10 @@ int add_solve_branch(mg_ctx* h, cudaGraph_t parent, double* x, const double* f, 
                                         cudaStreamCaptureModeThreadLocal));
   const int* done = h->ints + I_DONE;
   if (mixed) {
-    BindingT<float> b{d, r32, n};
+    BindingT<float> b{d, r32, h->ld32_0};
     st = emit_cycle(h, b, kappa, true, false, false, done, h->own);
-    ir_add_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, h->own>>>(x, d, len, done);
-    ir_residual_kernel<NT_VEC><<<agrid, NT_VEC, 0, h->own>>>(x, f, r32, h->coef, n, h->partial, done);
+    ir_add_kernel<NT_VEC><<<agrid, NT_VEC, 0, h->own>>>(x, d, n, h->ld32_0, done);
+    ir_residual_kernel<NT_VEC><<<agrid, NT_VEC, 0, h->own>>>(x, f, r32, h->ld32_0, h->coef, n, h->partial, done);
     finish_step_kernel<NT_VEC><<<1, NT_VEC, 0, h->own>>>(h->partial, napply, h->scal, h->ints, h->hist, ch, 1);
   } else {
     Binding b{x, f, n};
@@ -664,9 +713,10 @@ int ensure_levels32(mg_ctx* h) {
       h->lc32 = l;
       break;
     }
+  h->ld32_0 = round_up(h->n, 32);
   for (int l = 0; l < h->levels; ++l) {
     Level& L = h->lv[l];
-    const size_t bytes = sizeof(float) * (size_t)L.ld * L.n;
+    const size_t bytes = sizeof(float) * (size_t)(l == 0 ? h->ld32_0 : L.ld) * L.n;
     if (l < h->lc32) KC_CUDA(cudaMalloc(&L.tmp32, bytes));
     if (l <= h->lc32) {
       KC_CUDA(cudaMalloc(&L.v32, bytes));
@@ -911,10 +961,12 @@ static int pcg_impl(mg_handle h, double* x, const double* b, int kappa, double t
       Binding bz{h->pz, h->pr, h->n};
       return emit_cycle(h, bz, kappa, true, false, false, skip, o);
     }
-    convert_kernel<NT_VEC, double, float><<<VEC_BLOCKS, NT_VEC, 0, o>>>(r32, h->pr, len, skip);
-    BindingT<float> b32{z32, r32, h->n};
+    const int n = h->n;
+    dim3 cgrid((n + 31) / 32, (n + NT_VEC / 32 - 1) / (NT_VEC / 32));
+    convert_kernel<NT_VEC, double, float><<<cgrid, NT_VEC, 0, o>>>(r32, h->ld32_0, h->pr, n, n, skip);
+    BindingT<float> b32{z32, r32, h->ld32_0};
     KC_TRY(emit_cycle(h, b32, kappa, true, false, false, skip, o));
-    convert_kernel<NT_VEC, float, double><<<VEC_BLOCKS, NT_VEC, 0, o>>>(h->pz, z32, len, skip);
+    convert_kernel<NT_VEC, float, double><<<cgrid, NT_VEC, 0, o>>>(h->pz, n, z32, h->ld32_0, n, skip);
     KC_CUDA(cudaGetLastError());
     h->launch_count += 2;
     return MG_OK;
@@ -1014,7 +1066,6 @@ int mg_solve_mixed(mg_handle h, double* x, const double* f, int kappa, double to
   KC_TRY(ensure_hist(h, max_iters));
   cudaStream_t s = h->stream();
   const int n = h->n;
-  const size_t len = (size_t)n * n;
   float* d = h->lv[0].v32;
   float* r32 = h->lv[0].f32;
   const int napply = (int)apply_grid_blocks(n);
@@ -1023,14 +1074,14 @@ int mg_solve_mixed(mg_handle h, double* x, const double* f, int kappa, double to
   if (!ge) {
     GraphEntry e;
     e.kind = G_MIXED; e.kappa = kappa; e.p0 = x; e.p1 = f;
-    BindingT<float> b{d, r32, n};
+    BindingT<float> b{d, r32, h->ld32_0};
     const int* done = h->ints + I_DONE;
     KC_TRY(build_while_graph(h, [&](cudaGraphConditionalHandle ch) -> int {
       cudaStream_t o = h->own;
       // d = B r (FP32 kappa-cycle from zero), x += d, r = f - A x (FP64), stopping test
       KC_TRY(emit_cycle(h, b, kappa, true, false, false, done, o));
-      ir_add_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, o>>>(x, d, len, done);
-      ir_residual_kernel<NT_VEC><<<agrid, NT_VEC, 0, o>>>(x, f, r32, h->coef, n, h->partial, done);
+      ir_add_kernel<NT_VEC><<<agrid, NT_VEC, 0, o>>>(x, d, n, h->ld32_0, done);
+      ir_residual_kernel<NT_VEC><<<agrid, NT_VEC, 0, o>>>(x, f, r32, h->ld32_0, h->coef, n, h->partial, done);
       finish_step_kernel<NT_VEC><<<1, NT_VEC, 0, o>>>(h->partial, napply, h->scal, h->ints, h->hist, ch, 1);
       KC_CUDA(cudaGetLastError());
       h->launch_count += 3;
@@ -1041,7 +1092,7 @@ int mg_solve_mixed(mg_handle h, double* x, const double* f, int kappa, double to
   }
   KC_TRY(launch_norm2(h, f, h->scal + S_FNORM2, s));
   reset_state_kernel<<<1, 1, 0, s>>>(h->ints, max_iters, h->scal, tol);
-  ir_residual_kernel<NT_VEC><<<agrid, NT_VEC, 0, s>>>(x, f, r32, h->coef, n, h->partial, nullptr);
+  ir_residual_kernel<NT_VEC><<<agrid, NT_VEC, 0, s>>>(x, f, r32, h->ld32_0, h->coef, n, h->partial, nullptr);
   KC_CUDA(cudaGetLastError());
   KC_CUDA(cudaGraphLaunch(ge->exec, s));
   return read_result(h, s, tol, iters, final_relres, history);
@@ -1140,7 +1191,7 @@ int mg_profile_cycle(mg_handle h, double* v, const double* f, int kappa, int wit
   h->prof = true;
   int st;
   if (fp32) {  // the FP32 cycle of the mixed path: d = B32 r from zero on the handle's FP32 arrays
-    BindingT<float> b32{h->lv[0].v32, h->lv[0].f32, h->n};
+    BindingT<float> b32{h->lv[0].v32, h->lv[0].f32, h->ld32_0};
     st = emit_cycle(h, b32, kappa, true, false, false, nullptr, s);
   } else {
     st = emit_cycle(h, b, kappa, false, false, (with_norm & 1) != 0, nullptr, s);

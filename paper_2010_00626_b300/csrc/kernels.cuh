@@ -1004,20 +1004,21 @@ __global__ void __launch_bounds__(NT) grad_kernel(const double* lam, const doubl
 // ---------------------------------------------------------------------------------------------
 // Mixed precision: FP32 cycles inside FP64 iterative refinement.
 // ---------------------------------------------------------------------------------------------
-// x += d (FP64 += FP32 correction), pointwise
+// x += d (FP64 += FP32 correction), pointwise; x has pitch n, d pitch ldd
 template <int NT>
-__global__ void __launch_bounds__(NT) ir_add_kernel(double* x, const float* d, size_t len, const int* skip) {
+__global__ void __launch_bounds__(NT) ir_add_kernel(double* x, const float* d, int n, int ldd, const int* skip) {
   if (skip && *skip) return;
-  for (size_t k = blockIdx.x * (size_t)NT + threadIdx.x; k < len; k += (size_t)gridDim.x * NT)
-    x[k] += (double)d[k];
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int j = blockIdx.y * (NT / 32) + (threadIdx.x >> 5);
+  if (i < n && j < n) x[(size_t)j * n + i] += (double)d[(size_t)j * ldd + i];
 }
 
 // r = f - A x in FP64, stored rounded to FP32 as the right-hand side of the next FP32 cycle, with
 // partial sums of r^2 (FP64) for the stopping test
 template <int NT>
 __global__ void __launch_bounds__(NT) ir_residual_kernel(const double* __restrict__ x, const double* __restrict__ f,
-                                                         float* r32, const double* coef, int n, double* partial,
-                                                         const int* skip) {
+                                                         float* r32, int ldr, const double* coef, int n,
+                                                         double* partial, const int* skip) {
   if (skip && *skip) return;
   __shared__ double red[NT / 32];
   const int i = blockIdx.x * 32 + (threadIdx.x & 31);
@@ -1026,7 +1027,7 @@ __global__ void __launch_bounds__(NT) ir_residual_kernel(const double* __restric
   double ss = 0.0;
   if (i < n && j < n) {
     const double r = residual_at(neighbours_global(x, i, j, n, n), f[(size_t)j * n + i], c);
-    r32[(size_t)j * n + i] = (float)r;
+    r32[(size_t)j * ldr + i] = (float)r;
     ss = r * r;
   }
   const double t = block_sum<NT>(ss, red);
@@ -1035,9 +1036,11 @@ __global__ void __launch_bounds__(NT) ir_residual_kernel(const double* __restric
 
 // y = (double) x or y = (float) x, pointwise (mixed-precision preconditioner hand-off)
 template <int NT, typename S, typename D>
-__global__ void __launch_bounds__(NT) convert_kernel(D* y, const S* x, size_t len, const int* skip) {
+__global__ void __launch_bounds__(NT) convert_kernel(D* y, int ldy, const S* x, int ldx, int n, const int* skip) {
   if (skip && *skip) return;
-  for (size_t k = blockIdx.x * (size_t)NT + threadIdx.x; k < len; k += (size_t)gridDim.x * NT) y[k] = (D)x[k];
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int j = blockIdx.y * (NT / 32) + (threadIdx.x >> 5);
+  if (i < n && j < n) y[(size_t)j * ldy + i] = (D)x[(size_t)j * ldx + i];
 }
 
 __global__ void reset_state_kernel(int* ints, int max_iters, double* scal, double tol) {
