@@ -39,7 +39,7 @@ __all__ = [
     "cos_sin", "fine_stencil", "fine_stencil_derivatives", "apply_stencil", "restrict_fw",
     "prolong_bilinear", "galerkin_stencil", "zero_row_sum_centre", "jacobi", "Hierarchy", "CallRecorder",
     "kcycle", "gamma_cycle", "f_cycle", "kcycle_adjoint", "cycle", "cycle_adjoint",
-    "residual", "relres", "solve", "pcg", "param_grads", "level_sizes",
+    "residual", "relres", "solve", "solve_error_reduction", "pcg", "param_grads", "level_sizes",
 ]
 
 
@@ -267,6 +267,7 @@ class Hierarchy:
     nu1: int = 2
     nu2: int = 2
     omega: float = 0.8
+    coarse_op: str = "galerkin"   # or "rediscretized": the Section 4 stencil on each coarse grid
     stencils: list = field(default_factory=list)
     sizes: list = field(default_factory=list)
     _chol: object = None
@@ -278,8 +279,13 @@ class Hierarchy:
         self.sizes = level_sizes(self.n, self.levels)
         st = fine_stencil(self.theta, self.eps, self.n)
         self.stencils = [st]
-        for _ in range(self.levels - 1):
-            st = zero_row_sum_centre(galerkin_stencil(st))
+        for lvl in range(1, self.levels):
+            if self.coarse_op == "galerkin":
+                st = zero_row_sum_centre(galerkin_stencil(st))
+            elif self.coarse_op == "rediscretized":
+                st = fine_stencil(self.theta, self.eps, self.sizes[lvl])
+            else:
+                raise ValueError("coarse_op must be 'galerkin' or 'rediscretized'")
             self.stencils.append(st)
         # coarsest-level operator as a dense SPD matrix, factorised once
         nc = self.sizes[-1]
@@ -421,6 +427,22 @@ def solve(h: Hierarchy, f: np.ndarray, kappa: int, tol: float, max_cycles: int,
         rho = float(np.linalg.norm(residual(h.stencil(1), v, f)) / fnorm)
         hist.append(rho)
         if rho <= tol:
+            break
+    return v, hist
+
+
+def solve_error_reduction(h: Hierarchy, v0: np.ndarray, kappa: int, reduction: float, max_cycles: int):
+    """The error-reduction protocol of Section 4: right-hand side zero (so the exact solution is
+    zero and the iterate is the error), cycles from the initial guess v0 until
+    ||v_k||_2 <= reduction * ||v0||_2. Returns (v, history of ||v_k|| / ||v0||)."""
+    f = np.zeros_like(v0)
+    v = v0.copy()
+    n0 = np.linalg.norm(v0)
+    hist = []
+    for _ in range(max_cycles):
+        v = cycle(h, v, f, kappa)
+        hist.append(float(np.linalg.norm(v) / n0))
+        if hist[-1] <= reduction:
             break
     return v, hist
 

@@ -195,3 +195,22 @@ def test_coarsest_dense_when_levels_short():
     f = rhs_uniform(3, 7)
     v = h.coarsest_solve(f)
     assert np.allclose(oracle.apply_stencil(h.stencils[-1], v), f, rtol=0, atol=1e-13 * np.abs(f).max())
+
+
+def test_rediscretized_hierarchy_and_error_protocol():
+    """Rediscretized coarse operators are the Section 4 stencil with the coarse h; the error
+    protocol (f = 0) is the same cycle iteration, so its history is the iterate norm ratio and the
+    solution tends to zero."""
+    n, levels = 63, 6
+    h = oracle.Hierarchy(n, levels, math.pi / 4, 1e-2, coarse_op="rediscretized")
+    for lvl, m in enumerate(h.sizes):
+        assert np.array_equal(h.stencils[lvl], oracle.fine_stencil(math.pi / 4, 1e-2, m))
+    v0 = np.random.default_rng(2).uniform(-1, 1, (n, n))
+    v, hist = oracle.solve_error_reduction(h, v0, 3, 1e-8, 500)
+    assert hist[-1] <= 1e-8 and np.linalg.norm(v) <= 1e-8 * np.linalg.norm(v0)
+    w = v0.copy()
+    for _ in range(3):
+        w = oracle.cycle(h, w, np.zeros_like(v0), 3)
+    assert np.isclose(np.linalg.norm(w) / np.linalg.norm(v0), hist[2], rtol=1e-14)
+    with pytest.raises(ValueError):
+        oracle.Hierarchy(15, 3, 0.1, 0.1, coarse_op="other")
