@@ -353,6 +353,34 @@ def main():
                         "predicted_best_kappa": best_pred,
                         "measured_best_kappa": min(measured, key=measured.get) if measured else None}
 
+    # ---------------------------------------------------------------- the paper's own protocol (Table 4 setting)
+    paper_protocol = None
+    if not args.no_sweep and world == 1:
+        # 12 levels, phi = 45 deg, eps = 1e-4, damped Jacobi nu = 2+2, coarse operators rediscretized,
+        # f = 0 and a random start, until the L2 error (the iterate) is reduced by 1e8 (Section 4)
+        mp = kcycle.Multigrid(n, 1e-4, math.pi / 4, levels, 2, 2, omega=0.87)
+        mp.set_option(kcycle.MG_OPT_COARSE_OP, 1)
+        mp.set_option(kcycle.MG_OPT_STOP, 1)
+        zero = torch.zeros_like(f)
+        v0 = torch.tensor(np.random.default_rng(12345).uniform(-1.0, 1.0, (n, n)), device="cuda")
+        paper_cycles = {"1": 6909, "2": 1403, "3": 651, "4": 495, "W": 470}
+        paper_protocol = {"setting": "4095^2, 12 levels, phi=pi/4, eps=1e-4, omega=0.87, nu=2+2, rediscretized "
+                                     "coarse operators, f=0, v0~U(-1,1) seed 12345, ||v_k||/||v_0|| <= 1e-8",
+                          "paper_table4_cycles_gtx1060": paper_cycles}
+        for k in (1, 2, 3, 4, KAPPA_W):
+            vv = v0.clone()
+            mp.solve(vv, zero, k, 1e-8, 1, history=False)
+            vv = v0.clone()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            st_p, cyc_p, red_p, _ = mp.solve(vv, zero, k, 1e-8, 20000, history=False)
+            b.record()
+            torch.cuda.synchronize()
+            paper_protocol[kname(k)] = {"cycles": cyc_p, "ms": round(a.elapsed_time(b), 1),
+                                        "ms_per_cycle": round(a.elapsed_time(b) / max(cyc_p, 1), 3)}
+        mp.close()
+
     # ---------------------------------------------------------------- batched (256 ragged instances, one launch each)
     batched = None
     if not args.no_sweep and world == 1:
@@ -408,7 +436,8 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "roofline": roofline, "cycle_share": cycle_share, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clocks.summary(), "per_kappa": per_kappa,
-                "per_kappa_mixed": per_kappa_mixed, "batched": batched, "model": model_report}
+                "per_kappa_mixed": per_kappa_mixed, "batched": batched, "model": model_report,
+                "paper_protocol": paper_protocol}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

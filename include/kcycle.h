@@ -58,7 +58,11 @@ typedef enum {
   MG_OPT_LEVELS = 3,       /* read-only: number of levels                                          */
   MG_OPT_N = 4,            /* read-only: finest grid side                                          */
   MG_OPT_LAUNCHES = 5,     /* read-only: kernel launches in the last cycle graph built              */
-  MG_OPT_COARSE_N32 = 6    /* as MG_OPT_COARSE_N for the FP32 cycles of the mixed forms; default 63  */
+  MG_OPT_COARSE_N32 = 6,   /* as MG_OPT_COARSE_N for the FP32 cycles of the mixed forms; default 63  */
+  MG_OPT_COARSE_OP = 7,    /* coarse operators: 0 Galerkin R A P (default), 1 the Section 4 stencil
+                              rediscretized on each coarse grid                                     */
+  MG_OPT_STOP = 8          /* mg_solve's stopping test: 0 ||f - A v||/||f|| <= tol (default);
+                              1 ||v_k||/||v_0|| <= tol, the error reduction of Section 4 when f = 0  */
 } mg_option;
 
 /* Set up the hierarchy for the Section 4 problem on an n x n interior grid.

@@ -120,6 +120,8 @@ struct mg_ctx {
   int hist_cap = 0;
   bool have32 = false;  // FP32 hierarchy allocated
   int ld32_0 = 0;       // pitch of the FP32 level-0 arrays (multiple of 32 floats)
+  int rediscretized = 0;  // coarse operators: 0 Galerkin, 1 the Section 4 stencil on each coarse grid
+  int stop_rule = 0;      // 0: ||f - A v|| / ||f|| <= tol; 1: ||v_k|| / ||v_0|| <= tol (f = 0 protocol)
   double *pr = nullptr, *pp = nullptr, *pq = nullptr, *pz = nullptr, *pzold = nullptr;  // PCG vectors
   double *hv = nullptr, *hf = nullptr;  // device copies for mg_solve_host
   cudaStream_t own = nullptr;
@@ -659,15 +661,23 @@ int solve_impl(mg_handle h, double* v, const double* f, int kappa, double tol, i
   trim_graphs(h);
   KC_TRY(ensure_hist(h, max_cycles));
   cudaStream_t s = h->stream();
-  GraphEntry* ge = find_graph(h, G_SOLVE, kappa, adjoint ? 1 : 0, v, f);
+  const int gflag = (adjoint ? 1 : 0) | (h->stop_rule << 1);
+  GraphEntry* ge = find_graph(h, G_SOLVE, kappa, gflag, v, f);
   if (!ge) {
     GraphEntry e;
-    e.kind = G_SOLVE; e.kappa = kappa; e.flag = adjoint ? 1 : 0; e.p0 = v; e.p1 = f;
+    e.kind = G_SOLVE; e.kappa = kappa; e.flag = gflag; e.p0 = v; e.p1 = f;
     Binding b{v, f, h->n};
     const int np = norm_partials(h);
+    const bool err_rule = h->stop_rule == 1;
     KC_TRY(build_while_graph(h, [&](cudaGraphConditionalHandle ch) -> int {
-      KC_TRY(emit_cycle(h, b, kappa, false, adjoint, true, h->ints + I_DONE, h->own));
-      finish_step_kernel<NT_VEC><<<1, NT_VEC, 0, h->own>>>(h->partial, np, h->scal, h->ints, h->hist, ch, 1);
+      KC_TRY(emit_cycle(h, b, kappa, false, adjoint, !err_rule, h->ints + I_DONE, h->own));
+      if (err_rule) {  // ||v_k||^2 partial sums
+        dot_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, h->own>>>(v, v, nullptr, (size_t)h->n * h->n, h->partial,
+                                                              nullptr, h->ints + I_DONE);
+        ++h->launch_count;
+      }
+      finish_step_kernel<NT_VEC><<<1, NT_VEC, 0, h->own>>>(h->partial, err_rule ? VEC_BLOCKS : np, h->scal, h->ints,
+                                                           h->hist, ch, 1);
       KC_CUDA(cudaGetLastError());
       ++h->launch_count;
       return MG_OK;
@@ -675,7 +685,7 @@ int solve_impl(mg_handle h, double* v, const double* f, int kappa, double tol, i
     e.launches = h->launch_count;
     ge = add_graph(h, e);
   }
-  KC_TRY(launch_norm2(h, f, h->scal + S_FNORM2, s));
+  KC_TRY(launch_norm2(h, h->stop_rule == 1 ? v : f, h->scal + S_FNORM2, s));
   reset_state_kernel<<<1, 1, 0, s>>>(h->ints, max_cycles, h->scal, tol);
   KC_CUDA(cudaGetLastError());
   KC_CUDA(cudaGraphLaunch(ge->exec, s));
@@ -751,7 +761,7 @@ int free_levels(mg_ctx* h) {
 
 int run_setup_kernels(mg_ctx* h) {
   setup_stencils_kernel<<<1, 32, 0, h->own>>>(h->theta, h->eps, h->n, h->levels, h->omega, h->coef, h->coef32,
-                                             h->stencils, h->dstencil);
+                                             h->stencils, h->dstencil, h->rediscretized);
   KC_CUDA(cudaGetLastError());
   const int nc = h->lv[h->levels - 1].n;
   if (nc > 1) {
@@ -860,6 +870,19 @@ int mg_set_option(mg_handle h, int key, double value) {
       drop_graphs(h);
       return run_setup_kernels(h);
     }
+    case MG_OPT_COARSE_OP: {
+      if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
+      KC_CUDA(cudaStreamSynchronize(h->stream()));
+      h->rediscretized = (int)value;
+      drop_graphs(h);
+      return run_setup_kernels(h);
+    }
+    case MG_OPT_STOP: {
+      if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
+      h->stop_rule = (int)value;
+      drop_graphs(h);
+      return MG_OK;
+    }
     case MG_OPT_COARSE_N:
     case MG_OPT_COARSE_N32: {
       const int c = (int)value;
@@ -883,6 +906,8 @@ int mg_get_option(mg_handle h, int key, double* value) {
     case MG_OPT_OMEGA: *value = h->omega; return MG_OK;
     case MG_OPT_COARSE_N: *value = h->coarse_n; return MG_OK;
     case MG_OPT_COARSE_N32: *value = h->coarse_n32; return MG_OK;
+    case MG_OPT_COARSE_OP: *value = h->rediscretized; return MG_OK;
+    case MG_OPT_STOP: *value = h->stop_rule; return MG_OK;
     case MG_OPT_LEVELS: *value = h->levels; return MG_OK;
     case MG_OPT_N: *value = h->n; return MG_OK;
     case MG_OPT_LAUNCHES: *value = h->last_launches; return MG_OK;
@@ -1489,7 +1514,7 @@ extern "C" int mg_residual_norm_noalloc(int n, double eps, double theta, const d
   // the fine-level stencil of (n, eps, theta) into the scratch (the same setup kernel as mg_setup)
   setup_stencils_kernel<<<1, 32, 0, s>>>(theta, eps, n, 1, 0.8, sc + NA_OFF_COEF,
                                          reinterpret_cast<float*>(sc + NA_OFF_COEF32), sc + NA_OFF_ST,
-                                         sc + NA_OFF_DST);
+                                         sc + NA_OFF_DST, 0);
   residual_partials_fixed_grid_kernel<NT_VEC><<<NA_BLOCKS, NT_VEC, 0, s>>>(v, f, n, sc + NA_OFF_COEF,
                                                                           sc + NA_OFF_PART);
   sum_to_scalar_kernel<NT_VEC><<<1, NT_VEC, 0, s>>>(sc + NA_OFF_PART, NA_BLOCKS, sc + NA_OFF_RESULT);

@@ -673,17 +673,14 @@ __device__ inline void dd_cos_sin(double theta, double* c_out, double* s_out) {
 // operations (no contraction into fused multiply-adds) from correctly rounded cos and sin; each
 // Galerkin entry is a sum of exact products (the transfer weights are powers of two) accumulated
 // in double-double and rounded once; the coarse centre follows from the zero-row-sum identity.
-__global__ void setup_stencils_kernel(double theta, double eps, int n, int levels, double omega,
-                                      double* coef, float* coef32, double* stencils, double* dstencil) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double h = __ddiv_rn(1.0, (double)(n + 1));
+// Section 4 stencil on an m x m grid (h = 1/(m+1)) from correctly rounded C, S, as a fixed sequence
+// of correctly rounded operations.
+__device__ inline void section4_stencil(double C, double S, double eps, int m, double st[9]) {
+  const double h = __ddiv_rn(1.0, (double)(m + 1));
   const double h2 = __dmul_rn(h, h);
-  double C, S;
-  dd_cos_sin(theta, &C, &S);
   const double cross = __dmul_rn(__dmul_rn(__dmul_rn(0.5, __dsub_rn(1.0, eps)), C), S);  // ((0.5(1-eps))C)S
   const double we = -__dadd_rn(__dmul_rn(C, C), __dmul_rn(__dmul_rn(eps, S), S));       // -(CC + (eps S)S)
   const double ns = -__dadd_rn(__dmul_rn(__dmul_rn(eps, C), C), __dmul_rn(S, S));       // -((eps C)C + SS)
-  double st[9];
   st[4] = __dmul_rn(2.0, __dadd_rn(1.0, eps));
   st[3] = st[5] = we;
   st[1] = st[7] = ns;
@@ -692,6 +689,20 @@ __global__ void setup_stencils_kernel(double theta, double eps, int n, int level
   st[8] = -cross;  // NE
   st[0] = -cross;  // SW
   for (int q = 0; q < 9; ++q) st[q] = __ddiv_rn(st[q], h2);
+}
+
+// rediscretized != 0: coarse stencils are the Section 4 stencil on each coarse grid instead of
+// the Galerkin products.
+__global__ void setup_stencils_kernel(double theta, double eps, int n, int levels, double omega,
+                                      double* coef, float* coef32, double* stencils, double* dstencil,
+                                      int rediscretized) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double h = __ddiv_rn(1.0, (double)(n + 1));
+  const double h2 = __dmul_rn(h, h);
+  double C, S;
+  dd_cos_sin(theta, &C, &S);
+  double st[9];
+  section4_stencil(C, S, eps, n, st);
   // derivatives of the Section 4 entries with respect to theta and eps, scaled by 1/h^2
   {
     const double s2 = sin(2.0 * theta), c2 = cos(2.0 * theta);
@@ -737,6 +748,7 @@ __global__ void setup_stencils_kernel(double theta, double eps, int n, int level
       if (q != 4) off = __dadd_rn(off, sc[q]);
     sc[4] = -off;
     for (int q = 0; q < 9; ++q) st[q] = sc[q];
+    if (rediscretized) section4_stencil(C, S, eps, ((n + 1) >> (l + 1)) - 1, st);
   }
 }
 

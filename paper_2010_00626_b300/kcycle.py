@@ -20,6 +20,7 @@ MG_OK, MG_NOT_CONVERGED = 0, 1
 MG_KAPPA_W = 0x7FFFFFFF
 CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
 MG_OPT_OMEGA, MG_OPT_COARSE_N, MG_OPT_LEVELS, MG_OPT_N, MG_OPT_LAUNCHES, MG_OPT_COARSE_N32 = 1, 2, 3, 4, 5, 6
+MG_OPT_COARSE_OP, MG_OPT_STOP = 7, 8
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libkcycle.so is not built ({LIB_PATH}); run python -m paper_2010_00626_b300.build")

@@ -266,3 +266,29 @@ def test_large_solve_reaches_tolerance(lib):
     assert st == 0 and relres <= 1e-8
     assert all(b < a for a, b in zip(hist, hist[1:]))
     assert oracle.relres(h, to_np(vd), f) <= 1e-8 * (1 + 1e-6)
+
+
+def test_rediscretized_hierarchy_and_error_protocol(lib):
+    """Coarse operators rediscretized (Section 4 stencil at each coarse h): stencils bit for bit,
+    iterates to 1e-12; the error-reduction protocol (f = 0, random start, ||v_k|| / ||v_0||) gives
+    the oracle's cycle count and history."""
+    n, levels, theta, eps = 255, 8, math.pi / 4, 1e-3
+    h = oracle.Hierarchy(n, levels, theta, eps, coarse_op="rediscretized")
+    mg = lib.Multigrid(n, eps, theta, levels)
+    mg.set_option(lib.MG_OPT_COARSE_OP, 1)
+    st = mg.stencils()
+    for l in range(levels):
+        assert np.array_equal(st[l], h.stencils[l]), l
+    f = rhs_uniform(n, 3)
+    vd, v = torch_dev(np.zeros((n, n))), np.zeros((n, n))
+    for kappa in (1, 3, 9):
+        v = oracle.cycle(h, v, f, kappa)
+        mg.kcycle(vd, torch_dev(f), kappa)
+        assert rel(to_np(vd), v) <= ITER_TOL
+    v0 = np.random.default_rng(4).uniform(-1.0, 1.0, (n, n))
+    _, hist_or = oracle.solve_error_reduction(h, v0, 3, 1e-8, 2000)
+    mg.set_option(lib.MG_OPT_STOP, 1)
+    st_, cycles, red, hist = mg.solve(torch_dev(v0), torch_dev(np.zeros((n, n))), 3, 1e-8, 2000)
+    assert st_ == 0 and cycles == len(hist_or) and red <= 1e-8
+    for a, b in zip(hist, hist_or):
+        assert abs(a - b) <= HIST_TOL * b + ITER_TOL
