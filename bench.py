@@ -256,6 +256,10 @@ def main():
     ops, flops = dp_ops_per_point(0, cfg["nu1"], False)
     pts = n * n
     achieved_tflops = flops * pts / (dom_avg * 1e-3) / 1e12
+    # the FP64 pipe issues add, mul and fma at one rate: the ALU roofline counts FP64 operations
+    # against this device's measured FP64 operation rate (DFMA throughput probe, run live)
+    fp64_peak_ops = kcycle.fp64_rate()
+    achieved_ops = ops * pts / (dom_avg * 1e-3)
     bytes_alg = bytes_per_point(0, False) * pts
     peaks = {}
     try:
@@ -265,10 +269,11 @@ def main():
         pass
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     hbm_achieved = bytes_alg / (dom_avg * 1e-3) / 1e9
-    roofline = {"bound": "alu", "kernel": "pass_a level 0 (4095^2, FP64)", "achieved": achieved_tflops,
-                "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tflops / NOMINAL_FP64_TFLOPS,
-                "peak_source": "nominal FP64 rate (no FP64 figure in MEASURED_PEAKS.json)",
-                "fp64_instr_per_s": ops * pts / (dom_avg * 1e-3), "ms_per_launch": dom_avg,
+    roofline = {"bound": "alu", "kernel": "pass_a level 0 (4095^2, FP64)", "achieved": achieved_ops / 1e12,
+                "peak": fp64_peak_ops / 1e12, "unit": "T FP64 op/s", "frac": achieved_ops / fp64_peak_ops,
+                "peak_source": "measured live: FP64 FMA throughput probe (mg_fp64_rate); add/mul/fma count as one",
+                "algorithmic_ops_per_point": ops, "ms_per_launch": dom_avg,
+                "tflops_fma2": achieved_tflops, "frac_of_nominal_1.25_tflops": achieved_tflops / NOMINAL_FP64_TFLOPS,
                 "traffic": None,
                 "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
                         "algorithmic_bytes": bytes_alg}}

@@ -236,6 +236,11 @@ int mg_batch_solve(mg_batch b, double* const* x, const double* const* f, int kap
 int mg_batch_size(mg_batch b, int* count);
 int mg_batch_destroy(mg_batch b);
 
+/* Measured FP64 operation rate of the current device (fused multiply-adds per second, one add, mul
+ * or fma counting as one operation): the ALU peak the FP64 level kernels are reported against.
+ * A measurement hook with no counterpart in the paper. Synchronises the device. */
+int mg_fp64_rate(double* ops_per_second);
+
 /* Static string for a status code. */
 const char* mg_status_string(int status);
 

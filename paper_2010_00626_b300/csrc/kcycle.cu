@@ -148,7 +148,7 @@ template <int BX, int BY, int NT>
 struct TileCfg {
   static constexpr int bx = BX, by = BY, nt = NT;
 };
-using Tile64 = TileCfg<64, 64, NT_BIG>;
+using Tile64 = TileCfg<64, 48, NT_BIG>;  // 94 KB of FP64 shared memory: two CTAs per SM
 using Tile32 = TileCfg<32, 32, NT_SMALL>;
 using Tile16 = TileCfg<16, 16, NT_TINY>;
 using Tile8 = TileCfg<8, 8, NT_TINY>;
@@ -162,6 +162,7 @@ int tile_edge(int n) {
   }
   return 8;
 }
+int tile_rows(int n) { return tile_edge(n) == 64 ? 48 : tile_edge(n); }
 
 template <typename Cfg, typename T>
 int launch_pass_a(const PassAArgs<T>& a, cudaStream_t s) {
@@ -203,8 +204,7 @@ int set_all_smem_attrs() {
 }
 
 size_t pass_grid_blocks(int n) {
-  const size_t g = (n + tile_edge(n) - 1) / tile_edge(n);
-  return g * g;
+  return (size_t)((n + tile_edge(n) - 1) / tile_edge(n)) * (size_t)((n + tile_rows(n) - 1) / tile_rows(n));
 }
 
 size_t apply_grid_blocks(int n) {
@@ -1244,6 +1244,31 @@ int mg_profile_cycle(mg_handle h, double* v, const double* f, int kappa, int wit
   for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
   h->pev.clear();
   return result;
+}
+
+int mg_fp64_rate(double* ops_per_second) {
+  if (!ops_per_second) return MG_ERR_ARG;
+  int dev = 0, sms = 0;
+  KC_CUDA(cudaGetDevice(&dev));
+  KC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  double* sink = nullptr;
+  KC_CUDA(cudaMalloc(&sink, sizeof(double)));
+  cudaEvent_t e0, e1;
+  KC_CUDA(cudaEventCreate(&e0));
+  KC_CUDA(cudaEventCreate(&e1));
+  const int blocks = sms * 8, threads = 256, iters = 4000;
+  fp64_rate_kernel<<<blocks, threads>>>(sink, 10, 0.999, 1e-3);  // warm-up
+  KC_CUDA(cudaEventRecord(e0));
+  fp64_rate_kernel<<<blocks, threads>>>(sink, iters, 0.999, 1e-3);
+  KC_CUDA(cudaEventRecord(e1));
+  KC_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  KC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  *ops_per_second = (double)blocks * threads * iters * 8 / (ms * 1e-3);
+  return MG_OK;
 }
 
 }  // extern "C"

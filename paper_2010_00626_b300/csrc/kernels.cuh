@@ -1055,6 +1055,22 @@ __global__ void __launch_bounds__(NT) convert_kernel(D* y, int ldy, const S* x, 
   if (i < n && j < n) y[(size_t)j * ldy + i] = (D)x[(size_t)j * ldx + i];
 }
 
+// Throughput probe of the FP64 pipe: 8 independent chains of dependent fused multiply-adds per
+// thread (the result is consumed so the work cannot be removed).
+__global__ void fp64_rate_kernel(double* sink, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-3 + k;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  if (s == 12345.678) sink[0] = s;  // never true for these inputs
+}
+
 __global__ void reset_state_kernel(int* ints, int max_iters, double* scal, double tol) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     ints[I_DONE] = 0;

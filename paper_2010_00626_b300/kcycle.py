@@ -62,6 +62,7 @@ SIGNATURES = {
     "mg_batch_solve": (_i, [_h, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, _d, _i, _i, _ip, _dp]),
     "mg_batch_size": (_i, [_h, _ip]),
     "mg_batch_destroy": (_i, [_h]),
+    "mg_fp64_rate": (_i, [_dp]),
     "mg_status_string": (ctypes.c_char_p, [_i]),
     "mg_last_error": (ctypes.c_char_p, []),
 }
@@ -73,6 +74,13 @@ for _name, (_res, _args) in SIGNATURES.items():
 
 class MultigridError(RuntimeError):
     pass
+
+
+def fp64_rate():
+    """Measured FP64 operations per second of the current device (mg_fp64_rate)."""
+    out = ctypes.c_double()
+    _check(_lib.mg_fp64_rate(ctypes.byref(out)), "mg_fp64_rate")
+    return out.value
 
 
 def _check(status: int, what: str) -> int:
