@@ -37,7 +37,7 @@ import scipy.linalg
 
 __all__ = [
     "cos_sin", "fine_stencil", "fine_stencil_derivatives", "apply_stencil", "restrict_fw",
-    "prolong_bilinear", "galerkin_stencil", "zero_row_sum_centre", "jacobi", "Hierarchy", "CallRecorder",
+    "prolong_bilinear", "galerkin_stencil", "zero_row_sum_centre", "jacobi", "zebra_lines", "relax", "Hierarchy", "CallRecorder",
     "kcycle", "gamma_cycle", "f_cycle", "kcycle_adjoint", "cycle", "cycle_adjoint",
     "residual", "relres", "solve", "solve_error_reduction", "pcg", "param_grads", "level_sizes",
 ]
@@ -245,6 +245,46 @@ def jacobi(st: np.ndarray, v: np.ndarray, f: np.ndarray, omega: float, sweeps: i
     return v
 
 
+def zebra_lines(st: np.ndarray, v: np.ndarray, f: np.ndarray, axis: str) -> np.ndarray:
+    """One zebra line Gauss-Seidel relaxation (Section 4, solvers 3-4): every line is solved
+    exactly with its neighbouring lines held fixed, lines of even index first, then lines of odd
+    index (using the new even lines). axis 'x': the lines are rows j (unknowns coupled through the
+    west/east entries, a tridiagonal system); axis 'y': the lines are columns i (south/north).
+    Off-line stencil entries move to the right-hand side with the current neighbouring values."""
+    v = v.copy()
+    n = v.shape[0]
+    work = v if axis == "x" else v.T                 # work[line, position]
+    rhs_f = f if axis == "x" else f.T
+    # stencil as seen along the line: s[dl, dp] multiplies work[line+dl, pos+dp]
+    s = st if axis == "x" else st.T
+    ab = np.zeros((3, n))                            # banded storage for solve_banded
+    ab[0, 1:] = s[1, 2]                              # upper diagonal (position +1)
+    ab[1, :] = s[1, 1]                               # diagonal
+    ab[2, :-1] = s[1, 0]                             # lower diagonal (position -1)
+    for parity in (0, 1):
+        lines = np.arange(parity, n, 2)
+        padded = np.zeros((n + 2, n + 2))
+        padded[1:-1, 1:-1] = work
+        rhs = rhs_f[lines].copy()
+        for dl in (-1, 1):
+            for dp in (-1, 0, 1):
+                rhs -= s[1 + dl, 1 + dp] * padded[lines + 1 + dl, 1 + dp:1 + dp + n]
+        work[lines] = scipy.linalg.solve_banded((1, 1), ab, rhs.T).T
+    return v
+
+
+def relax(h: "Hierarchy", level: int, v: np.ndarray, f: np.ndarray, sweeps: int) -> np.ndarray:
+    """The hierarchy's smoother: damped Jacobi, or alternating zebra line relaxation where the
+    k-th relaxation runs along x for odd k and along y for even k (so two relaxations are one
+    in each direction, x first, as in Section 4)."""
+    st = h.stencil(level)
+    if h.smoother == "jacobi":
+        return jacobi(st, v, f, h.omega, sweeps)
+    for k in range(sweeps):
+        v = zebra_lines(st, v, f, "x" if k % 2 == 0 else "y")
+    return v
+
+
 def level_sizes(n: int, levels: int):
     """Grid side per level, finest first: n, (n-1)/2, ... (Table 3: N = (2^n - 1)^2)."""
     sizes = [n]
@@ -268,6 +308,7 @@ class Hierarchy:
     nu2: int = 2
     omega: float = 0.8
     coarse_op: str = "galerkin"   # or "rediscretized": the Section 4 stencil on each coarse grid
+    smoother: str = "jacobi"      # or "zebra": alternating zebra line Gauss-Seidel
     stencils: list = field(default_factory=list)
     sizes: list = field(default_factory=list)
     _chol: object = None
@@ -276,6 +317,8 @@ class Hierarchy:
         k = int(round(math.log2(self.n + 1)))
         if self.n < 1 or (1 << k) - 1 != self.n or not (1 <= self.levels <= k):
             raise ValueError("n must be 2^k - 1 and 1 <= levels <= k")
+        if self.smoother not in ("jacobi", "zebra"):
+            raise ValueError("smoother must be 'jacobi' or 'zebra'")
         self.sizes = level_sizes(self.n, self.levels)
         st = fine_stencil(self.theta, self.eps, self.n)
         self.stencils = [st]
@@ -333,14 +376,14 @@ def kcycle(h: Hierarchy, level: int, v: np.ndarray, f: np.ndarray, kappa: int,
     if last:                                              # coarsest: solve and return
         return h.coarsest_solve(f)
     st = h.stencil(level)
-    v = jacobi(st, v, f, h.omega, h.nu1)                  # relax nu1 times
+    v = relax(h, level, v, f, h.nu1)                      # relax nu1 times
     fc = restrict_fw(f - apply_stencil(st, v))            # restrict the residual
     vc = np.zeros_like(fc)                                # v^{l+1} <- 0
     vc = kcycle(h, level + 1, vc, fc, kappa, rec)         # call with counter kappa
     if kappa > 1:
         vc = kcycle(h, level + 1, vc, fc, kappa - 1, rec)  # then with kappa - 1
     v = v + prolong_bilinear(vc)                           # coarse-grid correction
-    v = jacobi(st, v, f, h.omega, h.nu2)                   # relax nu2 times
+    v = relax(h, level, v, f, h.nu2)                       # relax nu2 times
     return v
 
 
@@ -349,13 +392,13 @@ def gamma_cycle(h: Hierarchy, level: int, v: np.ndarray, f: np.ndarray, gamma: i
     if level == h.levels:
         return h.coarsest_solve(f)
     st = h.stencil(level)
-    v = jacobi(st, v, f, h.omega, h.nu1)
+    v = relax(h, level, v, f, h.nu1)
     fc = restrict_fw(f - apply_stencil(st, v))
     vc = np.zeros_like(fc)
     for _ in range(gamma):
         vc = gamma_cycle(h, level + 1, vc, fc, gamma)
     v = v + prolong_bilinear(vc)
-    return jacobi(st, v, f, h.omega, h.nu2)
+    return relax(h, level, v, f, h.nu2)
 
 
 def f_cycle(h: Hierarchy, level: int, v: np.ndarray, f: np.ndarray) -> np.ndarray:
@@ -363,13 +406,13 @@ def f_cycle(h: Hierarchy, level: int, v: np.ndarray, f: np.ndarray) -> np.ndarra
     if level == h.levels:
         return h.coarsest_solve(f)
     st = h.stencil(level)
-    v = jacobi(st, v, f, h.omega, h.nu1)
+    v = relax(h, level, v, f, h.nu1)
     fc = restrict_fw(f - apply_stencil(st, v))
     vc = np.zeros_like(fc)
     vc = f_cycle(h, level + 1, vc, fc)
     vc = gamma_cycle(h, level + 1, vc, fc, 1)
     v = v + prolong_bilinear(vc)
-    return jacobi(st, v, f, h.omega, h.nu2)
+    return relax(h, level, v, f, h.nu2)
 
 
 def kcycle_adjoint(h: Hierarchy, level: int, v: np.ndarray, f: np.ndarray, kappa: int) -> np.ndarray:
@@ -379,7 +422,10 @@ def kcycle_adjoint(h: Hierarchy, level: int, v: np.ndarray, f: np.ndarray, kappa
     error propagator swaps the pre- and post-smoothing counts and reverses the order of
     the two coarse calls: the call with counter kappa-1 runs first (from zero), then the
     call with counter kappa. Pinned by the dot-product test <x, B y> = <B^T x, y>.
+    Damped Jacobi only (the transposed zebra smoother would also reverse its line order).
     """
+    if h.smoother != "jacobi":
+        raise ValueError("the adjoint cycle is defined for the damped-Jacobi smoother")
     if level == h.levels:
         return h.coarsest_solve(f)
     st = h.stencil(level)

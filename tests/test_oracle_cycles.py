@@ -214,3 +214,96 @@ def test_rediscretized_hierarchy_and_error_protocol():
     assert np.isclose(np.linalg.norm(w) / np.linalg.norm(v0), hist[2], rtol=1e-14)
     with pytest.raises(ValueError):
         oracle.Hierarchy(15, 3, 0.1, 0.1, coarse_op="other")
+
+
+def _zebra_brute(st, v, f, axis):
+    """Line Gauss-Seidel in zebra order with explicit loops and a dense solve per line."""
+    n = v.shape[0]
+    v = v.copy()
+    for parity in (0, 1):
+        for L in range(parity, n, 2):
+            A = np.zeros((n, n))
+            b = np.zeros(n)
+            for p in range(n):
+                i, j = (p, L) if axis == "x" else (L, p)
+                b[p] = f[j, i]
+                for dy in (-1, 0, 1):
+                    for dx in (-1, 0, 1):
+                        ii, jj = i + dx, j + dy
+                        if not (0 <= ii < n and 0 <= jj < n):
+                            continue
+                        on_line = (jj == L) if axis == "x" else (ii == L)
+                        if on_line:
+                            A[p, ii if axis == "x" else jj] += st[1 + dy, 1 + dx]
+                        else:
+                            b[p] -= st[1 + dy, 1 + dx] * v[jj, ii]
+            x = np.linalg.solve(A, b)
+            for p in range(n):
+                if axis == "x":
+                    v[L, p] = x[p]
+                else:
+                    v[p, L] = x[p]
+    return v
+
+
+@pytest.mark.parametrize("axis", ["x", "y"])
+def test_zebra_lines_match_brute_force_and_zero_last_residual(axis):
+    n = 15
+    st = oracle.galerkin_stencil(oracle.fine_stencil(0.7, 1e-3, 31))  # a general 9-point stencil
+    rng = np.random.default_rng(8)
+    v, f = rng.standard_normal((2, n, n))
+    got = oracle.zebra_lines(st, v, f, axis)
+    ref = _zebra_brute(st, v, f, axis)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.abs(ref).max()
+    r = oracle.residual(st, got, f)
+    odd = r[1::2, :] if axis == "x" else r[:, 1::2]  # the lines solved last satisfy their equations
+    assert np.max(np.abs(odd)) <= 1e-12 * np.abs(f).max() * np.abs(st).sum()
+
+
+def test_zebra_cycles_solve_grid_aligned_anisotropy():
+    """theta = 0, eps = 1e-4: strong coupling along x. Zebra kappa-cycles reach the dense solution
+    quickly; damped point Jacobi cycles stall (the case Section 4 uses line relaxation for)."""
+    n, levels = 31, 5
+    hz = oracle.Hierarchy(n, levels, 0.0, 1e-4, smoother="zebra")
+    hj = oracle.Hierarchy(n, levels, 0.0, 1e-4)
+    f = rhs_uniform(n, 11)
+    vz, histz = oracle.solve(hz, f, 2, 1e-10, 200)
+    vj, histj = oracle.solve(hj, f, 2, 1e-10, 200)
+    assert histz[-1] <= 1e-10 and len(histz) < 40
+    assert len(histj) > 3 * len(histz)
+    A = dense_matrix_of(hz)
+    exact = scipy.linalg.solve(A, f.ravel(), assume_a="pos").reshape(n, n)
+    assert np.linalg.norm(vz - exact) <= 1e-9 * np.linalg.norm(exact)
+
+
+@pytest.mark.parametrize("axis", ["x", "y"])
+def test_zebra_exact_when_lines_decouple(axis):
+    """With no coupling between lines (a 1-D operator along the lines), one relaxation along the
+    lines is the exact solve, whatever the starting guess."""
+    n = 31
+    st = np.zeros((3, 3))
+    st[1, 1], st[1, 0], st[1, 2] = 2.3, -1.0, -1.0
+    if axis == "y":
+        st = st.T.copy()
+    rng = np.random.default_rng(12)
+    v0, f = rng.standard_normal((2, n, n))
+    got = oracle.zebra_lines(st, v0, f, axis)
+    T = np.diag(np.full(n, 2.3)) - np.diag(np.ones(n - 1), 1) - np.diag(np.ones(n - 1), -1)
+    exact = np.linalg.solve(T, f.T).T if axis == "x" else np.linalg.solve(T, f)
+    assert np.max(np.abs(got - exact)) <= 1e-13 * np.abs(exact).max()
+
+
+def test_zebra_two_relaxations_are_one_per_direction():
+    """nu = 2 is an x relaxation followed by a y relaxation (Section 4's alternating form)."""
+    n, levels = 15, 3
+    h = oracle.Hierarchy(n, levels, 0.4, 1e-3, smoother="zebra")
+    rng = np.random.default_rng(13)
+    v, f = rng.standard_normal((2, n, n))
+    st = h.stencil(1)
+    both = oracle.relax(h, 1, v, f, 2)
+    manual = oracle.zebra_lines(st, oracle.zebra_lines(st, v, f, "x"), f, "y")
+    assert np.array_equal(both, manual)
+    with pytest.raises(ValueError):
+        oracle.Hierarchy(n, levels, 0.4, 1e-3, smoother="sor")
+    with pytest.raises(ValueError):
+        oracle.cycle_adjoint(h, v, f, 2)
