@@ -61,8 +61,14 @@ typedef enum {
   MG_OPT_COARSE_N32 = 6,   /* as MG_OPT_COARSE_N for the FP32 cycles of the mixed forms; default 63  */
   MG_OPT_COARSE_OP = 7,    /* coarse operators: 0 Galerkin R A P (default), 1 the Section 4 stencil
                               rediscretized on each coarse grid                                     */
-  MG_OPT_STOP = 8          /* mg_solve's stopping test: 0 ||f - A v||/||f|| <= tol (default);
+  MG_OPT_STOP = 8,         /* mg_solve's stopping test: 0 ||f - A v||/||f|| <= tol (default);
                               1 ||v_k||/||v_0|| <= tol, the error reduction of Section 4 when f = 0  */
+  MG_OPT_SMOOTHER = 9      /* relaxation: 0 damped Jacobi (default); 1 alternating zebra line
+                              Gauss-Seidel (Section 4, solvers 3-4): the k-th relaxation of a
+                              smoothing step solves every row (k odd: x) or every column (k even: y)
+                              exactly, even-indexed lines first, then odd-indexed ones, with no
+                              damping; nu1 = nu2 = 2 is one relaxation in each direction. The
+                              adjoint entry points return MG_ERR_ARG under this smoother.       */
 } mg_option;
 
 /* Set up the hierarchy for the Section 4 problem on an n x n interior grid.

@@ -23,6 +23,7 @@
 
 #include "../../include/kcycle.h"
 #include "kernels.cuh"
+#include "lines.cuh"
 #include "stream_f32.cuh"
 
 using namespace kc;
@@ -122,6 +123,10 @@ struct mg_ctx {
   int ld32_0 = 0;       // pitch of the FP32 level-0 arrays (multiple of 32 floats)
   int rediscretized = 0;  // coarse operators: 0 Galerkin, 1 the Section 4 stencil on each coarse grid
   int stop_rule = 0;      // 0: ||f - A v|| / ||f|| <= tol; 1: ||v_k|| / ||v_0|| <= tol (f = 0 protocol)
+  int smoother = 0;       // 0 damped Jacobi, 1 alternating zebra line Gauss-Seidel
+  double* ltab = nullptr;  // line-solve tables (Thomas factors and chunk products) per level/direction
+  float* ltab32 = nullptr;
+  double* linv = nullptr;  // dense line inverses of the levels with side <= LINV_MAX
   double *pr = nullptr, *pp = nullptr, *pq = nullptr, *pz = nullptr, *pzold = nullptr;  // PCG vectors
   double *hv = nullptr, *hf = nullptr;  // device copies for mg_solve_host
   cudaStream_t own = nullptr;
@@ -192,14 +197,32 @@ int set_smem_attrs() {
   return MG_OK;
 }
 
+constexpr int LINE_R = 4;  // lines per CTA of the zebra line kernels
+
+template <typename T, int MC>
+int set_line_attrs() {
+  KC_CUDA(cudaFuncSetAttribute(line_relax_kernel<T, 0, LINE_R, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)line_smem<T, LINE_R, MC>()));
+  KC_CUDA(cudaFuncSetAttribute(line_relax_kernel<T, 1, LINE_R, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)line_smem<T, LINE_R, MC>()));
+  return MG_OK;
+}
+
 template <typename T>
 int set_all_smem_attrs() {
   KC_TRY((set_smem_attrs<Tile64, T>()));
   KC_TRY((set_smem_attrs<Tile32, T>()));
   KC_TRY((set_smem_attrs<Tile16, T>()));
   KC_TRY((set_smem_attrs<Tile8, T>()));
-  KC_CUDA(cudaFuncSetAttribute(coarse_kernel<T, nt_coarse<T>()>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  KC_CUDA(cudaFuncSetAttribute(coarse_kernel<T, nt_coarse<T>(), false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)coarse_smem<T>(MAX_COARSE_N, 6)));
+  KC_CUDA(cudaFuncSetAttribute(coarse_kernel<T, nt_coarse<T>(), true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)coarse_smem<T>(MAX_COARSE_N, 6)));
+  KC_TRY((set_line_attrs<T, 1>()));
+  KC_TRY((set_line_attrs<T, 2>()));
+  KC_TRY((set_line_attrs<T, 4>()));
+  KC_TRY((set_line_attrs<T, 8>()));
+  KC_TRY((set_line_attrs<T, 16>()));
   return MG_OK;
 }
 
@@ -223,6 +246,7 @@ struct Arr<double> {
   static double* tmp(mg_ctx* h, int l) { return h->lv[l].tmp; }
   static double* f(mg_ctx* h, int l) { return h->lv[l].f; }
   static const double* coef(mg_ctx* h) { return h->coef; }
+  static const double* ltab(mg_ctx* h) { return h->ltab; }
   static int ld(mg_ctx* h, int l) { return h->lv[l].ld; }
 };
 template <>
@@ -231,6 +255,7 @@ struct Arr<float> {
   static float* tmp(mg_ctx* h, int l) { return h->lv[l].tmp32; }
   static float* f(mg_ctx* h, int l) { return h->lv[l].f32; }
   static const float* coef(mg_ctx* h) { return h->coef32; }
+  static const float* ltab(mg_ctx* h) { return h->ltab32; }
   static int ld(mg_ctx* h, int l) { return l == 0 ? h->ld32_0 : h->lv[l].ld; }
 };
 
@@ -244,7 +269,7 @@ const T* lv_f(mg_ctx* h, const BindingT<T>& b, int l) { return l == 0 ? b.f0 : A
 template <typename T>
 int lv_ld(mg_ctx* h, const BindingT<T>& b, int l) { return l == 0 ? b.ld0 : Arr<T>::ld(h, l); }
 
-enum { K_PASS_A = 0, K_PASS_B = 1, K_COARSE = 2, K_APPLY = 3 };
+enum { K_PASS_A = 0, K_PASS_B = 1, K_COARSE = 2, K_APPLY = 3, K_LINES_X = 4, K_LINES_Y = 5 };
 
 void prof_begin(mg_ctx* h, int kind, int level, cudaStream_t s) {
   if (!h->prof) return;
@@ -314,20 +339,30 @@ int emit_coarse(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int zero1, bool
   a.k2 = k2;
   a.zero1 = zero1;
   a.adjoint = adjoint ? 1 : 0;
+  a.ltab = h->smoother == 1 ? Arr<T>::ltab(h) : nullptr;
+  a.linv = (h->smoother == 1 && std::is_same<T, double>::value) ? h->linv : nullptr;
+  a.k = h->k;
   const size_t sm = coarse_smem<T>(a.n_lc, a.L - a.lc);
   prof_begin(h, K_COARSE, lc, s);
-  coarse_kernel<T, nt_coarse<T>()><<<1, nt_coarse<T>(), sm, s>>>(a);
+  if (a.ltab)
+    coarse_kernel<T, nt_coarse<T>(), true><<<1, nt_coarse<T>(), sm, s>>>(a);
+  else
+    coarse_kernel<T, nt_coarse<T>(), false><<<1, nt_coarse<T>(), sm, s>>>(a);
   prof_end(h, s);
   KC_CUDA(cudaGetLastError());
   ++h->launch_count;
   return MG_OK;
 }
 
+// With `lines` (zebra smoothing done in place by the line kernels) pass A only restricts the
+// residual of the level's v: no relaxation and no copy of v.
 template <typename T>
-int emit_pass_a(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const int* skip, cudaStream_t s) {
+int emit_pass_a(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const int* skip, cudaStream_t s,
+                bool lines = false) {
   PassAArgs<T> a;
   a.vin = zero ? nullptr : lv_v(h, b, l);
-  a.vout = Arr<T>::tmp(h, l);
+  // lines mode from a zero start without pre-relaxation: v is written (as zero) for the post-smoothing
+  a.vout = lines ? (zero ? lv_v(h, b, l) : nullptr) : Arr<T>::tmp(h, l);
   a.f = lv_f(h, b, l);
   a.fc = Arr<T>::f(h, l + 1);
   a.coef = Arr<T>::coef(h);
@@ -343,7 +378,8 @@ int emit_pass_a(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const
   prof_begin(h, K_PASS_A, l, s);
   int st;
   if constexpr (std::is_same<T, float>::value) {
-    if (stream_ok(a.n, nu, a.vin, a.ldvin) && stream_ok(a.n, nu, a.f, a.ldf) && stream_ok(a.n, nu, a.vout, a.ldvout) &&
+    if (!lines && stream_ok(a.n, nu, a.vin, a.ldvin) && stream_ok(a.n, nu, a.f, a.ldf) &&
+        stream_ok(a.n, nu, a.vout, a.ldvout) &&
         ((uintptr_t)a.fc & 7) == 0 && (a.ldc & 1) == 0) {
       st = launch_pass_a_stream(a, s);
       prof_end(h, s);
@@ -360,10 +396,12 @@ int emit_pass_a(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const
   return st;
 }
 
+// With `lines` pass B only adds the prolonged correction to the level's v, in place.
 template <typename T>
-int emit_pass_b(mg_ctx* h, const BindingT<T>& b, int l, int nu, double* partial, const int* skip, cudaStream_t s) {
+int emit_pass_b(mg_ctx* h, const BindingT<T>& b, int l, int nu, double* partial, const int* skip, cudaStream_t s,
+                bool lines = false) {
   PassBArgs<T> a;
-  a.vin = Arr<T>::tmp(h, l);
+  a.vin = lines ? lv_v(h, b, l) : Arr<T>::tmp(h, l);
   a.vout = lv_v(h, b, l);
   a.f = lv_f(h, b, l);
   a.vc = Arr<T>::v(h, l + 1);
@@ -381,7 +419,7 @@ int emit_pass_b(mg_ctx* h, const BindingT<T>& b, int l, int nu, double* partial,
   prof_begin(h, K_PASS_B, l, s);
   int st;
   if constexpr (std::is_same<T, float>::value) {
-    if (partial == nullptr && stream_ok(a.n, nu, a.vin, a.ldvin) && stream_ok(a.n, nu, a.f, a.ldf) &&
+    if (!lines && partial == nullptr && stream_ok(a.n, nu, a.vin, a.ldvin) && stream_ok(a.n, nu, a.f, a.ldf) &&
         stream_ok(a.n, nu, a.vout, a.ldvout) && ((uintptr_t)a.vc & 7) == 0 && (a.ldc & 1) == 0) {
       st = launch_pass_b_stream(a, s);
       prof_end(h, s);
@@ -396,6 +434,66 @@ int emit_pass_b(mg_ctx* h, const BindingT<T>& b, int l, int nu, double* partial,
   }
   prof_end(h, s);
   return st;
+}
+
+int emit_apply(mg_ctx* h, const double* v, const double* f, double* out, double* partial, const int* skip,
+               cudaStream_t s) {
+  const int n = h->n;
+  dim3 grid((n + 31) / 32, (n + NT_VEC / 32 - 1) / (NT_VEC / 32));
+  prof_begin(h, K_APPLY, 0, s);
+  apply_kernel<double, NT_VEC><<<grid, NT_VEC, 0, s>>>(v, f, out, h->coef, 0, n, n, partial, skip);
+  prof_end(h, s);
+  KC_CUDA(cudaGetLastError());
+  ++h->launch_count;
+  return MG_OK;
+}
+
+template <typename T, int DIR>
+int launch_lines(const LineArgs<T>& a, cudaStream_t s) {
+  const int nl = (a.n - a.colour + 1) / 2;
+  const int blocks = (nl + LINE_R - 1) / LINE_R;
+  switch (line_chunk(a.n)) {
+    case 16: line_relax_kernel<T, DIR, LINE_R, 16><<<blocks, 32 * LINE_R, line_smem<T, LINE_R, 16>(), s>>>(a); break;
+    case 8: line_relax_kernel<T, DIR, LINE_R, 8><<<blocks, 32 * LINE_R, line_smem<T, LINE_R, 8>(), s>>>(a); break;
+    case 4: line_relax_kernel<T, DIR, LINE_R, 4><<<blocks, 32 * LINE_R, line_smem<T, LINE_R, 4>(), s>>>(a); break;
+    case 2: line_relax_kernel<T, DIR, LINE_R, 2><<<blocks, 32 * LINE_R, line_smem<T, LINE_R, 2>(), s>>>(a); break;
+    default: line_relax_kernel<T, DIR, LINE_R, 1><<<blocks, 32 * LINE_R, line_smem<T, LINE_R, 1>(), s>>>(a); break;
+  }
+  KC_CUDA(cudaGetLastError());
+  return MG_OK;
+}
+
+// `sweeps` zebra relaxations of level l in place: the k-th (from 0) along x for even k, along y for
+// odd k, each colour 0 then colour 1. From a zero start the first half-sweep sees zero neighbours.
+// With vc (post-smoothing) the first launch reads its neighbouring rows as v + P vc, which folds the
+// coarse-grid correction into it: every line is then solved before its own old value is needed.
+template <typename T>
+int emit_lines(mg_ctx* h, const BindingT<T>& b, int l, int sweeps, bool zero, const int* skip, cudaStream_t s,
+               const T* vc = nullptr, int ldc = 0) {
+  LineArgs<T> a;
+  a.ldc = ldc;
+  a.v = lv_v(h, b, l);
+  a.f = lv_f(h, b, l);
+  a.coef = Arr<T>::coef(h);
+  a.skip = skip;
+  a.n = h->lv[l].n;
+  a.ld = lv_ld(h, b, l);
+  a.level = l;
+  for (int k = 0; k < sweeps; ++k) {
+    const int dir = k & 1;
+    a.tab = Arr<T>::ltab(h) + line_tab_offset(h->k, l, dir);
+    for (int colour = 0; colour < 2; ++colour) {
+      a.colour = colour;
+      a.zero = (zero && k == 0 && colour == 0) ? 1 : 0;
+      a.vc = (k == 0 && colour == 0) ? vc : nullptr;
+      ++h->launch_count;
+      prof_begin(h, dir == 0 ? K_LINES_X : K_LINES_Y, l, s);
+      const int st = dir == 0 ? launch_lines<T, 0>(a, s) : launch_lines<T, 1>(a, s);
+      prof_end(h, s);
+      KC_TRY(st);
+    }
+  }
+  return MG_OK;
 }
 
 // Counters of the two coarse calls made by a call with counter kappa (Algorithm 3); the adjoint
@@ -416,7 +514,13 @@ int emit_call(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero, bool
               const int* skip, cudaStream_t s) {
   const int nu_pre = adjoint ? h->nu2 : h->nu1;
   const int nu_post = adjoint ? h->nu1 : h->nu2;
-  KC_TRY(emit_pass_a(h, b, l, zero, nu_pre, skip, s));
+  const bool lines = h->smoother == 1;
+  if (lines && nu_pre > 0) {
+    KC_TRY(emit_lines(h, b, l, nu_pre, zero, skip, s));
+    KC_TRY(emit_pass_a(h, b, l, false, 0, skip, s, true));
+  } else {
+    KC_TRY(emit_pass_a(h, b, l, zero, lines ? 0 : nu_pre, skip, s, lines));
+  }
   int k1, k2;
   child_counters(kappa, adjoint, &k1, &k2);
   if (l + 1 >= lc_of<T>(h)) {
@@ -425,20 +529,22 @@ int emit_call(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero, bool
     KC_TRY(emit_call(h, b, l + 1, k1, true, adjoint, false, skip, s));
     if (k2 > 0) KC_TRY(emit_call(h, b, l + 1, k2, false, adjoint, false, skip, s));
   }
-  return emit_pass_b(h, b, l, nu_post, norm && l == 0 ? h->partial : nullptr, skip, s);
-}
-
-int emit_apply(mg_ctx* h, const double* v, const double* f, double* out, double* partial, const int* skip,
-               cudaStream_t s) {
-  const int n = h->n;
-  dim3 grid((n + 31) / 32, (n + NT_VEC / 32 - 1) / (NT_VEC / 32));
-  prof_begin(h, K_APPLY, 0, s);
-  apply_kernel<double, NT_VEC><<<grid, NT_VEC, 0, s>>>(v, f, out, h->coef, 0, n, n, partial, skip);
-  prof_end(h, s);
-  KC_CUDA(cudaGetLastError());
-  ++h->launch_count;
+  if (!lines) return emit_pass_b(h, b, l, nu_post, norm && l == 0 ? h->partial : nullptr, skip, s);
+  if (nu_post > 0) {
+    KC_TRY(emit_lines(h, b, l, nu_post, false, skip, s, Arr<T>::v(h, l + 1), Arr<T>::ld(h, l + 1)));
+  } else {
+    KC_TRY(emit_pass_b(h, b, l, 0, nullptr, skip, s, true));
+  }
+  if (norm && l == 0) {
+    if constexpr (std::is_same<T, double>::value) {
+      KC_TRY(emit_apply(h, b.v0, b.f0, nullptr, h->partial, skip, s));
+    } else {
+      return MG_ERR_ARG;
+    }
+  }
   return MG_OK;
 }
+
 
 // One finest-level cycle. With norm (FP64 only), the last pass writes residual partial sums (or,
 // when the coarse kernel handles level 0, a separate residual pass does).
@@ -459,7 +565,9 @@ int emit_cycle(mg_ctx* h, const BindingT<T>& b, int kappa, bool zero, bool adjoi
   return emit_call(h, b, 0, kappa, zero, adjoint, norm, skip, s);
 }
 
-int norm_partials(mg_ctx* h) { return (int)(h->lc == 0 ? apply_grid_blocks(h->n) : pass_grid_blocks(h->n)); }
+int norm_partials(mg_ctx* h) {
+  return (int)((h->lc == 0 || h->smoother == 1) ? apply_grid_blocks(h->n) : pass_grid_blocks(h->n));
+}
 
 // ------------------------------------------------------------------------------------------
 // Graph cache
@@ -658,6 +766,7 @@ int solve_impl(mg_handle h, double* v, const double* f, int kappa, double tol, i
                double* final_relres, double* history, bool adjoint = false) {
   if (!valid_handle(h)) return MG_ERR_STATE;
   if (!v || !f || kappa < 1 || !(tol > 0) || max_cycles < 1) return MG_ERR_ARG;
+  if (adjoint && h->smoother == 1) return MG_ERR_ARG;
   trim_graphs(h);
   KC_TRY(ensure_hist(h, max_cycles));
   cudaStream_t s = h->stream();
@@ -763,6 +872,8 @@ int run_setup_kernels(mg_ctx* h) {
   setup_stencils_kernel<<<1, 32, 0, h->own>>>(h->theta, h->eps, h->n, h->levels, h->omega, h->coef, h->coef32,
                                              h->stencils, h->dstencil, h->rediscretized);
   KC_CUDA(cudaGetLastError());
+  line_tables_kernel<<<1, 32, 0, h->own>>>(h->coef, h->k, h->levels, h->ltab, h->ltab32, h->linv);
+  KC_CUDA(cudaGetLastError());
   const int nc = h->lv[h->levels - 1].n;
   if (nc > 1) {
     coarsest_inverse_kernel<<<1, 256, 0, h->own>>>(h->stencils, h->levels - 1, nc, h->work, h->cinv, h->cinv32);
@@ -799,7 +910,7 @@ int mg_destroy(mg_handle h) {
   if (h->own) cudaStreamSynchronize(h->own);
   drop_graphs(h);
   free_levels(h);
-  void* ptrs[] = {h->coef, h->coef32, h->stencils, h->dstencil, h->cinv, h->cinv32, h->work, h->partial,
+  void* ptrs[] = {h->coef, h->coef32, h->stencils, h->dstencil, h->ltab, h->ltab32, h->linv, h->cinv, h->cinv32, h->work, h->partial,
                   h->partial2, h->scal, h->ints, h->hist, h->pr, h->pp, h->pq, h->pz, h->pzold, h->hv, h->hf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -841,6 +952,9 @@ int mg_setup(int n, double eps, double theta, int levels, int nu1, int nu2, mg_h
   ALLOC(h->coef32, sizeof(float) * MAXL * NCOEF);
   ALLOC(h->stencils, sizeof(double) * MAXL * 9);
   ALLOC(h->dstencil, sizeof(double) * 18);
+  ALLOC(h->ltab, sizeof(double) * line_tab_size(k, levels));
+  ALLOC(h->ltab32, sizeof(float) * line_tab_size(k, levels));
+  ALLOC(h->linv, sizeof(double) * std::max<size_t>(1, line_inv_offset(k, levels, 0)));
   ALLOC(h->partial, sizeof(double) * np);
   ALLOC(h->partial2, sizeof(double) * np);
   ALLOC(h->scal, sizeof(double) * NSCAL);
@@ -883,6 +997,13 @@ int mg_set_option(mg_handle h, int key, double value) {
       drop_graphs(h);
       return MG_OK;
     }
+    case MG_OPT_SMOOTHER: {
+      if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
+      KC_CUDA(cudaStreamSynchronize(h->stream()));
+      h->smoother = (int)value;
+      drop_graphs(h);
+      return MG_OK;
+    }
     case MG_OPT_COARSE_N:
     case MG_OPT_COARSE_N32: {
       const int c = (int)value;
@@ -908,6 +1029,7 @@ int mg_get_option(mg_handle h, int key, double* value) {
     case MG_OPT_COARSE_N32: *value = h->coarse_n32; return MG_OK;
     case MG_OPT_COARSE_OP: *value = h->rediscretized; return MG_OK;
     case MG_OPT_STOP: *value = h->stop_rule; return MG_OK;
+    case MG_OPT_SMOOTHER: *value = h->smoother; return MG_OK;
     case MG_OPT_LEVELS: *value = h->levels; return MG_OK;
     case MG_OPT_N: *value = h->n; return MG_OK;
     case MG_OPT_LAUNCHES: *value = h->last_launches; return MG_OK;
@@ -925,6 +1047,7 @@ int mg_set_stream(mg_handle h, void* stream) {
 static int kcycle_common(mg_handle h, double* v, const double* f, int kappa, bool adjoint) {
   if (!valid_handle(h)) return MG_ERR_STATE;
   if (!v || !f || kappa < 1) return MG_ERR_ARG;
+  if (adjoint && h->smoother == 1) return MG_ERR_ARG;
   trim_graphs(h);
   GraphEntry* ge;
   KC_TRY(get_cycle_graph(h, v, f, kappa, adjoint ? 2 : 0, &ge));

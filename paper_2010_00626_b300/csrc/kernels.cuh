@@ -149,7 +149,7 @@ __device__ __forceinline__ double block_sum(double x, double* red) {
 template <typename T>
 struct PassAArgs {
   const T* vin;   // nullptr: zero initial guess (the v^{l+1} <- 0 of Algorithm 3)
-  T* vout;        // relaxed v (must not alias vin)
+  T* vout;        // relaxed v (must not alias vin); nullptr: not written
   const T* f;
   T* fc;          // coarse right-hand side, (n-1)/2 square
   const T* coef;
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(NT) pass_a_kernel(const PassAArgs<T> a) {
   // relaxed v on the tile
   for_region<NT>(BX, BY, [&](int tx, int ty) {
     const int gx = x0 + tx, gy = y0 + ty;
-    if (inside(gx, gy, n)) a.vout[(size_t)gy * a.ldvout + gx] = src[(ty + H) * W + tx + H];
+    if (a.vout && inside(gx, gy, n)) a.vout[(size_t)gy * a.ldvout + gx] = src[(ty + H) * W + tx + H];
   });
   // residual on the tile plus one column/row beyond it (full weighting reads it)
   for_region<NT>(BX + 1, BY + 1, [&](int tx, int ty) {
@@ -330,6 +330,42 @@ __global__ void __launch_bounds__(NT) pass_b_kernel(const PassBArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// Zebra line relaxation tables (the kernels are in lines.cuh): per level and direction the Thomas
+// factors mm, cp of the line operator and the chunk products pi, rho of the chunked solve.
+// ---------------------------------------------------------------------------------------------
+// Chunk length of the line solves of a level of side n: the largest power of two <= 16 whose
+// 32-lane segment still fits in the line.
+__host__ __device__ inline int line_chunk(int n) {
+  int mc = 16;
+  while (mc > 1 && 32 * mc > n + 1) mc >>= 1;
+  return mc;
+}
+
+// Offset of the tables of (level l, direction dir) in the table array: per level 2 directions x 4
+// tables (mm, cp, pi, rho) of n_l entries; n_l = 2^(k-l) - 1.
+__host__ __device__ inline size_t line_tab_offset(int k, int l, int dir) {
+  size_t off = 0;
+  for (int q = 0; q < l; ++q) off += size_t(8) * ((1 << (k - q)) - 1);
+  return off + size_t(dir) * 4 * ((1 << (k - l)) - 1);
+}
+
+__host__ __device__ inline size_t line_tab_size(int k, int levels) { return line_tab_offset(k, levels, 0); }
+
+// Dense inverses of the line operators of the levels with side <= LINV_MAX, per level and
+// direction n*n entries (row-major, FP64): the FP64 coarse kernel applies them as one short
+// matrix-vector product per point instead of the two dependent Thomas sweeps.
+constexpr int LINV_MAX = 15;
+__host__ __device__ inline size_t line_inv_offset(int k, int l, int dir) {
+  size_t off = 0;
+  for (int q = 0; q < l; ++q) {
+    const size_t m = (size_t(1) << (k - q)) - 1;
+    if (m <= LINV_MAX) off += 2 * m * m;
+  }
+  const size_t n = (size_t(1) << (k - l)) - 1;
+  return off + size_t(dir) * n * n;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Coarse levels: one CTA walks Algorithm 3 for levels lc..L-1 entirely in shared memory.
 // ---------------------------------------------------------------------------------------------
 template <typename T>
@@ -347,6 +383,9 @@ struct CoarseArgs {
   int k1, k2;      // counters of the (up to) two calls made at level lc; k2 = 0: one call
   int zero1;       // first call starts from zero
   int adjoint;     // adjoint cycle: nu1 <-> nu2 and the kappa-1 call first
+  const T* ltab;   // zebra line tables (precision T); nullptr: damped Jacobi
+  const double* linv;  // dense line inverses of the levels with side <= LINV_MAX (FP64 cycles) or nullptr
+  int k;           // finest side 2^k - 1 (locates the line tables of a level)
 };
 
 __host__ __device__ inline int coarse_side(int n_lc, int d) {
@@ -366,7 +405,21 @@ __device__ __forceinline__ T jacobi_update_tree(const Nb<T>& nb, T fv, const Coe
 }
 
 // Shared memory of the coarse kernel: per level two v buffers and f, each (side+2)^2 with a zero
-// border, plus one temporary of the largest level.
+// border, plus one temporary of the largest level; then the zebra line tables of its levels (mm
+// and cp per direction, precision T) and the dense line inverses (FP64) of the sides <= LINV_MAX.
+__host__ __device__ inline size_t coarse_line_tables(int n_lc, int nlev) {
+  size_t tot = 0;
+  for (int d = 0; d < nlev; ++d) tot += 4 * size_t(coarse_side(n_lc, d));
+  return tot;
+}
+__host__ __device__ inline size_t coarse_line_inverses(int n_lc, int nlev) {
+  size_t tot = 0;
+  for (int d = 0; d < nlev; ++d) {
+    const size_t s = coarse_side(n_lc, d);
+    if (s <= LINV_MAX) tot += 2 * s * s;
+  }
+  return tot;
+}
 template <typename T>
 __host__ __device__ inline size_t coarse_smem(int n_lc, int nlev) {
   size_t tot = 0;
@@ -375,10 +428,12 @@ __host__ __device__ inline size_t coarse_smem(int n_lc, int nlev) {
     tot += 3 * size_t(s) * s;
   }
   tot += size_t(n_lc + 2) * (n_lc + 2);
-  return tot * sizeof(T);
+  tot += coarse_line_tables(n_lc, nlev);
+  tot = (tot * sizeof(T) + 15) / 16 * 16;
+  return tot + coarse_line_inverses(n_lc, nlev) * sizeof(double);
 }
 
-template <typename T, int NT>
+template <typename T, int NT, bool LINES>
 __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -400,6 +455,26 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
   }
   __syncthreads();
   T* tmp = base + g_off[nlev];
+  // zebra tables: level d's mm/cp of direction dir at ltab_s + 4 * (sum of the sides above) + 2 * dir * s
+  T* ltab_s = tmp + (a.n_lc + 2) * (a.n_lc + 2);
+  double* linv_s = reinterpret_cast<double*>(
+      smem_raw + ((size_t)(ltab_s + coarse_line_tables(a.n_lc, nlev) - base) * sizeof(T) + 15) / 16 * 16);
+  if (LINES) {
+    size_t o = 0, oi = 0;
+    for (int d = 0; d < nlev; ++d) {
+      const int s = g_side[d];
+      for (int dir = 0; dir < 2; ++dir) {
+        const T* src = a.ltab + line_tab_offset(a.k, a.lc + d, dir);
+        for (int e = threadIdx.x; e < 2 * s; e += NT) ltab_s[o + e] = src[e];
+        o += 2 * s;
+        if (a.linv && s <= LINV_MAX) {
+          const double* isrc = a.linv + line_inv_offset(a.k, a.lc + d, dir);
+          for (int e = threadIdx.x; e < s * s; e += NT) linv_s[oi + e] = isrc[e];
+          oi += (size_t)s * s;
+        }
+      }
+    }
+  }
   // Only the zero borders of the v buffers are ever read before being written (f, the temporary
   // and v interiors are written first), so only those are cleared.
   for (int d = 0; d < nlev; ++d) {
@@ -463,6 +538,90 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
       cur ^= 1u << d;
       __syncthreads();
     }
+  };
+  // `sweeps` alternating zebra relaxations on level d, in place: the k-th along x (rows) for even
+  // k, along y (columns) for odd k; colour 0 lines then colour 1 lines, one thread per line
+  // running the Thomas recurrences with the level's tabulated factors
+  auto relax_lines = [&](int d, int sweeps, bool zero) {
+    const int s = g_side[d], P = s + 2;
+    T* v = vcur(d);
+    const T* f = fbuf(d);
+    const Coef<T> c = cf[d];
+    if (zero) {
+      for (int k = threadIdx.x; k < s * s; k += NT) v[pos(d, k)] = T(0);
+      __syncthreads();
+    }
+    size_t o = 0, oi = 0;  // this level's tables in shared memory
+    for (int q = 0; q < d; ++q) {
+      o += 4 * (size_t)g_side[q];
+      if (a.linv && g_side[q] <= LINV_MAX) oi += 2 * (size_t)g_side[q] * g_side[q];
+    }
+    const bool dense = a.linv && s <= LINV_MAX;
+    for (int it = 0; it < sweeps; ++it) {
+      const int dir = it & 1;
+      const T* mm = ltab_s + o + 2 * dir * s;
+      const T* cp = mm + s;
+      const double* inv = linv_s + oi + (size_t)dir * s * s;
+      const T cl = dir == 0 ? c.cns : c.cwe;
+      const int pstep = dir == 0 ? 1 : P, lstep = dir == 0 ? P : 1;
+      for (int colour = 0; colour < 2; ++colour) {
+        if (dense) {
+          // r of every point of this colour's lines into tmp (line-major), then x = T^-1 r
+          const int nl = (s - colour + 1) / 2;
+          for (int e = threadIdx.x; e < nl * s; e += NT) {
+            const int li = e / s, t = e - li * s, L = colour + 2 * li;
+            const T* x = v + (L + 1) * lstep + (t + 1) * pstep;
+            T r = f[(L + 1) * lstep + (t + 1) * pstep];
+            r = fma(-cl, x[-lstep] + x[lstep], r);
+            r = fma(-c.cnw, x[-lstep + pstep] + x[lstep - pstep], r);
+            r = fma(-c.cne, x[-lstep - pstep] + x[lstep + pstep], r);
+            tmp[e] = r;
+          }
+          __syncthreads();
+          for (int e = threadIdx.x; e < nl * s; e += NT) {
+            const int li = e / s, t = e - li * s, L = colour + 2 * li;
+            const T* r = tmp + li * s;
+            const double* row = inv + (size_t)t * s;
+            double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0;
+            int q = 0;
+            for (; q + 2 < s; q += 3) {
+              acc0 = fma(row[q], (double)r[q], acc0);
+              acc1 = fma(row[q + 1], (double)r[q + 1], acc1);
+              acc2 = fma(row[q + 2], (double)r[q + 2], acc2);
+            }
+            for (; q < s; ++q) acc0 = fma(row[q], (double)r[q], acc0);
+            v[(L + 1) * lstep + (t + 1) * pstep] = (T)((acc0 + acc1) + acc2);
+          }
+          __syncthreads();
+          continue;
+        }
+        for (int L = colour + 2 * (int)threadIdx.x; L < s; L += 2 * NT) {
+          T* x = v + (L + 1) * lstep + pstep;  // point 0 of line L; borders of the buffer are zero
+          const T* fl = f + (L + 1) * lstep + pstep;
+          const T* Pl = x - lstep;
+          const T* Ql = x + lstep;
+          T y = T(0);
+          for (int t = 0; t < s; ++t) {
+            const int o = t * pstep;
+            T r = fl[o];
+            r = fma(-cl, Pl[o] + Ql[o], r);
+            r = fma(-c.cnw, Pl[o + pstep] + Ql[o - pstep], r);
+            r = fma(-c.cne, Pl[o - pstep] + Ql[o + pstep], r);
+            y = fma(-cp[t], y, mm[t] * r);
+            x[o] = y;
+          }
+          T z = T(0);
+          for (int t = s - 1; t >= 0; --t) {
+            z = fma(-cp[t], z, x[t * pstep]);
+            x[t * pstep] = z;
+          }
+        }
+        __syncthreads();
+      }
+    }
+  };
+  auto smooth = [&](int d, int sweeps, bool zero) {
+    if constexpr (LINES) relax_lines(d, sweeps, zero); else relax(d, sweeps, zero);
   };
   // f_{d+1} = R (f_d - A v_d)
   auto restrict_residual = [&](int d) {
@@ -542,7 +701,7 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
         continue;
       }
       if (fr.state == 0) {
-        relax(fr.d, nu_pre, fr.zero != 0);
+        smooth(fr.d, nu_pre, fr.zero != 0);
         restrict_residual(fr.d);
         fr.state = 1;
         const int kf = a.adjoint ? (fr.k > 1 ? fr.k - 1 : fr.k) : fr.k;
@@ -558,7 +717,7 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
         }
       }
       prolong_add(fr.d);
-      relax(fr.d, nu_post, false);
+      smooth(fr.d, nu_post, false);
       --sp;
     }
   }
