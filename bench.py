@@ -171,6 +171,57 @@ def bytes_per_point(kind, norm):
     return 8 + 8 + 8 + 2 if kind == 0 else 8 + 8 + 2 + 8
 
 
+PAPER_TABLE6 = {"10": {"2": 589, "3": 274, "4": 206, "W": 193}, "45": {"2": 1725, "3": 706, "4": 463, "W": 385}}
+PAPER_TABLE7 = {"10": {"4": 36}, "45": {"4": 53}}
+
+
+def zebra_tables(n, levels, tol, v0_host, f, settings):
+    """Alternating zebra relaxation with Galerkin coarse operators at eps = 1e-5 (Section 4, solvers
+    3-4): stand-alone cycles from a random start with f = 0 until the L2 error (the iterate) is
+    reduced by 1e8 (the Table 6 protocol), and MGCG with the kappa = 4 cycle on f ~ N(0, 1) to
+    `tol` relative residual (Table 7's solver; mg_pcg starts from x0 = 0, so the f = 0 protocol
+    does not apply to it)."""
+    import torch
+    from paper_2010_00626_b300 import kcycle
+    out = {"setting": (f"{n}^2, {levels} levels, eps=1e-5, alternating zebra x then y (nu=2+2: one "
+                       "relaxation per direction), Galerkin coarse operators; stand-alone: f=0, "
+                       "v0~U(-1,1) seed 12345, ||v_k||/||v_0|| <= 1e-8; MGCG: f~N(0,1) seed 0, x0=0, "
+                       f"relres <= {tol:g}"),
+           "paper_table6_cycles_16383_rtx3090": PAPER_TABLE6, "paper_table7_iters_16383_rtx3090": PAPER_TABLE7}
+    v0 = torch.tensor(v0_host, device="cuda")
+    zero = torch.zeros_like(v0)
+    for deg, kappas in settings:
+        mz = kcycle.Multigrid(n, 1e-5, math.radians(deg), levels, 2, 2, smoother="zebra")
+        mz.set_option(kcycle.MG_OPT_STOP, 1)
+        row = {}
+        for k in kappas:
+            vv = v0.clone()
+            mz.solve(vv, zero, k, 1e-8, 1, history=False)  # builds the graph
+            vv = v0.clone()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            st_z, cyc_z, red_z, _ = mz.solve(vv, zero, k, 1e-8, 20000, history=False)
+            b.record()
+            torch.cuda.synchronize()
+            row[kname(k)] = {"cycles": cyc_z, "ms": round(a.elapsed_time(b), 1),
+                             "ms_per_cycle": round(a.elapsed_time(b) / max(cyc_z, 1), 3), "status": st_z}
+        mz.set_option(kcycle.MG_OPT_STOP, 0)
+        x = torch.zeros_like(v0)
+        mz.pcg(x, f, 4, tol, 1, history=False)
+        x.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        st_c, it_c, rel_c, _ = mz.pcg(x, f, 4, tol, 2000, history=False)
+        b.record()
+        torch.cuda.synchronize()
+        row["mgcg_k4"] = {"iterations": it_c, "ms": round(a.elapsed_time(b), 1), "relres": rel_c, "status": st_c}
+        out[f"{deg}deg"] = row
+        mz.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -180,6 +231,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-sweep", action="store_true", help="skip the per-kappa sweep")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--paper-scale", action="store_true",
+                    help="also run the zebra Table 6/7 setting at the paper's 16383^2 (about a minute)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -386,6 +439,20 @@ def main():
                                         "ms_per_cycle": round(a.elapsed_time(b) / max(cyc_p, 1), 3)}
         mp.close()
 
+    # ---------------------------------------------------------------- zebra line relaxation (Tables 6-7 setting)
+    zebra = None
+    if not args.no_sweep and world == 1:
+        zebra = zebra_tables(n, levels, tol, np.random.default_rng(12345).uniform(-1.0, 1.0, (n, n)),
+                             f, ((10, (2, 3, 4, KAPPA_W)), (45, (3, 4))))
+    paper_scale = None
+    if args.paper_scale and world == 1:
+        # the paper's own size: 14 levels, 16383^2 (268M unknowns), 45 degrees
+        n14 = 16383
+        f14 = torch.tensor(rhs_normal(n14, 0), device="cuda")
+        paper_scale = zebra_tables(n14, 14, tol, np.random.default_rng(12345).uniform(-1.0, 1.0, (n14, n14)),
+                                   f14, ((45, (4,)),))
+        del f14
+
     # ---------------------------------------------------------------- batched (256 ragged instances, one launch each)
     batched = None
     if not args.no_sweep and world == 1:
@@ -397,8 +464,8 @@ def main():
         batched = {"workload": "256 instances, n uniform over {127,255,511,1023}, theta~U[0,pi), "
                                "log10 eps~U[-5,-1], f~U(-1,1), kappa=3, tol 1e-8, cap 3000 iterations",
                    "dof": int(sum(n * n for n in ns))}
-        for mixed in (True, False):
-            bt = kcycle.Batch(ns, [d["eps"] for d in inst], [d["theta"] for d in inst])
+        for mixed, smoother in ((True, "jacobi"), (False, "jacobi"), (True, "zebra"), (False, "zebra")):
+            bt = kcycle.Batch(ns, [d["eps"] for d in inst], [d["theta"] for d in inst], smoother=smoother)
             chosen = bt.autotune(3, mixed=mixed)
             for xb in xs_b:
                 xb.zero_()
@@ -411,13 +478,14 @@ def main():
             ms_b = 1e3 * (time.perf_counter() - t0)
             conv = [i for i in range(len(ns)) if rel_b[i] <= tol]
             q = sorted(it_b)
-            batched["mixed" if mixed else "fp64"] = {
+            batched[("mixed" if mixed else "fp64") + ("_zebra" if smoother == "zebra" else "")] = {
                 "ms_one_launch": round(ms_b, 1), "converged": len(conv), "of": len(ns),
                 "iterations_quartiles": [q[0], q[len(q) // 4], q[len(q) // 2], q[3 * len(q) // 4], q[-1]],
                 "autotuned_coarse_n": {str(k): v for k, v in chosen.items()}}
             bt.close()
-        batched["note"] = ("instances that miss tol are near-grid-aligned with small eps, where damped point "
-                           "Jacobi does not smooth (Section 4 uses line relaxation there)")
+        batched["note"] = ("damped-Jacobi instances that miss tol are near-grid-aligned with small eps, where "
+                           "point relaxation does not smooth; the *_zebra runs use alternating zebra line "
+                           "relaxation (Section 4) on every instance")
 
     # ---------------------------------------------------------------- oracle on the host cores
     cpu = None
@@ -442,7 +510,9 @@ def main():
                 "roofline": roofline, "cycle_share": cycle_share, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clocks.summary(), "per_kappa": per_kappa,
                 "per_kappa_mixed": per_kappa_mixed, "batched": batched, "model": model_report,
-                "paper_protocol": paper_protocol}
+                "paper_protocol": paper_protocol, "zebra": zebra}
+        if paper_scale is not None:
+            line["zebra_16383"] = paper_scale
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -239,6 +239,11 @@ int mg_batch_autotune(mg_batch b, int kappa, int mixed, int* chosen);
 int mg_batch_solve(mg_batch b, double* const* x, const double* const* f, int kappa, double tol,
                    int max_iters, int mixed, int* iters, double* relres);
 
+/* mg_set_option on every instance of the batch (for example MG_OPT_SMOOTHER = 1: zebra line
+ * relaxation everywhere, which also smooths the near-grid-aligned instances that damped Jacobi
+ * cannot). Returns the first failing status, MG_ERR_ARG for read-only keys. Synchronises. */
+int mg_batch_set_option(mg_batch b, int key, double value);
+
 int mg_batch_size(mg_batch b, int* count);
 int mg_batch_destroy(mg_batch b);
 

@@ -1518,6 +1518,14 @@ int mg_batch_autotune(mg_batch b, int kappa, int mixed, int* chosen) {
   return MG_OK;
 }
 
+int mg_batch_set_option(mg_batch b, int key, double value) {
+  if (!b) return MG_ERR_ARG;
+  if (key == MG_OPT_LEVELS || key == MG_OPT_N || key == MG_OPT_LAUNCHES) return MG_ERR_ARG;
+  for (mg_handle h : b->inst) KC_TRY(mg_set_option(h, key, value));
+  batch_drop_graph(b);
+  return MG_OK;
+}
+
 int mg_batch_solve(mg_batch b, double* const* x, const double* const* f, int kappa, double tol, int max_iters,
                    int mixed, int* iters, double* relres) {
   if (!b || !x || !f || kappa < 1 || !(tol > 0) || max_iters < 1) return MG_ERR_ARG;

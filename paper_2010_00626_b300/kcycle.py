@@ -61,6 +61,7 @@ SIGNATURES = {
     "mg_batch_create": (_i, [_i, _ip, _dp, _dp, _ip, _i, _i, ctypes.POINTER(_h)]),
     "mg_batch_autotune": (_i, [_h, _i, _i, _ip]),
     "mg_batch_solve": (_i, [_h, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, _d, _i, _i, _ip, _dp]),
+    "mg_batch_set_option": (_i, [_h, _i, _d]),
     "mg_batch_size": (_i, [_h, _ip]),
     "mg_batch_destroy": (_i, [_h]),
     "mg_fp64_rate": (_i, [_dp]),
@@ -265,7 +266,7 @@ class Multigrid:
 class Batch:
     """Many independent instances solved by one graph launch (``mg_batch_*``)."""
 
-    def __init__(self, ns, epss, thetas, nu1=2, nu2=2, levels=None):
+    def __init__(self, ns, epss, thetas, nu1=2, nu2=2, levels=None, smoother="jacobi"):
         cnt = len(ns)
         h = _h()
         arr_i = (ctypes.c_int * cnt)(*[int(v) for v in ns])
@@ -275,6 +276,14 @@ class Batch:
         _check(_lib.mg_batch_create(cnt, arr_i, arr_e, arr_t, arr_l, int(nu1), int(nu2), ctypes.byref(h)),
                "mg_batch_create")
         self._h, self.ns = h, [int(v) for v in ns]
+        if smoother not in SMOOTHERS:
+            self.close()
+            raise ValueError(f"smoother must be one of {sorted(SMOOTHERS)}")
+        if smoother != "jacobi":
+            self.set_option(MG_OPT_SMOOTHER, SMOOTHERS[smoother])
+
+    def set_option(self, key, value):
+        _check(_lib.mg_batch_set_option(self._h, int(key), float(value)), "mg_batch_set_option")
 
     def close(self):
         if getattr(self, "_h", None):

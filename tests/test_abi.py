@@ -55,5 +55,7 @@ def test_setup_rejects_bad_arguments_without_touching_the_gpu(libk):
         assert lib.mg_setup(*args, ctypes.byref(h)) == -1, args
         assert not h.value
     assert lib.mg_kcycle(None, None, None, 1) == -5
+    assert lib.mg_set_option(None, 9, 1.0) == -5      # MG_OPT_SMOOTHER on no handle
+    assert lib.mg_batch_set_option(None, 9, 1.0) == -1
     assert lib.mg_destroy(None) == 0
     assert lib.mg_status_string(-1) == b"invalid argument"
