@@ -32,6 +32,9 @@ from paper_2010_00626_b300.inputs import KAPPA_W, LARGE, rhs_normal  # noqa: E40
 METRIC = "ms to 1e-8 rel. residual per kappa (FP64 vs mixed/batched) and % of HBM peak"
 WORKLOAD = "large standalone 4095^2 (12 levels, theta=pi/3, eps=1e-4, FP64)"
 NOMINAL_FP64_TFLOPS = 1.25  # recipe's nominal B300 FP64 rate
+# DRAM bytes (read + write) of one level-0 pass A launch at 4095^2, from the ncu capture summarised in
+# profiles/pass_a_fp64_4095_L0.md; to be retaken whenever pass_a_kernel changes
+PASS_A_L0_DRAM_BYTES = 268_368_896 + 133_466_112
 
 
 def kname(k):
@@ -327,7 +330,8 @@ def main():
                 "peak_source": "measured live: FP64 FMA throughput probe (mg_fp64_rate); add/mul/fma count as one",
                 "algorithmic_ops_per_point": ops, "ms_per_launch": dom_avg,
                 "tflops_fma2": achieved_tflops, "frac_of_nominal_1.25_tflops": achieved_tflops / NOMINAL_FP64_TFLOPS,
-                "traffic": None,
+                "traffic": PASS_A_L0_DRAM_BYTES if n == 4095 else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch",
                 "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
                         "algorithmic_bytes": bytes_alg}}
     cycle_share = {f"{kinds[k]}@L{l}": round(t / total, 4) for (k, l), t in sorted(share.items(), key=lambda x: -x[1])[:8]}
