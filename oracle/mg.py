@@ -37,7 +37,8 @@ import scipy.linalg
 
 __all__ = [
     "cos_sin", "fine_stencil", "fine_stencil_derivatives", "apply_stencil", "restrict_fw",
-    "prolong_bilinear", "galerkin_stencil", "zero_row_sum_centre", "jacobi", "zebra_lines", "relax", "Hierarchy", "CallRecorder",
+    "prolong_bilinear", "galerkin_stencil", "zero_row_sum_centre", "jacobi", "zebra_lines", "relax",
+    "restrict_fw_y", "prolong_y", "galerkin_stencil_y", "Hierarchy", "CallRecorder",
     "kcycle", "gamma_cycle", "f_cycle", "kcycle_adjoint", "cycle", "cycle_adjoint",
     "residual", "relres", "solve", "solve_error_reduction", "pcg", "param_grads", "level_sizes",
 ]
@@ -216,6 +217,58 @@ def galerkin_stencil(st: np.ndarray) -> np.ndarray:
     return out
 
 
+def restrict_fw_y(r: np.ndarray) -> np.ndarray:
+    """Semi-coarsening restriction along y only (Section 4, solvers 5-6): the 1-D full weighting
+    (1/4)[1 2 1] across rows; fine rows 2m+1 -> coarse rows m, coarse row J sits on fine row
+    2J+1, every column kept."""
+    m = (r.shape[0] - 1) // 2
+    rows = 2 * np.arange(m) + 1
+    return 0.25 * r[rows - 1] + 0.5 * r[rows] + 0.25 * r[rows + 1]
+
+
+def prolong_y(vc: np.ndarray) -> np.ndarray:
+    """Linear interpolation along y only: coarse row J is injected at fine row 2J+1; fine row
+    2J averages coarse rows J-1 and J (zero Dirichlet rows outside)."""
+    m, nx = vc.shape
+    pc = np.zeros((m + 2, nx))
+    pc[1:-1] = vc
+    out = np.zeros((2 * m + 1, nx))
+    out[1::2] = vc
+    out[0::2] = 0.5 * (pc[:-1] + pc[1:])
+    return out
+
+
+def galerkin_stencil_y(st: np.ndarray) -> np.ndarray:
+    """Coarse stencil of A_c = R_y A P_y for semi-coarsening along y (Section 4, solvers 5-6).
+
+    The definition written out as for ``galerkin_stencil``: P_y, then A, then R_y applied to a
+    coarse unit vector far from the boundary, on a 7-column by 11-row fine grid (5 coarse rows),
+    in exact rational arithmetic on the FP64 entries, rounded once to FP64.
+    """
+    m, c, nxg, cx = 5, 2, 7, 3
+    nf = 2 * m + 1
+    S = [[Fraction(float(st[a, b])) for b in range(3)] for a in range(3)]
+    half = Fraction(1, 2)
+
+    def hat(fine, coarse):  # linear weight of coarse row `coarse` at fine row `fine`
+        d = abs(fine - (2 * coarse + 1))
+        return Fraction(1) if d == 0 else (half if d == 1 else Fraction(0))
+
+    pe = [[hat(j, c) * (1 if i == cx else 0) for i in range(nxg)] for j in range(nf)]      # P_y e_c
+    ape = [[sum((S[1 + dy][1 + dx] * pe[j + dy][i + dx]
+                 for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+                 if 0 <= j + dy < nf and 0 <= i + dx < nxg), Fraction(0))
+            for i in range(nxg)] for j in range(nf)]                                        # A P_y e_c
+    fw = {-1: Fraction(1, 4), 0: Fraction(1, 2), 1: Fraction(1, 4)}
+    col = [[sum((fw[dy] * ape[2 * J + 1 + dy][i] for dy in (-1, 0, 1)), Fraction(0))
+            for i in range(nxg)] for J in range(m)]                                         # R_y A P_y e_c
+    out = np.zeros((3, 3))
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            out[1 + dy, 1 + dx] = float(col[c - dy][cx - dx])
+    return out
+
+
 def zero_row_sum_centre(st: np.ndarray) -> np.ndarray:
     """Coarse stencil with its centre evaluated from the zero-row-sum identity.
 
@@ -252,9 +305,9 @@ def zebra_lines(st: np.ndarray, v: np.ndarray, f: np.ndarray, axis: str) -> np.n
     west/east entries, a tridiagonal system); axis 'y': the lines are columns i (south/north).
     Off-line stencil entries move to the right-hand side with the current neighbouring values."""
     v = v.copy()
-    n = v.shape[0]
     work = v if axis == "x" else v.T                 # work[line, position]
     rhs_f = f if axis == "x" else f.T
+    nl, n = work.shape                               # number of lines, points per line
     # stencil as seen along the line: s[dl, dp] multiplies work[line+dl, pos+dp]
     s = st if axis == "x" else st.T
     ab = np.zeros((3, n))                            # banded storage for solve_banded
@@ -262,8 +315,10 @@ def zebra_lines(st: np.ndarray, v: np.ndarray, f: np.ndarray, axis: str) -> np.n
     ab[1, :] = s[1, 1]                               # diagonal
     ab[2, :-1] = s[1, 0]                             # lower diagonal (position -1)
     for parity in (0, 1):
-        lines = np.arange(parity, n, 2)
-        padded = np.zeros((n + 2, n + 2))
+        lines = np.arange(parity, nl, 2)
+        if lines.size == 0:
+            continue
+        padded = np.zeros((nl + 2, n + 2))
         padded[1:-1, 1:-1] = work
         rhs = rhs_f[lines].copy()
         for dl in (-1, 1):
@@ -274,14 +329,15 @@ def zebra_lines(st: np.ndarray, v: np.ndarray, f: np.ndarray, axis: str) -> np.n
 
 
 def relax(h: "Hierarchy", level: int, v: np.ndarray, f: np.ndarray, sweeps: int) -> np.ndarray:
-    """The hierarchy's smoother: damped Jacobi, or alternating zebra line relaxation where the
-    k-th relaxation runs along x for odd k and along y for even k (so two relaxations are one
-    in each direction, x first, as in Section 4)."""
+    """The hierarchy's smoother: damped Jacobi; alternating zebra line relaxation ("zebra"), where
+    the k-th relaxation runs along x for odd k and along y for even k (so two relaxations are one
+    in each direction, x first, as in Section 4, solvers 3-4); or zebra relaxation along x only
+    ("xzebra", Section 4, solvers 5-6)."""
     st = h.stencil(level)
     if h.smoother == "jacobi":
         return jacobi(st, v, f, h.omega, sweeps)
     for k in range(sweeps):
-        v = zebra_lines(st, v, f, "x" if k % 2 == 0 else "y")
+        v = zebra_lines(st, v, f, "x" if (k % 2 == 0 or h.smoother == "xzebra") else "y")
     return v
 
 
@@ -308,7 +364,8 @@ class Hierarchy:
     nu2: int = 2
     omega: float = 0.8
     coarse_op: str = "galerkin"   # or "rediscretized": the Section 4 stencil on each coarse grid
-    smoother: str = "jacobi"      # or "zebra": alternating zebra line Gauss-Seidel
+    smoother: str = "jacobi"      # or "zebra": alternating zebra line Gauss-Seidel; "xzebra": x lines only
+    coarsening: str = "full"      # or "y": semi-coarsening along y only (every level keeps n columns)
     stencils: list = field(default_factory=list)
     sizes: list = field(default_factory=list)
     _chol: object = None
@@ -317,19 +374,27 @@ class Hierarchy:
         k = int(round(math.log2(self.n + 1)))
         if self.n < 1 or (1 << k) - 1 != self.n or not (1 <= self.levels <= k):
             raise ValueError("n must be 2^k - 1 and 1 <= levels <= k")
-        if self.smoother not in ("jacobi", "zebra"):
-            raise ValueError("smoother must be 'jacobi' or 'zebra'")
-        self.sizes = level_sizes(self.n, self.levels)
+        if self.smoother not in ("jacobi", "zebra", "xzebra"):
+            raise ValueError("smoother must be 'jacobi', 'zebra' or 'xzebra'")
+        if self.coarsening not in ("full", "y"):
+            raise ValueError("coarsening must be 'full' or 'y'")
+        if self.coarsening == "y" and (self.coarse_op != "galerkin" or self.levels != k):
+            raise ValueError("semi-coarsening uses Galerkin operators down to a single row")
+        self.sizes = level_sizes(self.n, self.levels)   # grid side; under "y" the number of rows
         st = fine_stencil(self.theta, self.eps, self.n)
         self.stencils = [st]
         for lvl in range(1, self.levels):
-            if self.coarse_op == "galerkin":
+            if self.coarsening == "y":
+                st = zero_row_sum_centre(galerkin_stencil_y(st))
+            elif self.coarse_op == "galerkin":
                 st = zero_row_sum_centre(galerkin_stencil(st))
             elif self.coarse_op == "rediscretized":
                 st = fine_stencil(self.theta, self.eps, self.sizes[lvl])
             else:
                 raise ValueError("coarse_op must be 'galerkin' or 'rediscretized'")
             self.stencils.append(st)
+        if self.coarsening == "y":
+            return                     # the coarsest level is one row: a tridiagonal solve
         # coarsest-level operator as a dense SPD matrix, factorised once
         nc = self.sizes[-1]
         dense = np.zeros((nc * nc, nc * nc))
@@ -342,8 +407,21 @@ class Hierarchy:
     def stencil(self, level: int) -> np.ndarray:
         return self.stencils[level - 1]
 
+    def restrict(self, r: np.ndarray) -> np.ndarray:
+        return restrict_fw_y(r) if self.coarsening == "y" else restrict_fw(r)
+
+    def prolong(self, vc: np.ndarray) -> np.ndarray:
+        return prolong_y(vc) if self.coarsening == "y" else prolong_bilinear(vc)
+
     def coarsest_solve(self, f: np.ndarray) -> np.ndarray:
-        """Exact solve on the coarsest level: division for 1x1, dense Cholesky otherwise."""
+        """Exact solve on the coarsest level: division for 1x1, dense Cholesky otherwise; under
+        semi-coarsening the single remaining row's tridiagonal system (west, centre, east)."""
+        if self.coarsening == "y":
+            st = self.stencils[-1]
+            n = f.shape[1]
+            ab = np.zeros((3, n))
+            ab[0, 1:], ab[1, :], ab[2, :-1] = st[1, 2], st[1, 1], st[1, 0]
+            return scipy.linalg.solve_banded((1, 1), ab, f[0]).reshape(1, n)
         nc = self.sizes[-1]
         if nc == 1:
             return f / self.stencils[-1][1, 1]
@@ -377,12 +455,12 @@ def kcycle(h: Hierarchy, level: int, v: np.ndarray, f: np.ndarray, kappa: int,
         return h.coarsest_solve(f)
     st = h.stencil(level)
     v = relax(h, level, v, f, h.nu1)                      # relax nu1 times
-    fc = restrict_fw(f - apply_stencil(st, v))            # restrict the residual
+    fc = h.restrict(f - apply_stencil(st, v))             # restrict the residual
     vc = np.zeros_like(fc)                                # v^{l+1} <- 0
     vc = kcycle(h, level + 1, vc, fc, kappa, rec)         # call with counter kappa
     if kappa > 1:
         vc = kcycle(h, level + 1, vc, fc, kappa - 1, rec)  # then with kappa - 1
-    v = v + prolong_bilinear(vc)                           # coarse-grid correction
+    v = v + h.prolong(vc)                                  # coarse-grid correction
     v = relax(h, level, v, f, h.nu2)                       # relax nu2 times
     return v
 
@@ -393,11 +471,11 @@ def gamma_cycle(h: Hierarchy, level: int, v: np.ndarray, f: np.ndarray, gamma: i
         return h.coarsest_solve(f)
     st = h.stencil(level)
     v = relax(h, level, v, f, h.nu1)
-    fc = restrict_fw(f - apply_stencil(st, v))
+    fc = h.restrict(f - apply_stencil(st, v))
     vc = np.zeros_like(fc)
     for _ in range(gamma):
         vc = gamma_cycle(h, level + 1, vc, fc, gamma)
-    v = v + prolong_bilinear(vc)
+    v = v + h.prolong(vc)
     return relax(h, level, v, f, h.nu2)
 
 
@@ -407,11 +485,11 @@ def f_cycle(h: Hierarchy, level: int, v: np.ndarray, f: np.ndarray) -> np.ndarra
         return h.coarsest_solve(f)
     st = h.stencil(level)
     v = relax(h, level, v, f, h.nu1)
-    fc = restrict_fw(f - apply_stencil(st, v))
+    fc = h.restrict(f - apply_stencil(st, v))
     vc = np.zeros_like(fc)
     vc = f_cycle(h, level + 1, vc, fc)
     vc = gamma_cycle(h, level + 1, vc, fc, 1)
-    v = v + prolong_bilinear(vc)
+    v = v + h.prolong(vc)
     return relax(h, level, v, f, h.nu2)
 
 
@@ -424,8 +502,8 @@ def kcycle_adjoint(h: Hierarchy, level: int, v: np.ndarray, f: np.ndarray, kappa
     call with counter kappa. Pinned by the dot-product test <x, B y> = <B^T x, y>.
     Damped Jacobi only (the transposed zebra smoother would also reverse its line order).
     """
-    if h.smoother != "jacobi":
-        raise ValueError("the adjoint cycle is defined for the damped-Jacobi smoother")
+    if h.smoother != "jacobi" or h.coarsening != "full":
+        raise ValueError("the adjoint cycle is defined for damped Jacobi with full coarsening")
     if level == h.levels:
         return h.coarsest_solve(f)
     st = h.stencil(level)

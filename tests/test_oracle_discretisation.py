@@ -228,3 +228,66 @@ def test_galerkin_exact_matches_float_probing():
         col = oracle.restrict_fw(oracle.apply_stencil(st, oracle.prolong_bilinear(e)))
         probe = np.array([[col[2 - dy, 2 - dx] for dx in (-1, 0, 1)] for dy in (-1, 0, 1)])
         assert np.max(np.abs(oracle.galerkin_stencil(st) - probe)) <= 16 * np.finfo(float).eps * np.abs(st).max()
+
+
+# --------------------------------------------------------------------------------------------
+# Semi-coarsening along y (Section 4, solvers 5-6)
+# --------------------------------------------------------------------------------------------
+
+def test_semi_restriction_is_half_prolongation_transpose():
+    nyf, nx = 15, 9
+    P = dense(oracle.prolong_y, ((nyf - 1) // 2, nx))
+    R = dense(oracle.restrict_fw_y, (nyf, nx))
+    assert np.array_equal(R, P.T / 2)
+
+
+def test_semi_transfers_exact_on_linear_functions_of_y():
+    nyf, nx = 15, 5
+    y = (np.arange(nyf) + 1) / (nyf + 1)
+    yc = (np.arange(7) + 1) / 8
+    g = lambda yy, x: (0.3 - 1.7 * yy)[:, None] * (1.0 + x)[None, :]
+    x = np.linspace(0.1, 0.9, nx)
+    assert np.allclose(oracle.restrict_fw_y(g(y, x)), g(yc, x), rtol=0, atol=1e-14)
+    # interior fine rows (every coarse neighbour interior) are reproduced exactly
+    assert np.allclose(oracle.prolong_y(g(yc, x))[1:-1], g(y, x)[1:-1], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("theta,eps", CASES)
+def test_semi_galerkin_equals_dense_rap(theta, eps):
+    """Dense R_y A P_y on 15 rows -> 7 rows (9 columns kept) equals the constant coarse stencil on
+    every row, boundary rows and columns included."""
+    nyf, nyc, nx = 15, 7, 9
+    st = oracle.fine_stencil(theta, eps, 15)
+    A = dense(lambda v: oracle.apply_stencil(st, v), (nyf, nx))
+    P = dense(oracle.prolong_y, (nyc, nx))
+    R = dense(oracle.restrict_fw_y, (nyf, nx))
+    Ac = R @ A @ P
+    stc = oracle.galerkin_stencil_y(st)
+    Ac_st = dense(lambda v: oracle.apply_stencil(stc, v), (nyc, nx))
+    assert np.max(np.abs(Ac - Ac_st)) <= 1e-14 * np.abs(Ac).max()
+    assert np.allclose(Ac, Ac.T, rtol=0, atol=1e-14 * np.abs(Ac).max())
+
+
+def test_semi_galerkin_of_laplacian_closed_form():
+    """eps=1, theta=0 is the 5-point Laplacian (1/h^2)[0 -1 0; -1 4 -1; 0 -1 0]. With linear
+    interpolation in y and R = P^T / 2, the x part becomes (-u_xx) x (1/2) P^T P = rows
+    [1/8, 3/4, 1/8] and the y part (1/2)(1-D Galerkin [-1/2, 1, -1/2]): in all
+    (1/h^2)[-1/8 0 -1/8; -3/4 2 -3/4; -1/8 0 -1/8]."""
+    n = 31
+    h = 1.0 / (n + 1)   # fine spacing: semi-coarsening keeps h in x (the y spacing doubles)
+    stc = oracle.galerkin_stencil_y(oracle.fine_stencil(0.0, 1.0, n))
+    expect = np.array([[-0.125, 0.0, -0.125], [-0.75, 2.0, -0.75], [-0.125, 0.0, -0.125]]) / h ** 2
+    assert np.allclose(stc, expect, rtol=1e-14, atol=1e-14 / h ** 2)
+
+
+def test_semi_hierarchy_coarsest_is_one_row_solved_exactly():
+    n = 31
+    h = oracle.Hierarchy(n, 5, 0.4, 1e-3, smoother="xzebra", coarsening="y")
+    assert h.sizes == [31, 15, 7, 3, 1]
+    f = np.random.default_rng(3).standard_normal((1, n))
+    x = h.coarsest_solve(f)
+    assert x.shape == (1, n)
+    r = f - oracle.apply_stencil(h.stencil(5), x)
+    assert np.max(np.abs(r)) <= 1e-12 * np.abs(f).max()
+    with pytest.raises(ValueError):
+        oracle.Hierarchy(n, 4, 0.4, 1e-3, smoother="xzebra", coarsening="y")
