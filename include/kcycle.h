@@ -63,12 +63,20 @@ typedef enum {
                               rediscretized on each coarse grid                                     */
   MG_OPT_STOP = 8,         /* mg_solve's stopping test: 0 ||f - A v||/||f|| <= tol (default);
                               1 ||v_k||/||v_0|| <= tol, the error reduction of Section 4 when f = 0  */
-  MG_OPT_SMOOTHER = 9      /* relaxation: 0 damped Jacobi (default); 1 alternating zebra line
+  MG_OPT_SMOOTHER = 9,     /* relaxation: 0 damped Jacobi (default); 1 alternating zebra line
                               Gauss-Seidel (Section 4, solvers 3-4): the k-th relaxation of a
                               smoothing step solves every row (k odd: x) or every column (k even: y)
                               exactly, even-indexed lines first, then odd-indexed ones, with no
-                              damping; nu1 = nu2 = 2 is one relaxation in each direction. The
-                              adjoint entry points return MG_ERR_ARG under this smoother.       */
+                              damping; nu1 = nu2 = 2 is one relaxation in each direction; 2 zebra
+                              along x only (every relaxation solves the rows). The adjoint entry
+                              points return MG_ERR_ARG under the line smoothers.                 */
+  MG_OPT_COARSENING = 10   /* 0 full coarsening (default); 1 semi-coarsening along y only
+                              (Section 4, solvers 5-6): every level keeps the n columns and halves
+                              the rows, transfers are (1/4)[1 2 1] and linear interpolation across
+                              rows, coarse operators Galerkin, smoother forced to 2 (x lines), and
+                              the coarsest level is a single row solved exactly. Needs levels = k
+                              and Galerkin operators (else MG_ERR_ARG). Reallocates the hierarchy;
+                              the mixed-precision entry points return MG_ERR_ARG under it.      */
 } mg_option;
 
 /* Set up the hierarchy for the Section 4 problem on an n x n interior grid.

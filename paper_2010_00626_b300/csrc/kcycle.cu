@@ -63,7 +63,8 @@ constexpr int MAX_COARSE_N = 63;
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 struct Level {
-  int n = 0, ld = 0;
+  int n = 0, ld = 0;      // rows (the side, except under semi-coarsening) and pitch
+  int nx = 0;             // columns: n, or the finest side at every level under semi-coarsening
   double* v = nullptr;    // current estimate (level 0: the caller's array)
   double* tmp = nullptr;  // relaxed v between pass A and pass B
   double* f = nullptr;    // right-hand side (level 0: the caller's array)
@@ -123,7 +124,8 @@ struct mg_ctx {
   int ld32_0 = 0;       // pitch of the FP32 level-0 arrays (multiple of 32 floats)
   int rediscretized = 0;  // coarse operators: 0 Galerkin, 1 the Section 4 stencil on each coarse grid
   int stop_rule = 0;      // 0: ||f - A v|| / ||f|| <= tol; 1: ||v_k|| / ||v_0|| <= tol (f = 0 protocol)
-  int smoother = 0;       // 0 damped Jacobi, 1 alternating zebra line Gauss-Seidel
+  int smoother = 0;       // 0 damped Jacobi, 1 alternating zebra line Gauss-Seidel, 2 zebra along x only
+  int semi = 0;           // 1: semi-coarsening along y (every level keeps the n columns)
   double* ltab = nullptr;  // line-solve tables (Thomas factors and chunk products) per level/direction
   float* ltab32 = nullptr;
   double* linv = nullptr;  // dense line inverses of the levels with side <= LINV_MAX
@@ -270,6 +272,7 @@ template <typename T>
 int lv_ld(mg_ctx* h, const BindingT<T>& b, int l) { return l == 0 ? b.ld0 : Arr<T>::ld(h, l); }
 
 enum { K_PASS_A = 0, K_PASS_B = 1, K_COARSE = 2, K_APPLY = 3, K_LINES_X = 4, K_LINES_Y = 5 };
+// (under semi-coarsening K_PASS_A is the y restriction and K_PASS_B the y prolongation)
 
 void prof_begin(mg_ctx* h, int kind, int level, cudaStream_t s) {
   if (!h->prof) return;
@@ -342,6 +345,7 @@ int emit_coarse(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int zero1, bool
   a.ltab = h->smoother == 1 ? Arr<T>::ltab(h) : nullptr;
   a.linv = (h->smoother == 1 && std::is_same<T, double>::value) ? h->linv : nullptr;
   a.k = h->k;
+  a.xonly = h->smoother == 2 ? 1 : 0;
   const size_t sm = coarse_smem<T>(a.n_lc, a.L - a.lc);
   prof_begin(h, K_COARSE, lc, s);
   if (a.ltab)
@@ -450,7 +454,7 @@ int emit_apply(mg_ctx* h, const double* v, const double* f, double* out, double*
 
 template <typename T, int DIR>
 int launch_lines(const LineArgs<T>& a, cudaStream_t s) {
-  const int nl = (a.n - a.colour + 1) / 2;
+  const int nl = (a.nl - a.colour + 1) / 2;
   const int blocks = (nl + LINE_R - 1) / LINE_R;
   switch (line_chunk(a.n)) {
     case 16: line_relax_kernel<T, DIR, LINE_R, 16><<<blocks, 32 * LINE_R, line_smem<T, LINE_R, 16>(), s>>>(a); break;
@@ -476,12 +480,14 @@ int emit_lines(mg_ctx* h, const BindingT<T>& b, int l, int sweeps, bool zero, co
   a.f = lv_f(h, b, l);
   a.coef = Arr<T>::coef(h);
   a.skip = skip;
-  a.n = h->lv[l].n;
+  a.n = h->lv[l].nx;  // points per row; columns (full coarsening only) have as many
+  a.nl = h->lv[l].n;
   a.ld = lv_ld(h, b, l);
   a.level = l;
+  a.semi = h->semi;
   for (int k = 0; k < sweeps; ++k) {
-    const int dir = k & 1;
-    a.tab = Arr<T>::ltab(h) + line_tab_offset(h->k, l, dir);
+    const int dir = h->smoother == 2 ? 0 : (k & 1);
+    a.tab = Arr<T>::ltab(h) + line_tab_offset(h->k, l, dir, h->semi);
     for (int colour = 0; colour < 2; ++colour) {
       a.colour = colour;
       a.zero = (zero && k == 0 && colour == 0) ? 1 : 0;
@@ -491,6 +497,77 @@ int emit_lines(mg_ctx* h, const BindingT<T>& b, int l, int sweeps, bool zero, co
       const int st = dir == 0 ? launch_lines<T, 0>(a, s) : launch_lines<T, 1>(a, s);
       prof_end(h, s);
       KC_TRY(st);
+    }
+  }
+  return MG_OK;
+}
+
+// Semi-coarsening along y with x-line zebra (Section 4, solvers 5-6): every level, the coarsest
+// included, runs as multi-CTA launches (the levels keep all n columns, so none is small enough for
+// the single-CTA kernel). The coarsest level is one row: its x-line solve is the exact solve.
+template <typename T>
+int emit_call_semi(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero, bool norm, const int* skip,
+                   cudaStream_t s) {
+  const int L = h->levels;
+  const int nx = h->lv[l].nx;
+  if (l == L - 1) {
+    LineArgs<T> a;
+    a.v = lv_v(h, b, l);
+    a.f = lv_f(h, b, l);
+    a.coef = Arr<T>::coef(h);
+    a.tab = Arr<T>::ltab(h) + line_tab_offset(h->k, l, 0, 1);
+    a.skip = skip;
+    a.vc = nullptr;
+    a.n = nx;
+    a.nl = h->lv[l].n;
+    a.ld = lv_ld(h, b, l);
+    a.level = l;
+    a.ldc = 0;
+    a.colour = 0;
+    a.zero = 1;
+    a.semi = 1;
+    ++h->launch_count;
+    prof_begin(h, K_LINES_X, l, s);
+    const int st = launch_lines<T, 0>(a, s);
+    prof_end(h, s);
+    return st;
+  }
+  const int nu_pre = h->nu1, nu_post = h->nu2;
+  const int nyc = h->lv[l + 1].n;
+  if (nu_pre > 0) KC_TRY(emit_lines(h, b, l, nu_pre, zero, skip, s));
+  {
+    dim3 grid((nx + 31) / 32, (nyc + NT_VEC / 32 - 1) / (NT_VEC / 32));
+    ++h->launch_count;
+    prof_begin(h, K_PASS_A, l, s);
+    restrict_y_kernel<T, NT_VEC><<<grid, NT_VEC, 0, s>>>(lv_v(h, b, l), lv_f(h, b, l), Arr<T>::f(h, l + 1),
+                                                          Arr<T>::coef(h), l, nx, nyc, lv_ld(h, b, l),
+                                                          lv_ld(h, b, l), Arr<T>::ld(h, l + 1),
+                                                          (zero && nu_pre == 0) ? 1 : 0, skip);
+    prof_end(h, s);
+    KC_CUDA(cudaGetLastError());
+  }
+  if (zero && nu_pre == 0) {  // v^l = 0 before the correction is added
+    KC_CUDA(cudaMemset2DAsync(lv_v(h, b, l), sizeof(T) * lv_ld(h, b, l), 0, sizeof(T) * nx, h->lv[l].n, s));
+  }
+  int k1 = kappa, k2 = kappa > 1 ? kappa - 1 : 0;
+  KC_TRY(emit_call_semi(h, b, l + 1, k1, true, false, skip, s));
+  if (k2 > 0) KC_TRY(emit_call_semi(h, b, l + 1, k2, false, false, skip, s));
+  if (nu_post > 0) {
+    KC_TRY(emit_lines(h, b, l, nu_post, false, skip, s, Arr<T>::v(h, l + 1), Arr<T>::ld(h, l + 1)));
+  } else {
+    dim3 grid((nx + 31) / 32, (h->lv[l].n + NT_VEC / 32 - 1) / (NT_VEC / 32));
+    ++h->launch_count;
+    prof_begin(h, K_PASS_B, l, s);
+    prolong_y_add_kernel<T, NT_VEC><<<grid, NT_VEC, 0, s>>>(lv_v(h, b, l), Arr<T>::v(h, l + 1), nx, nyc,
+                                                             lv_ld(h, b, l), Arr<T>::ld(h, l + 1), skip);
+    prof_end(h, s);
+    KC_CUDA(cudaGetLastError());
+  }
+  if (norm && l == 0) {
+    if constexpr (std::is_same<T, double>::value) {
+      KC_TRY(emit_apply(h, b.v0, b.f0, nullptr, h->partial, skip, s));
+    } else {
+      return MG_ERR_ARG;
     }
   }
   return MG_OK;
@@ -551,6 +628,7 @@ int emit_call(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero, bool
 template <typename T>
 int emit_cycle(mg_ctx* h, const BindingT<T>& b, int kappa, bool zero, bool adjoint, bool norm, const int* skip,
                cudaStream_t s) {
+  if (h->semi) return emit_call_semi(h, b, 0, kappa, zero, norm, skip, s);
   if (lc_of<T>(h) == 0) {
     KC_TRY(emit_coarse(h, b, kappa, 0, zero ? 1 : 0, adjoint, skip, s));
     if (norm) {
@@ -566,7 +644,7 @@ int emit_cycle(mg_ctx* h, const BindingT<T>& b, int kappa, bool zero, bool adjoi
 }
 
 int norm_partials(mg_ctx* h) {
-  return (int)((h->lc == 0 || h->smoother == 1) ? apply_grid_blocks(h->n) : pass_grid_blocks(h->n));
+  return (int)((h->lc == 0 || h->smoother != 0) ? apply_grid_blocks(h->n) : pass_grid_blocks(h->n));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -766,7 +844,7 @@ int solve_impl(mg_handle h, double* v, const double* f, int kappa, double tol, i
                double* final_relres, double* history, bool adjoint = false) {
   if (!valid_handle(h)) return MG_ERR_STATE;
   if (!v || !f || kappa < 1 || !(tol > 0) || max_cycles < 1) return MG_ERR_ARG;
-  if (adjoint && h->smoother == 1) return MG_ERR_ARG;
+  if (adjoint && h->smoother != 0) return MG_ERR_ARG;
   trim_graphs(h);
   KC_TRY(ensure_hist(h, max_cycles));
   cudaStream_t s = h->stream();
@@ -801,7 +879,29 @@ int solve_impl(mg_handle h, double* v, const double* f, int kappa, double tol, i
   return read_result(h, s, tol, cycles, final_relres, history);
 }
 
+// Level shapes: rows 2^(k-l) - 1; columns the same (full coarsening) or n at every level (semi).
+void set_geometry(mg_ctx* h) {
+  for (int l = 0; l < h->levels; ++l) {
+    h->lv[l].n = (1 << (h->k - l)) - 1;
+    h->lv[l].nx = h->semi ? h->n : h->lv[l].n;
+    h->lv[l].ld = l == 0 ? h->n : round_up(h->lv[l].nx, 32);
+  }
+}
+
 int alloc_levels(mg_ctx* h) {
+  set_geometry(h);
+  if (h->semi) {  // in-place line relaxation everywhere: v and f per coarse level, no temporaries
+    h->lc = h->levels;
+    for (int l = 1; l < h->levels; ++l) {
+      Level& L = h->lv[l];
+      const size_t bytes = sizeof(double) * (size_t)L.ld * L.n;
+      KC_CUDA(cudaMalloc(&L.v, bytes));
+      KC_CUDA(cudaMalloc(&L.f, bytes));
+      KC_CUDA(cudaMemsetAsync(L.v, 0, bytes, h->own));
+      KC_CUDA(cudaMemsetAsync(L.f, 0, bytes, h->own));
+    }
+    return MG_OK;
+  }
   // coarse-kernel levels: the first level whose side is <= coarse_n (at least the coarsest)
   h->lc = h->levels - 1;
   for (int l = 0; l < h->levels; ++l)
@@ -825,6 +925,7 @@ int alloc_levels(mg_ctx* h) {
 
 // FP32 hierarchy of the mixed cycle: same shapes as the FP64 one, plus level 0 (d and r32).
 int ensure_levels32(mg_ctx* h) {
+  if (h->semi) return MG_ERR_ARG;  // the FP32 cycles use full coarsening
   if (h->have32) return MG_OK;
   h->lc32 = h->levels - 1;
   for (int l = 0; l < h->levels; ++l)
@@ -870,12 +971,12 @@ int free_levels(mg_ctx* h) {
 
 int run_setup_kernels(mg_ctx* h) {
   setup_stencils_kernel<<<1, 32, 0, h->own>>>(h->theta, h->eps, h->n, h->levels, h->omega, h->coef, h->coef32,
-                                             h->stencils, h->dstencil, h->rediscretized);
+                                             h->stencils, h->dstencil, h->rediscretized, h->semi);
   KC_CUDA(cudaGetLastError());
-  line_tables_kernel<<<1, 32, 0, h->own>>>(h->coef, h->k, h->levels, h->ltab, h->ltab32, h->linv);
+  line_tables_kernel<<<1, 32, 0, h->own>>>(h->coef, h->k, h->levels, h->ltab, h->ltab32, h->linv, h->semi);
   KC_CUDA(cudaGetLastError());
   const int nc = h->lv[h->levels - 1].n;
-  if (nc > 1) {
+  if (nc > 1 && !h->semi) {
     coarsest_inverse_kernel<<<1, 256, 0, h->own>>>(h->stencils, h->levels - 1, nc, h->work, h->cinv, h->cinv32);
     KC_CUDA(cudaGetLastError());
   }
@@ -932,10 +1033,7 @@ int mg_setup(int n, double eps, double theta, int levels, int nu1, int nu2, mg_h
   mg_ctx* h = new (std::nothrow) mg_ctx();
   if (!h) return MG_ERR_NOMEM;
   h->n = n; h->k = k; h->levels = levels; h->nu1 = nu1; h->nu2 = nu2; h->eps = eps; h->theta = theta;
-  for (int l = 0; l < levels; ++l) {
-    h->lv[l].n = (1 << (k - l)) - 1;
-    h->lv[l].ld = l == 0 ? n : round_up(h->lv[l].n, 32);
-  }
+  set_geometry(h);
   auto fail = [&](int st) {
     mg_destroy(h);
     return st;
@@ -952,8 +1050,8 @@ int mg_setup(int n, double eps, double theta, int levels, int nu1, int nu2, mg_h
   ALLOC(h->coef32, sizeof(float) * MAXL * NCOEF);
   ALLOC(h->stencils, sizeof(double) * MAXL * 9);
   ALLOC(h->dstencil, sizeof(double) * 18);
-  ALLOC(h->ltab, sizeof(double) * line_tab_size(k, levels));
-  ALLOC(h->ltab32, sizeof(float) * line_tab_size(k, levels));
+  ALLOC(h->ltab, sizeof(double) * line_tab_size(k, levels, 1));  // the semi-coarsening layout is the larger
+  ALLOC(h->ltab32, sizeof(float) * line_tab_size(k, levels, 1));
   ALLOC(h->linv, sizeof(double) * std::max<size_t>(1, line_inv_offset(k, levels, 0)));
   ALLOC(h->partial, sizeof(double) * np);
   ALLOC(h->partial2, sizeof(double) * np);
@@ -986,6 +1084,7 @@ int mg_set_option(mg_handle h, int key, double value) {
     }
     case MG_OPT_COARSE_OP: {
       if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
+      if (h->semi && value != 0.0) return MG_ERR_ARG;
       KC_CUDA(cudaStreamSynchronize(h->stream()));
       h->rediscretized = (int)value;
       drop_graphs(h);
@@ -998,11 +1097,25 @@ int mg_set_option(mg_handle h, int key, double value) {
       return MG_OK;
     }
     case MG_OPT_SMOOTHER: {
-      if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
+      if (!(value == 0.0 || value == 1.0 || value == 2.0)) return MG_ERR_ARG;
+      if (h->semi && value != 2.0) return MG_ERR_ARG;
       KC_CUDA(cudaStreamSynchronize(h->stream()));
       h->smoother = (int)value;
       drop_graphs(h);
       return MG_OK;
+    }
+    case MG_OPT_COARSENING: {
+      if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
+      if (value == 1.0 && (h->levels != h->k || h->rediscretized)) return MG_ERR_ARG;
+      if ((int)value == h->semi) return MG_OK;
+      KC_CUDA(cudaStreamSynchronize(h->stream()));
+      drop_graphs(h);
+      KC_TRY(free_levels(h));
+      h->semi = (int)value;
+      h->smoother = h->semi ? 2 : 0;
+      KC_TRY(alloc_levels(h));
+      KC_CUDA(cudaStreamSynchronize(h->own));
+      return run_setup_kernels(h);
     }
     case MG_OPT_COARSE_N:
     case MG_OPT_COARSE_N32: {
@@ -1030,6 +1143,7 @@ int mg_get_option(mg_handle h, int key, double* value) {
     case MG_OPT_COARSE_OP: *value = h->rediscretized; return MG_OK;
     case MG_OPT_STOP: *value = h->stop_rule; return MG_OK;
     case MG_OPT_SMOOTHER: *value = h->smoother; return MG_OK;
+    case MG_OPT_COARSENING: *value = h->semi; return MG_OK;
     case MG_OPT_LEVELS: *value = h->levels; return MG_OK;
     case MG_OPT_N: *value = h->n; return MG_OK;
     case MG_OPT_LAUNCHES: *value = h->last_launches; return MG_OK;
@@ -1047,7 +1161,7 @@ int mg_set_stream(mg_handle h, void* stream) {
 static int kcycle_common(mg_handle h, double* v, const double* f, int kappa, bool adjoint) {
   if (!valid_handle(h)) return MG_ERR_STATE;
   if (!v || !f || kappa < 1) return MG_ERR_ARG;
-  if (adjoint && h->smoother == 1) return MG_ERR_ARG;
+  if (adjoint && h->smoother != 0) return MG_ERR_ARG;
   trim_graphs(h);
   GraphEntry* ge;
   KC_TRY(get_cycle_graph(h, v, f, kappa, adjoint ? 2 : 0, &ge));
@@ -1309,15 +1423,24 @@ int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* l
     void call(int l, int kap) {
       calls[l] += 1;
       if (l >= h->lc) ++coarse;
-      if (l == h->levels - 1) return;
-      if (l < h->lc) fine_launches += 2;  // pass A + pass B
+      if (l == h->levels - 1) {
+        if (h->semi) ++fine_launches;  // the one-row line solve
+        return;
+      }
+      if (l < h->lc) {
+        if (h->smoother == 0) {
+          fine_launches += 2;  // pass A + pass B
+        } else {                // line launches (two per relaxation), restriction, folded prolongation
+          fine_launches += (h->nu1 > 0 ? 2 * h->nu1 : 0) + 1 + (h->nu2 > 0 ? 2 * h->nu2 : 1);
+        }
+      }
       call(l + 1, kap);
       if (kap > 1) call(l + 1, kap - 1);
     }
   } w{h, calls, fine_launches, coarse};
   w.call(0, std::min(kappa, h->levels + 1));
   // one coarse-kernel launch serves both calls of a fine parent (or the whole cycle when lc == 0)
-  const long long coarse_launches = h->lc == 0 ? 1 : calls[h->lc - 1];
+  const long long coarse_launches = h->lc >= h->levels ? 0 : (h->lc == 0 ? 1 : calls[h->lc - 1]);
   if (calls_per_level)
     for (int l = 0; l < h->levels; ++l) calls_per_level[l] = calls[l];
   if (launches) *launches = fine_launches + coarse_launches;

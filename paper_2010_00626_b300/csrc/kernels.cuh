@@ -343,13 +343,18 @@ __host__ __device__ inline int line_chunk(int n) {
 
 // Offset of the tables of (level l, direction dir) in the table array: per level 2 directions x 4
 // tables (mm, cp, pi, rho) of n_l entries; n_l = 2^(k-l) - 1.
-__host__ __device__ inline size_t line_tab_offset(int k, int l, int dir) {
+// Under semi-coarsening (semi != 0) every level keeps the 2^k - 1 columns, so every table has that
+// length.
+__host__ __device__ inline size_t line_tab_offset(int k, int l, int dir, int semi = 0) {
+  if (semi) return (size_t(2) * l + dir) * 4 * ((size_t(1) << k) - 1);
   size_t off = 0;
   for (int q = 0; q < l; ++q) off += size_t(8) * ((1 << (k - q)) - 1);
   return off + size_t(dir) * 4 * ((1 << (k - l)) - 1);
 }
 
-__host__ __device__ inline size_t line_tab_size(int k, int levels) { return line_tab_offset(k, levels, 0); }
+__host__ __device__ inline size_t line_tab_size(int k, int levels, int semi = 0) {
+  return line_tab_offset(k, levels, 0, semi);
+}
 
 // Dense inverses of the line operators of the levels with side <= LINV_MAX, per level and
 // direction n*n entries (row-major, FP64): the FP64 coarse kernel applies them as one short
@@ -386,6 +391,7 @@ struct CoarseArgs {
   const T* ltab;   // zebra line tables (precision T); nullptr: damped Jacobi
   const double* linv;  // dense line inverses of the levels with side <= LINV_MAX (FP64 cycles) or nullptr
   int k;           // finest side 2^k - 1 (locates the line tables of a level)
+  int xonly;       // zebra relaxations all along x (no alternation)
 };
 
 __host__ __device__ inline int coarse_side(int n_lc, int d) {
@@ -558,7 +564,7 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
     }
     const bool dense = a.linv && s <= LINV_MAX;
     for (int it = 0; it < sweeps; ++it) {
-      const int dir = it & 1;
+      const int dir = a.xonly ? 0 : (it & 1);
       const T* mm = ltab_s + o + 2 * dir * s;
       const T* cp = mm + s;
       const double* inv = linv_s + oi + (size_t)dir * s * s;
@@ -854,7 +860,7 @@ __device__ inline void section4_stencil(double C, double S, double eps, int m, d
 // the Galerkin products.
 __global__ void setup_stencils_kernel(double theta, double eps, int n, int levels, double omega,
                                       double* coef, float* coef32, double* stencils, double* dstencil,
-                                      int rediscretized) {
+                                      int rediscretized, int semi = 0) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double h = __ddiv_rn(1.0, (double)(n + 1));
   const double h2 = __dmul_rn(h, h);
@@ -884,16 +890,20 @@ __global__ void setup_stencils_kernel(double theta, double eps, int n, int level
     fill_coef(st, omega, coef + l * NCOEF, coef32 + l * NCOEF);
     // A_c(D) = sum_{a,b} r(a) S(b) p(a + b - 2D) with r = p/4, p the bilinear hat (separable):
     // (A P e_J)(y) = sum_b S(b) p(y + b - 2J) and (R g)(I) = sum_a r(a) g(2I + a).
+    // Semi-coarsening along y: the x factors are the identity (r_x = p_x = delta, no halving), and
+    // r_y = p_y / 2. Every product is the entry times a power of two, so the sum is exact.
     double sc[9];
     for (int Dy = -1; Dy <= 1; ++Dy)
       for (int Dx = -1; Dx <= 1; ++Dx) {
         DD acc{0.0, 0.0};
         for (int ay = -1; ay <= 1; ++ay)
           for (int ax = -1; ax <= 1; ++ax) {
-            const double r = 0.25 * hat1(ay) * hat1(ax);
+            const double r = semi ? (ax == 0 ? 0.5 * hat1(ay) : 0.0) : 0.25 * hat1(ay) * hat1(ax);
+            if (r == 0.0) continue;
             for (int by = -1; by <= 1; ++by)
               for (int bx = -1; bx <= 1; ++bx) {
-                const double pv = hat1(ay + by - 2 * Dy) * hat1(ax + bx - 2 * Dx);
+                const double px = semi ? (ax + bx == Dx ? 1.0 : 0.0) : hat1(ax + bx - 2 * Dx);
+                const double pv = hat1(ay + by - 2 * Dy) * px;
                 if (pv != 0.0) acc = dd_add(acc, DD{__dmul_rn(__dmul_rn(r, st[(by + 1) * 3 + (bx + 1)]), pv), 0.0});
               }
           }

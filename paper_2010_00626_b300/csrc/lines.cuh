@@ -25,16 +25,17 @@
 namespace kc {
 
 // One thread per (level, direction). Levels with side <= LINV_MAX also get the dense inverse
-// (column q solves T x = e_q with the same factors).
+// (column q solves T x = e_q with the same factors). Under semi-coarsening every line has 2^k - 1
+// points.
 __global__ void line_tables_kernel(const double* coef, int k, int levels, double* tab, float* tab32,
-                                   double* linv) {
+                                   double* linv, int semi) {
   const int id = blockIdx.x * blockDim.x + threadIdx.x;
   if (id >= 2 * levels) return;
   const int l = id >> 1, dir = id & 1;
-  const int n = (1 << (k - l)) - 1, mc = line_chunk(n);
+  const int n = semi ? (1 << k) - 1 : (1 << (k - l)) - 1, mc = line_chunk(n);
   const double d = coef[l * NCOEF + C_C0];
   const double a = coef[l * NCOEF + (dir == 0 ? C_WE : C_NS)];
-  const size_t off = line_tab_offset(k, l, dir);
+  const size_t off = line_tab_offset(k, l, dir, semi);
   double* mm = tab + off;
   double* cp = mm + n;
   double* pi = cp + n;
@@ -52,7 +53,7 @@ __global__ void line_tables_kernel(const double* coef, int k, int levels, double
     rho[t] = last ? -cp[t] : rho[t + 1] * -cp[t];
   }
   for (int q = 0; q < 4 * n; ++q) tab32[off + q] = (float)tab[off + q];
-  if (n <= LINV_MAX) {
+  if (!semi && n <= LINV_MAX) {
     double* inv = linv + line_inv_offset(k, l, dir);
     for (int q = 0; q < n; ++q) {
       double y[LINV_MAX];
@@ -77,11 +78,14 @@ struct LineArgs {
   const T* coef;   // coefficient table (precision T)
   const T* tab;    // mm, cp, pi, rho of this level and direction, n entries each
   const int* skip;
-  const T* vc;     // nullable (rows only): neighbouring lines are read as v + P vc, the bilinear
-                   // coarse-grid correction of Algorithm 3 applied on the fly (pass B folded in)
-  int n, ld, level, ldc;
+  const T* vc;     // nullable (rows only): neighbouring lines are read as v + P vc, the coarse-grid
+                   // correction of Algorithm 3 applied on the fly (pass B folded in)
+  int n;           // points per line
+  int nl;          // number of lines (n for square grids; the rows of a semi-coarsened level)
+  int ld, level, ldc;
   int colour;      // 0: lines 0, 2, ...; 1: lines 1, 3, ...
   int zero;        // neighbouring lines are zero (first relaxation from a zero start)
+  int semi;        // vc is a semi-coarsened correction: fine row 2J+1 receives coarse row J
 };
 
 // Bilinear prolongation of the coarse correction at fine (gx, gy), in the arithmetic order of
@@ -171,15 +175,18 @@ __global__ void __launch_bounds__(32 * R) line_relax_kernel(const LineArgs<T> a)
     tile(R + 1, S + 2, [&](int q, int u) {
       const int L = first - 1 + 2 * q, t = s0 - 1 + u;
       T val = T(0);
-      if (!a.zero && L >= 0 && L < n && t >= 0 && t < n) {
+      if (!a.zero && L >= 0 && L < a.nl && t >= 0 && t < n) {
         val = a.v[(size_t)L * lstr + (size_t)t * pstr];
-        if (DIR == 0 && a.vc) val = val + prolong_point(a.vc, a.ldc, nc, t, L);
+        if (DIR == 0 && a.vc) {
+          // colour-0 neighbours are odd rows: under semi-coarsening row 2J+1 takes coarse row J
+          val = val + (a.semi ? a.vc[(size_t)(L >> 1) * a.ldc + t] : prolong_point(a.vc, a.ldc, nc, t, L));
+        }
       }
       nb[q * G::PADN + G::pad(u)] = val;
     });
     tile(R, S, [&](int q, int u) {
       const int L = first + 2 * q, t = s0 + u;
-      fs[q * G::PADS + G::pad(u)] = (L < n && t < n) ? a.f[(size_t)L * lstr + (size_t)t * pstr] : T(0);
+      fs[q * G::PADS + G::pad(u)] = (L < a.nl && t < n) ? a.f[(size_t)L * lstr + (size_t)t * pstr] : T(0);
     });
     for (int u = threadIdx.x; u < S; u += NT) {
       const int t = s0 + u;
@@ -231,7 +238,7 @@ __global__ void __launch_bounds__(32 * R) line_relax_kernel(const LineArgs<T> a)
     __syncthreads();
     tile(R, S, [&](int q, int u) {
       const int L = first + 2 * q, t = s0 + u;
-      if (L < n && t < n) a.v[(size_t)L * lstr + (size_t)t * pstr] = fs[q * G::PADS + G::pad(u)];
+      if (L < a.nl && t < n) a.v[(size_t)L * lstr + (size_t)t * pstr] = fs[q * G::PADS + G::pad(u)];
     });
   }
 
@@ -243,7 +250,7 @@ __global__ void __launch_bounds__(32 * R) line_relax_kernel(const LineArgs<T> a)
     if (sg < nseg - 1) {
       tile(R, S, [&](int q, int u) {
         const int L = first + 2 * q, t = s0 + u;
-        fs[q * G::PADS + G::pad(u)] = (L < n && t < n) ? a.v[(size_t)L * lstr + (size_t)t * pstr] : T(0);
+        fs[q * G::PADS + G::pad(u)] = (L < a.nl && t < n) ? a.v[(size_t)L * lstr + (size_t)t * pstr] : T(0);
       });
     }
     for (int u = threadIdx.x; u < S; u += NT) {
@@ -283,9 +290,70 @@ __global__ void __launch_bounds__(32 * R) line_relax_kernel(const LineArgs<T> a)
     __syncthreads();
     tile(R, S, [&](int q, int u) {
       const int L = first + 2 * q, t = s0 + u;
-      if (L < n && t < n) a.v[(size_t)L * lstr + (size_t)t * pstr] = fs[q * G::PADS + G::pad(u)];
+      if (L < a.nl && t < n) a.v[(size_t)L * lstr + (size_t)t * pstr] = fs[q * G::PADS + G::pad(u)];
     });
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Semi-coarsening along y (Section 4, solvers 5-6): f_c = R_y (f - A v), R_y = (1/4)[1 2 1] across
+// rows, and v += P_y v_c (coarse row J on fine row 2J+1, rows 2J averaging J-1 and J). Every level
+// keeps the nx columns; rows are ny (fine) and (ny-1)/2 (coarse).
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T residual_rect(const T* v, const T* f, int i, int j, int nx, int ny, int ldv, int ldf,
+                                           const Coef<T>& c) {
+  auto at = [&](int x, int y) { return ((unsigned)x < (unsigned)nx && (unsigned)y < (unsigned)ny) ? v[(size_t)y * ldv + x] : T(0); };
+  Nb<T> nb;
+  nb.c = at(i, j);
+  nb.we = at(i - 1, j) + at(i + 1, j);
+  nb.ns = at(i, j - 1) + at(i, j + 1);
+  nb.d1 = at(i - 1, j + 1) + at(i + 1, j - 1);
+  nb.d2 = at(i + 1, j + 1) + at(i - 1, j - 1);
+  return residual_at(nb, f[(size_t)j * ldf + i], c);
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) restrict_y_kernel(const T* __restrict__ v, const T* __restrict__ f, T* fc,
+                                                       const T* coef, int level, int nx, int nyc, int ldv, int ldf,
+                                                       int ldc, int vzero, const int* skip) {
+  if (skip && *skip) return;
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int J = blockIdx.y * (NT / 32) + (threadIdx.x >> 5);
+  if (i >= nx || J >= nyc) return;
+  const Coef<T> c = load_coef(coef, level);
+  const int ny = 2 * nyc + 1, y = 2 * J + 1;
+  T r0, r1, r2;
+  if (vzero) {
+    r0 = f[(size_t)(y - 1) * ldf + i];
+    r1 = f[(size_t)y * ldf + i];
+    r2 = f[(size_t)(y + 1) * ldf + i];
+  } else {
+    r0 = residual_rect(v, f, i, y - 1, nx, ny, ldv, ldf, c);
+    r1 = residual_rect(v, f, i, y, nx, ny, ldv, ldf, c);
+    r2 = residual_rect(v, f, i, y + 1, nx, ny, ldv, ldf, c);
+  }
+  fc[(size_t)J * ldc + i] = fma(T(0.25), r2, fma(T(0.5), r1, T(0.25) * r0));
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) prolong_y_add_kernel(T* v, const T* __restrict__ vc, int nx, int nyc, int ldv,
+                                                          int ldc, const int* skip) {
+  if (skip && *skip) return;
+  const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int y = blockIdx.y * (NT / 32) + (threadIdx.x >> 5);
+  const int ny = 2 * nyc + 1;
+  if (i >= nx || y >= ny) return;
+  T p;
+  if (y & 1) {
+    p = vc[(size_t)(y >> 1) * ldc + i];
+  } else {
+    const int J = y >> 1;  // between coarse rows J - 1 and J
+    const T lo = J >= 1 ? vc[(size_t)(J - 1) * ldc + i] : T(0);
+    const T hi = J < nyc ? vc[(size_t)J * ldc + i] : T(0);
+    p = T(0.5) * (lo + hi);
+  }
+  v[(size_t)y * ldv + i] += p;
 }
 
 }  // namespace kc

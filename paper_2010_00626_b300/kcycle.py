@@ -20,8 +20,9 @@ MG_OK, MG_NOT_CONVERGED = 0, 1
 MG_KAPPA_W = 0x7FFFFFFF
 CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
 MG_OPT_OMEGA, MG_OPT_COARSE_N, MG_OPT_LEVELS, MG_OPT_N, MG_OPT_LAUNCHES, MG_OPT_COARSE_N32 = 1, 2, 3, 4, 5, 6
-MG_OPT_COARSE_OP, MG_OPT_STOP, MG_OPT_SMOOTHER = 7, 8, 9
-SMOOTHERS = {"jacobi": 0, "zebra": 1}
+MG_OPT_COARSE_OP, MG_OPT_STOP, MG_OPT_SMOOTHER, MG_OPT_COARSENING = 7, 8, 9, 10
+SMOOTHERS = {"jacobi": 0, "zebra": 1, "xzebra": 2}
+COARSENINGS = {"full": 0, "y": 1}
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libkcycle.so is not built ({LIB_PATH}); run python -m paper_2010_00626_b300.build")
@@ -113,7 +114,8 @@ def _host(a, n, writable=False):
 class Multigrid:
     """One hierarchy for the Section 4 problem: ``mg_setup(n, eps, theta, levels, nu1, nu2)``."""
 
-    def __init__(self, n, eps, theta, levels, nu1=2, nu2=2, omega=None, coarse_n=None, smoother="jacobi"):
+    def __init__(self, n, eps, theta, levels, nu1=2, nu2=2, omega=None, coarse_n=None, smoother="jacobi",
+                 coarsening="full"):
         h = _h()
         _check(_lib.mg_setup(int(n), float(eps), float(theta), int(levels), int(nu1), int(nu2), ctypes.byref(h)),
                "mg_setup")
@@ -123,12 +125,14 @@ class Multigrid:
             self.set_option(MG_OPT_OMEGA, omega)
         if coarse_n is not None:
             self.set_option(MG_OPT_COARSE_N, coarse_n)
-        if smoother not in SMOOTHERS:
+        if smoother not in SMOOTHERS or coarsening not in COARSENINGS:
             self.close()
-            raise ValueError(f"smoother must be one of {sorted(SMOOTHERS)}")
-        if smoother != "jacobi":
+            raise ValueError(f"smoother must be one of {sorted(SMOOTHERS)}, coarsening one of {sorted(COARSENINGS)}")
+        if coarsening != "full":
+            self.set_option(MG_OPT_COARSENING, COARSENINGS[coarsening])  # selects x-line zebra
+        elif smoother != "jacobi":
             self.set_option(MG_OPT_SMOOTHER, SMOOTHERS[smoother])
-        self.smoother = smoother
+        self.smoother, self.coarsening = smoother, coarsening
 
     def close(self):
         if getattr(self, "_h", None):

@@ -226,4 +226,14 @@ def test_zebra_rejects_adjoint_and_switches_back(lib):
     mg.kcycle(vd, torch_dev(f), 3)
     assert rel(to_np(vd), oracle.cycle(h, np.zeros((n, n)), f, 3)) <= ITER_TOL
     with pytest.raises(lib.MultigridError):
-        mg.set_option(lib.MG_OPT_SMOOTHER, 2)
+        mg.set_option(lib.MG_OPT_SMOOTHER, 3)
+
+
+@pytest.mark.parametrize("kappa", [1, 3, KAPPA_W])
+@pytest.mark.parametrize("nu", [(2, 2), (0, 2), (2, 0)])
+def test_zebra_counters_match_graph(lib, kappa, nu):
+    n, levels = 1023, 10
+    mg = lib.Multigrid(n, 1e-4, 0.4, levels, nu1=nu[0], nu2=nu[1], smoother="zebra")
+    calls, launches, coarse = mg.counters(kappa)
+    mg.kcycle(torch_dev(np.zeros((n, n))), torch_dev(rhs_normal(n, 0)), kappa)
+    assert mg.get_option(lib.MG_OPT_LAUNCHES) == launches
