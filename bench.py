@@ -176,25 +176,33 @@ def bytes_per_point(kind, norm):
 
 PAPER_TABLE6 = {"10": {"2": 589, "3": 274, "4": 206, "W": 193}, "45": {"2": 1725, "3": 706, "4": 463, "W": 385}}
 PAPER_TABLE7 = {"10": {"4": 36}, "45": {"4": 53}}
+PAPER_TABLE8 = {"10": {"1": 1705, "2": 371, "3": 187, "4": 148}, "45": {"2": 1093, "3": 410, "4": 254}}
+PAPER_TABLE9 = {"10": {"2": 45}, "45": {"2": 79}}
 
 
-def zebra_tables(n, levels, tol, v0_host, f, settings):
-    """Alternating zebra relaxation with Galerkin coarse operators at eps = 1e-5 (Section 4, solvers
-    3-4): stand-alone cycles from a random start with f = 0 until the L2 error (the iterate) is
-    reduced by 1e8 (the Table 6 protocol), and MGCG with the kappa = 4 cycle on f ~ N(0, 1) to
-    `tol` relative residual (Table 7's solver; mg_pcg starts from x0 = 0, so the f = 0 protocol
-    does not apply to it)."""
+def zebra_tables(n, levels, tol, v0_host, f, settings, coarsening="full", mgcg_kappa=4):
+    """Zebra line relaxation with Galerkin coarse operators at eps = 1e-5 (Section 4): alternating
+    x/y relaxation with full coarsening (solvers 3-4, Tables 6-7), or x-line relaxation with
+    semi-coarsening along y (coarsening="y", solvers 5-6, Tables 8-9). Stand-alone cycles from a
+    random start with f = 0 until the L2 error (the iterate) is reduced by 1e8 (the tables'
+    protocol), and MGCG with the `mgcg_kappa` cycle on f ~ N(0, 1) to `tol` relative residual
+    (mg_pcg starts from x0 = 0, so the f = 0 protocol does not apply to it)."""
     import torch
     from paper_2010_00626_b300 import kcycle
-    out = {"setting": (f"{n}^2, {levels} levels, eps=1e-5, alternating zebra x then y (nu=2+2: one "
-                       "relaxation per direction), Galerkin coarse operators; stand-alone: f=0, "
-                       "v0~U(-1,1) seed 12345, ||v_k||/||v_0|| <= 1e-8; MGCG: f~N(0,1) seed 0, x0=0, "
-                       f"relres <= {tol:g}"),
-           "paper_table6_cycles_16383_rtx3090": PAPER_TABLE6, "paper_table7_iters_16383_rtx3090": PAPER_TABLE7}
+    semi = coarsening == "y"
+    relax = ("x-line zebra (nu=2+2, both along x), semi-coarsening along y" if semi else
+             "alternating zebra x then y (nu=2+2: one relaxation per direction)")
+    out = {"setting": (f"{n}^2, {levels} levels, eps=1e-5, {relax}, Galerkin coarse operators; stand-alone: "
+                       "f=0, v0~U(-1,1) seed 12345, ||v_k||/||v_0|| <= 1e-8; MGCG: f~N(0,1) seed 0, x0=0, "
+                       f"relres <= {tol:g}")}
+    if semi:
+        out.update({"paper_table8_cycles_16383_rtx3090": PAPER_TABLE8, "paper_table9_iters_16383_rtx3090": PAPER_TABLE9})
+    else:
+        out.update({"paper_table6_cycles_16383_rtx3090": PAPER_TABLE6, "paper_table7_iters_16383_rtx3090": PAPER_TABLE7})
     v0 = torch.tensor(v0_host, device="cuda")
     zero = torch.zeros_like(v0)
     for deg, kappas in settings:
-        mz = kcycle.Multigrid(n, 1e-5, math.radians(deg), levels, 2, 2, smoother="zebra")
+        mz = kcycle.Multigrid(n, 1e-5, math.radians(deg), levels, 2, 2, smoother="zebra", coarsening=coarsening)
         mz.set_option(kcycle.MG_OPT_STOP, 1)
         row = {}
         for k in kappas:
@@ -211,15 +219,16 @@ def zebra_tables(n, levels, tol, v0_host, f, settings):
                              "ms_per_cycle": round(a.elapsed_time(b) / max(cyc_z, 1), 3), "status": st_z}
         mz.set_option(kcycle.MG_OPT_STOP, 0)
         x = torch.zeros_like(v0)
-        mz.pcg(x, f, 4, tol, 1, history=False)
+        mz.pcg(x, f, mgcg_kappa, tol, 1, history=False)
         x.zero_()
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        st_c, it_c, rel_c, _ = mz.pcg(x, f, 4, tol, 2000, history=False)
+        st_c, it_c, rel_c, _ = mz.pcg(x, f, mgcg_kappa, tol, 2000, history=False)
         b.record()
         torch.cuda.synchronize()
-        row["mgcg_k4"] = {"iterations": it_c, "ms": round(a.elapsed_time(b), 1), "relres": rel_c, "status": st_c}
+        row[f"mgcg_k{mgcg_kappa}"] = {"iterations": it_c, "ms": round(a.elapsed_time(b), 1), "relres": rel_c,
+                                      "status": st_c}
         out[f"{deg}deg"] = row
         mz.close()
     return out
@@ -444,10 +453,12 @@ def main():
         mp.close()
 
     # ---------------------------------------------------------------- zebra line relaxation (Tables 6-7 setting)
-    zebra = None
+    zebra = semi = None
     if not args.no_sweep and world == 1:
         zebra = zebra_tables(n, levels, tol, np.random.default_rng(12345).uniform(-1.0, 1.0, (n, n)),
                              f, ((10, (2, 3, 4, KAPPA_W)), (45, (3, 4))))
+        semi = zebra_tables(n, levels, tol, np.random.default_rng(12345).uniform(-1.0, 1.0, (n, n)),
+                            f, ((10, (2, 3)), (45, (2, 3))), coarsening="y", mgcg_kappa=2)
     paper_scale = None
     if args.paper_scale and world == 1:
         # the paper's own size: 14 levels, 16383^2 (268M unknowns), 45 degrees
@@ -514,7 +525,7 @@ def main():
                 "roofline": roofline, "cycle_share": cycle_share, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clocks.summary(), "per_kappa": per_kappa,
                 "per_kappa_mixed": per_kappa_mixed, "batched": batched, "model": model_report,
-                "paper_protocol": paper_protocol, "zebra": zebra}
+                "paper_protocol": paper_protocol, "zebra": zebra, "semi_coarsening": semi}
         if paper_scale is not None:
             line["zebra_16383"] = paper_scale
         print(json.dumps(line), flush=True)

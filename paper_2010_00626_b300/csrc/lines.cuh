@@ -20,6 +20,8 @@
 // update is in place.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "kernels.cuh"
 
 namespace kc {
@@ -293,6 +295,141 @@ __global__ void __launch_bounds__(32 * R) line_relax_kernel(const LineArgs<T> a)
       if (L < a.nl && t < n) a.v[(size_t)L * lstr + (size_t)t * pstr] = fs[q * G::PADS + G::pad(u)];
     });
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Long rows, few of them (the deep levels of semi-coarsening keep every column): one row per
+// cluster of CL CTAs (CL SMs), so no segments and no single SM's FP64 pipe in the way (one SM
+// needs about 15 us for a 4095-point row). Each thread streams its chunk from global memory; the
+// chunk products are formed on the fly (two more FP64 operations per point than the tabulated
+// ones), so only mm and cp are read. CTA rank r of a cluster owns
+// points [r NT MC, (r+1) NT MC) of the cluster's row; the CTA totals of the two scans are
+// exchanged through distributed shared memory between cluster barriers.
+// ---------------------------------------------------------------------------------------------
+template <typename T, int MC, int NT, int CL>
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) line_cluster_kernel(const LineArgs<T> a) {
+  namespace cg = cooperative_groups;
+  if (a.skip && *a.skip) return;  // the flag is the same for every CTA of the grid
+  constexpr int NW = NT / 32;
+  static_assert(NW <= 32, "one warp scans the warp totals");
+  __shared__ T wa[NW], wb[NW];
+  __shared__ T ca, cb;  // this CTA's total map, read by the other CTAs of the cluster
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int n = a.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int L = a.colour + 2 * (blockIdx.x / CL);  // one row per cluster
+  const size_t ld = (size_t)a.ld;
+  const Coef<T> c = load_coef(a.coef, a.level);
+  const T* mmg = a.tab;
+  const T* cpg = mmg + n;
+  const int t0 = (rank * NT + threadIdx.x) * MC;
+  const int cnt = max(0, min(MC, n - t0));
+  const bool hasP = !a.zero && L - 1 >= 0, hasQ = !a.zero && L + 1 < a.nl;
+  const int nc = (n - 1) / 2;
+  auto nbv = [&](bool has, int row, int t) -> T {
+    if (!has || t < 0 || t >= n) return T(0);
+    T val = a.v[(size_t)row * ld + t];
+    if (a.vc) val = val + (a.semi ? a.vc[(size_t)(row >> 1) * a.ldc + t] : prolong_point(a.vc, a.ldc, nc, t, row));
+    return val;
+  };
+  const T* fl = a.f + (size_t)L * ld;
+
+  T bv[MC], gv[MC];
+  {
+    T pm = nbv(hasP, L - 1, t0 - 1), p0 = nbv(hasP, L - 1, t0);
+    T qm = nbv(hasQ, L + 1, t0 - 1), q0 = nbv(hasQ, L + 1, t0);
+#pragma unroll
+    for (int j = 0; j < MC; ++j) {
+      bv[j] = T(0);
+      gv[j] = T(1);
+      if (j < cnt) {
+        const int t = t0 + j;
+        const T pp = nbv(hasP, L - 1, t + 1), qp = nbv(hasQ, L + 1, t + 1);
+        T r = fl[t];
+        r = fma(-c.cns, p0 + q0, r);
+        r = fma(-c.cnw, pp + qm, r);
+        r = fma(-c.cne, pm + qp, r);
+        bv[j] = mmg[t] * r;
+        gv[j] = -cpg[t];
+        pm = p0; p0 = pp; qm = q0; q0 = qp;
+      }
+    }
+  }
+  // ---- forward
+  T y = T(0), A = T(1);
+#pragma unroll
+  for (int j = 0; j < MC; ++j) {
+    if (j < cnt) {
+      y = fma(gv[j], y, bv[j]);
+      bv[j] = y;
+      A = A * gv[j];
+    }
+  }
+  T B = y;
+  affine_scan<true>(A, B, lane);
+  if (lane == 31) { wa[warp] = A; wb[warp] = B; }
+  __syncthreads();
+  if (warp == 0) {
+    T a2 = lane < NW ? wa[lane] : T(1), b2 = lane < NW ? wb[lane] : T(0);
+    affine_scan<true>(a2, b2, lane);
+    if (lane < NW) { wa[lane] = a2; wb[lane] = b2; }
+    if (lane == NW - 1) { ca = a2; cb = b2; }
+  }
+  cluster.sync();
+  T ycta = T(0);  // y entering this CTA's first point: the lower ranks' maps applied from zero
+  for (int q = 0; q < rank; ++q) ycta = fma(*cluster.map_shared_rank(&ca, q), ycta, *cluster.map_shared_rank(&cb, q));
+  T Ain = __shfl_up_sync(0xffffffffu, A, 1), Bin = __shfl_up_sync(0xffffffffu, B, 1);
+  if (lane == 0) { Ain = T(1); Bin = T(0); }
+  const T ywarp = warp > 0 ? fma(wa[warp - 1], ycta, wb[warp - 1]) : ycta;
+  const T yin = fma(Ain, ywarp, Bin);
+  {
+    T pr = T(1);
+#pragma unroll
+    for (int j = 0; j < MC; ++j) {
+      if (j < cnt) {
+        pr = pr * gv[j];
+        bv[j] = fma(pr, yin, bv[j]);
+      }
+    }
+  }
+  // ---- backward
+  T x = T(0), E = T(1);
+#pragma unroll
+  for (int j = MC - 1; j >= 0; --j) {
+    if (j < cnt) {
+      x = fma(gv[j], x, bv[j]);
+      bv[j] = x;
+      E = E * gv[j];
+    }
+  }
+  T D = x;
+  affine_scan<false>(E, D, lane);
+  cluster.sync();  // every CTA has read the forward totals (ca, cb, wa, wb)
+  if (lane == 0) { wa[warp] = E; wb[warp] = D; }
+  __syncthreads();
+  if (warp == 0) {
+    T a2 = lane < NW ? wa[lane] : T(1), b2 = lane < NW ? wb[lane] : T(0);
+    affine_scan<false>(a2, b2, lane);
+    if (lane < NW) { wa[lane] = a2; wb[lane] = b2; }
+    if (lane == 0) { ca = a2; cb = b2; }
+  }
+  cluster.sync();
+  T xcta = T(0);  // x at the first point after this CTA: the higher ranks' maps applied from zero
+  for (int q = CL - 1; q > rank; --q) xcta = fma(*cluster.map_shared_rank(&ca, q), xcta, *cluster.map_shared_rank(&cb, q));
+  T Eup = __shfl_down_sync(0xffffffffu, E, 1), Dup = __shfl_down_sync(0xffffffffu, D, 1);
+  if (lane == 31) { Eup = T(1); Dup = T(0); }
+  const T xwarp = warp + 1 < NW ? fma(wa[warp + 1], xcta, wb[warp + 1]) : xcta;
+  const T xin = fma(Eup, xwarp, Dup);
+  T* vl = a.v + (size_t)L * ld;
+  T q = T(1);
+#pragma unroll
+  for (int j = MC - 1; j >= 0; --j) {
+    if (j < cnt) {
+      q = q * gv[j];
+      vl[t0 + j] = fma(q, xin, bv[j]);
+    }
+  }
+  cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 // ---------------------------------------------------------------------------------------------
