@@ -452,22 +452,25 @@ int emit_apply(mg_ctx* h, const double* v, const double* f, double* out, double*
   return MG_OK;
 }
 
-// Rows of at least 512 points in at most LONG_ROWS lines of one colour: one CTA per row.
+// Semi-coarsened levels with at most LONG_ROWS rows of one colour: one cluster per row. (Under full
+// coarsening a level has as many lines as points per line, and the segment kernel fits.)
 constexpr int LONG_ROWS = 512;
 
 template <typename T>
 bool long_rows(const LineArgs<T>& a) {
-  return a.n >= 512 && a.n <= 16384 && (a.nl - a.colour + 1) / 2 <= LONG_ROWS;
+  return a.semi && a.n <= 16384 && (a.nl - a.colour + 1) / 2 <= LONG_ROWS;
 }
 
-// One row per cluster of 8 CTAs of 128 threads (8 SMs per row): 4, 8 or 16 points per thread.
+// One row per cluster of 8 CTAs of 128 threads (8 SMs per row): 1 to 16 points per thread.
 constexpr int ROW_CLUSTER = 8;
 
 template <typename T>
 int launch_long_rows(const LineArgs<T>& a, cudaStream_t s) {
   const int nl = (a.nl - a.colour + 1) / 2;
   const int grid = nl * ROW_CLUSTER;
-  if (a.n <= 4096) line_cluster_kernel<T, 4, 128, ROW_CLUSTER><<<grid, 128, 0, s>>>(a);
+  if (a.n <= 1024) line_cluster_kernel<T, 1, 128, ROW_CLUSTER><<<grid, 128, 0, s>>>(a);
+  else if (a.n <= 2048) line_cluster_kernel<T, 2, 128, ROW_CLUSTER><<<grid, 128, 0, s>>>(a);
+  else if (a.n <= 4096) line_cluster_kernel<T, 4, 128, ROW_CLUSTER><<<grid, 128, 0, s>>>(a);
   else if (a.n <= 8192) line_cluster_kernel<T, 8, 128, ROW_CLUSTER><<<grid, 128, 0, s>>>(a);
   else line_cluster_kernel<T, 16, 128, ROW_CLUSTER><<<grid, 128, 0, s>>>(a);
   KC_CUDA(cudaGetLastError());
