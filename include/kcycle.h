@@ -70,13 +70,18 @@ typedef enum {
                               damping; nu1 = nu2 = 2 is one relaxation in each direction; 2 zebra
                               along x only (every relaxation solves the rows). The adjoint entry
                               points return MG_ERR_ARG under the line smoothers.                 */
-  MG_OPT_COARSENING = 10   /* 0 full coarsening (default); 1 semi-coarsening along y only
+  MG_OPT_COARSENING = 10,  /* 0 full coarsening (default); 1 semi-coarsening along y only
                               (Section 4, solvers 5-6): every level keeps the n columns and halves
                               the rows, transfers are (1/4)[1 2 1] and linear interpolation across
                               rows, coarse operators Galerkin, smoother forced to 2 (x lines), and
                               the coarsest level is a single row solved exactly. Needs levels = k
                               and Galerkin operators (else MG_ERR_ARG). Reallocates the hierarchy;
                               the mixed-precision entry points return MG_ERR_ARG under it.      */
+  MG_OPT_PRECOND = 11      /* MGCG preconditioner: 0 one kappa-cycle B from zero (default); 1 the
+                              symmetrised B + B^T - B^T A B (one cycle, the residual, one adjoint
+                              cycle: error propagator (I - B^T A)(I - B A)), symmetric for every
+                              kappa. Option 1 needs damped Jacobi, full coarsening and FP64:
+                              mg_pcg returns MG_ERR_ARG otherwise, mg_pcg_mixed always.         */
 } mg_option;
 
 /* Set up the hierarchy for the Section 4 problem on an n x n interior grid.

@@ -40,7 +40,7 @@ __all__ = [
     "prolong_bilinear", "galerkin_stencil", "zero_row_sum_centre", "jacobi", "zebra_lines", "relax",
     "restrict_fw_y", "prolong_y", "galerkin_stencil_y", "Hierarchy", "CallRecorder",
     "kcycle", "gamma_cycle", "f_cycle", "kcycle_adjoint", "cycle", "cycle_adjoint",
-    "residual", "relres", "solve", "solve_error_reduction", "pcg", "param_grads", "level_sizes",
+    "residual", "relres", "solve", "solve_error_reduction", "pcg", "precondition", "param_grads", "level_sizes",
 ]
 
 
@@ -571,7 +571,19 @@ def solve_error_reduction(h: Hierarchy, v0: np.ndarray, kappa: int, reduction: f
     return v, hist
 
 
-def pcg(h: Hierarchy, b: np.ndarray, kappa: int, tol: float, max_iters: int, flexible: bool = False):
+def precondition(h: Hierarchy, r: np.ndarray, kappa: int, symmetric: bool = False) -> np.ndarray:
+    """z = B r, one kappa-cycle from zero; with ``symmetric`` the symmetrised preconditioner
+    z = (B + B^T - B^T A B) r = B r + B^T (r - A B r): the cycle, then the adjoint cycle on the
+    remaining residual, so that I - M A = (I - B^T A)(I - B A)."""
+    z = cycle(h, np.zeros_like(r), r, kappa)
+    if not symmetric:
+        return z
+    w = r - apply_stencil(h.stencil(1), z)
+    return z + cycle_adjoint(h, np.zeros_like(r), w, kappa)
+
+
+def pcg(h: Hierarchy, b: np.ndarray, kappa: int, tol: float, max_iters: int, flexible: bool = False,
+        symmetric: bool = False):
     """Conjugate gradients preconditioned by one kappa-cycle from a zero start (MGCG).
 
     x0 = 0, r = b, z = B r, p = z; each iteration: q = A p, alpha = (r.z)/(p.q),
@@ -583,7 +595,7 @@ def pcg(h: Hierarchy, b: np.ndarray, kappa: int, tol: float, max_iters: int, fle
     x = np.zeros_like(b)
     r = b.copy()
     bnorm = np.linalg.norm(b)
-    z = cycle(h, np.zeros_like(b), r, kappa)
+    z = precondition(h, r, kappa, symmetric)
     p = z.copy()
     rz = float(np.sum(r * z))
     hist = []
@@ -596,7 +608,7 @@ def pcg(h: Hierarchy, b: np.ndarray, kappa: int, tol: float, max_iters: int, fle
         hist.append(rho)
         if rho <= tol:
             break
-        z_new = cycle(h, np.zeros_like(b), r, kappa)
+        z_new = precondition(h, r, kappa, symmetric)
         if flexible:
             rz_new = float(np.sum(r * z_new))
             beta = float(np.sum(r * (z_new - z))) / rz

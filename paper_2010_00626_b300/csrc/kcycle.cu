@@ -126,10 +126,12 @@ struct mg_ctx {
   int stop_rule = 0;      // 0: ||f - A v|| / ||f|| <= tol; 1: ||v_k|| / ||v_0|| <= tol (f = 0 protocol)
   int smoother = 0;       // 0 damped Jacobi, 1 alternating zebra line Gauss-Seidel, 2 zebra along x only
   int semi = 0;           // 1: semi-coarsening along y (every level keeps the n columns)
+  int precond = 0;        // MGCG preconditioner: 0 the kappa-cycle B, 1 B + B^T - B^T A B
   double* ltab = nullptr;  // line-solve tables (Thomas factors and chunk products) per level/direction
   float* ltab32 = nullptr;
   double* linv = nullptr;  // dense line inverses of the levels with side <= LINV_MAX
   double *pr = nullptr, *pp = nullptr, *pq = nullptr, *pz = nullptr, *pzold = nullptr;  // PCG vectors
+  double *pw = nullptr, *pz2 = nullptr;  // symmetrised preconditioner: r - A B r and B^T (r - A B r)
   double *hv = nullptr, *hf = nullptr;  // device copies for mg_solve_host
   cudaStream_t own = nullptr;
   cudaStream_t ext = nullptr;
@@ -1037,7 +1039,7 @@ int mg_destroy(mg_handle h) {
   if (h->own) cudaStreamSynchronize(h->own);
   drop_graphs(h);
   free_levels(h);
-  void* ptrs[] = {h->coef, h->coef32, h->stencils, h->dstencil, h->ltab, h->ltab32, h->linv, h->cinv, h->cinv32, h->work, h->partial,
+  void* ptrs[] = {h->pw, h->pz2, h->coef, h->coef32, h->stencils, h->dstencil, h->ltab, h->ltab32, h->linv, h->cinv, h->cinv32, h->work, h->partial,
                   h->partial2, h->scal, h->ints, h->hist, h->pr, h->pp, h->pq, h->pz, h->pzold, h->hv, h->hf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -1130,6 +1132,12 @@ int mg_set_option(mg_handle h, int key, double value) {
       drop_graphs(h);
       return MG_OK;
     }
+    case MG_OPT_PRECOND: {
+      if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
+      h->precond = (int)value;
+      drop_graphs(h);
+      return MG_OK;
+    }
     case MG_OPT_COARSENING: {
       if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
       if (value == 1.0 && (h->levels != h->k || h->rediscretized)) return MG_ERR_ARG;
@@ -1170,6 +1178,7 @@ int mg_get_option(mg_handle h, int key, double* value) {
     case MG_OPT_STOP: *value = h->stop_rule; return MG_OK;
     case MG_OPT_SMOOTHER: *value = h->smoother; return MG_OK;
     case MG_OPT_COARSENING: *value = h->semi; return MG_OK;
+    case MG_OPT_PRECOND: *value = h->precond; return MG_OK;
     case MG_OPT_LEVELS: *value = h->levels; return MG_OK;
     case MG_OPT_N: *value = h->n; return MG_OK;
     case MG_OPT_LAUNCHES: *value = h->last_launches; return MG_OK;
@@ -1232,22 +1241,41 @@ static int pcg_impl(mg_handle h, double* x, const double* b, int kappa, double t
                     bool mixed, int* iters, double* final_relres, double* history) {
   if (!valid_handle(h)) return MG_ERR_STATE;
   if (!x || !b || kappa < 1 || !(tol > 0) || max_iters < 1) return MG_ERR_ARG;
+  const bool sym = h->precond == 1;
+  if (sym && (mixed || h->smoother != 0)) return MG_ERR_ARG;  // the adjoint cycle: FP64 damped Jacobi
   trim_graphs(h);
   const size_t len = (size_t)h->n * h->n, bytes = sizeof(double) * len;
   double** vecs[] = {&h->pr, &h->pp, &h->pq, &h->pz, &h->pzold};
   for (double** p : vecs)
     if (!*p) KC_CUDA(cudaMalloc(p, bytes));
+  if (sym) {
+    if (!h->pw) KC_CUDA(cudaMalloc(&h->pw, bytes));
+    if (!h->pz2) KC_CUDA(cudaMalloc(&h->pz2, bytes));
+  }
   if (mixed) KC_TRY(ensure_levels32(h));
   KC_TRY(ensure_hist(h, max_iters));
   cudaStream_t s = h->stream();
   const int* done = h->ints + I_DONE;
   float* r32 = h->lv[0].f32;
   float* z32 = h->lv[0].v32;
-  // z = B r from a zero start: FP64 cycle, or r -> FP32, FP32 cycle, z <- FP64
+  // z = B r from a zero start: FP64 cycle, or r -> FP32, FP32 cycle, z <- FP64; symmetrised:
+  // z = B r, w = r - A z, z += B^T w (the adjoint cycle from zero)
   auto emit_precond = [&](cudaStream_t o, const int* skip) -> int {
     if (!mixed) {
       Binding bz{h->pz, h->pr, h->n};
-      return emit_cycle(h, bz, kappa, true, false, false, skip, o);
+      KC_TRY(emit_cycle(h, bz, kappa, true, false, false, skip, o));
+      if (!sym) return MG_OK;
+      const int n = h->n;
+      dim3 agrid((n + 31) / 32, (n + NT_VEC / 32 - 1) / (NT_VEC / 32));
+      apply_kernel<double, NT_VEC><<<agrid, NT_VEC, 0, o>>>(h->pz, h->pr, h->pw, h->coef, 0, n, n, nullptr, skip);
+      KC_CUDA(cudaGetLastError());
+      ++h->launch_count;
+      Binding bw{h->pz2, h->pw, h->n};
+      KC_TRY(emit_cycle(h, bw, kappa, true, true, false, skip, o));
+      vec_add_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, o>>>(h->pz, h->pz2, len, skip);
+      KC_CUDA(cudaGetLastError());
+      ++h->launch_count;
+      return MG_OK;
     }
     const int n = h->n;
     dim3 cgrid((n + 31) / 32, (n + NT_VEC / 32 - 1) / (NT_VEC / 32));
@@ -1259,7 +1287,7 @@ static int pcg_impl(mg_handle h, double* x, const double* b, int kappa, double t
     h->launch_count += 2;
     return MG_OK;
   };
-  const int fl = (flexible ? 1 : 0) | (mixed ? 2 : 0);
+  const int fl = (flexible ? 1 : 0) | (mixed ? 2 : 0) | (sym ? 4 : 0);
   GraphEntry* ge = find_graph(h, G_PCG, kappa, fl, x, b);
   if (!ge) {
     GraphEntry e;

@@ -1152,6 +1152,13 @@ __global__ void __launch_bounds__(NT) pcg_p_kernel(double* p, const double* z, d
   }
 }
 
+// x += y (the two halves of the symmetrised preconditioner).
+template <int NT>
+__global__ void __launch_bounds__(NT) vec_add_kernel(double* x, const double* y, size_t len, const int* skip) {
+  if (skip && *skip) return;
+  for (size_t k = blockIdx.x * (size_t)NT + threadIdx.x; k < len; k += (size_t)gridDim.x * NT) x[k] += y[k];
+}
+
 // Parameter gradients: partial sums of lambda . (dA/dtheta u) and lambda . (dA/deps u).
 template <int NT>
 __global__ void __launch_bounds__(NT) grad_kernel(const double* lam, const double* u, int n, const double* dst,

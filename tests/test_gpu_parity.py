@@ -292,3 +292,25 @@ def test_rediscretized_hierarchy_and_error_protocol(lib):
     assert st_ == 0 and cycles == len(hist_or) and red <= 1e-8
     for a, b in zip(hist, hist_or):
         assert abs(a - b) <= HIST_TOL * b + ITER_TOL
+
+
+@pytest.mark.parametrize("kappa", [2, 3, 4])
+def test_symmetrised_pcg_matches_oracle(lib, kappa):
+    """MGCG with M = B + B^T - B^T A B (a cycle, the residual, an adjoint cycle)."""
+    n, levels, theta, eps = 255, 8, 0.7, 1e-4
+    h = oracle.Hierarchy(n, levels, theta, eps)
+    b = rhs_uniform(n, 7)
+    x_or, hist_or = oracle.pcg(h, b, kappa, 1e-10, 200, symmetric=True)
+    mg = lib.Multigrid(n, eps, theta, levels)
+    mg.set_option(lib.MG_OPT_PRECOND, 1)
+    xd = torch_dev(np.zeros((n, n)))
+    st, iters, relres, hist = mg.pcg(xd, torch_dev(b), kappa, 1e-10, 200)
+    assert st == 0 and iters == len(hist_or)
+    for a, c in zip(hist, hist_or):
+        assert abs(a - c) <= HIST_TOL * c + 1e-13
+    assert rel(to_np(xd), x_or) <= 1e-10
+    with pytest.raises(lib.MultigridError):
+        mg.pcg(xd, torch_dev(b), kappa, 1e-10, 200, mixed=True)
+    mg.set_option(lib.MG_OPT_SMOOTHER, 1)
+    with pytest.raises(lib.MultigridError):
+        mg.pcg(xd, torch_dev(b), kappa, 1e-10, 200)

@@ -97,3 +97,41 @@ def test_adjoint_solve_gives_lambda():
     lam, hist = oracle.solve(h, g, 3, 1e-13, 300, adjoint=True)
     exact = scipy.linalg.solve(dense_A(h.stencil(1), n), g.ravel(), assume_a="pos").reshape(n, n)
     assert np.linalg.norm(lam - exact) <= 1e-10 * np.linalg.norm(exact)
+
+
+def _dense_map(fn, n):
+    cols = []
+    for k in range(n * n):
+        e = np.zeros(n * n)
+        e[k] = 1.0
+        cols.append(fn(e.reshape(n, n)).ravel())
+    return np.stack(cols, axis=1)
+
+
+@pytest.mark.parametrize("kappa", [2, 3])
+def test_symmetrised_preconditioner_is_symmetric_and_two_sided(kappa):
+    """For 1 < kappa < levels the kappa-cycle B is not symmetric; M = B + B^T - B^T A B is, and its
+    error propagator is (I - B^T A)(I - B A): a cycle followed by the adjoint cycle."""
+    n, levels = 31, 5
+    h = oracle.Hierarchy(n, levels, 0.7, 1e-2)
+    A = dense_A(h.stencil(1), n)
+    B = _dense_map(lambda r: oracle.cycle(h, np.zeros((n, n)), r, kappa), n)
+    Bt = _dense_map(lambda r: oracle.cycle_adjoint(h, np.zeros((n, n)), r, kappa), n)
+    M = _dense_map(lambda r: oracle.precondition(h, r, kappa, symmetric=True), n)
+    scale = np.abs(M).max()
+    assert np.abs(B - B.T).max() > 1e-6 * np.abs(B).max()          # B itself is not symmetric
+    assert np.abs(M - M.T).max() <= 1e-12 * scale
+    I = np.eye(n * n)
+    assert np.abs((I - M @ A) - (I - Bt @ A) @ (I - B @ A)).max() <= 1e-12
+    assert np.all(np.linalg.eigvalsh(0.5 * (M + M.T)) > 0)         # a valid CG preconditioner here
+
+
+def test_symmetrised_pcg_converges_to_dense_solution():
+    n, levels = 31, 5
+    h = oracle.Hierarchy(n, levels, 1.1, 1e-4)
+    b = rhs_uniform(n, 12)
+    exact = scipy.linalg.solve(dense_A(h.stencil(1), n), b.ravel(), assume_a="pos").reshape(n, n)
+    for kappa in (2, 3):
+        x, hist = oracle.pcg(h, b, kappa, 1e-12, 200, symmetric=True)
+        assert hist[-1] <= 1e-12
+        assert np.linalg.norm(x - exact) <= 1e-9 * np.linalg.norm(exact)
