@@ -468,6 +468,36 @@ def main():
                                    f14, ((45, (4,)),))
         del f14
 
+    # ---------------------------------------------------------------- MGCG 8191^2 (the preconditioner workload)
+    mgcg = None
+    if not args.no_sweep and world == 1:
+        from paper_2010_00626_b300.inputs import PCG_LARGE, pcg_theta
+        n8, lev8, eps8 = PCG_LARGE["n"], PCG_LARGE["levels"], 1e-5
+        th8 = pcg_theta(0)
+        m8 = kcycle.Multigrid(n8, eps8, th8, lev8)
+        b8 = torch.tensor(rhs_normal(n8, 0), device="cuda")
+        x8 = torch.zeros_like(b8)
+        mgcg = {"workload": f"{n8}^2, {lev8} levels, theta={th8:.6f} (seed 0), eps={eps8:g}, b~N(0,1), x0=0, "
+                            "tol 1e-10; kappa>1 cycles are not symmetric: flexible beta, or the symmetrised "
+                            "preconditioner B+B^T-B^TAB with plain CG"}
+        runs = [("fp64", 1, 0, False), ("fp64", 2, 0, True), ("fp64", 3, 0, True), ("fp64", 4, 0, True),
+                ("fp64_symmetrised", 2, 1, False), ("fp64_symmetrised", 3, 1, False), ("mixed", 3, 0, True)]
+        for name, k8, sym, flex in runs:
+            m8.set_option(kcycle.MG_OPT_PRECOND, sym)
+            mixed = name == "mixed"
+            m8.pcg(x8, b8, k8, 1e-10, 1, flexible=flex, mixed=mixed, history=False)  # builds the graph
+            x8.zero_()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            st8, it8, rel8, _ = m8.pcg(x8, b8, k8, 1e-10, 2000, flexible=flex, mixed=mixed, history=False)
+            b.record()
+            torch.cuda.synchronize()
+            mgcg[f"{name}_k{k8}"] = {"ms": round(a.elapsed_time(b), 1), "iterations": it8, "relres": rel8,
+                                     "status": st8, "flexible": flex}
+        m8.close()
+        del b8, x8
+
     # ---------------------------------------------------------------- batched (256 ragged instances, one launch each)
     batched = None
     if not args.no_sweep and world == 1:
@@ -525,7 +555,7 @@ def main():
                 "roofline": roofline, "cycle_share": cycle_share, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clocks.summary(), "per_kappa": per_kappa,
                 "per_kappa_mixed": per_kappa_mixed, "batched": batched, "model": model_report,
-                "paper_protocol": paper_protocol, "zebra": zebra, "semi_coarsening": semi}
+                "paper_protocol": paper_protocol, "zebra": zebra, "semi_coarsening": semi, "mgcg_8191": mgcg}
         if paper_scale is not None:
             line["zebra_16383"] = paper_scale
         print(json.dumps(line), flush=True)

@@ -193,9 +193,14 @@ __global__ void __launch_bounds__(NT) pass_a_kernel(const PassAArgs<T> a) {
   for (int s = 1; s <= a.nu; ++s) {
     const int g = a.nu - s + 1;  // sweep s is needed on the tile grown by g
     const int lo = H - g, R = BX + 2 * g + 1, Ry = BY + 2 * g + 1;
+    // from a zero start the first sweep is v = w f, which is what the update gives on zeros
+    // (fma(w, f, 0) and every further fma(b, 0, t) = t), in one operation instead of ten
+    const bool from_zero = s == 1 && a.vin == nullptr;
     for_region<NT>(R, Ry, [&](int rx, int ry) {
       const int lx = lo + rx, ly = lo + ry, k = ly * W + lx;
-      dst[k] = inside(gx0 + lx, gy0 + ly, n) ? jacobi_update(neighbours(src, k, W), fs[k], c) : T(0);
+      dst[k] = inside(gx0 + lx, gy0 + ly, n)
+                   ? (from_zero ? c.w * fs[k] : jacobi_update(neighbours(src, k, W), fs[k], c))
+                   : T(0);
     });
     __syncthreads();
     T* t = src; src = dst; dst = t;
