@@ -127,6 +127,11 @@ struct mg_ctx {
   int smoother = 0;       // 0 damped Jacobi, 1 alternating zebra line Gauss-Seidel, 2 zebra along x only
   int semi = 0;           // 1: semi-coarsening along y (every level keeps the n columns)
   int precond = 0;        // MGCG preconditioner: 0 the kappa-cycle B, 1 B + B^T - B^T A B
+  // condensed coarse calls: the affine maps of a call at the side-7 level, per counter class, for
+  // the FP64 and FP32 coarse kernels (valid while the flags are set)
+  double* cmap = nullptr;
+  float* cmap32 = nullptr;
+  bool maps_ok = false, maps32_ok = false;
   double* ltab = nullptr;  // line-solve tables (Thomas factors and chunk products) per level/direction
   float* ltab32 = nullptr;
   double* linv = nullptr;  // dense line inverses of the levels with side <= LINV_MAX
@@ -251,6 +256,8 @@ struct Arr<double> {
   static double* f(mg_ctx* h, int l) { return h->lv[l].f; }
   static const double* coef(mg_ctx* h) { return h->coef; }
   static const double* ltab(mg_ctx* h) { return h->ltab; }
+  static double* cmap(mg_ctx* h) { return h->cmap; }
+  static bool maps_ok(mg_ctx* h) { return h->maps_ok; }
   static int ld(mg_ctx* h, int l) { return h->lv[l].ld; }
 };
 template <>
@@ -260,6 +267,8 @@ struct Arr<float> {
   static float* f(mg_ctx* h, int l) { return h->lv[l].f32; }
   static const float* coef(mg_ctx* h) { return h->coef32; }
   static const float* ltab(mg_ctx* h) { return h->ltab32; }
+  static float* cmap(mg_ctx* h) { return h->cmap32; }
+  static bool maps_ok(mg_ctx* h) { return h->maps32_ok; }
   static int ld(mg_ctx* h, int l) { return l == 0 ? h->ld32_0 : h->lv[l].ld; }
 };
 
@@ -322,6 +331,15 @@ int launch_pass_b_stream(const PassBArgs<float>& a, cudaStream_t s) {
   return MG_OK;
 }
 
+// Level whose calls the coarse kernel condenses into precomputed affine maps: the side-7 level,
+// when a coarser level exists (-1 otherwise, and under semi-coarsening).
+int map_level(const mg_ctx* h) {
+  const int d = h->k - 3;
+  return (!h->semi && d >= 0 && d < h->levels - 1) ? d : -1;
+}
+constexpr int MAP_S = 49;       // unknowns of the side-7 level
+constexpr int MAP_CLASSES = 3;  // at most two levels below it: counters 1, 2, >= 3
+
 template <typename T>
 int emit_coarse(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int zero1, bool adjoint, const int* skip,
                 cudaStream_t s) {
@@ -348,6 +366,12 @@ int emit_coarse(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int zero1, bool
   a.linv = (h->smoother == 1 && std::is_same<T, double>::value) ? h->linv : nullptr;
   a.k = h->k;
   a.xonly = h->smoother == 2 ? 1 : 0;
+  const int dm = map_level(h);
+  a.cmap = (!adjoint && dm >= lc && Arr<T>::maps_ok(h)) ? Arr<T>::cmap(h) : nullptr;
+  a.dcond = dm - lc;
+  a.ncls = h->levels - dm;
+  a.basis = 0;
+  a.cmap_out = nullptr;
   const size_t sm = coarse_smem<T>(a.n_lc, a.L - a.lc);
   prof_begin(h, K_COARSE, lc, s);
   if (a.ltab)
@@ -358,6 +382,53 @@ int emit_coarse(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int zero1, bool
   KC_CUDA(cudaGetLastError());
   ++h->launch_count;
   return MG_OK;
+}
+
+// The maps of condensed calls: one map-mode launch of the coarse kernel per counter class, whose
+// 2 S blocks run a call at the side-7 level from each unit vector of v and of f. Runs on the
+// handle's own stream outside any capture.
+template <typename T>
+int compute_maps(mg_ctx* h) {
+  const int dm = map_level(h);
+  if (dm < 0) return MG_OK;
+  CoarseArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  a.coef = Arr<T>::coef(h);
+  a.coef64 = h->coef;
+  a.cinv = h->cinv;
+  a.n_lc = 7;
+  a.lc = dm;
+  a.L = h->levels;
+  a.nu1 = h->nu1;
+  a.nu2 = h->nu2;
+  a.k2 = 0;
+  a.zero1 = 0;
+  a.adjoint = 0;
+  a.ltab = h->smoother != 0 ? Arr<T>::ltab(h) : nullptr;
+  a.linv = (h->smoother != 0 && std::is_same<T, double>::value) ? h->linv : nullptr;
+  a.k = h->k;
+  a.xonly = h->smoother == 2 ? 1 : 0;
+  a.cmap = nullptr;
+  a.basis = 1;
+  const size_t sm = coarse_smem<T>(7, h->levels - dm);
+  for (int c = 1; c <= h->levels - dm; ++c) {
+    a.k1 = c;
+    a.cmap_out = Arr<T>::cmap(h) + (size_t)(c - 1) * 2 * MAP_S * MAP_S;
+    if (a.ltab)
+      coarse_kernel<T, nt_coarse<T>(), true><<<2 * MAP_S, nt_coarse<T>(), sm, h->own>>>(a);
+    else
+      coarse_kernel<T, nt_coarse<T>(), false><<<2 * MAP_S, nt_coarse<T>(), sm, h->own>>>(a);
+    KC_CUDA(cudaGetLastError());
+  }
+  KC_CUDA(cudaStreamSynchronize(h->own));
+  return MG_OK;
+}
+
+// Compute whichever maps are stale (the FP32 ones only once the FP32 hierarchy exists). A
+// failure leaves the flag clear: the coarse kernel then runs those calls step by step.
+void ensure_maps(mg_ctx* h) {
+  if (!h->maps_ok && compute_maps<double>(h) == MG_OK) h->maps_ok = true;
+  if (h->have32 && !h->maps32_ok && compute_maps<float>(h) == MG_OK) h->maps32_ok = true;
 }
 
 // With `lines` (zebra smoothing done in place by the line kernels) pass A only restricts the
@@ -699,7 +770,10 @@ GraphEntry* add_graph(mg_ctx* h, const GraphEntry& e) {
 
 // Bounded cache: forget the oldest graphs. Called only at the start of a public entry point, so
 // no GraphEntry pointer held by a caller inside the library is invalidated.
+void ensure_maps(mg_ctx* h);
+
 void trim_graphs(mg_ctx* h) {
+  ensure_maps(h);
   while (h->graphs.size() > 24) {
     auto& g = h->graphs.front();
     if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -975,6 +1049,7 @@ int ensure_levels32(mg_ctx* h) {
   }
   KC_CUDA(cudaStreamSynchronize(h->own));
   h->have32 = true;
+  ensure_maps(h);
   return MG_OK;
 }
 
@@ -998,6 +1073,7 @@ int free_levels(mg_ctx* h) {
 }
 
 int run_setup_kernels(mg_ctx* h) {
+  h->maps_ok = h->maps32_ok = false;
   setup_stencils_kernel<<<1, 32, 0, h->own>>>(h->theta, h->eps, h->n, h->levels, h->omega, h->coef, h->coef32,
                                              h->stencils, h->dstencil, h->rediscretized, h->semi);
   KC_CUDA(cudaGetLastError());
@@ -1039,7 +1115,7 @@ int mg_destroy(mg_handle h) {
   if (h->own) cudaStreamSynchronize(h->own);
   drop_graphs(h);
   free_levels(h);
-  void* ptrs[] = {h->pw, h->pz2, h->coef, h->coef32, h->stencils, h->dstencil, h->ltab, h->ltab32, h->linv, h->cinv, h->cinv32, h->work, h->partial,
+  void* ptrs[] = {h->cmap, h->cmap32, h->pw, h->pz2, h->coef, h->coef32, h->stencils, h->dstencil, h->ltab, h->ltab32, h->linv, h->cinv, h->cinv32, h->work, h->partial,
                   h->partial2, h->scal, h->ints, h->hist, h->pr, h->pp, h->pq, h->pz, h->pzold, h->hv, h->hf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -1081,6 +1157,8 @@ int mg_setup(int n, double eps, double theta, int levels, int nu1, int nu2, mg_h
   ALLOC(h->ltab, sizeof(double) * line_tab_size(k, levels, 1));  // the semi-coarsening layout is the larger
   ALLOC(h->ltab32, sizeof(float) * line_tab_size(k, levels, 1));
   ALLOC(h->linv, sizeof(double) * std::max<size_t>(1, line_inv_offset(k, levels, 0)));
+  ALLOC(h->cmap, sizeof(double) * MAP_CLASSES * 2 * MAP_S * MAP_S);
+  ALLOC(h->cmap32, sizeof(float) * MAP_CLASSES * 2 * MAP_S * MAP_S);
   ALLOC(h->partial, sizeof(double) * np);
   ALLOC(h->partial2, sizeof(double) * np);
   ALLOC(h->scal, sizeof(double) * NSCAL);
@@ -1129,6 +1207,7 @@ int mg_set_option(mg_handle h, int key, double value) {
       if (h->semi && value != 2.0) return MG_ERR_ARG;
       KC_CUDA(cudaStreamSynchronize(h->stream()));
       h->smoother = (int)value;
+      h->maps_ok = h->maps32_ok = false;
       drop_graphs(h);
       return MG_OK;
     }
@@ -1725,6 +1804,7 @@ int mg_batch_solve(mg_batch b, double* const* x, const double* const* f, int kap
     for (mg_handle h : b->inst) {
       KC_TRY(ensure_hist(h, max_iters));
       if (mixed) KC_TRY(ensure_levels32(h));
+      ensure_maps(h);
     }
     KC_CUDA(cudaGraphCreate(&b->graph, 0));
     for (size_t i = 0; i < cnt; ++i) {

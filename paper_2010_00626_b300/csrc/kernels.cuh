@@ -397,6 +397,16 @@ struct CoarseArgs {
   const double* linv;  // dense line inverses of the levels with side <= LINV_MAX (FP64 cycles) or nullptr
   int k;           // finest side 2^k - 1 (locates the line tables of a level)
   int xonly;       // zebra relaxations all along x (no alternation)
+  // Condensed calls: a call at relative level dcond with counter c is the affine map
+  // v <- M_c v + N_c f (S = side^2 unknowns), precomputed from this kernel's own recursion;
+  // cmap holds, per class c = 1..ncls (counters >= ncls use the last), M_c then N_c, each stored
+  // by columns (entry (k, b) at b * S + k). nullptr: no condensation.
+  const T* cmap;
+  int dcond, ncls;
+  // basis != 0: map mode. Block b runs one call of counter k1 at the top level from v = e_b
+  // (b < S) or f = e_(b-S) and writes the result to cmap_out + b * S.
+  int basis;
+  T* cmap_out;
 };
 
 __host__ __device__ inline int coarse_side(int n_lc, int d) {
@@ -514,10 +524,18 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
     const int s = a.n_lc;
     T* fv = fbuf(0);
     T* vv = vbuf(0, 0);
-    for (int k = threadIdx.x; k < s * s; k += NT) {
-      const int j = (int)__umulhi((unsigned)k, (unsigned)g_magic[0]), i = k - j * s;
-      fv[pos(0, k)] = a.f[(size_t)j * a.ldf + i];
-      if (!a.zero1) vv[pos(0, k)] = a.v[(size_t)j * a.ldv + i];
+    if (a.basis) {
+      const int S = s * s, b = blockIdx.x;
+      for (int k = threadIdx.x; k < S; k += NT) {
+        vv[pos(0, k)] = (b < S && k == b) ? T(1) : T(0);
+        fv[pos(0, k)] = (b >= S && k == b - S) ? T(1) : T(0);
+      }
+    } else {
+      for (int k = threadIdx.x; k < s * s; k += NT) {
+        const int j = (int)__umulhi((unsigned)k, (unsigned)g_magic[0]), i = k - j * s;
+        fv[pos(0, k)] = a.f[(size_t)j * a.ldf + i];
+        if (!a.zero1) vv[pos(0, k)] = a.v[(size_t)j * a.ldv + i];
+      }
     }
   }
   __syncthreads();
@@ -711,6 +729,34 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
         --sp;
         continue;
       }
+      if (a.cmap && fr.d == a.dcond) {  // condensed call: v <- M_c v + N_c f in one pass
+        const int d = fr.d, s = g_side[d], S = s * s;
+        const int cls = (fr.k < a.ncls ? fr.k : a.ncls) - 1;
+        const T* Mt = a.cmap + (size_t)cls * 2 * S * S;
+        const T* Nt = Mt + (size_t)S * S;
+        const unsigned bsel = (cur >> d) & 1u;
+        const T* vsrc = vbuf(d, bsel);
+        T* dst = vbuf(d, bsel ^ 1u);
+        const T* f = fbuf(d);
+        // four threads per output row (aligned lane groups), each taking every fourth column
+        for (int base = 0; base < 4 * S; base += NT) {
+          const int tid = base + (int)threadIdx.x, k = tid >> 2, p = tid & 3;
+          T acc0 = T(0), acc1 = T(0);
+          if (k < S) {
+            if (!fr.zero)
+              for (int b = p; b < S; b += 4) acc0 = fma(Mt[(size_t)b * S + k], vsrc[pos(d, b)], acc0);
+            for (int b = p; b < S; b += 4) acc1 = fma(Nt[(size_t)b * S + k], f[pos(d, b)], acc1);
+          }
+          T acc = acc0 + acc1;
+          acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+          acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+          if (k < S && p == 0) dst[pos(d, k)] = acc;
+        }
+        cur ^= 1u << d;
+        __syncthreads();
+        --sp;
+        continue;
+      }
       if (fr.state == 0) {
         smooth(fr.d, nu_pre, fr.zero != 0);
         restrict_residual(fr.d);
@@ -735,9 +781,14 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
   {
     const int s = a.n_lc;
     const T* vv = vcur(0);
-    for (int k = threadIdx.x; k < s * s; k += NT) {
-      const int j = (int)__umulhi((unsigned)k, (unsigned)g_magic[0]), i = k - j * s;
-      a.v[(size_t)j * a.ldv + i] = vv[pos(0, k)];
+    if (a.basis) {
+      T* out = a.cmap_out + (size_t)blockIdx.x * s * s;
+      for (int k = threadIdx.x; k < s * s; k += NT) out[k] = vv[pos(0, k)];
+    } else {
+      for (int k = threadIdx.x; k < s * s; k += NT) {
+        const int j = (int)__umulhi((unsigned)k, (unsigned)g_magic[0]), i = k - j * s;
+        a.v[(size_t)j * a.ldv + i] = vv[pos(0, k)];
+      }
     }
   }
 }
