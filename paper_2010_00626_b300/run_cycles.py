@@ -1,7 +1,7 @@
 """Run a fixed number of kappa-cycles on one synthetic problem through the C ABI, for profiling.
 
     python -m paper_2010_00626_b300.run_cycles --n 4095 --levels 12 --kappa 4 --cycles 1 \
-        [--smoother zebra] [--theta 1.0471975511965976] [--eps 1e-4] [--fp32]
+        [--smoother zebra] [--coarsening y] [--theta 1.0471975511965976] [--eps 1e-4] [--fp32]
 
 The right-hand side is f ~ N(0, 1) (seed 0) and the start v = 0. With --fp32 the cycles are the
 FP32 cycles of the mixed forms (mg_kcycle_f32). Prints one JSON line with the wall time; the
@@ -21,7 +21,8 @@ def main():
     ap.add_argument("--cycles", type=int, default=1)
     ap.add_argument("--theta", type=float, default=math.pi / 3)
     ap.add_argument("--eps", type=float, default=1e-4)
-    ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "zebra"])
+    ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "zebra", "xzebra"])
+    ap.add_argument("--coarsening", default="full", choices=["full", "y"])
     ap.add_argument("--fp32", action="store_true")
     args = ap.parse_args()
 
@@ -34,7 +35,7 @@ def main():
 
     n = args.n
     levels = args.levels or int(round(math.log2(n + 1)))
-    mg = kcycle.Multigrid(n, args.eps, args.theta, levels, smoother=args.smoother)
+    mg = kcycle.Multigrid(n, args.eps, args.theta, levels, smoother=args.smoother, coarsening=args.coarsening)
     dt = torch.float32 if args.fp32 else torch.float64
     f = torch.tensor(rhs_normal(n, 0), device="cuda").to(dt)
     v = torch.zeros_like(f)
@@ -47,7 +48,7 @@ def main():
             mg.kcycle(v, f, args.kappa)
     torch.cuda.synchronize()
     print(json.dumps({"n": n, "levels": levels, "kappa": args.kappa, "cycles": args.cycles,
-                      "smoother": args.smoother, "fp32": args.fp32,
+                      "smoother": args.smoother, "coarsening": args.coarsening, "fp32": args.fp32,
                       "wall_ms": 1e3 * (time.perf_counter() - t0)}))
 
 
