@@ -36,7 +36,7 @@ import numpy as np
 import scipy.linalg
 
 __all__ = [
-    "cos_sin", "fine_stencil", "fine_stencil_derivatives", "apply_stencil", "restrict_fw",
+    "cos_sin", "fine_stencil", "convection_stencil", "fine_stencil_derivatives", "apply_stencil", "restrict_fw",
     "prolong_bilinear", "galerkin_stencil", "zero_row_sum_centre", "jacobi", "zebra_lines", "relax",
     "restrict_fw_y", "prolong_y", "galerkin_stencil_y", "Hierarchy", "CallRecorder",
     "kcycle", "gamma_cycle", "f_cycle", "kcycle_adjoint", "cycle", "cycle_adjoint",
@@ -96,6 +96,28 @@ def fine_stencil(theta: float, eps: float, n: int) -> np.ndarray:
     st[2, 2] = -cross                             # north-east
     st[0, 0] = -cross                             # south-west
     return st / (h * h)
+
+
+def convection_stencil(st: np.ndarray, bx: float, by: float, n: int) -> np.ndarray:
+    """The Section 4 stencil plus first-order upwind convection b . grad u, b = (bx, by): the
+    non-symmetric test problem the conclusions suggest (Section 5), -div(K grad u) + b . grad u.
+    bx > 0 differences u backwards in x, (u_i - u_(i-1)) / h: centre +bx/h, west -bx/h; bx < 0
+    forwards: centre +|bx|/h, east -|bx|/h; likewise in y (south / north). With 1/h = n + 1:
+    cx = |bx| (n + 1), cy = |by| (n + 1), centre += (cx + cy), each step rounded once.
+    """
+    out = st.copy()
+    cx = abs(bx) * float(n + 1)
+    cy = abs(by) * float(n + 1)
+    out[1, 1] = out[1, 1] + (cx + cy)
+    if bx > 0:
+        out[1, 0] = out[1, 0] - cx
+    elif bx < 0:
+        out[1, 2] = out[1, 2] - cx
+    if by > 0:
+        out[0, 1] = out[0, 1] - cy
+    elif by < 0:
+        out[2, 1] = out[2, 1] - cy
+    return out
 
 
 def fine_stencil_derivatives(theta: float, eps: float, n: int):
@@ -366,9 +388,12 @@ class Hierarchy:
     coarse_op: str = "galerkin"   # or "rediscretized": the Section 4 stencil on each coarse grid
     smoother: str = "jacobi"      # or "zebra": alternating zebra line Gauss-Seidel; "xzebra": x lines only
     coarsening: str = "full"      # or "y": semi-coarsening along y only (every level keeps n columns)
+    bx: float = 0.0               # convection b = (bx, by), upwind (a non-symmetric operator when nonzero)
+    by: float = 0.0
     stencils: list = field(default_factory=list)
     sizes: list = field(default_factory=list)
     _chol: object = None
+    _lu: object = None
 
     def __post_init__(self):
         k = int(round(math.log2(self.n + 1)))
@@ -382,6 +407,8 @@ class Hierarchy:
             raise ValueError("semi-coarsening uses Galerkin operators down to a single row")
         self.sizes = level_sizes(self.n, self.levels)   # grid side; under "y" the number of rows
         st = fine_stencil(self.theta, self.eps, self.n)
+        if self.bx != 0.0 or self.by != 0.0:
+            st = convection_stencil(st, self.bx, self.by, self.n)
         self.stencils = [st]
         for lvl in range(1, self.levels):
             if self.coarsening == "y":
@@ -390,6 +417,8 @@ class Hierarchy:
                 st = zero_row_sum_centre(galerkin_stencil(st))
             elif self.coarse_op == "rediscretized":
                 st = fine_stencil(self.theta, self.eps, self.sizes[lvl])
+                if self.bx != 0.0 or self.by != 0.0:
+                    st = convection_stencil(st, self.bx, self.by, self.sizes[lvl])
             else:
                 raise ValueError("coarse_op must be 'galerkin' or 'rediscretized'")
             self.stencils.append(st)
@@ -402,7 +431,10 @@ class Hierarchy:
             e = np.zeros(nc * nc)
             e[col] = 1.0
             dense[:, col] = apply_stencil(self.stencils[-1], e.reshape(nc, nc)).ravel()
-        self._chol = scipy.linalg.cho_factor(dense, lower=True)
+        if self.bx != 0.0 or self.by != 0.0:   # non-symmetric: LU
+            self._lu = scipy.linalg.lu_factor(dense)
+        else:
+            self._chol = scipy.linalg.cho_factor(dense, lower=True)
 
     def stencil(self, level: int) -> np.ndarray:
         return self.stencils[level - 1]
@@ -425,6 +457,8 @@ class Hierarchy:
         nc = self.sizes[-1]
         if nc == 1:
             return f / self.stencils[-1][1, 1]
+        if self.bx != 0.0 or self.by != 0.0:
+            return scipy.linalg.lu_solve(self._lu, f.ravel()).reshape(nc, nc)
         return scipy.linalg.cho_solve(self._chol, f.ravel()).reshape(nc, nc)
 
 

@@ -342,3 +342,24 @@ def test_semi_coarsening_levels_keep_every_column():
         oracle.mg.relax = orig
     assert {lv: s for lv, s in shapes} == {1: (15, 15), 2: (7, 15), 3: (3, 15)}
     assert rec.per_level[1:] == [1, 2, 3, 4]   # the F-cycle counts of Algorithm 3, as with full coarsening
+
+
+@pytest.mark.parametrize("bx,by", [(30.0, 10.0), (-50.0, 20.0)])
+def test_convection_diffusion_cycles_reach_dense_solution(bx, by):
+    """The kappa-cycle on the non-symmetric upwind convection-diffusion operator (damped Jacobi,
+    upwind operators rediscretized on every level, LU at the coarsest level) converges to the
+    dense solution. (Galerkin products of the upwind operator lose the upwind structure on the
+    coarse grids, where the cell Peclet number doubles per level, and Jacobi diverges there.)"""
+    n, levels = 31, 5
+    h = oracle.Hierarchy(n, levels, math.pi / 6, 1e-2, bx=bx, by=by, coarse_op="rediscretized")
+    f = rhs_uniform(n, 15)
+    A = dense_matrix_of(h)
+    assert np.abs(A - A.T).max() > 1.0
+    exact = scipy.linalg.solve(A, f.ravel()).reshape(n, n)
+    for kappa in (1, 3):
+        v, hist = oracle.solve(h, f, kappa, 1e-10, 300)
+        assert hist[-1] <= 1e-10 and len(hist) < 40
+        assert np.linalg.norm(v - exact) <= 1e-8 * np.linalg.norm(exact)
+    g = oracle.Hierarchy(n, levels, math.pi / 6, 1e-2, bx=bx, by=by)   # Galerkin: diverges
+    with np.errstate(all="ignore"):
+        assert not oracle.solve(g, f, 1, 1e-10, 30)[1][-1] <= 1.0

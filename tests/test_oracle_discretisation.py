@@ -291,3 +291,40 @@ def test_semi_hierarchy_coarsest_is_one_row_solved_exactly():
     assert np.max(np.abs(r)) <= 1e-12 * np.abs(f).max()
     with pytest.raises(ValueError):
         oracle.Hierarchy(n, 4, 0.4, 1e-3, smoother="xzebra", coarsening="y")
+
+
+# --------------------------------------------------------------------------------------------
+# Convection-diffusion (the non-symmetric problem Section 5 proposes): upwind convection
+# --------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bx,by", [(30.0, 10.0), (-20.0, 5.0), (7.0, -40.0), (-3.0, -3.0)])
+def test_upwind_convection_exact_on_linear_and_quadratic(bx, by):
+    """Linear u: the diffusion part vanishes and one-sided differences are exact, so A u = b . grad u
+    at interior points. u = x^2 (or y^2): the one-sided difference of x^2 is 2x - h (backward) or
+    2x + h (forward), so A u = -2 K_xx + bx (2x -/+ h) exactly."""
+    n, theta, eps = 15, 0.6, 0.1
+    h = 1.0 / (n + 1)
+    st = oracle.convection_stencil(oracle.fine_stencil(theta, eps, n), bx, by, n)
+    X, Y = grid(n)
+    inner = (slice(1, -1), slice(1, -1))
+    lin = 0.3 + 1.7 * X - 0.4 * Y
+    Au = oracle.apply_stencil(st, lin)
+    assert np.allclose(Au[inner], bx * 1.7 + by * (-0.4), rtol=0, atol=1e-9 * np.abs(st).max())
+    K = diffusion_tensor(theta, eps)
+    quad = X ** 2
+    expect = -2 * K[0, 0] + bx * (2 * X - np.sign(bx) * h)
+    assert np.allclose(oracle.apply_stencil(st, quad)[inner], expect[inner], rtol=0, atol=1e-9 * np.abs(st).max())
+
+
+@pytest.mark.parametrize("bx,by", [(30.0, 10.0), (-20.0, 5.0)])
+def test_galerkin_of_nonsymmetric_equals_dense_rap(bx, by):
+    nf, nc = 15, 7
+    st = oracle.convection_stencil(oracle.fine_stencil(0.7, 1e-2, nf), bx, by, nf)
+    A = dense(lambda v: oracle.apply_stencil(st, v), (nf, nf))
+    assert np.abs(A - A.T).max() > 1.0                              # not symmetric
+    P = dense(oracle.prolong_bilinear, (nc, nc))
+    R = dense(oracle.restrict_fw, (nf, nf))
+    Ac = R @ A @ P
+    stc = oracle.galerkin_stencil(st)
+    Ac_st = dense(lambda v: oracle.apply_stencil(stc, v), (nc, nc))
+    assert np.max(np.abs(Ac - Ac_st)) <= 1e-14 * np.abs(Ac).max()
