@@ -468,6 +468,27 @@ def main():
                                    f14, ((45, (4,)),))
         del f14
 
+    # ---------------------------------------------------------------- convection-diffusion (Section 5's proposal)
+    convection = None
+    if not args.no_sweep and world == 1:
+        bc = (1000.0, 500.0)
+        mc = kcycle.Multigrid(n, 1e-2, math.pi / 6, levels, convection=bc, coarse_op="rediscretized")
+        vc_ = torch.zeros_like(f)
+        convection = {"workload": f"{n}^2, {levels} levels, theta=pi/6, eps=1e-2, b=({bc[0]:g}, {bc[1]:g}) upwind, "
+                                  "damped Jacobi, rediscretized upwind coarse operators, f~N(0,1), tol 1e-8"}
+        for k in (1, 2, 3, 4, KAPPA_W):
+            vc_.zero_()
+            mc.solve(vc_, f, k, tol, 1, history=False)
+            vc_.zero_()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            st_c, cyc_c, rel_c, _ = mc.solve(vc_, f, k, tol, 5000, history=False)
+            b.record()
+            torch.cuda.synchronize()
+            convection[kname(k)] = {"cycles": cyc_c, "ms": round(a.elapsed_time(b), 1), "status": st_c}
+        mc.close()
+
     # ---------------------------------------------------------------- MGCG 8191^2 (the preconditioner workload)
     mgcg = None
     if not args.no_sweep and world == 1:
@@ -555,7 +576,8 @@ def main():
                 "roofline": roofline, "cycle_share": cycle_share, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clocks.summary(), "per_kappa": per_kappa,
                 "per_kappa_mixed": per_kappa_mixed, "batched": batched, "model": model_report,
-                "paper_protocol": paper_protocol, "zebra": zebra, "semi_coarsening": semi, "mgcg_8191": mgcg}
+                "paper_protocol": paper_protocol, "zebra": zebra, "semi_coarsening": semi, "mgcg_8191": mgcg,
+                "convection_diffusion": convection}
         if paper_scale is not None:
             line["zebra_16383"] = paper_scale
         print(json.dumps(line), flush=True)

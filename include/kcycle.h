@@ -58,7 +58,7 @@ typedef enum {
   MG_OPT_LEVELS = 3,       /* read-only: number of levels                                          */
   MG_OPT_N = 4,            /* read-only: finest grid side                                          */
   MG_OPT_LAUNCHES = 5,     /* read-only: kernel launches in the last cycle graph built              */
-  MG_OPT_COARSE_N32 = 6,   /* as MG_OPT_COARSE_N for the FP32 cycles of the mixed forms; default 63  */
+  MG_OPT_COARSE_N32 = 6,   /* as MG_OPT_COARSE_N for the FP32 cycles of the mixed forms; default 31  */
   MG_OPT_COARSE_OP = 7,    /* coarse operators: 0 Galerkin R A P (default), 1 the Section 4 stencil
                               rediscretized on each coarse grid                                     */
   MG_OPT_STOP = 8,         /* mg_solve's stopping test: 0 ||f - A v||/||f|| <= tol (default);
@@ -77,11 +77,21 @@ typedef enum {
                               the coarsest level is a single row solved exactly. Needs levels = k
                               and Galerkin operators (else MG_ERR_ARG). Reallocates the hierarchy;
                               the mixed-precision entry points return MG_ERR_ARG under it.      */
-  MG_OPT_PRECOND = 11      /* MGCG preconditioner: 0 one kappa-cycle B from zero (default); 1 the
+  MG_OPT_PRECOND = 11,     /* MGCG preconditioner: 0 one kappa-cycle B from zero (default); 1 the
                               symmetrised B + B^T - B^T A B (one cycle, the residual, one adjoint
                               cycle: error propagator (I - B^T A)(I - B A)), symmetric for every
                               kappa. Option 1 needs damped Jacobi, full coarsening and FP64:
                               mg_pcg returns MG_ERR_ARG otherwise, mg_pcg_mixed always.         */
+  MG_OPT_CONV_X = 12,      /* convection b = (bx, by), x component (see MG_OPT_CONV_Y)          */
+  MG_OPT_CONV_Y = 13       /* y component: the problem becomes -div(K grad u) + b.grad u, the
+                              non-symmetric test problem proposed in Section 5, with b.grad u by
+                              first-order upwind differences (default 0: the Section 4 problem).
+                              Nonzero b: damped Jacobi, full coarsening and FP64 only (otherwise
+                              MG_ERR_ARG when set); mg_pcg, the mixed forms and the adjoint entry
+                              points return MG_ERR_ARG. Galerkin products of the upwind operator
+                              lose its upwind structure on coarse grids and the cycle can diverge;
+                              MG_OPT_COARSE_OP = 1 (rediscretized upwind operators) is the stable
+                              choice. Recomputes the stencils.                                    */
 } mg_option;
 
 /* Set up the hierarchy for the Section 4 problem on an n x n interior grid.

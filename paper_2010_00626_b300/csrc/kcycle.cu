@@ -103,8 +103,8 @@ struct mg_ctx {
   int coarse_n = 15;  // largest side handled by the coarse kernel (FP64 cycles)
   int lc = 0;         // first level handled by the coarse kernel (FP64 cycles)
   int lc32 = 0;       // same for the FP32 cycles of the mixed path
-  int coarse_n32 = 63;  // FP32 threshold: one SM does FP32 at 64x the FP64 rate, so the single-CTA
-                        // kernel takes more levels
+  int coarse_n32 = 31;  // FP32 threshold: one SM does FP32 at 64x the FP64 rate, so the single-CTA
+                        // kernel takes more levels (31 measured best at 4095^2 for kappa 3 and 4)
   Level lv[MAXL];
   double* coef = nullptr;
   float* coef32 = nullptr;
@@ -127,6 +127,8 @@ struct mg_ctx {
   int smoother = 0;       // 0 damped Jacobi, 1 alternating zebra line Gauss-Seidel, 2 zebra along x only
   int semi = 0;           // 1: semi-coarsening along y (every level keeps the n columns)
   int precond = 0;        // MGCG preconditioner: 0 the kappa-cycle B, 1 B + B^T - B^T A B
+  double bx = 0.0, by = 0.0;  // upwind convection b . grad u (Section 5's non-symmetric problem)
+  bool nonsym = false;        // bx or by nonzero: general-stencil kernels, FP64 damped Jacobi only
   // condensed coarse calls: the affine maps of a call at the side-7 level, per counter class, for
   // the FP64 and FP32 coarse kernels (valid while the flags are set)
   double* cmap = nullptr;
@@ -178,18 +180,35 @@ int tile_edge(int n) {
 }
 int tile_rows(int n) { return tile_edge(n) == 64 ? 48 : tile_edge(n); }
 
+// ns: the general (non-symmetric) stencil variant, FP64 only.
 template <typename Cfg, typename T>
-int launch_pass_a(const PassAArgs<T>& a, cudaStream_t s) {
+int launch_pass_a(const PassAArgs<T>& a, cudaStream_t s, bool ns = false) {
   dim3 grid((a.n + Cfg::bx - 1) / Cfg::bx, (a.n + Cfg::by - 1) / Cfg::by);
   const size_t sm = pass_a_smem<T, Cfg::bx, Cfg::by>(a.nu);
+  if constexpr (std::is_same<T, double>::value) {
+    if (ns) {
+      pass_a_kernel<T, Cfg::bx, Cfg::by, Cfg::nt, true><<<grid, Cfg::nt, sm, s>>>(a);
+      KC_CUDA(cudaGetLastError());
+      return MG_OK;
+    }
+  }
+  if (ns) return MG_ERR_ARG;
   pass_a_kernel<T, Cfg::bx, Cfg::by, Cfg::nt><<<grid, Cfg::nt, sm, s>>>(a);
   KC_CUDA(cudaGetLastError());
   return MG_OK;
 }
 template <typename Cfg, typename T>
-int launch_pass_b(const PassBArgs<T>& a, cudaStream_t s) {
+int launch_pass_b(const PassBArgs<T>& a, cudaStream_t s, bool ns = false) {
   dim3 grid((a.n + Cfg::bx - 1) / Cfg::bx, (a.n + Cfg::by - 1) / Cfg::by);
   const size_t sm = pass_b_smem<T, Cfg::bx, Cfg::by>(a.nu, a.partial != nullptr);
+  if constexpr (std::is_same<T, double>::value) {
+    if (ns) {
+      pass_b_kernel<T, Cfg::bx, Cfg::by, Cfg::nt, true><<<grid, Cfg::nt, sm, s>>>(a);
+      KC_CUDA(cudaGetLastError());
+      return MG_OK;
+    }
+  }
+  if (ns) return MG_ERR_ARG;
   pass_b_kernel<T, Cfg::bx, Cfg::by, Cfg::nt><<<grid, Cfg::nt, sm, s>>>(a);
   KC_CUDA(cudaGetLastError());
   return MG_OK;
@@ -203,6 +222,14 @@ int set_smem_attrs() {
   KC_CUDA(cudaFuncSetAttribute(pass_b_kernel<T, Cfg::bx, Cfg::by, Cfg::nt>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)pass_b_smem<T, Cfg::bx, Cfg::by>(MAX_NU, true)));
+  if constexpr (std::is_same<T, double>::value) {
+    KC_CUDA(cudaFuncSetAttribute(pass_a_kernel<T, Cfg::bx, Cfg::by, Cfg::nt, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pass_a_smem<T, Cfg::bx, Cfg::by>(MAX_NU)));
+    KC_CUDA(cudaFuncSetAttribute(pass_b_kernel<T, Cfg::bx, Cfg::by, Cfg::nt, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pass_b_smem<T, Cfg::bx, Cfg::by>(MAX_NU, true)));
+  }
   return MG_OK;
 }
 
@@ -227,6 +254,10 @@ int set_all_smem_attrs() {
                                (int)coarse_smem<T>(MAX_COARSE_N, 6)));
   KC_CUDA(cudaFuncSetAttribute(coarse_kernel<T, nt_coarse<T>(), true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)coarse_smem<T>(MAX_COARSE_N, 6)));
+  if constexpr (std::is_same<T, double>::value) {
+    KC_CUDA(cudaFuncSetAttribute(coarse_kernel<T, nt_coarse<T>(), false, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coarse_smem<T>(MAX_COARSE_N, 6)));
+  }
   KC_TRY((set_line_attrs<T, 1>()));
   KC_TRY((set_line_attrs<T, 2>()));
   KC_TRY((set_line_attrs<T, 4>()));
@@ -331,6 +362,25 @@ int launch_pass_b_stream(const PassBArgs<float>& a, cudaStream_t s) {
   return MG_OK;
 }
 
+// The coarse kernel variant for the handle: line relaxation (symmetric operators) or damped
+// Jacobi on the symmetric or the general stencil.
+template <typename T>
+int launch_coarse(const mg_ctx* h, const CoarseArgs<T>& a, int blocks, size_t sm, cudaStream_t s) {
+  if (a.ltab) {
+    coarse_kernel<T, nt_coarse<T>(), true><<<blocks, nt_coarse<T>(), sm, s>>>(a);
+  } else if (h->nonsym) {
+    if constexpr (std::is_same<T, double>::value) {
+      coarse_kernel<T, nt_coarse<T>(), false, true><<<blocks, nt_coarse<T>(), sm, s>>>(a);
+    } else {
+      return MG_ERR_ARG;
+    }
+  } else {
+    coarse_kernel<T, nt_coarse<T>(), false><<<blocks, nt_coarse<T>(), sm, s>>>(a);
+  }
+  KC_CUDA(cudaGetLastError());
+  return MG_OK;
+}
+
 // Level whose calls the coarse kernel condenses into precomputed affine maps: the side-7 level,
 // when a coarser level exists (-1 otherwise, and under semi-coarsening).
 int map_level(const mg_ctx* h) {
@@ -374,10 +424,7 @@ int emit_coarse(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int zero1, bool
   a.cmap_out = nullptr;
   const size_t sm = coarse_smem<T>(a.n_lc, a.L - a.lc);
   prof_begin(h, K_COARSE, lc, s);
-  if (a.ltab)
-    coarse_kernel<T, nt_coarse<T>(), true><<<1, nt_coarse<T>(), sm, s>>>(a);
-  else
-    coarse_kernel<T, nt_coarse<T>(), false><<<1, nt_coarse<T>(), sm, s>>>(a);
+  KC_TRY(launch_coarse(h, a, 1, sm, s));
   prof_end(h, s);
   KC_CUDA(cudaGetLastError());
   ++h->launch_count;
@@ -414,10 +461,7 @@ int compute_maps(mg_ctx* h) {
   for (int c = 1; c <= h->levels - dm; ++c) {
     a.k1 = c;
     a.cmap_out = Arr<T>::cmap(h) + (size_t)(c - 1) * 2 * MAP_S * MAP_S;
-    if (a.ltab)
-      coarse_kernel<T, nt_coarse<T>(), true><<<2 * MAP_S, nt_coarse<T>(), sm, h->own>>>(a);
-    else
-      coarse_kernel<T, nt_coarse<T>(), false><<<2 * MAP_S, nt_coarse<T>(), sm, h->own>>>(a);
+    KC_TRY(launch_coarse(h, a, 2 * MAP_S, sm, h->own));
     KC_CUDA(cudaGetLastError());
   }
   KC_CUDA(cudaStreamSynchronize(h->own));
@@ -464,10 +508,10 @@ int emit_pass_a(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const
     }
   }
   switch (tile_edge(a.n)) {
-    case 64: st = launch_pass_a<Tile64>(a, s); break;
-    case 32: st = launch_pass_a<Tile32>(a, s); break;
-    case 16: st = launch_pass_a<Tile16>(a, s); break;
-    default: st = launch_pass_a<Tile8>(a, s); break;
+    case 64: st = launch_pass_a<Tile64>(a, s, h->nonsym); break;
+    case 32: st = launch_pass_a<Tile32>(a, s, h->nonsym); break;
+    case 16: st = launch_pass_a<Tile16>(a, s, h->nonsym); break;
+    default: st = launch_pass_a<Tile8>(a, s, h->nonsym); break;
   }
   prof_end(h, s);
   return st;
@@ -504,10 +548,10 @@ int emit_pass_b(mg_ctx* h, const BindingT<T>& b, int l, int nu, double* partial,
     }
   }
   switch (tile_edge(a.n)) {
-    case 64: st = launch_pass_b<Tile64>(a, s); break;
-    case 32: st = launch_pass_b<Tile32>(a, s); break;
-    case 16: st = launch_pass_b<Tile16>(a, s); break;
-    default: st = launch_pass_b<Tile8>(a, s); break;
+    case 64: st = launch_pass_b<Tile64>(a, s, h->nonsym); break;
+    case 32: st = launch_pass_b<Tile32>(a, s, h->nonsym); break;
+    case 16: st = launch_pass_b<Tile16>(a, s, h->nonsym); break;
+    default: st = launch_pass_b<Tile8>(a, s, h->nonsym); break;
   }
   prof_end(h, s);
   return st;
@@ -518,7 +562,10 @@ int emit_apply(mg_ctx* h, const double* v, const double* f, double* out, double*
   const int n = h->n;
   dim3 grid((n + 31) / 32, (n + NT_VEC / 32 - 1) / (NT_VEC / 32));
   prof_begin(h, K_APPLY, 0, s);
-  apply_kernel<double, NT_VEC><<<grid, NT_VEC, 0, s>>>(v, f, out, h->coef, 0, n, n, partial, skip);
+  if (h->nonsym)
+    apply_kernel<double, NT_VEC, true><<<grid, NT_VEC, 0, s>>>(v, f, out, h->coef, 0, n, n, partial, skip);
+  else
+    apply_kernel<double, NT_VEC><<<grid, NT_VEC, 0, s>>>(v, f, out, h->coef, 0, n, n, partial, skip);
   prof_end(h, s);
   KC_CUDA(cudaGetLastError());
   ++h->launch_count;
@@ -946,7 +993,7 @@ int solve_impl(mg_handle h, double* v, const double* f, int kappa, double tol, i
                double* final_relres, double* history, bool adjoint = false) {
   if (!valid_handle(h)) return MG_ERR_STATE;
   if (!v || !f || kappa < 1 || !(tol > 0) || max_cycles < 1) return MG_ERR_ARG;
-  if (adjoint && h->smoother != 0) return MG_ERR_ARG;
+  if (adjoint && (h->smoother != 0 || h->nonsym)) return MG_ERR_ARG;
   trim_graphs(h);
   KC_TRY(ensure_hist(h, max_cycles));
   cudaStream_t s = h->stream();
@@ -1027,7 +1074,7 @@ int alloc_levels(mg_ctx* h) {
 
 // FP32 hierarchy of the mixed cycle: same shapes as the FP64 one, plus level 0 (d and r32).
 int ensure_levels32(mg_ctx* h) {
-  if (h->semi) return MG_ERR_ARG;  // the FP32 cycles use full coarsening
+  if (h->semi || h->nonsym) return MG_ERR_ARG;  // the FP32 cycles: full coarsening, symmetric operators
   if (h->have32) return MG_OK;
   h->lc32 = h->levels - 1;
   for (int l = 0; l < h->levels; ++l)
@@ -1075,7 +1122,7 @@ int free_levels(mg_ctx* h) {
 int run_setup_kernels(mg_ctx* h) {
   h->maps_ok = h->maps32_ok = false;
   setup_stencils_kernel<<<1, 32, 0, h->own>>>(h->theta, h->eps, h->n, h->levels, h->omega, h->coef, h->coef32,
-                                             h->stencils, h->dstencil, h->rediscretized, h->semi);
+                                             h->stencils, h->dstencil, h->rediscretized, h->semi, h->bx, h->by);
   KC_CUDA(cudaGetLastError());
   line_tables_kernel<<<1, 32, 0, h->own>>>(h->coef, h->k, h->levels, h->ltab, h->ltab32, h->linv, h->semi);
   KC_CUDA(cudaGetLastError());
@@ -1205,11 +1252,24 @@ int mg_set_option(mg_handle h, int key, double value) {
     case MG_OPT_SMOOTHER: {
       if (!(value == 0.0 || value == 1.0 || value == 2.0)) return MG_ERR_ARG;
       if (h->semi && value != 2.0) return MG_ERR_ARG;
+      if (h->nonsym && value != 0.0) return MG_ERR_ARG;
       KC_CUDA(cudaStreamSynchronize(h->stream()));
       h->smoother = (int)value;
       h->maps_ok = h->maps32_ok = false;
       drop_graphs(h);
       return MG_OK;
+    }
+    case MG_OPT_CONV_X:
+    case MG_OPT_CONV_Y: {
+      if (!(std::fabs(value) <= 1e12)) return MG_ERR_ARG;
+      const double bx = key == MG_OPT_CONV_X ? value : h->bx, by = key == MG_OPT_CONV_Y ? value : h->by;
+      if ((bx != 0.0 || by != 0.0) && (h->smoother != 0 || h->semi)) return MG_ERR_ARG;
+      KC_CUDA(cudaStreamSynchronize(h->stream()));
+      h->bx = bx;
+      h->by = by;
+      h->nonsym = bx != 0.0 || by != 0.0;
+      drop_graphs(h);
+      return run_setup_kernels(h);
     }
     case MG_OPT_PRECOND: {
       if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
@@ -1219,7 +1279,7 @@ int mg_set_option(mg_handle h, int key, double value) {
     }
     case MG_OPT_COARSENING: {
       if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
-      if (value == 1.0 && (h->levels != h->k || h->rediscretized)) return MG_ERR_ARG;
+      if (value == 1.0 && (h->levels != h->k || h->rediscretized || h->nonsym)) return MG_ERR_ARG;
       if ((int)value == h->semi) return MG_OK;
       KC_CUDA(cudaStreamSynchronize(h->stream()));
       drop_graphs(h);
@@ -1258,6 +1318,8 @@ int mg_get_option(mg_handle h, int key, double* value) {
     case MG_OPT_SMOOTHER: *value = h->smoother; return MG_OK;
     case MG_OPT_COARSENING: *value = h->semi; return MG_OK;
     case MG_OPT_PRECOND: *value = h->precond; return MG_OK;
+    case MG_OPT_CONV_X: *value = h->bx; return MG_OK;
+    case MG_OPT_CONV_Y: *value = h->by; return MG_OK;
     case MG_OPT_LEVELS: *value = h->levels; return MG_OK;
     case MG_OPT_N: *value = h->n; return MG_OK;
     case MG_OPT_LAUNCHES: *value = h->last_launches; return MG_OK;
@@ -1275,7 +1337,7 @@ int mg_set_stream(mg_handle h, void* stream) {
 static int kcycle_common(mg_handle h, double* v, const double* f, int kappa, bool adjoint) {
   if (!valid_handle(h)) return MG_ERR_STATE;
   if (!v || !f || kappa < 1) return MG_ERR_ARG;
-  if (adjoint && h->smoother != 0) return MG_ERR_ARG;
+  if (adjoint && (h->smoother != 0 || h->nonsym)) return MG_ERR_ARG;
   trim_graphs(h);
   GraphEntry* ge;
   KC_TRY(get_cycle_graph(h, v, f, kappa, adjoint ? 2 : 0, &ge));
@@ -1322,6 +1384,7 @@ static int pcg_impl(mg_handle h, double* x, const double* b, int kappa, double t
   if (!x || !b || kappa < 1 || !(tol > 0) || max_iters < 1) return MG_ERR_ARG;
   const bool sym = h->precond == 1;
   if (sym && (mixed || h->smoother != 0)) return MG_ERR_ARG;  // the adjoint cycle: FP64 damped Jacobi
+  if (h->nonsym) return MG_ERR_ARG;                            // CG needs a symmetric operator
   trim_graphs(h);
   const size_t len = (size_t)h->n * h->n, bytes = sizeof(double) * len;
   double** vecs[] = {&h->pr, &h->pp, &h->pq, &h->pz, &h->pzold};

@@ -100,6 +100,59 @@ __device__ __forceinline__ T apply_at(const Nb<T>& nb, const Coef<T>& c) {
   return t;
 }
 
+// The stencil operations of the level kernels, for a symmetric stencil (pair sums, NS = false)
+// or a general one (NS = true: the non-symmetric convection-diffusion operator, every entry
+// separately; the same count of FP64 operations, the pair additions become multiply-adds).
+template <typename T, bool NS>
+struct StencilOp;
+
+template <typename T>
+struct StencilOp<T, false> {
+  Coef<T> c;
+  __device__ __forceinline__ void load(const T* __restrict__ tab, int level) { c = load_coef(tab, level); }
+  __device__ __forceinline__ T w() const { return c.w; }
+  __device__ __forceinline__ T jac(const T* s, int k, int W, T fv) const { return jacobi_update(neighbours(s, k, W), fv, c); }
+  __device__ __forceinline__ T res(const T* s, int k, int W, T fv) const { return residual_at(neighbours(s, k, W), fv, c); }
+  __device__ __forceinline__ T app(const T* s, int k, int W) const { return apply_at(neighbours(s, k, W), c); }
+};
+
+template <typename T>
+struct StencilOp<T, true> {
+  T wv, b0, st[9], b[9];  // b[q] = -w st[q]; st[(dy+1)*3 + (dx+1)] multiplies v[j+dy][i+dx]
+  __device__ __forceinline__ void load(const T* __restrict__ tab, int level) {
+    const T* p = tab + level * NCOEF;
+    wv = p[C_W];
+    b0 = p[C_B0];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      st[q] = p[C_ST + q];
+      b[q] = -wv * st[q];
+    }
+  }
+  __device__ __forceinline__ T w() const { return wv; }
+  __device__ __forceinline__ T jac(const T* s, int k, int W, T fv) const {
+    T t = b0 * s[k];
+    t = fma(wv, fv, t);
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+      if (q != 4) t = fma(b[q], s[k + (q / 3 - 1) * W + (q % 3 - 1)], t);
+    return t;
+  }
+  __device__ __forceinline__ T res(const T* s, int k, int W, T fv) const {
+    T t = fv;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) t = fma(-st[q], s[k + (q / 3 - 1) * W + (q % 3 - 1)], t);
+    return t;
+  }
+  __device__ __forceinline__ T app(const T* s, int k, int W) const {
+    T t = st[4] * s[k];
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+      if (q != 4) t = fma(st[q], s[k + (q / 3 - 1) * W + (q % 3 - 1)], t);
+    return t;
+  }
+};
+
 // Full weighting (1/16)[1 2 1; 2 4 2; 1 2 1] of r around position k (row stride W).
 template <typename T>
 __device__ __forceinline__ T full_weight(const T* r, int k, int W) {
@@ -164,7 +217,7 @@ __host__ __device__ constexpr size_t pass_a_smem(int nu) {
   return size_t(3) * (BX + 2 * (nu + 1) + 1) * (BY + 2 * (nu + 1) + 1) * sizeof(T);
 }
 
-template <typename T, int BX, int BY, int NT>
+template <typename T, int BX, int BY, int NT, bool NS = false>
 __global__ void __launch_bounds__(NT) pass_a_kernel(const PassAArgs<T> a) {
   if (a.skip && *a.skip) return;
   static_assert(BX % 2 == 0 && BY % 2 == 0, "tiles start on even fine indices");
@@ -177,7 +230,8 @@ __global__ void __launch_bounds__(NT) pass_a_kernel(const PassAArgs<T> a) {
   const int n = a.n;
   const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
   const int gx0 = x0 - H, gy0 = y0 - H;
-  const Coef<T> c = load_coef(a.coef, a.level);
+  StencilOp<T, NS> op;
+  op.load(a.coef, a.level);
 
   // local (lx, ly) <-> global (gx0 + lx, gy0 + ly)
   for_region<NT>(W, Hh, [&](int lx, int ly) {
@@ -199,7 +253,7 @@ __global__ void __launch_bounds__(NT) pass_a_kernel(const PassAArgs<T> a) {
     for_region<NT>(R, Ry, [&](int rx, int ry) {
       const int lx = lo + rx, ly = lo + ry, k = ly * W + lx;
       dst[k] = inside(gx0 + lx, gy0 + ly, n)
-                   ? (from_zero ? c.w * fs[k] : jacobi_update(neighbours(src, k, W), fs[k], c))
+                   ? (from_zero ? op.w() * fs[k] : op.jac(src, k, W, fs[k]))
                    : T(0);
     });
     __syncthreads();
@@ -214,7 +268,7 @@ __global__ void __launch_bounds__(NT) pass_a_kernel(const PassAArgs<T> a) {
   // residual on the tile plus one column/row beyond it (full weighting reads it)
   for_region<NT>(BX + 1, BY + 1, [&](int tx, int ty) {
     const int lx = H + tx, ly = H + ty, k = ly * W + lx;
-    dst[k] = inside(gx0 + lx, gy0 + ly, n) ? residual_at(neighbours(src, k, W), fs[k], c) : T(0);
+    dst[k] = inside(gx0 + lx, gy0 + ly, n) ? op.res(src, k, W, fs[k]) : T(0);
   });
   __syncthreads();
   // coarse point (I, J) sits on fine (2I+1, 2J+1); this tile owns I in [x0/2, x0/2 + BX/2)
@@ -253,7 +307,7 @@ __host__ __device__ constexpr size_t pass_b_smem(int nu, bool norm) {
          size_t(BX / 2 + nu + (norm ? 1 : 0) + 3) * (BY / 2 + nu + (norm ? 1 : 0) + 3) * sizeof(T);
 }
 
-template <typename T, int BX, int BY, int NT>
+template <typename T, int BX, int BY, int NT, bool NS = false>
 __global__ void __launch_bounds__(NT) pass_b_kernel(const PassBArgs<T> a) {
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -271,7 +325,8 @@ __global__ void __launch_bounds__(NT) pass_b_kernel(const PassBArgs<T> a) {
   T* s1 = s0 + W * Hh;
   T* fs = s1 + W * Hh;
   T* cs = fs + W * Hh;
-  const Coef<T> c = load_coef(a.coef, a.level);
+  StencilOp<T, NS> op;
+  op.load(a.coef, a.level);
 
   for_region<NT>(CW, CH, [&](int lx, int ly) {
     const int cx = cx0 + lx, cy = cy0 + ly;
@@ -311,7 +366,7 @@ __global__ void __launch_bounds__(NT) pass_b_kernel(const PassBArgs<T> a) {
     const int lo = H - g, R = BX + 2 * g, Ry = BY + 2 * g;
     for_region<NT>(R, Ry, [&](int rx, int ry) {
       const int lx = lo + rx, ly = lo + ry, k = ly * W + lx;
-      dst[k] = inside(gx0 + lx, gy0 + ly, n) ? jacobi_update(neighbours(src, k, W), fs[k], c) : T(0);
+      dst[k] = inside(gx0 + lx, gy0 + ly, n) ? op.jac(src, k, W, fs[k]) : T(0);
     });
     __syncthreads();
     T* t = src; src = dst; dst = t;
@@ -323,7 +378,7 @@ __global__ void __launch_bounds__(NT) pass_b_kernel(const PassBArgs<T> a) {
       const int k = (ty + H) * W + tx + H;
       a.vout[(size_t)gy * a.ldvout + gx] = src[k];
       if (E) {
-        const double r = (double)residual_at(neighbours(src, k, W), fs[k], c);
+        const double r = (double)op.res(src, k, W, fs[k]);
         ss = fma(r, r, ss);
       }
     }
@@ -454,15 +509,16 @@ __host__ __device__ inline size_t coarse_smem(int n_lc, int nlev) {
   return tot + coarse_line_inverses(n_lc, nlev) * sizeof(double);
 }
 
-template <typename T, int NT, bool LINES>
+template <typename T, int NT, bool LINES, bool NS = false>
 __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
+  static_assert(!(LINES && NS), "line relaxation is for the symmetric operators");
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ Coef<T> cf[MAXL];
+  __shared__ StencilOp<T, NS> cf[MAXL];
   __shared__ int g_side[MAXL], g_off[MAXL + 1], g_magic[MAXL];
   const int nlev = a.L - a.lc;
   T* base = reinterpret_cast<T*>(smem_raw);
-  if (threadIdx.x < nlev) cf[threadIdx.x] = load_coef(a.coef, a.lc + threadIdx.x);
+  if (threadIdx.x < nlev) cf[threadIdx.x].load(a.coef, a.lc + threadIdx.x);
   if (threadIdx.x == 0) {
     int off = 0;
     for (int d = 0; d < nlev; ++d) {
@@ -548,7 +604,7 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
   auto relax = [&](int d, int sweeps, bool zero) {
     const int s = g_side[d], P = s + 2;
     const T* f = fbuf(d);
-    const Coef<T> c = cf[d];
+    const StencilOp<T, NS>& op = cf[d];
     if (zero && sweeps == 0) {
       T* v = vcur(d);
       for (int k = threadIdx.x; k < s * s; k += NT) v[pos(d, k)] = T(0);
@@ -562,7 +618,11 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
       const bool from_zero = zero && it == 0;
       for (int k = threadIdx.x; k < s * s; k += NT) {
         const int kk = pos(d, k);
-        dst[kk] = from_zero ? c.w * f[kk] : jacobi_update_tree(neighbours(src, kk, P), f[kk], c);
+        if constexpr (NS) {
+          dst[kk] = from_zero ? op.w() * f[kk] : op.jac(src, kk, P, f[kk]);
+        } else {
+          dst[kk] = from_zero ? op.c.w * f[kk] : jacobi_update_tree(neighbours(src, kk, P), f[kk], op.c);
+        }
       }
       cur ^= 1u << d;
       __syncthreads();
@@ -572,10 +632,11 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
   // k, along y (columns) for odd k; colour 0 lines then colour 1 lines, one thread per line
   // running the Thomas recurrences with the level's tabulated factors
   auto relax_lines = [&](int d, int sweeps, bool zero) {
+    if constexpr (!NS) {
     const int s = g_side[d], P = s + 2;
     T* v = vcur(d);
     const T* f = fbuf(d);
-    const Coef<T> c = cf[d];
+    const Coef<T> c = cf[d].c;
     if (zero) {
       for (int k = threadIdx.x; k < s * s; k += NT) v[pos(d, k)] = T(0);
       __syncthreads();
@@ -648,6 +709,7 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
         __syncthreads();
       }
     }
+    }
   };
   auto smooth = [&](int d, int sweeps, bool zero) {
     if constexpr (LINES) relax_lines(d, sweeps, zero); else relax(d, sweeps, zero);
@@ -657,10 +719,10 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
     const int s = g_side[d], P = s + 2;
     const T* v = vcur(d);
     const T* f = fbuf(d);
-    const Coef<T> c = cf[d];
+    const StencilOp<T, NS>& op = cf[d];
     for (int k = threadIdx.x; k < s * s; k += NT) {
       const int kk = pos(d, k);
-      tmp[kk] = residual_at(neighbours(v, kk, P), f[kk], c);
+      tmp[kk] = op.res(v, kk, P, f[kk]);
     }
     __syncthreads();
     const int sc = g_side[d + 1];
@@ -914,9 +976,22 @@ __device__ inline void section4_stencil(double C, double S, double eps, int m, d
 
 // rediscretized != 0: coarse stencils are the Section 4 stencil on each coarse grid instead of
 // the Galerkin products.
+// First-order upwind convection b . grad u added to a stencil of grid side m (1/h = m + 1), the
+// same rounded operations as the oracle: cx = |bx| (m+1), cy = |by| (m+1), centre += (cx + cy),
+// and the upwind neighbour (west for bx > 0, east for bx < 0; south / north for by) -= cx (cy).
+__device__ inline void add_convection(double bx, double by, int m, double st[9]) {
+  const double cx = __dmul_rn(fabs(bx), (double)(m + 1));
+  const double cy = __dmul_rn(fabs(by), (double)(m + 1));
+  st[4] = __dadd_rn(st[4], __dadd_rn(cx, cy));
+  if (bx > 0.0) st[3] = __dsub_rn(st[3], cx);
+  else if (bx < 0.0) st[5] = __dsub_rn(st[5], cx);
+  if (by > 0.0) st[1] = __dsub_rn(st[1], cy);
+  else if (by < 0.0) st[7] = __dsub_rn(st[7], cy);
+}
+
 __global__ void setup_stencils_kernel(double theta, double eps, int n, int levels, double omega,
                                       double* coef, float* coef32, double* stencils, double* dstencil,
-                                      int rediscretized, int semi = 0) {
+                                      int rediscretized, int semi = 0, double bx = 0.0, double by = 0.0) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double h = __ddiv_rn(1.0, (double)(n + 1));
   const double h2 = __dmul_rn(h, h);
@@ -924,6 +999,7 @@ __global__ void setup_stencils_kernel(double theta, double eps, int n, int level
   dd_cos_sin(theta, &C, &S);
   double st[9];
   section4_stencil(C, S, eps, n, st);
+  if (bx != 0.0 || by != 0.0) add_convection(bx, by, n, st);
   // derivatives of the Section 4 entries with respect to theta and eps, scaled by 1/h^2
   {
     const double s2 = sin(2.0 * theta), c2 = cos(2.0 * theta);
@@ -973,7 +1049,10 @@ __global__ void setup_stencils_kernel(double theta, double eps, int n, int level
       if (q != 4) off = __dadd_rn(off, sc[q]);
     sc[4] = -off;
     for (int q = 0; q < 9; ++q) st[q] = sc[q];
-    if (rediscretized) section4_stencil(C, S, eps, ((n + 1) >> (l + 1)) - 1, st);
+    if (rediscretized) {
+      section4_stencil(C, S, eps, ((n + 1) >> (l + 1)) - 1, st);
+      if (bx != 0.0 || by != 0.0) add_convection(bx, by, ((n + 1) >> (l + 1)) - 1, st);
+    }
   }
 }
 
@@ -1036,7 +1115,7 @@ __device__ __forceinline__ Nb<T> neighbours_global(const T* v, int i, int j, int
 }
 
 // out = A v (f == nullptr) or out = f - A v; partial sums of out^2 when partial != nullptr.
-template <typename T, int NT>
+template <typename T, int NT, bool NS = false>
 __global__ void __launch_bounds__(NT) apply_kernel(const T* __restrict__ v, const T* __restrict__ f, T* out,
                                                    const T* coef, int level, int n, int ld, double* partial,
                                                    const int* skip) {
@@ -1044,13 +1123,29 @@ __global__ void __launch_bounds__(NT) apply_kernel(const T* __restrict__ v, cons
   __shared__ double red[NT / 32];
   const int i = blockIdx.x * 32 + (threadIdx.x & 31);
   const int j = blockIdx.y * (NT / 32) + (threadIdx.x >> 5);
-  const Coef<T> c = load_coef(coef, level);
   double ss = 0.0;
-  if (i < n && j < n) {
-    const Nb<T> nb = neighbours_global(v, i, j, n, ld);
-    const T r = f ? residual_at(nb, f[(size_t)j * ld + i], c) : apply_at(nb, c);
-    if (out) out[(size_t)j * ld + i] = r;
-    ss = (double)r * (double)r;
+  if constexpr (NS) {
+    StencilOp<T, true> op;
+    op.load(coef, level);
+    if (i < n && j < n) {
+      T s9[9];  // the 3x3 neighbourhood, zero outside the grid; centre at index 4, row stride 3
+#pragma unroll
+      for (int q = 0; q < 9; ++q) {
+        const int ii = i + q % 3 - 1, jj = j + q / 3 - 1;
+        s9[q] = inside(ii, jj, n) ? v[(size_t)jj * ld + ii] : T(0);
+      }
+      const T r = f ? op.res(s9, 4, 3, f[(size_t)j * ld + i]) : op.app(s9, 4, 3);
+      if (out) out[(size_t)j * ld + i] = r;
+      ss = (double)r * (double)r;
+    }
+  } else {
+    const Coef<T> c = load_coef(coef, level);
+    if (i < n && j < n) {
+      const Nb<T> nb = neighbours_global(v, i, j, n, ld);
+      const T r = f ? residual_at(nb, f[(size_t)j * ld + i], c) : apply_at(nb, c);
+      if (out) out[(size_t)j * ld + i] = r;
+      ss = (double)r * (double)r;
+    }
   }
   if (partial) {
     const double t = block_sum<NT>(ss, red);

@@ -21,6 +21,7 @@ MG_KAPPA_W = 0x7FFFFFFF
 CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
 MG_OPT_OMEGA, MG_OPT_COARSE_N, MG_OPT_LEVELS, MG_OPT_N, MG_OPT_LAUNCHES, MG_OPT_COARSE_N32 = 1, 2, 3, 4, 5, 6
 MG_OPT_COARSE_OP, MG_OPT_STOP, MG_OPT_SMOOTHER, MG_OPT_COARSENING, MG_OPT_PRECOND = 7, 8, 9, 10, 11
+MG_OPT_CONV_X, MG_OPT_CONV_Y = 12, 13
 SMOOTHERS = {"jacobi": 0, "zebra": 1, "xzebra": 2}
 COARSENINGS = {"full": 0, "y": 1}
 
@@ -115,7 +116,7 @@ class Multigrid:
     """One hierarchy for the Section 4 problem: ``mg_setup(n, eps, theta, levels, nu1, nu2)``."""
 
     def __init__(self, n, eps, theta, levels, nu1=2, nu2=2, omega=None, coarse_n=None, smoother="jacobi",
-                 coarsening="full"):
+                 coarsening="full", convection=None, coarse_op=None):
         h = _h()
         _check(_lib.mg_setup(int(n), float(eps), float(theta), int(levels), int(nu1), int(nu2), ctypes.byref(h)),
                "mg_setup")
@@ -133,6 +134,11 @@ class Multigrid:
         elif smoother != "jacobi":
             self.set_option(MG_OPT_SMOOTHER, SMOOTHERS[smoother])
         self.smoother, self.coarsening = smoother, coarsening
+        if coarse_op is not None:
+            self.set_option(MG_OPT_COARSE_OP, {"galerkin": 0, "rediscretized": 1}[coarse_op])
+        if convection is not None:
+            self.set_option(MG_OPT_CONV_X, convection[0])
+            self.set_option(MG_OPT_CONV_Y, convection[1])
 
     def close(self):
         if getattr(self, "_h", None):
