@@ -306,6 +306,20 @@ __global__ void __launch_bounds__(32 * R) line_relax_kernel(const LineArgs<T> a)
 // points [r NT MC, (r+1) NT MC) of the cluster's row; the CTA totals of the two scans are
 // exchanged through distributed shared memory between cluster barriers.
 // ---------------------------------------------------------------------------------------------
+// The same scan over the first N lanes only (log2 N steps); lanes >= N are not read.
+template <bool UP, int N, typename T>
+__device__ __forceinline__ void affine_scan_n(T& A, T& B, int lane) {
+#pragma unroll
+  for (int o = 1; o < N; o <<= 1) {
+    const T Ao = UP ? __shfl_up_sync(0xffffffffu, A, o) : __shfl_down_sync(0xffffffffu, A, o);
+    const T Bo = UP ? __shfl_up_sync(0xffffffffu, B, o) : __shfl_down_sync(0xffffffffu, B, o);
+    if (UP ? lane >= o : lane + o < N) {
+      B = fma(A, Bo, B);
+      A = A * Ao;
+    }
+  }
+}
+
 template <typename T, int MC, int NT, int CL>
 __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) line_cluster_kernel(const LineArgs<T> a) {
   namespace cg = cooperative_groups;
@@ -371,13 +385,24 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) line_cluster_ke
   __syncthreads();
   if (warp == 0) {
     T a2 = lane < NW ? wa[lane] : T(1), b2 = lane < NW ? wb[lane] : T(0);
-    affine_scan<true>(a2, b2, lane);
+    affine_scan_n<true, NW>(a2, b2, lane);
     if (lane < NW) { wa[lane] = a2; wb[lane] = b2; }
     if (lane == NW - 1) { ca = a2; cb = b2; }
   }
   cluster.sync();
-  T ycta = T(0);  // y entering this CTA's first point: the lower ranks' maps applied from zero
-  for (int q = 0; q < rank; ++q) ycta = fma(*cluster.map_shared_rank(&ca, q), ycta, *cluster.map_shared_rank(&cb, q));
+  // y entering this CTA's first point: the lower ranks' maps composed in parallel (lane q reads
+  // rank q's total) and applied from zero
+  T ycta;
+  {
+    T qa = T(1), qb = T(0);
+    if (lane < rank) {
+      qa = *cluster.map_shared_rank(&ca, lane);
+      qb = *cluster.map_shared_rank(&cb, lane);
+    }
+    affine_scan_n<true, CL>(qa, qb, lane);
+    ycta = __shfl_sync(0xffffffffu, qb, rank > 0 ? rank - 1 : 0);
+    if (rank == 0) ycta = T(0);
+  }
   T Ain = __shfl_up_sync(0xffffffffu, A, 1), Bin = __shfl_up_sync(0xffffffffu, B, 1);
   if (lane == 0) { Ain = T(1); Bin = T(0); }
   const T ywarp = warp > 0 ? fma(wa[warp - 1], ycta, wb[warp - 1]) : ycta;
@@ -409,13 +434,23 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(NT) line_cluster_ke
   __syncthreads();
   if (warp == 0) {
     T a2 = lane < NW ? wa[lane] : T(1), b2 = lane < NW ? wb[lane] : T(0);
-    affine_scan<false>(a2, b2, lane);
+    affine_scan_n<false, NW>(a2, b2, lane);
     if (lane < NW) { wa[lane] = a2; wb[lane] = b2; }
     if (lane == 0) { ca = a2; cb = b2; }
   }
   cluster.sync();
-  T xcta = T(0);  // x at the first point after this CTA: the higher ranks' maps applied from zero
-  for (int q = CL - 1; q > rank; --q) xcta = fma(*cluster.map_shared_rank(&ca, q), xcta, *cluster.map_shared_rank(&cb, q));
+  // x at the first point after this CTA: the higher ranks' maps composed in parallel, from zero
+  T xcta;
+  {
+    T qa = T(1), qb = T(0);
+    if (lane > rank && lane < CL) {
+      qa = *cluster.map_shared_rank(&ca, lane);
+      qb = *cluster.map_shared_rank(&cb, lane);
+    }
+    affine_scan_n<false, CL>(qa, qb, lane);
+    xcta = __shfl_sync(0xffffffffu, qb, rank + 1 < CL ? rank + 1 : 0);
+    if (rank + 1 >= CL) xcta = T(0);
+  }
   T Eup = __shfl_down_sync(0xffffffffu, E, 1), Dup = __shfl_down_sync(0xffffffffu, D, 1);
   if (lane == 31) { Eup = T(1); Dup = T(0); }
   const T xwarp = warp + 1 < NW ? fma(wa[warp + 1], xcta, wb[warp + 1]) : xcta;
