@@ -479,8 +479,9 @@ void ensure_maps(mg_ctx* h) {
 // residual of the level's v: no relaxation and no copy of v.
 template <typename T>
 int emit_pass_a(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const int* skip, cudaStream_t s,
-                bool lines = false) {
+                bool lines = false, double* norm_partial = nullptr) {
   PassAArgs<T> a;
+  a.partial = norm_partial;
   a.vin = zero ? nullptr : lv_v(h, b, l);
   // lines mode from a zero start without pre-relaxation: v is written (as zero) for the post-smoothing
   a.vout = lines ? (zero ? lv_v(h, b, l) : nullptr) : Arr<T>::tmp(h, l);
@@ -789,6 +790,33 @@ int emit_cycle(mg_ctx* h, const BindingT<T>& b, int kappa, bool zero, bool adjoi
   return emit_call(h, b, 0, kappa, zero, adjoint, norm, skip, s);
 }
 
+// A stand-alone solve cycle whose stopping test comes first: pass A at level 0 forms the residual
+// of the incoming iterate in its first sweep (the residual form of the same update) and writes its
+// squares; finish_step (pre mode) records it as the residual after the previous cycle and stops
+// there, skipping the rest of the cycle, or lets the cycle run. This drops the separate residual
+// stage of pass B at level 0 (10 FP64 operations per point per cycle) for one extra pass A when
+// the solve ends. Used for FP64 damped Jacobi with full coarsening, nu1 >= 1 and a fine level
+// above the coarse kernel.
+bool prenorm_ok(const mg_ctx* h) { return h->smoother == 0 && !h->semi && h->lc > 0 && h->nu1 >= 1; }
+
+int emit_solve_cycle_prenorm(mg_ctx* h, const Binding& b, int kappa, cudaGraphConditionalHandle ch,
+                             const int* skip, cudaStream_t s) {
+  KC_TRY(emit_pass_a(h, b, 0, false, h->nu1, skip, s, false, h->partial));
+  finish_step_kernel<NT_VEC><<<1, NT_VEC, 0, s>>>(h->partial, (int)pass_grid_blocks(h->n), h->scal, h->ints, h->hist,
+                                                   ch, 1, 1);
+  KC_CUDA(cudaGetLastError());
+  ++h->launch_count;
+  int k1, k2;
+  child_counters(kappa, false, &k1, &k2);
+  if (1 >= h->lc) {
+    KC_TRY(emit_coarse(h, b, k1, k2, 1, false, skip, s));
+  } else {
+    KC_TRY(emit_call(h, b, 1, k1, true, false, false, skip, s));
+    if (k2 > 0) KC_TRY(emit_call(h, b, 1, k2, false, false, false, skip, s));
+  }
+  return emit_pass_b(h, b, 0, h->nu2, nullptr, skip, s);
+}
+
 int norm_partials(mg_ctx* h) {
   return (int)((h->lc == 0 || h->smoother != 0) ? apply_grid_blocks(h->n) : pass_grid_blocks(h->n));
 }
@@ -974,6 +1002,9 @@ int add_solve_branch(mg_ctx* h, cudaGraph_t parent, double* x, const double* f, 
     ir_add_kernel<NT_VEC><<<agrid, NT_VEC, 0, h->own>>>(x, d, n, h->ld32_0, done);
     ir_residual_kernel<NT_VEC><<<agrid, NT_VEC, 0, h->own>>>(x, f, r32, h->ld32_0, h->coef, n, h->partial, done);
     finish_step_kernel<NT_VEC><<<1, NT_VEC, 0, h->own>>>(h->partial, napply, h->scal, h->ints, h->hist, ch, 1);
+  } else if (prenorm_ok(h)) {
+    Binding b{x, f, n};
+    st = emit_solve_cycle_prenorm(h, b, kappa, ch, done, h->own);
   } else {
     Binding b{x, f, n};
     st = emit_cycle(h, b, kappa, false, false, true, done, h->own);
@@ -1005,7 +1036,9 @@ int solve_impl(mg_handle h, double* v, const double* f, int kappa, double tol, i
     Binding b{v, f, h->n};
     const int np = norm_partials(h);
     const bool err_rule = h->stop_rule == 1;
+    const bool pre = !adjoint && !err_rule && prenorm_ok(h);
     KC_TRY(build_while_graph(h, [&](cudaGraphConditionalHandle ch) -> int {
+      if (pre) return emit_solve_cycle_prenorm(h, b, kappa, ch, h->ints + I_DONE, h->own);
       KC_TRY(emit_cycle(h, b, kappa, false, adjoint, !err_rule, h->ints + I_DONE, h->own));
       if (err_rule) {  // ||v_k||^2 partial sums
         dot_kernel<NT_VEC><<<VEC_BLOCKS, NT_VEC, 0, h->own>>>(v, v, nullptr, (size_t)h->n * h->n, h->partial,

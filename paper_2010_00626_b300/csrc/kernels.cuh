@@ -207,6 +207,8 @@ struct PassAArgs {
   T* fc;          // coarse right-hand side, (n-1)/2 square
   const T* coef;
   const int* skip;  // nullable; kernel returns at once when *skip != 0
+  double* partial;  // nullable (nu >= 1): per-block sum of squared residuals of vin over the tile,
+                    // formed by the first sweep, written as v + w (f - A v)
   int ldvin, ldvout, ldf, ldc;
   int n, nu, level;
 };
@@ -244,20 +246,41 @@ __global__ void __launch_bounds__(NT) pass_a_kernel(const PassAArgs<T> a) {
 
   T* src = s0;
   T* dst = s1;
+  double ss = 0.0;  // squared residuals of vin on the tile (with a.partial)
   for (int s = 1; s <= a.nu; ++s) {
     const int g = a.nu - s + 1;  // sweep s is needed on the tile grown by g
     const int lo = H - g, R = BX + 2 * g + 1, Ry = BY + 2 * g + 1;
     // from a zero start the first sweep is v = w f, which is what the update gives on zeros
     // (fma(w, f, 0) and every further fma(b, 0, t) = t), in one operation instead of ten
     const bool from_zero = s == 1 && a.vin == nullptr;
-    for_region<NT>(R, Ry, [&](int rx, int ry) {
-      const int lx = lo + rx, ly = lo + ry, k = ly * W + lx;
-      dst[k] = inside(gx0 + lx, gy0 + ly, n)
-                   ? (from_zero ? op.w() * fs[k] : op.jac(src, k, W, fs[k]))
-                   : T(0);
-    });
+    if (s == 1 && a.partial && !from_zero) {
+      // the same update as v + w r with the residual r = f - A v explicit, whose squares over the
+      // tile's own points give the stopping test of the previous cycle
+      for_region<NT>(R, Ry, [&](int rx, int ry) {
+        const int lx = lo + rx, ly = lo + ry, k = ly * W + lx;
+        T val = T(0);
+        if (inside(gx0 + lx, gy0 + ly, n)) {
+          const T r = op.res(src, k, W, fs[k]);
+          val = fma(op.w(), r, src[k]);
+          if ((unsigned)(lx - H) < (unsigned)BX && (unsigned)(ly - H) < (unsigned)BY) ss = fma((double)r, (double)r, ss);
+        }
+        dst[k] = val;
+      });
+    } else {
+      for_region<NT>(R, Ry, [&](int rx, int ry) {
+        const int lx = lo + rx, ly = lo + ry, k = ly * W + lx;
+        dst[k] = inside(gx0 + lx, gy0 + ly, n)
+                     ? (from_zero ? op.w() * fs[k] : op.jac(src, k, W, fs[k]))
+                     : T(0);
+      });
+    }
     __syncthreads();
     T* t = src; src = dst; dst = t;
+  }
+  if (a.partial) {
+    __shared__ double red[NT / 32];
+    const double tot = block_sum<NT>(ss, red);
+    if (threadIdx.x == 0) a.partial[blockIdx.y * gridDim.x + blockIdx.x] = tot;
   }
 
   // relaxed v on the tile
@@ -1226,13 +1249,30 @@ __global__ void __launch_bounds__(NT) sum_to_scalar_kernel(const double* partial
 template <int NT>
 __global__ void __launch_bounds__(NT) finish_step_kernel(const double* partial, int np, double* scal, int* ints,
                                                          double* hist, cudaGraphConditionalHandle cond,
-                                                         int use_cond) {
+                                                         int use_cond, int pre = 0) {
   __shared__ double red[NT / 32];
   if (ints[I_DONE]) {
     if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional(cond, 0);
     return;
   }
   const double s = sum_partials<NT>(partial, np, red);
+  if (pre && threadIdx.x == 0) {
+    // the norm is that of the iterate before this cycle (formed by its first sweep): after
+    // k = ints[I_COUNT] completed cycles. Stop before the cycle (the rest of it is skipped)
+    // once k >= 1 cycles reached tol, or k reached the limit; otherwise count the cycle.
+    const double fn = sqrt(scal[S_FNORM2]);
+    const double rho = fn > 0.0 ? sqrt(s) / fn : sqrt(s);
+    const int k = ints[I_COUNT];
+    if (k >= 1) {
+      hist[k - 1] = rho;
+      scal[S_LAST] = rho;
+    }
+    const bool stop = k >= 1 && ((rho <= scal[S_TOL]) || (k >= ints[I_MAX]));
+    if (stop) ints[I_DONE] = 1;
+    else ints[I_COUNT] = k + 1;
+    if (use_cond) cudaGraphSetConditional(cond, stop ? 0 : 1);
+    return;
+  }
   if (threadIdx.x == 0) {
     const double fn = sqrt(scal[S_FNORM2]);
     const double rho = fn > 0.0 ? sqrt(s) / fn : sqrt(s);
