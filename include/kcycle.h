@@ -208,9 +208,11 @@ int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* l
  * launch with a CUDA event pair around every kernel instead of through a graph, and report each
  * launch: ms[r] its duration in milliseconds, kind[r] 0 = pass A (relax + residual + restrict),
  * 1 = pass B (interpolate + correct + relax), 2 = coarse-level kernel, 3 = whole-grid residual;
- * level[r] its level (0 finest). Flags in with_norm: bit 0 adds the residual partial sums of a
- * solve cycle; bit 1 profiles instead the FP32 cycle of mg_solve_mixed (zero start on the handle's
- * FP32 level-0 arrays; v and f are then not used).
+ * level[r] its level (0 finest); kinds 4 and 5 are zebra row and column relaxations. Flags in
+ * with_norm: bit 0 profiles the launches of a stand-alone solve cycle (with the residual partial
+ * sums of its stopping test, formed by the first sweep of pass A at level 0 where mg_solve does so,
+ * else by the last pass); bit 1 profiles instead the FP32 cycle of mg_solve_mixed (zero start on the
+ * handle's FP32 level-0 arrays; v and f are then not used).
  * ms, kind, level: host, nullable, max_records entries; *count: number of launches (may exceed
  * max_records). Measurement hook with no counterpart in the paper. Synchronises. */
 int mg_profile_cycle(mg_handle h, double* v, const double* f, int kappa, int with_norm, int max_records,

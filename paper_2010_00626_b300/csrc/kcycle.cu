@@ -799,13 +799,16 @@ int emit_cycle(mg_ctx* h, const BindingT<T>& b, int kappa, bool zero, bool adjoi
 // above the coarse kernel.
 bool prenorm_ok(const mg_ctx* h) { return h->smoother == 0 && !h->semi && h->lc > 0 && h->nu1 >= 1; }
 
+// (finish = false: the same launches without the stopping test, for per-launch profiling)
 int emit_solve_cycle_prenorm(mg_ctx* h, const Binding& b, int kappa, cudaGraphConditionalHandle ch,
-                             const int* skip, cudaStream_t s) {
+                             const int* skip, cudaStream_t s, bool finish = true) {
   KC_TRY(emit_pass_a(h, b, 0, false, h->nu1, skip, s, false, h->partial));
-  finish_step_kernel<NT_VEC><<<1, NT_VEC, 0, s>>>(h->partial, (int)pass_grid_blocks(h->n), h->scal, h->ints, h->hist,
-                                                   ch, 1, 1);
-  KC_CUDA(cudaGetLastError());
-  ++h->launch_count;
+  if (finish) {
+    finish_step_kernel<NT_VEC><<<1, NT_VEC, 0, s>>>(h->partial, (int)pass_grid_blocks(h->n), h->scal, h->ints,
+                                                     h->hist, ch, 1, 1);
+    KC_CUDA(cudaGetLastError());
+    ++h->launch_count;
+  }
   int k1, k2;
   child_counters(kappa, false, &k1, &k2);
   if (1 >= h->lc) {
@@ -1693,6 +1696,8 @@ int mg_profile_cycle(mg_handle h, double* v, const double* f, int kappa, int wit
   if (fp32) {  // the FP32 cycle of the mixed path: d = B32 r from zero on the handle's FP32 arrays
     BindingT<float> b32{h->lv[0].v32, h->lv[0].f32, h->ld32_0};
     st = emit_cycle(h, b32, kappa, true, false, false, nullptr, s);
+  } else if ((with_norm & 1) && prenorm_ok(h)) {  // the launches of a stand-alone solve cycle
+    st = emit_solve_cycle_prenorm(h, b, kappa, cudaGraphConditionalHandle{}, nullptr, s, false);
   } else {
     st = emit_cycle(h, b, kappa, false, false, (with_norm & 1) != 0, nullptr, s);
   }
