@@ -1,7 +1,7 @@
 """Run a fixed number of kappa-cycles on one synthetic problem through the C ABI, for profiling.
 
     python -m paper_2010_00626_b300.run_cycles --n 4095 --levels 12 --kappa 4 --cycles 1 \
-        [--smoother zebra] [--coarsening y] [--theta 1.0471975511965976] [--eps 1e-4] [--fp32]
+        [--smoother zebra] [--coarsening y] [--theta 1.0471975511965976] [--eps 1e-4] [--fp32] [--solve]
 
 The right-hand side is f ~ N(0, 1) (seed 0) and the start v = 0. With --fp32 the cycles are the
 FP32 cycles of the mixed forms (mg_kcycle_f32). Prints one JSON line with the wall time; the
@@ -24,6 +24,10 @@ def main():
     ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "zebra", "xzebra"])
     ap.add_argument("--coarsening", default="full", choices=["full", "y"])
     ap.add_argument("--fp32", action="store_true")
+    ap.add_argument("--solve", action="store_true", help="run the launches of stand-alone solve cycles (with the "
+                                                         "stopping test's norm) one by one, as mg_profile_cycle "
+                                                         "does, instead of bare cycles (a solve's own graph has "
+                                                         "conditional nodes, whose kernels profilers skip)")
     args = ap.parse_args()
 
     import torch
@@ -41,7 +45,9 @@ def main():
     v = torch.zeros_like(f)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.cycles):
+    for _ in range(args.cycles if args.solve else 0):
+        mg.profile_cycle(v, f, args.kappa, with_norm=True)
+    for _ in range(0 if args.solve else args.cycles):
         if args.fp32:
             mg.kcycle_f32(v, f, args.kappa)
         else:
@@ -49,6 +55,7 @@ def main():
     torch.cuda.synchronize()
     print(json.dumps({"n": n, "levels": levels, "kappa": args.kappa, "cycles": args.cycles,
                       "smoother": args.smoother, "coarsening": args.coarsening, "fp32": args.fp32,
+                      "solve": args.solve,
                       "wall_ms": 1e3 * (time.perf_counter() - t0)}))
 
 
