@@ -268,6 +268,41 @@ def test_large_solve_reaches_tolerance(lib):
     assert oracle.relres(h, to_np(vd), f) <= 1e-8 * (1 + 1e-6)
 
 
+@pytest.mark.parametrize("kappa", [1, 2, 3, 4, 5, KAPPA_W])
+def test_large_solve_matches_oracle_cycle_counts(lib, kappa):
+    """4095^2 solves against the oracle's own full-size runs (tests/golden, written by
+    oracle/full_size_cycles.py): identical cycle counts and residual histories."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", f"large_standalone_cycles_k{kappa_eff(kappa, 12)}.json")
+    if not os.path.exists(path):
+        pytest.skip("no oracle run stored for this counter")
+    g = json.load(open(path))
+    n, levels = g["n"], g["levels"]
+    mg = lib.Multigrid(n, g["eps"], g["theta"], levels)
+    vd = torch_dev(np.zeros((n, n)))
+    st, cycles, relres, hist = mg.solve(vd, torch_dev(rhs_normal(n, 0)), kappa, g["tol"], 3000)
+    assert st == 0 and cycles == g["cycles"]
+    # iterates agree to 1e-12, so the histories agree to that bound relative to the early
+    # residuals, which is far below 1e-10 of the late ones
+    for a, b in zip(hist, g["history"]):
+        assert abs(a - b) <= HIST_TOL * b + 1e-12 * g["history"][0], (a, b)
+
+
+def test_largest_grid_solve(lib):
+    """16383^2 (14 levels, the paper's largest): kappa=3 solve to 1e-8; the oracle recomputes the
+    residual of the result (a property that holds at any size)."""
+    n, levels, theta, eps = 16383, 14, math.pi / 3, 1e-4
+    f = rhs_normal(n, 0)
+    mg = lib.Multigrid(n, eps, theta, levels)
+    vd = torch_dev(np.zeros((n, n)))
+    st, cycles, relres, hist = mg.solve(vd, torch_dev(f), 3, 1e-8, 3000, history=False)
+    assert st == 0 and relres <= 1e-8
+    st_fine = oracle.fine_stencil(theta, eps, n)
+    r = f - oracle.apply_stencil(st_fine, to_np(vd))
+    assert np.linalg.norm(r) / np.linalg.norm(f) <= 1e-8 * (1 + 1e-6)
+
+
 def test_rediscretized_hierarchy_and_error_protocol(lib):
     """Coarse operators rediscretized (Section 4 stencil at each coarse h): stencils bit for bit,
     iterates to 1e-12; the error-reduction protocol (f = 0, random start, ||v_k|| / ||v_0||) gives
