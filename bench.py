@@ -176,6 +176,55 @@ def bytes_per_point(kind, norm):
     return 8 + 8 + 8 + 2 if kind == 0 else 8 + 8 + 2 + 8
 
 
+def per_level_report(mg, prof, fp32, fp64_peak_ops, hbm_peak, norm_l0, sms):
+    """Per level of one profiled cycle (launch-by-launch CUDA events, eager launches): launches,
+    microseconds per launch, CTAs per launch (mg_level_grid), algorithmic bytes and FP64 operations
+    per launch (each field read or written once; no halo recomputation; v counted as read), the
+    achieved HBM GB/s and FP64 op/s with their fractions of the measured peaks, and the time during
+    which SMs hold no CTA (a launch of c < 148 CTAs leaves 148 - c SMs without work)."""
+    ms, kind, level = prof
+    esz = 4 if fp32 else 8
+    rows, idle_ms, total_ms, coarse_ms, coarse_idle = {}, 0.0, 0.0, 0.0, 0.0
+    for t, k, l in zip(ms, kind, level):
+        key = (int(l), int(k))
+        r = rows.setdefault(key, [0, 0.0])
+        r[0] += 1
+        r[1] += float(t)
+    grids = {}
+    out = []
+    for (l, k), (cnt, t) in sorted(rows.items()):
+        if l not in grids:
+            grids[l] = mg.level_grid(l, fp32=fp32)
+        n_l, ctas = grids[l]
+        busy = min(ctas, sms)
+        idle = t * (sms - busy) / sms
+        total_ms += t
+        idle_ms += idle
+        if ctas < sms:
+            coarse_ms += t
+            coarse_idle += idle
+        e = {"level": l, "n": n_l, "kind": {0: "pass_a", 1: "pass_b", 2: "coarse"}.get(k, str(k)),
+             "launches": cnt, "us_per_launch": round(1e3 * t / cnt, 2), "ctas": ctas}
+        if k in (0, 1):
+            pts = n_l * n_l
+            # pass A: v, f read, relaxed v written, coarse f written (a quarter); pass B: relaxed v,
+            # f read, coarse v read (a quarter), v written
+            nbytes = pts * esz * 3.25
+            ops = dp_ops_per_point(k, 2, norm_l0 and k == 0 and l == 0)[0] * pts
+            sec = 1e-3 * t / cnt
+            e["gb_s"] = round(nbytes / sec / 1e9, 1)
+            e["hbm_frac"] = round(nbytes / sec / 1e9 / hbm_peak, 4)
+            if not fp32:
+                e["fp64_frac"] = round(ops / sec / fp64_peak_ops, 4)
+        out.append(e)
+    return {"levels": out,
+            "sm_idle": {"ms_per_cycle": round(idle_ms, 4), "frac_of_cycle": round(idle_ms / total_ms, 4),
+                        "launches_below_one_wave_ms": round(coarse_ms, 4),
+                        "idle_within_those_ms": round(coarse_idle, 4),
+                        "note": "eager launches timed with CUDA events; an SM idles while a launch has fewer "
+                                "CTAs than SMs (the coarse levels and the one-CTA coarse kernel)"}}
+
+
 PAPER_TABLE6 = {"10": {"2": 589, "3": 274, "4": 206, "W": 193}, "45": {"2": 1725, "3": 706, "4": 463, "W": 385}}
 PAPER_TABLE7 = {"10": {"4": 36}, "45": {"4": 53}}
 PAPER_TABLE8 = {"10": {"1": 1705, "2": 371, "3": 187, "4": 148}, "45": {"2": 1093, "3": 410, "4": 254}}
@@ -349,6 +398,10 @@ def main():
                 "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
                         "algorithmic_bytes": bytes_alg}}
     cycle_share = {f"{kinds[k]}@L{l}": round(t / total, 4) for (k, l), t in sorted(share.items(), key=lambda x: -x[1])[:8]}
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    per_level = per_level_report(mg, (prof_ms, prof_kind, prof_level), False, fp64_peak_ops, hbm_peak, True, sms)
+    per_level["cycle"] = f"FP64 kappa={kname(kappa)} stand-alone solve cycle"
+    per_level["fine_dof_per_s"] = n * n / (ms_step / cycles * 1e-3)
 
     # ---------------------------------------------------------------- end to end (host buffers)
     e2e = None
@@ -558,6 +611,14 @@ def main():
                            "point relaxation does not smooth; the *_zebra runs use alternating zebra line "
                            "relaxation (Section 4) on every instance")
 
+    # ---------------------------------------------------------------- FP32 cycle of the mixed solve, per level
+    per_level32 = None
+    if not args.no_sweep:
+        for _ in range(3):
+            prof32 = mg.profile_cycle(v, f, kappa, fp32=True)
+        per_level32 = per_level_report(mg, prof32, True, fp64_peak_ops, hbm_peak, False, sms)
+        per_level32["cycle"] = f"FP32 kappa={kname(kappa)} cycle of the mixed solve (from zero)"
+
     # ---------------------------------------------------------------- oracle on the host cores
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -578,7 +639,8 @@ def main():
                            "omega": cfg["omega"], "cycles": cycles, "ms_per_cycle": ms_step / cycles,
                            "l2": "inputs larger than L2 (each 4095^2 FP64 array is 134 MB)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-                "roofline": roofline, "cycle_share": cycle_share, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "cycle_share": cycle_share, "per_level": per_level,
+                "per_level_fp32": per_level32, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clocks.summary(), "per_kappa": per_kappa,
                 "per_kappa_mixed": per_kappa_mixed, "batched": batched, "model": model_report,
                 "paper_protocol": paper_protocol, "zebra": zebra, "semi_coarsening": semi, "mgcg_8191": mgcg,

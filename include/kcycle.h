@@ -204,6 +204,14 @@ int mg_stencils(mg_handle h, double* out, int max_levels, int* written);
 int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* launches,
                 long long* coarse_calls);
 
+/* Launch shape of the level passes, for reports of SM occupancy: *n_level = the side of `level`
+ * and *ctas = the CTAs of one pass-A or pass-B launch there (both passes use one grid) in the FP64
+ * cycle (fp32 = 0) or the FP32 cycle of the mixed forms (fp32 = 1; level 0 assumes caller arrays
+ * aligned to 16 bytes, as mg_solve_mixed's own are). For a level handled inside the coarse-level
+ * kernel *ctas = 1, that kernel's one CTA. Damped-Jacobi smoother with full coarsening only (else
+ * MG_ERR_ARG). Host pointers, both required. No device work. */
+int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas);
+
 /* Run one finest-level kappa-cycle like mg_kcycle (from the initial guess in v), but launch by
  * launch with a CUDA event pair around every kernel instead of through a graph, and report each
  * launch: ms[r] its duration in milliseconds, kind[r] 0 = pass A (relax + residual + restrict),

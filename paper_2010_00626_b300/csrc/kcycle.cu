@@ -1680,6 +1680,35 @@ int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* l
   return MG_OK;
 }
 
+int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas) {
+  if (!valid_handle(h)) return MG_ERR_STATE;
+  if (!n_level || !ctas || level < 0 || level >= h->levels) return MG_ERR_ARG;
+  if (h->smoother != 0 || h->semi) return MG_ERR_ARG;
+  const int n = h->lv[level].n;
+  *n_level = n;
+  int lc = h->lc;
+  if (fp32) {  // the FP32 coarse level, as ensure_levels32 places it
+    lc = h->levels - 1;
+    for (int l = 0; l < h->levels; ++l)
+      if (h->lv[l].n <= h->coarse_n32) {
+        lc = l;
+        break;
+      }
+  }
+  if (level >= lc) {
+    *ctas = 1;
+    return MG_OK;
+  }
+  if (fp32 && n >= 2047 && std::max(h->nu1, h->nu2) <= 2) {  // streaming passes (stream_ok)
+    const int strips = (n + SF_COLS - 1) / SF_COLS, R = stream_rows(n);
+    *ctas = ((strips + SF_WARPS - 1) / SF_WARPS) * ((n + R - 1) / R);
+    return MG_OK;
+  }
+  const int bx = tile_edge(n), by = tile_rows(n);
+  *ctas = ((n + bx - 1) / bx) * ((n + by - 1) / by);
+  return MG_OK;
+}
+
 int mg_profile_cycle(mg_handle h, double* v, const double* f, int kappa, int with_norm, int max_records,
                      double* ms, int* kind, int* level, int* count) {
   if (!valid_handle(h)) return MG_ERR_STATE;

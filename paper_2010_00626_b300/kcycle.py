@@ -56,6 +56,7 @@ SIGNATURES = {
     "mg_param_grads": (_i, [_h, _p, _p, _dp, _dp]),
     "mg_stencils": (_i, [_h, _dp, _i, _ip]),
     "mg_counters": (_i, [_h, _i, _llp, _llp, _llp]),
+    "mg_level_grid": (_i, [_h, _i, _i, _ip, _ip]),
     "mg_profile_cycle": (_i, [_h, _p, _p, _i, _i, _i, _dp, _ip, _ip, _ip]),
     "mg_residual_norm_noalloc": (_i, [_i, _d, _d, _p, _p, _p, _dp]),
     "mg_solve_mixed": (_i, [_h, _p, _p, _i, _d, _i, _ip, _dp, _dp]),
@@ -265,6 +266,14 @@ class Multigrid:
                                      level.ctypes.data_as(_ip), ctypes.byref(cnt)), "mg_profile_cycle")
         k = min(cnt.value, max_records)
         return ms[:k], kind[:k], level[:k]
+
+    def level_grid(self, level, fp32=False):
+        """(side of `level`, CTAs of one of its pass launches) in the FP64 or the FP32 cycle; 1 CTA
+        for the levels inside the coarse-level kernel."""
+        n, c = _i(), _i()
+        _check(_lib.mg_level_grid(self._h, int(level), int(bool(fp32)), ctypes.byref(n), ctypes.byref(c)),
+               "mg_level_grid")
+        return n.value, c.value
 
     def counters(self, kappa):
         calls = (ctypes.c_longlong * self.levels)()

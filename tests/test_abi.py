@@ -57,5 +57,7 @@ def test_setup_rejects_bad_arguments_without_touching_the_gpu(libk):
     assert lib.mg_kcycle(None, None, None, 1) == -5
     assert lib.mg_set_option(None, 9, 1.0) == -5      # MG_OPT_SMOOTHER on no handle
     assert lib.mg_batch_set_option(None, 9, 1.0) == -1
+    n_l, ctas = ctypes.c_int(), ctypes.c_int()
+    assert lib.mg_level_grid(None, 0, 0, ctypes.byref(n_l), ctypes.byref(ctas)) == -5
     assert lib.mg_destroy(None) == 0
     assert lib.mg_status_string(-1) == b"invalid argument"
