@@ -176,12 +176,14 @@ def bytes_per_point(kind, norm):
     return 8 + 8 + 8 + 2 if kind == 0 else 8 + 8 + 2 + 8
 
 
-def per_level_report(mg, prof, fp32, fp64_peak_ops, hbm_peak, norm_l0, sms):
+def per_level_report(mg, prof, fp32, fp64_peak_ops, hbm_peak, norm_l0, sms, kappa, l0_zero):
     """Per level of one profiled cycle (launch-by-launch CUDA events, eager launches): launches,
     microseconds per launch, CTAs per launch (mg_level_grid), algorithmic bytes and FP64 operations
-    per launch (each field read or written once; no halo recomputation; v counted as read), the
-    achieved HBM GB/s and FP64 op/s with their fractions of the measured peaks, and the time during
-    which SMs hold no CTA (a launch of c < 148 CTAs leaves 148 - c SMs without work)."""
+    per launch (each field read or written once; no halo recomputation; a pass A that starts from
+    zero reads no v and its first sweep is one operation: the first call below each parent call, and
+    level 0 when l0_zero), the achieved HBM GB/s and FP64 op/s with their fractions of the measured
+    peaks, and the time during which SMs hold no CTA (a launch of c < 148 CTAs leaves 148 - c SMs
+    without work)."""
     ms, kind, level = prof
     esz = 4 if fp32 else 8
     rows, idle_ms, total_ms, coarse_ms, coarse_idle = {}, 0.0, 0.0, 0.0, 0.0
@@ -192,6 +194,7 @@ def per_level_report(mg, prof, fp32, fp64_peak_ops, hbm_peak, norm_l0, sms):
         r[1] += float(t)
     grids = {}
     out = []
+    calls = mg.counters(kappa)[0]
     for (l, k), (cnt, t) in sorted(rows.items()):
         if l not in grids:
             grids[l] = mg.level_grid(l, fp32=fp32)
@@ -211,6 +214,11 @@ def per_level_report(mg, prof, fp32, fp64_peak_ops, hbm_peak, norm_l0, sms):
             # f read, coarse v read (a quarter), v written
             nbytes = pts * esz * 3.25
             ops = dp_ops_per_point(k, 2, norm_l0 and k == 0 and l == 0)[0] * pts
+            if k == 0:
+                # from zero the first sweep is v = w f: one operation instead of ten, and no v read
+                zero = ((1 if l0_zero else 0) if l == 0 else calls[l - 1]) / max(calls[l], 1)
+                nbytes -= pts * esz * zero
+                ops -= 9 * pts * zero
             sec = 1e-3 * t / cnt
             e["gb_s"] = round(nbytes / sec / 1e9, 1)
             e["hbm_frac"] = round(nbytes / sec / 1e9 / hbm_peak, 4)
@@ -399,7 +407,8 @@ def main():
                         "algorithmic_bytes": bytes_alg}}
     cycle_share = {f"{kinds[k]}@L{l}": round(t / total, 4) for (k, l), t in sorted(share.items(), key=lambda x: -x[1])[:8]}
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    per_level = per_level_report(mg, (prof_ms, prof_kind, prof_level), False, fp64_peak_ops, hbm_peak, True, sms)
+    per_level = per_level_report(mg, (prof_ms, prof_kind, prof_level), False, fp64_peak_ops, hbm_peak, True, sms,
+                                 kappa, False)
     per_level["cycle"] = f"FP64 kappa={kname(kappa)} stand-alone solve cycle"
     per_level["fine_dof_per_s"] = n * n / (ms_step / cycles * 1e-3)
 
@@ -616,7 +625,7 @@ def main():
     if not args.no_sweep:
         for _ in range(3):
             prof32 = mg.profile_cycle(v, f, kappa, fp32=True)
-        per_level32 = per_level_report(mg, prof32, True, fp64_peak_ops, hbm_peak, False, sms)
+        per_level32 = per_level_report(mg, prof32, True, fp64_peak_ops, hbm_peak, False, sms, kappa, True)
         per_level32["cycle"] = f"FP32 kappa={kname(kappa)} cycle of the mixed solve (from zero)"
 
     # ---------------------------------------------------------------- oracle on the host cores

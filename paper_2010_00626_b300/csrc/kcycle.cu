@@ -52,7 +52,7 @@ constexpr int NT_SMALL = 256;
 constexpr int NT_TINY = 128;
 constexpr int NT_BIG = 512;
 constexpr int NT_COARSE = 256;     // coarse kernel, FP64 (bound by the SM's FP64 pipe)
-constexpr int NT_COARSE32 = 256;   // coarse kernel, FP32
+constexpr int NT_COARSE32 = 512;   // coarse kernel, FP32 (latency bound: more threads per phase)
 template <typename T>
 constexpr int nt_coarse() { return std::is_same<T, double>::value ? NT_COARSE : NT_COARSE32; }
 constexpr int NT_VEC = 256;
