@@ -176,6 +176,11 @@ def bytes_per_point(kind, norm):
     return 8 + 8 + 8 + 2 if kind == 0 else 8 + 8 + 2 + 8
 
 
+# launch kinds of mg_profile_cycle
+PROFILE_KINDS = {0: "pass_a", 1: "pass_b", 2: "coarse", 3: "residual", 4: "lines_x", 5: "lines_y",
+                 6: "call"}  # call: pass A, the coarse walk and pass B of one call in one cluster launch
+
+
 def per_level_report(mg, prof, fp32, fp64_peak_ops, hbm_peak, norm_l0, sms, kappa, l0_zero):
     """Per level of one profiled cycle (launch-by-launch CUDA events, eager launches): launches,
     microseconds per launch, CTAs per launch (mg_level_grid), algorithmic bytes and FP64 operations
@@ -206,7 +211,7 @@ def per_level_report(mg, prof, fp32, fp64_peak_ops, hbm_peak, norm_l0, sms, kapp
         if ctas < sms:
             coarse_ms += t
             coarse_idle += idle
-        e = {"level": l, "n": n_l, "kind": {0: "pass_a", 1: "pass_b", 2: "coarse"}.get(k, str(k)),
+        e = {"level": l, "n": n_l, "kind": PROFILE_KINDS.get(k, str(k)),
              "launches": cnt, "us_per_launch": round(1e3 * t / cnt, 2), "ctas": ctas}
         if k in (0, 1):
             pts = n_l * n_l
@@ -372,7 +377,7 @@ def main():
         share[key] = share.get(key, 0.0) + float(t)
     total = sum(share.values())
     top = max(share, key=share.get)
-    kinds = {0: "pass_a", 1: "pass_b", 2: "coarse", 3: "residual"}
+    kinds = PROFILE_KINDS
     # the finest-level pass A: the dominant fused kernel of the FP64 path
     dom = (0, 0)
     dom_ms = [float(t) for t, k, l in zip(prof_ms, prof_kind, prof_level) if (k, l) == dom]

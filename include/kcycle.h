@@ -83,7 +83,7 @@ typedef enum {
                               kappa. Option 1 needs damped Jacobi, full coarsening and FP64:
                               mg_pcg returns MG_ERR_ARG otherwise, mg_pcg_mixed always.         */
   MG_OPT_CONV_X = 12,      /* convection b = (bx, by), x component (see MG_OPT_CONV_Y)          */
-  MG_OPT_CONV_Y = 13       /* y component: the problem becomes -div(K grad u) + b.grad u, the
+  MG_OPT_CONV_Y = 13,      /* y component: the problem becomes -div(K grad u) + b.grad u, the
                               non-symmetric test problem proposed in Section 5, with b.grad u by
                               first-order upwind differences (default 0: the Section 4 problem).
                               Nonzero b: damped Jacobi, full coarsening and FP64 only (otherwise
@@ -92,6 +92,12 @@ typedef enum {
                               lose its upwind structure on coarse grids and the cycle can diverge;
                               MG_OPT_COARSE_OP = 1 (rediscretized upwind operators) is the stable
                               choice. Recomputes the stencils.                                    */
+  MG_OPT_FUSED_CALL = 14   /* 1 (default): with damped Jacobi and full coarsening, each call at the
+                              level just above the coarse-level kernel's runs as one launch of a
+                              thread-block cluster (pass A over that level's tiles, the coarse
+                              walk on one CTA, pass B), instead of three launches; same results
+                              bit for bit. 0: three launches. Ignored (three launches) where the
+                              device cannot run the cluster.                                    */
 } mg_option;
 
 /* Set up the hierarchy for the Section 4 problem on an n x n interior grid.
@@ -208,7 +214,8 @@ int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* l
  * and *ctas = the CTAs of one pass-A or pass-B launch there (both passes use one grid) in the FP64
  * cycle (fp32 = 0) or the FP32 cycle of the mixed forms (fp32 = 1; level 0 assumes caller arrays
  * aligned to 16 bytes, as mg_solve_mixed's own are). For a level handled inside the coarse-level
- * kernel *ctas = 1, that kernel's one CTA. Damped-Jacobi smoother with full coarsening only (else
+ * kernel *ctas = 1, that kernel's one CTA; for the level whose calls run as one cluster launch
+ * (MG_OPT_FUSED_CALL), the cluster's CTAs. Damped-Jacobi smoother with full coarsening only (else
  * MG_ERR_ARG). Host pointers, both required. No device work. */
 int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas);
 
@@ -216,7 +223,8 @@ int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas);
  * launch with a CUDA event pair around every kernel instead of through a graph, and report each
  * launch: ms[r] its duration in milliseconds, kind[r] 0 = pass A (relax + residual + restrict),
  * 1 = pass B (interpolate + correct + relax), 2 = coarse-level kernel, 3 = whole-grid residual;
- * level[r] its level (0 finest); kinds 4 and 5 are zebra row and column relaxations. Flags in
+ * level[r] its level (0 finest); kinds 4 and 5 are zebra row and column relaxations, kind 6 a call
+ * run as one cluster launch (pass A, the coarse-level walk, pass B; MG_OPT_FUSED_CALL). Flags in
  * with_norm: bit 0 profiles the launches of a stand-alone solve cycle (with the residual partial
  * sums of its stopping test, formed by the first sweep of pass A at level 0 where mg_solve does so,
  * else by the last pass); bit 1 profiles instead the FP32 cycle of mg_solve_mixed (zero start on the

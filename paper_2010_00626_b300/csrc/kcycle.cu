@@ -103,6 +103,7 @@ struct mg_ctx {
   int coarse_n = 15;  // largest side handled by the coarse kernel (FP64 cycles)
   int lc = 0;         // first level handled by the coarse kernel (FP64 cycles)
   int lc32 = 0;       // same for the FP32 cycles of the mixed path
+  int fused = 1;         // calls just above the coarse kernel as one cluster launch (MG_OPT_FUSED_CALL)
   int coarse_n32 = 31;  // FP32 threshold: one SM does FP32 at 64x the FP64 rate, so the single-CTA
                         // kernel takes more levels (31 measured best at 4095^2 for kappa 3 and 4)
   Level lv[MAXL];
@@ -313,7 +314,7 @@ const T* lv_f(mg_ctx* h, const BindingT<T>& b, int l) { return l == 0 ? b.f0 : A
 template <typename T>
 int lv_ld(mg_ctx* h, const BindingT<T>& b, int l) { return l == 0 ? b.ld0 : Arr<T>::ld(h, l); }
 
-enum { K_PASS_A = 0, K_PASS_B = 1, K_COARSE = 2, K_APPLY = 3, K_LINES_X = 4, K_LINES_Y = 5 };
+enum { K_PASS_A = 0, K_PASS_B = 1, K_COARSE = 2, K_APPLY = 3, K_LINES_X = 4, K_LINES_Y = 5, K_CALL = 6 };
 // (under semi-coarsening K_PASS_A is the y restriction and K_PASS_B the y prolongation)
 
 void prof_begin(mg_ctx* h, int kind, int level, cudaStream_t s) {
@@ -391,8 +392,8 @@ constexpr int MAP_S = 49;       // unknowns of the side-7 level
 constexpr int MAP_CLASSES = 3;  // at most two levels below it: counters 1, 2, >= 3
 
 template <typename T>
-int emit_coarse(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int zero1, bool adjoint, const int* skip,
-                cudaStream_t s) {
+CoarseArgs<T> coarse_args(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int zero1, bool adjoint,
+                          const int* skip) {
   const int lc = lc_of<T>(h);
   CoarseArgs<T> a;
   a.v = lv_v(h, b, lc);
@@ -422,6 +423,14 @@ int emit_coarse(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int zero1, bool
   a.ncls = h->levels - dm;
   a.basis = 0;
   a.cmap_out = nullptr;
+  return a;
+}
+
+template <typename T>
+int emit_coarse(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int zero1, bool adjoint, const int* skip,
+                cudaStream_t s) {
+  const int lc = lc_of<T>(h);
+  const CoarseArgs<T> a = coarse_args(h, b, k1, k2, zero1, adjoint, skip);
   const size_t sm = coarse_smem<T>(a.n_lc, a.L - a.lc);
   prof_begin(h, K_COARSE, lc, s);
   KC_TRY(launch_coarse(h, a, 1, sm, s));
@@ -478,8 +487,8 @@ void ensure_maps(mg_ctx* h) {
 // With `lines` (zebra smoothing done in place by the line kernels) pass A only restricts the
 // residual of the level's v: no relaxation and no copy of v.
 template <typename T>
-int emit_pass_a(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const int* skip, cudaStream_t s,
-                bool lines = false, double* norm_partial = nullptr) {
+PassAArgs<T> pass_a_args(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const int* skip, bool lines,
+                         double* norm_partial) {
   PassAArgs<T> a;
   a.partial = norm_partial;
   a.vin = zero ? nullptr : lv_v(h, b, l);
@@ -496,6 +505,13 @@ int emit_pass_a(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const
   a.n = h->lv[l].n;
   a.nu = nu;
   a.level = l;
+  return a;
+}
+
+template <typename T>
+int emit_pass_a(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const int* skip, cudaStream_t s,
+                bool lines = false, double* norm_partial = nullptr) {
+  const PassAArgs<T> a = pass_a_args(h, b, l, zero, nu, skip, lines, norm_partial);
   ++h->launch_count;
   prof_begin(h, K_PASS_A, l, s);
   int st;
@@ -520,8 +536,8 @@ int emit_pass_a(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const
 
 // With `lines` pass B only adds the prolonged correction to the level's v, in place.
 template <typename T>
-int emit_pass_b(mg_ctx* h, const BindingT<T>& b, int l, int nu, double* partial, const int* skip, cudaStream_t s,
-                bool lines = false) {
+PassBArgs<T> pass_b_args(mg_ctx* h, const BindingT<T>& b, int l, int nu, double* partial, const int* skip,
+                         bool lines) {
   PassBArgs<T> a;
   a.vin = lines ? lv_v(h, b, l) : Arr<T>::tmp(h, l);
   a.vout = lv_v(h, b, l);
@@ -537,6 +553,13 @@ int emit_pass_b(mg_ctx* h, const BindingT<T>& b, int l, int nu, double* partial,
   a.n = h->lv[l].n;
   a.nu = nu;
   a.level = l;
+  return a;
+}
+
+template <typename T>
+int emit_pass_b(mg_ctx* h, const BindingT<T>& b, int l, int nu, double* partial, const int* skip, cudaStream_t s,
+                bool lines = false) {
+  const PassBArgs<T> a = pass_b_args(h, b, l, nu, partial, skip, lines);
   ++h->launch_count;
   prof_begin(h, K_PASS_B, l, s);
   int st;
@@ -733,9 +756,102 @@ void child_counters(int kappa, bool adjoint, int* first, int* second) {
 }
 
 // emit call(l, kappa) for a fine level l < lc; `norm` adds residual partial sums at level 0
+// Calls at the level just above the coarse kernel's as one cluster launch: FP64 tiles of 8 (so a
+// 31^2 level has 16 CTAs, each with the FP64 work of one 8 x 8 tile), FP32 tiles of 16 (63^2: 16
+// CTAs).
+template <typename T>
+constexpr int call_tile() { return std::is_same<T, double>::value ? 8 : 16; }
+
+template <typename T>
+int call_ctas(const mg_ctx* h, int l) {
+  const int t = (h->lv[l].n + call_tile<T>() - 1) / call_tile<T>();
+  return t * t;
+}
+
+// Whether the device runs the call clusters (the cluster size above 8 is non-portable); checked
+// once per process and kernel variant.
+template <typename T, bool NS>
+bool call_cluster_supported() {
+  static int ok = -1;
+  if (ok < 0) {
+    auto kern = call_cluster_kernel<T, nt_coarse<T>(), call_tile<T>(), NS>;
+    const size_t sm = std::max(call_cluster_smem_tiles<T, call_tile<T>()>(MAX_NU, MAX_NU),
+                               coarse_smem<T>(MAX_COARSE_N, 6));
+    ok = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = CALL_MAX_CTAS;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(CALL_MAX_CTAS);
+      cfg.blockDim = dim3(nt_coarse<T>());
+      cfg.dynamicSmemBytes = sm;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int clusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters >= 1) ok = 1;
+    }
+    cudaGetLastError();  // a refused attribute leaves no sticky error
+  }
+  return ok == 1;
+}
+
+// (lc: the first coarse-kernel level of the cycle in T; -1: the handle's current one)
+template <typename T>
+bool fused_call_ok(const mg_ctx* h, int l, bool adjoint, int lc = -1) {
+  if (lc < 0) lc = lc_of<T>(h);
+  if (!h->fused || adjoint || h->smoother != 0 || h->semi || l < 1 || l + 1 != lc) return false;
+  if (h->nu1 > MAX_NU || h->nu2 > MAX_NU || call_ctas<T>(h, l) > CALL_MAX_CTAS) return false;
+  if (h->nonsym) {
+    if constexpr (std::is_same<T, double>::value) return call_cluster_supported<T, true>();
+    return false;
+  }
+  return call_cluster_supported<T, false>();
+}
+
+template <typename T>
+int emit_call_fused(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero, const int* skip,
+                    cudaStream_t s) {
+  int k1, k2;
+  child_counters(kappa, false, &k1, &k2);
+  const PassAArgs<T> pa = pass_a_args(h, b, l, zero, h->nu1, skip, false, nullptr);
+  const CoarseArgs<T> ca = coarse_args(h, b, k1, k2, 1, false, skip);
+  const PassBArgs<T> pb = pass_b_args(h, b, l, h->nu2, nullptr, skip, false);
+  constexpr int NT = nt_coarse<T>(), TILE = call_tile<T>();
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = call_ctas<T>(h, l);
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(call_ctas<T>(h, l));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = std::max(call_cluster_smem_tiles<T, TILE>(h->nu1, h->nu2), coarse_smem<T>(ca.n_lc, ca.L - ca.lc));
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ++h->launch_count;
+  prof_begin(h, K_CALL, l, s);
+  if constexpr (std::is_same<T, double>::value) {
+    if (h->nonsym) {
+      KC_CUDA(cudaLaunchKernelEx(&cfg, call_cluster_kernel<T, NT, TILE, true>, pa, ca, pb));
+    } else {
+      KC_CUDA(cudaLaunchKernelEx(&cfg, call_cluster_kernel<T, NT, TILE, false>, pa, ca, pb));
+    }
+  } else {
+    KC_CUDA(cudaLaunchKernelEx(&cfg, call_cluster_kernel<T, NT, TILE, false>, pa, ca, pb));
+  }
+  prof_end(h, s);
+  return MG_OK;
+}
+
 template <typename T>
 int emit_call(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero, bool adjoint, bool norm,
               const int* skip, cudaStream_t s) {
+  if (fused_call_ok<T>(h, l, adjoint)) return emit_call_fused(h, b, l, kappa, zero, skip, s);
   const int nu_pre = adjoint ? h->nu2 : h->nu1;
   const int nu_post = adjoint ? h->nu1 : h->nu2;
   const bool lines = h->smoother == 1;
@@ -1256,6 +1372,10 @@ int mg_setup(int n, double eps, double theta, int levels, int nu1, int nu2, mg_h
   if (cudaMemsetAsync(h->scal, 0, sizeof(double) * NSCAL, h->own) != cudaSuccess) return fail(MG_ERR_CUDA);
   if ((st = run_setup_kernels(h)) < 0) return fail(st);
   if ((st = set_all_smem_attrs<double>()) < 0 || (st = set_all_smem_attrs<float>()) < 0) return fail(st);
+  // the cluster support of the fused calls, checked here, outside any stream capture
+  call_cluster_supported<double, false>();
+  call_cluster_supported<double, true>();
+  call_cluster_supported<float, false>();
   h->ok = true;
   *out = h;
   return MG_OK;
@@ -1313,6 +1433,12 @@ int mg_set_option(mg_handle h, int key, double value) {
       drop_graphs(h);
       return MG_OK;
     }
+    case MG_OPT_FUSED_CALL: {
+      if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
+      h->fused = (int)value;
+      drop_graphs(h);
+      return MG_OK;
+    }
     case MG_OPT_COARSENING: {
       if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
       if (value == 1.0 && (h->levels != h->k || h->rediscretized || h->nonsym)) return MG_ERR_ARG;
@@ -1354,6 +1480,7 @@ int mg_get_option(mg_handle h, int key, double* value) {
     case MG_OPT_SMOOTHER: *value = h->smoother; return MG_OK;
     case MG_OPT_COARSENING: *value = h->semi; return MG_OK;
     case MG_OPT_PRECOND: *value = h->precond; return MG_OK;
+    case MG_OPT_FUSED_CALL: *value = h->fused; return MG_OK;
     case MG_OPT_CONV_X: *value = h->bx; return MG_OK;
     case MG_OPT_CONV_Y: *value = h->by; return MG_OK;
     case MG_OPT_LEVELS: *value = h->levels; return MG_OK;
@@ -1660,7 +1787,9 @@ int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* l
         return;
       }
       if (l < h->lc) {
-        if (h->smoother == 0) {
+        if (fused_call_ok<double>(h, l, false)) {
+          // one cluster launch: counted with the coarse-kernel launches below
+        } else if (h->smoother == 0) {
           fine_launches += 2;  // pass A + pass B
         } else {                // line launches (two per relaxation), restriction, folded prolongation
           fine_launches += (h->nu1 > 0 ? 2 * h->nu1 : 0) + 1 + (h->nu2 > 0 ? 2 * h->nu2 : 1);
@@ -1697,6 +1826,10 @@ int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas) {
   }
   if (level >= lc) {
     *ctas = 1;
+    return MG_OK;
+  }
+  if (fp32 ? fused_call_ok<float>(h, level, false, lc) : fused_call_ok<double>(h, level, false, lc)) {
+    *ctas = fp32 ? call_ctas<float>(h, level) : call_ctas<double>(h, level);
     return MG_OK;
   }
   if (fp32 && n >= 2047 && std::max(h->nu1, h->nu2) <= 2) {  // streaming passes (stream_ok)

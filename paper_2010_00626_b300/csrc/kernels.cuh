@@ -17,6 +17,7 @@
 // All level arithmetic is done in T (double on the FP64 path); norms and dot products always
 // accumulate in double.
 #pragma once
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -219,18 +220,18 @@ __host__ __device__ constexpr size_t pass_a_smem(int nu) {
   return size_t(3) * (BX + 2 * (nu + 1) + 1) * (BY + 2 * (nu + 1) + 1) * sizeof(T);
 }
 
-template <typename T, int BX, int BY, int NT, bool NS = false>
-__global__ void __launch_bounds__(NT) pass_a_kernel(const PassAArgs<T> a) {
-  if (a.skip && *a.skip) return;
+// One BX x BY tile of pass A: tile column bx, tile row by; pidx is the tile's slot in a.partial.
+template <typename T, int BX, int BY, int NT, bool NS>
+__device__ __forceinline__ void pass_a_tile(const PassAArgs<T>& a, int bx, int by, int pidx,
+                                            unsigned char* smem_raw) {
   static_assert(BX % 2 == 0 && BY % 2 == 0, "tiles start on even fine indices");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int H = a.nu + 1;
   const int W = BX + 2 * H + 1, Hh = BY + 2 * H + 1;
   T* s0 = reinterpret_cast<T*>(smem_raw);
   T* s1 = s0 + W * Hh;
   T* fs = s1 + W * Hh;
   const int n = a.n;
-  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+  const int x0 = bx * BX, y0 = by * BY;
   const int gx0 = x0 - H, gy0 = y0 - H;
   StencilOp<T, NS> op;
   op.load(a.coef, a.level);
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(NT) pass_a_kernel(const PassAArgs<T> a) {
   if (a.partial) {
     __shared__ double red[NT / 32];
     const double tot = block_sum<NT>(ss, red);
-    if (threadIdx.x == 0) a.partial[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+    if (threadIdx.x == 0) a.partial[pidx] = tot;
   }
 
   // relaxed v on the tile
@@ -303,6 +304,13 @@ __global__ void __launch_bounds__(NT) pass_a_kernel(const PassAArgs<T> a) {
       a.fc[(size_t)J * a.ldc + I] = full_weight(dst, k, W);
     }
   });
+}
+
+template <typename T, int BX, int BY, int NT, bool NS = false>
+__global__ void __launch_bounds__(NT) pass_a_kernel(const PassAArgs<T> a) {
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pass_a_tile<T, BX, BY, NT, NS>(a, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, smem_raw);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -330,15 +338,15 @@ __host__ __device__ constexpr size_t pass_b_smem(int nu, bool norm) {
          size_t(BX / 2 + nu + (norm ? 1 : 0) + 3) * (BY / 2 + nu + (norm ? 1 : 0) + 3) * sizeof(T);
 }
 
-template <typename T, int BX, int BY, int NT, bool NS = false>
-__global__ void __launch_bounds__(NT) pass_b_kernel(const PassBArgs<T> a) {
-  if (a.skip && *a.skip) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// One BX x BY tile of pass B (tile column bx, row by; pidx: the tile's slot in a.partial).
+template <typename T, int BX, int BY, int NT, bool NS>
+__device__ __forceinline__ void pass_b_tile(const PassBArgs<T>& a, int bx, int by, int pidx,
+                                            unsigned char* smem_raw) {
   const int E = a.partial ? 1 : 0;
   const int H = a.nu + E;
   const int W = BX + 2 * H, Hh = BY + 2 * H;
   const int n = a.n, nc = (n - 1) / 2;
-  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+  const int x0 = bx * BX, y0 = by * BY;
   const int gx0 = x0 - H, gy0 = y0 - H;
   // coarse indices that bilinear interpolation reads for fine x in [gx0, gx0 + W)
   const int cx0 = (gx0 >> 1) - 1, cy0 = (gy0 >> 1) - 1;
@@ -408,8 +416,15 @@ __global__ void __launch_bounds__(NT) pass_b_kernel(const PassBArgs<T> a) {
   });
   if (E) {
     const double tot = block_sum<NT>(ss, red);
-    if (threadIdx.x == 0) a.partial[blockIdx.y * gridDim.x + blockIdx.x] = tot;
+    if (threadIdx.x == 0) a.partial[pidx] = tot;
   }
+}
+
+template <typename T, int BX, int BY, int NT, bool NS = false>
+__global__ void __launch_bounds__(NT) pass_b_kernel(const PassBArgs<T> a) {
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pass_b_tile<T, BX, BY, NT, NS>(a, blockIdx.x, blockIdx.y, blockIdx.y * gridDim.x + blockIdx.x, smem_raw);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -532,11 +547,11 @@ __host__ __device__ inline size_t coarse_smem(int n_lc, int nlev) {
   return tot + coarse_line_inverses(n_lc, nlev) * sizeof(double);
 }
 
-template <typename T, int NT, bool LINES, bool NS = false>
-__global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
+// The coarse-level walk, run by one CTA (block index blockIdx.x only in map mode) on the dynamic
+// shared memory at smem_raw.
+template <typename T, int NT, bool LINES, bool NS>
+__device__ __forceinline__ void coarse_body(const CoarseArgs<T>& a, unsigned char* smem_raw) {
   static_assert(!(LINES && NS), "line relaxation is for the symmetric operators");
-  if (a.skip && *a.skip) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ StencilOp<T, NS> cf[MAXL];
   __shared__ int g_side[MAXL], g_off[MAXL + 1], g_magic[MAXL];
   const int nlev = a.L - a.lc;
@@ -875,6 +890,53 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
         a.v[(size_t)j * a.ldv + i] = vv[pos(0, k)];
       }
     }
+  }
+}
+
+template <typename T, int NT, bool LINES, bool NS = false>
+__global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  coarse_body<T, NT, LINES, NS>(a, smem_raw);
+}
+
+// ---------------------------------------------------------------------------------------------
+// One call at the level just above the coarse kernel's, in one launch: a cluster with one CTA per
+// TILE x TILE tile of that level runs pass A, then its CTA of rank 0 walks the coarse calls below
+// it (the coarse kernel's work), then the cluster runs pass B. The two hand-offs go through global
+// memory (the relaxed v and coarse f of pass A, the coarse v of the walk) between cluster barriers,
+// whose release/acquire order makes those writes visible to every CTA of the cluster. Replaces the
+// three launches pass A, coarse kernel, pass B of that call with one; every point's arithmetic is
+// the same, so results equal the three-launch form bit for bit. Launched with a cluster of
+// ceil(n / TILE)^2 CTAs (at most 16, the non-portable cluster size).
+// ---------------------------------------------------------------------------------------------
+constexpr int CALL_MAX_CTAS = 16;
+
+template <typename T, int TILE>
+__host__ __device__ constexpr size_t call_cluster_smem_tiles(int nu1, int nu2) {
+  return pass_a_smem<T, TILE, TILE>(nu1) > pass_b_smem<T, TILE, TILE>(nu2, false)
+             ? pass_a_smem<T, TILE, TILE>(nu1)
+             : pass_b_smem<T, TILE, TILE>(nu2, false);
+}
+
+template <typename T, int NT, int TILE, bool NS = false>
+__global__ void __launch_bounds__(NT)
+    call_cluster_kernel(const PassAArgs<T> pa, const CoarseArgs<T> ca, const PassBArgs<T> pb) {
+  if (pa.skip && *pa.skip) return;  // the same flag for every CTA: the whole cluster returns
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
+  const int rank = (int)cluster.block_rank(), size = (int)cluster.num_blocks();
+  const int tx = (pa.n + TILE - 1) / TILE, ntiles = tx * tx;
+  for (int t = rank; t < ntiles; t += size) {
+    pass_a_tile<T, TILE, TILE, NT, NS>(pa, t % tx, t / tx, 0, smem_raw);
+    __syncthreads();  // the next tile reuses the shared memory
+  }
+  cluster.sync();
+  if (rank == 0) coarse_body<T, NT, false, NS>(ca, smem_raw);
+  cluster.sync();
+  for (int t = rank; t < ntiles; t += size) {
+    pass_b_tile<T, TILE, TILE, NT, NS>(pb, t % tx, t / tx, 0, smem_raw);
+    __syncthreads();
   }
 }
 

@@ -19,7 +19,8 @@ namespace kc {
 
 constexpr int SF_COLS = 120;  // output columns per warp
 constexpr int SF_WARPS = 4;   // warps per CTA (independent strips)
-constexpr int SF_AHEAD = 3;   // input rows loaded ahead of use
+constexpr int SF_AHEAD = 3;   // input rows loaded ahead of use (pass A)
+constexpr int SF_AHEAD_B = 4; // same for pass B (at 4095^2: 115 -> 107 us; pass A got slower at 4)
 
 struct Row6 {  // 4 columns of one row plus the neighbouring column on each side
   float l, v[4], r;
@@ -260,9 +261,9 @@ __global__ void __launch_bounds__(32 * SF_WARPS) pass_b_stream_f32(const PassBAr
     const int y_first = ys - DEPTH - 1;
     const int steps = R + 2 * DEPTH + 2;
     // interpolated coarse rows: cr_lo = coarse row J_lo, cr_hi = J_lo + 1 (x-interpolated)
-    float qv[SF_AHEAD][4], qf[SF_AHEAD][4];
+    float qv[SF_AHEAD_B][4], qf[SF_AHEAD_B][4];
 #pragma unroll
-    for (int r = 0; r < SF_AHEAD; ++r) {
+    for (int r = 0; r < SF_AHEAD_B; ++r) {
       load4(a.vin, a.ldvin, y_first + r, x0, n, qv[r]);
       load4(a.f, a.ldf, y_first + r, x0, n, qf[r]);
     }
@@ -274,12 +275,12 @@ __global__ void __launch_bounds__(32 * SF_WARPS) pass_b_stream_f32(const PassBAr
 #pragma unroll
       for (int k = 0; k < 4; ++k) { cv[k] = qv[0][k]; cf[k] = qf[0][k]; }
 #pragma unroll
-      for (int r = 0; r + 1 < SF_AHEAD; ++r)
+      for (int r = 0; r + 1 < SF_AHEAD_B; ++r)
 #pragma unroll
         for (int k = 0; k < 4; ++k) { qv[r][k] = qv[r + 1][k]; qf[r][k] = qf[r + 1][k]; }
-      if (t + SF_AHEAD < steps) {
-        load4(a.vin, a.ldvin, y_in + SF_AHEAD, x0, n, qv[SF_AHEAD - 1]);
-        load4(a.f, a.ldf, y_in + SF_AHEAD, x0, n, qf[SF_AHEAD - 1]);
+      if (t + SF_AHEAD_B < steps) {
+        load4(a.vin, a.ldvin, y_in + SF_AHEAD_B, x0, n, qv[SF_AHEAD_B - 1]);
+        load4(a.f, a.ldf, y_in + SF_AHEAD_B, x0, n, qf[SF_AHEAD_B - 1]);
       }
       // stage 0: corrected row y_in = v + P v_c (fine odd rows sit on coarse row (y-1)/2; even rows
       // average coarse rows y/2 - 1 and y/2)
