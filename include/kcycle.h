@@ -96,7 +96,9 @@ typedef enum {
                               level just above the coarse-level kernel's runs as one launch of a
                               thread-block cluster (pass A over that level's tiles, the coarse
                               walk on one CTA, pass B), instead of three launches; same results
-                              bit for bit. 0: three launches. Ignored (three launches) where the
+                              bit for bit. 0: three launches (the default for the instances of a
+                              batch, whose concurrent branches need the SMs a cluster would hold
+                              while one of them walks). Ignored (three launches) where the
                               device cannot run the cluster.                                    */
 } mg_option;
 

@@ -8,9 +8,10 @@ Paper form (eq. 3.1, Table 3):  T = alpha * N_gpuCalls + beta * N_ops, with
 alpha and beta come from a least-squares fit over measured per-cycle times (eq. 3.2); the turning
 point n_tp where alpha N_gpuCalls = beta N_ops follows the Appendix's fixed-point iteration.
 
-B300 form: this implementation launches two fused kernels per fine-level call and serves every
-call at or below the coarse threshold inside one persistent kernel, so the per-call overhead
-splits into a launch term and a coarse-call term:
+B300 form: this implementation launches two fused kernels per fine-level call, serves every call
+at or below the coarse threshold inside one persistent kernel, and runs each call at the level just
+above the threshold (not the finest) with its subtree as one cluster launch, so the per-call
+overhead splits into a launch term and a coarse-call term:
   T = alpha_f * N_fine_launches + alpha_c * N_coarse_calls + beta * N_ops.
 kappa pre-selection: argmin_kappa T(kappa) * ceil(log(tol) / log(rho_kappa)), with rho_kappa the
 contraction per cycle estimated from the first cycles' residual history.
@@ -87,11 +88,14 @@ def turning_point(alpha: float, beta: float, kappa: int, nu: int, iters: int = 2
 
 
 # ------------------------------------------------------------------------------------------- B300
-def b300_counts(kappa: int, levels: int, coarse_level: int):
+def b300_counts(kappa: int, levels: int, coarse_level: int, fused: bool = True):
     """(fine launches, coarse calls) of one cycle here: 2 launches per call on levels above the
     coarse threshold (0-based level < coarse_level), every call at or below it inside the coarse
-    kernel."""
-    fine = sum(2 * level_calls(kappa, l + 1) for l in range(min(coarse_level, levels)))
+    kernel; with fused calls, 1 launch per call at 0-based level coarse_level - 1 when that is not
+    level 0 (pass A, the coarse walk and pass B in one cluster launch)."""
+    top = min(coarse_level, levels)
+    fine = sum((1 if fused and l == coarse_level - 1 and l >= 1 else 2) * level_calls(kappa, l + 1)
+               for l in range(top))
     coarse = sum(level_calls(kappa, l + 1) for l in range(coarse_level, levels))
     return fine, coarse
 

@@ -65,9 +65,14 @@ def test_fit_recovers_parameters():
 
 
 def test_b300_counts_and_preselection():
-    fine, coarse = model.b300_counts(4, 12, 8)
+    fine, coarse = model.b300_counts(4, 12, 8, fused=False)
     assert fine == 2 * sum(model.level_calls(4, l) for l in range(1, 9))
     assert coarse == sum(model.level_calls(4, l) for l in range(9, 13))
+    # fused calls: one launch per call at 0-based level 7 (1-based 8), the level above the threshold
+    fine_f, coarse_f = model.b300_counts(4, 12, 8)
+    assert fine_f == fine - model.level_calls(4, 8) and coarse_f == coarse
+    # the level above the threshold is the finest: nothing fused
+    assert model.b300_counts(3, 5, 1) == model.b300_counts(3, 5, 1, fused=False)
     k, table = model.preselect_kappa({1: 1.0, 2: 1.5, 3: 2.0}, {1: 0.99, 2: 0.9, 3: 0.88}, 1e-8)
     assert k == 2 and table[1] > table[2]
     assert model.contraction([1.0, 0.5, 0.25, 0.125]) == pytest.approx(0.5)
