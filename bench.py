@@ -34,7 +34,7 @@ WORKLOAD = "large standalone 4095^2 (12 levels, theta=pi/3, eps=1e-4, FP64)"
 NOMINAL_FP64_TFLOPS = 1.25  # recipe's nominal B300 FP64 rate
 # DRAM bytes (read + write) of one level-0 pass A launch of a solve cycle at 4095^2, from the ncu
 # capture summarised in profiles/pass_a_fp64_4095_L0.md; to be retaken whenever pass_a_kernel changes
-PASS_A_L0_DRAM_BYTES = 268_374_528 + 134_524_672
+PASS_A_L0_DRAM_BYTES = 269_017_856 + 134_404_608
 
 
 def kname(k):

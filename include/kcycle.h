@@ -213,9 +213,10 @@ int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* l
                 long long* coarse_calls);
 
 /* Launch shape of the level passes, for reports of SM occupancy: *n_level = the side of `level`
- * and *ctas = the CTAs of one pass-A or pass-B launch there (both passes use one grid) in the FP64
- * cycle (fp32 = 0) or the FP32 cycle of the mixed forms (fp32 = 1; level 0 assumes caller arrays
- * aligned to 16 bytes, as mg_solve_mixed's own are). For a level handled inside the coarse-level
+ * and *ctas = the CTAs of one pass-A or pass-B launch there that writes no residual sums, in the
+ * FP64 cycle (fp32 = 0) or the FP32 cycle of the mixed forms (fp32 = 1; level 0 assumes caller
+ * arrays aligned to 16 bytes, as mg_solve_mixed's own are). A pass that also writes residual sums
+ * (the level-0 pass A of a stand-alone FP64 solve) uses 64 x 48 tiles where the others use 64 x 32. For a level handled inside the coarse-level
  * kernel *ctas = 1, that kernel's one CTA; for the level whose calls run as one cluster launch
  * (MG_OPT_FUSED_CALL), the cluster's CTAs. Damped-Jacobi smoother with full coarsening only (else
  * MG_ERR_ARG). Host pointers, both required. No device work. */
