@@ -177,11 +177,13 @@ using Tile16 = TileCfg<16, 16, NT_TINY>;
 using Tile8 = TileCfg<8, 8, NT_TINY>;
 
 // FP64 level passes are bound by the FP64 pipe of each SM, so a launch must spread over all SMs:
-// take the largest tile that still gives about two waves of CTAs (tile edge 64, 32, 16 or 8).
+// take the largest tile that still gives about two waves of CTAs at edge 64 and one wave at
+// edges 32 and 16 (measured: the smaller tiles' halo recomputation costs more than the imbalance
+// of a single wave at 511^2 and 255^2).
 int tile_edge(int n) {
   for (int b : {64, 32, 16}) {
     const int g = (n + b - 1) / b;
-    if (g * g >= 2 * 148) return b;
+    if (g * g >= (b == 64 ? 2 : 1) * 148) return b;
   }
   return 8;
 }

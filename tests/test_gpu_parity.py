@@ -230,15 +230,15 @@ def test_counters_match_closed_forms(lib, kappa):
 
 
 def test_level_grid_reports_the_launch_shapes(lib):
-    """CTAs per pass launch at 4095^2: 64x32 tiles at 4095 and 2047, 32^2 at 1023, 16^2 at 511,
-    8^2 below (about two waves per launch), one coarse-kernel CTA at 15^2 and below; the FP32
+    """CTAs per pass launch at 4095^2: 64x32 tiles at 4095 and 2047 (about two waves), 32^2 at 1023
+    and 511, 16^2 at 255, 8^2 below (about one wave), one coarse-kernel CTA at 15^2 and below; the FP32
     streaming passes at 4095 and 2047 (35 and 18 strips of 120 columns, 4 per CTA, chunks of 64 and
     32 rows) and the FP32 coarse kernel from 31^2. The level just above the coarse kernel runs its
     calls as one cluster launch: 16 CTAs of 8^2 tiles at 31^2 (FP64), of 16^2 tiles at 63^2 (FP32);
     without the fused calls 64 CTAs at 63^2 (FP32)."""
     mg = lib.Multigrid(4095, 1e-4, math.pi / 3, 12)
     fp64 = [mg.level_grid(l) for l in range(12)]
-    assert [c for _, c in fp64] == [64 * 128, 32 * 64, 32 * 32, 32 * 32, 32 * 32, 16 * 16, 8 * 8, 4 * 4,
+    assert [c for _, c in fp64] == [64 * 128, 32 * 64, 32 * 32, 16 * 16, 16 * 16, 16 * 16, 8 * 8, 4 * 4,
                                      1, 1, 1, 1]
     assert [m for m, _ in fp64] == [2 ** (12 - l) - 1 for l in range(12)]
     fp32 = [mg.level_grid(l, fp32=True)[1] for l in range(12)]
