@@ -59,6 +59,9 @@ constexpr int NT_VEC = 256;
 constexpr int MAX_NU = 8;
 constexpr int VEC_BLOCKS = 148 * 8;
 constexpr int MAX_COARSE_N = 63;
+constexpr size_t SMEM_CAP = 220 * 1024;  // dynamic shared memory per CTA (227 KB less static use)
+constexpr int MAP_S = 49;       // unknowns of the side-7 level
+constexpr int MAP_CLASSES = 3;  // at most two levels below it: counters 1, 2, >= 3
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
@@ -254,6 +257,13 @@ int set_line_attrs() {
   return MG_OK;
 }
 
+// The largest dynamic shared memory a coarse walk asks for: its levels (up to side MAX_COARSE_N),
+// plus the condensed-call maps where they fit under SMEM_CAP.
+template <typename T>
+size_t coarse_smem_max() {
+  return std::min(SMEM_CAP, coarse_smem<T>(MAX_COARSE_N, 6) + coarse_map_smem<T>(MAP_CLASSES));
+}
+
 template <typename T>
 int set_all_smem_attrs() {
   KC_TRY((set_smem_attrs<Tile64, T>()));
@@ -262,12 +272,12 @@ int set_all_smem_attrs() {
   KC_TRY((set_smem_attrs<Tile16, T>()));
   KC_TRY((set_smem_attrs<Tile8, T>()));
   KC_CUDA(cudaFuncSetAttribute(coarse_kernel<T, nt_coarse<T>(), false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)coarse_smem<T>(MAX_COARSE_N, 6)));
+                               (int)coarse_smem_max<T>()));
   KC_CUDA(cudaFuncSetAttribute(coarse_kernel<T, nt_coarse<T>(), true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)coarse_smem<T>(MAX_COARSE_N, 6)));
+                               (int)coarse_smem_max<T>()));
   if constexpr (std::is_same<T, double>::value) {
     KC_CUDA(cudaFuncSetAttribute(coarse_kernel<T, nt_coarse<T>(), false, true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coarse_smem<T>(MAX_COARSE_N, 6)));
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coarse_smem_max<T>()));
   }
   KC_TRY((set_line_attrs<T, 1>()));
   KC_TRY((set_line_attrs<T, 2>()));
@@ -398,8 +408,6 @@ int map_level(const mg_ctx* h) {
   const int d = h->k - 3;
   return (!h->semi && d >= 0 && d < h->levels - 1) ? d : -1;
 }
-constexpr int MAP_S = 49;       // unknowns of the side-7 level
-constexpr int MAP_CLASSES = 3;  // at most two levels below it: counters 1, 2, >= 3
 
 template <typename T>
 CoarseArgs<T> coarse_args(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int zero1, bool adjoint,
@@ -433,15 +441,32 @@ CoarseArgs<T> coarse_args(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int z
   a.ncls = h->levels - dm;
   a.basis = 0;
   a.cmap_out = nullptr;
+  a.map_smem = 0;
   return a;
+}
+
+// Dynamic shared memory of a coarse walk with these arguments; turns on the shared-memory copy of
+// the condensed-call maps when they fit, for FP32 walks only. Measured at 4095^2: FP32 walks gain
+// (mixed kappa=4 solve 904 -> 888 ms), while copying the FP64 maps (115 KB per launch) costs more
+// than their reads from L2 do (FP64 kappa=4 solve 2,107 -> 2,140 ms).
+template <typename T>
+size_t coarse_walk_smem(const mg_ctx* h, CoarseArgs<T>& a) {
+  (void)h;
+  const size_t base = coarse_smem<T>(a.n_lc, a.L - a.lc);
+  a.map_smem = 0;
+  if (std::is_same<T, float>::value && a.cmap && base + coarse_map_smem<T>(a.ncls) <= coarse_smem_max<T>()) {
+    a.map_smem = 1;
+    return base + coarse_map_smem<T>(a.ncls);
+  }
+  return base;
 }
 
 template <typename T>
 int emit_coarse(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int zero1, bool adjoint, const int* skip,
                 cudaStream_t s) {
   const int lc = lc_of<T>(h);
-  const CoarseArgs<T> a = coarse_args(h, b, k1, k2, zero1, adjoint, skip);
-  const size_t sm = coarse_smem<T>(a.n_lc, a.L - a.lc);
+  CoarseArgs<T> a = coarse_args(h, b, k1, k2, zero1, adjoint, skip);
+  const size_t sm = coarse_walk_smem(h, a);
   prof_begin(h, K_COARSE, lc, s);
   KC_TRY(launch_coarse(h, a, 1, sm, s));
   prof_end(h, s);
@@ -785,8 +810,7 @@ bool call_cluster_supported() {
   static int ok = -1;
   if (ok < 0) {
     auto kern = call_cluster_kernel<T, nt_coarse<T>(), call_tile<T>(), NS>;
-    const size_t sm = std::max(call_cluster_smem_tiles<T, call_tile<T>()>(MAX_NU, MAX_NU),
-                               coarse_smem<T>(MAX_COARSE_N, 6));
+    const size_t sm = std::max(call_cluster_smem_tiles<T, call_tile<T>()>(MAX_NU, MAX_NU), coarse_smem_max<T>());
     ok = 0;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) == cudaSuccess) {
@@ -828,7 +852,8 @@ int emit_call_fused(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero
   int k1, k2;
   child_counters(kappa, false, &k1, &k2);
   const PassAArgs<T> pa = pass_a_args(h, b, l, zero, h->nu1, skip, false, nullptr);
-  const CoarseArgs<T> ca = coarse_args(h, b, k1, k2, 1, false, skip);
+  CoarseArgs<T> ca = coarse_args(h, b, k1, k2, 1, false, skip);
+  const size_t sm_walk = coarse_walk_smem(h, ca);
   const PassBArgs<T> pb = pass_b_args(h, b, l, h->nu2, nullptr, skip, false);
   constexpr int NT = nt_coarse<T>(), TILE = call_tile<T>();
   cudaLaunchConfig_t cfg = {};
@@ -839,7 +864,7 @@ int emit_call_fused(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero
   attr[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3(call_ctas<T>(h, l));
   cfg.blockDim = dim3(NT);
-  cfg.dynamicSmemBytes = std::max(call_cluster_smem_tiles<T, TILE>(h->nu1, h->nu2), coarse_smem<T>(ca.n_lc, ca.L - ca.lc));
+  cfg.dynamicSmemBytes = std::max(call_cluster_smem_tiles<T, TILE>(h->nu1, h->nu2), sm_walk);
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;

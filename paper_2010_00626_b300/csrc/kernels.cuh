@@ -496,6 +496,7 @@ struct CoarseArgs {
   // by columns (entry (k, b) at b * S + k). nullptr: no condensation.
   const T* cmap;
   int dcond, ncls;
+  int map_smem;    // copy the maps into shared memory (after the levels) at the start of the walk
   // basis != 0: map mode. Block b runs one call of counter k1 at the top level from v = e_b
   // (b < S) or f = e_(b-S) and writes the result to cmap_out + b * S.
   int basis;
@@ -549,6 +550,13 @@ __host__ __device__ inline size_t coarse_smem(int n_lc, int nlev) {
 
 // The coarse-level walk, run by one CTA (block index blockIdx.x only in map mode) on the dynamic
 // shared memory at smem_raw.
+// Shared memory for the condensed-call maps (ncls classes of M and N, S = 49 unknowns each), placed
+// after coarse_smem's regions.
+template <typename T>
+__host__ __device__ inline size_t coarse_map_smem(int ncls) {
+  return size_t(ncls) * 2 * 49 * 49 * sizeof(T);
+}
+
 template <typename T, int NT, bool LINES, bool NS>
 __device__ __forceinline__ void coarse_body(const CoarseArgs<T>& a, unsigned char* smem_raw) {
   static_assert(!(LINES && NS), "line relaxation is for the symmetric operators");
@@ -602,6 +610,14 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs<T>& a, unsigned cha
       v0[k] = T(0);
       v1[k] = T(0);
     }
+  }
+  // condensed-call maps: from shared memory when the launch provides room for them
+  const T* cmap = a.cmap;
+  if (a.cmap && a.map_smem && !a.basis) {
+    T* ms = reinterpret_cast<T*>(smem_raw + coarse_smem<T>(a.n_lc, nlev));
+    const int tot = a.ncls * 2 * 49 * 49;
+    for (int e = threadIdx.x; e < tot; e += NT) ms[e] = a.cmap[e];
+    cmap = ms;
   }
   __syncthreads();
 
@@ -829,10 +845,10 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs<T>& a, unsigned cha
         --sp;
         continue;
       }
-      if (a.cmap && fr.d == a.dcond) {  // condensed call: v <- M_c v + N_c f in one pass
+      if (cmap && fr.d == a.dcond) {  // condensed call: v <- M_c v + N_c f in one pass
         const int d = fr.d, s = g_side[d], S = s * s;
         const int cls = (fr.k < a.ncls ? fr.k : a.ncls) - 1;
-        const T* Mt = a.cmap + (size_t)cls * 2 * S * S;
+        const T* Mt = cmap + (size_t)cls * 2 * S * S;
         const T* Nt = Mt + (size_t)S * S;
         const unsigned bsel = (cur >> d) & 1u;
         const T* vsrc = vbuf(d, bsel);
