@@ -557,6 +557,13 @@ __host__ __device__ inline size_t coarse_map_smem(int ncls) {
   return size_t(ncls) * 2 * 49 * 49 * sizeof(T);
 }
 
+// Padded position ((side + 2)^2 buffer with a zero border) of interior point k of a level of the
+// given side; magic = ceil(2^32 / side), so that k / side == umulhi(k, magic) for k < 4096.
+__device__ __forceinline__ int pad_pos(int k, int side, unsigned magic) {
+  const int j = (int)__umulhi((unsigned)k, magic);
+  return (j + 1) * (side + 2) + (k - j * side) + 1;
+}
+
 template <typename T, int NT, bool LINES, bool NS>
 __device__ __forceinline__ void coarse_body(const CoarseArgs<T>& a, unsigned char* smem_raw) {
   static_assert(!(LINES && NS), "line relaxation is for the symmetric operators");
@@ -656,12 +663,15 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs<T>& a, unsigned cha
   // `sweeps` damped-Jacobi sweeps on level d, ping-ponging between its two v buffers; a zero
   // start makes the first sweep v = w f (the update of v = 0)
   auto relax = [&](int d, int sweeps, bool zero) {
+    // level geometry and stencil in registers: the sweeps store to shared memory, which would
+    // otherwise make every point reload them
     const int s = g_side[d], P = s + 2;
+    const unsigned mg = g_magic[d];
     const T* f = fbuf(d);
-    const StencilOp<T, NS>& op = cf[d];
+    const StencilOp<T, NS> op = cf[d];
     if (zero && sweeps == 0) {
       T* v = vcur(d);
-      for (int k = threadIdx.x; k < s * s; k += NT) v[pos(d, k)] = T(0);
+      for (int k = threadIdx.x; k < s * s; k += NT) v[pad_pos(k, s, mg)] = T(0);
       __syncthreads();
       return;
     }
@@ -671,7 +681,7 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs<T>& a, unsigned cha
       T* dst = vbuf(d, b ^ 1u);
       const bool from_zero = zero && it == 0;
       for (int k = threadIdx.x; k < s * s; k += NT) {
-        const int kk = pos(d, k);
+        const int kk = pad_pos(k, s, mg);
         if constexpr (NS) {
           dst[kk] = from_zero ? op.w() * f[kk] : op.jac(src, kk, P, f[kk]);
         } else {
@@ -773,28 +783,31 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs<T>& a, unsigned cha
     const int s = g_side[d], P = s + 2;
     const T* v = vcur(d);
     const T* f = fbuf(d);
-    const StencilOp<T, NS>& op = cf[d];
+    const StencilOp<T, NS> op = cf[d];
+    const unsigned mg = g_magic[d];
     for (int k = threadIdx.x; k < s * s; k += NT) {
-      const int kk = pos(d, k);
+      const int kk = pad_pos(k, s, mg);
       tmp[kk] = op.res(v, kk, P, f[kk]);
     }
     __syncthreads();
     const int sc = g_side[d + 1];
+    const unsigned mgc = g_magic[d + 1];
     T* fc = fbuf(d + 1);
     for (int k = threadIdx.x; k < sc * sc; k += NT) {
-      const int J = (int)__umulhi((unsigned)k, (unsigned)g_magic[d + 1]), I = k - J * sc;
+      const int J = (int)__umulhi((unsigned)k, mgc), I = k - J * sc;
       // coarse (I, J) sits on fine (2I+1, 2J+1), padded position (2J+2, 2I+2)
-      fc[pos(d + 1, k)] = full_weight(tmp, (2 * J + 2) * P + (2 * I + 2), P);
+      fc[(J + 1) * (sc + 2) + I + 1] = full_weight(tmp, (2 * J + 2) * P + (2 * I + 2), P);
     }
     __syncthreads();
   };
   // v_d += P v_{d+1}; the padded coarse index of coarse (I, J) is (J+1)*Pc + I+1
   auto prolong_add = [&](int d) {
     const int s = g_side[d], Pc = g_side[d + 1] + 2;
+    const unsigned mg = g_magic[d];
     T* v = vcur(d);
     const T* vc = vcur(d + 1);
     for (int k = threadIdx.x; k < s * s; k += NT) {
-      const int j = (int)__umulhi((unsigned)k, (unsigned)g_magic[d]), i = k - j * s;
+      const int j = (int)__umulhi((unsigned)k, mg), i = k - j * s;
       const int hx = i >> 1, hy = j >> 1;
       T p;
       const bool xo = i & 1, yo = j & 1;
@@ -822,10 +835,11 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs<T>& a, unsigned cha
       if (threadIdx.x == 0) dst[4] = (T)((double)f[4] / a.coef64[(a.L - 1) * NCOEF + C_C0]);
     } else {
       const int N = s * s;
+      const unsigned mg = g_magic[d];
       for (int r = threadIdx.x; r < N; r += NT) {
         double acc = 0.0;
-        for (int q = 0; q < N; ++q) acc = fma(a.cinv[(size_t)r * N + q], (double)f[pos(d, q)], acc);
-        dst[pos(d, r)] = (T)acc;
+        for (int q = 0; q < N; ++q) acc = fma(a.cinv[(size_t)r * N + q], (double)f[pad_pos(q, s, mg)], acc);
+        dst[pad_pos(r, s, mg)] = (T)acc;
       }
     }
     cur ^= 1u << d;
@@ -847,6 +861,7 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs<T>& a, unsigned cha
       }
       if (cmap && fr.d == a.dcond) {  // condensed call: v <- M_c v + N_c f in one pass
         const int d = fr.d, s = g_side[d], S = s * s;
+        const unsigned mg = g_magic[d];
         const int cls = (fr.k < a.ncls ? fr.k : a.ncls) - 1;
         const T* Mt = cmap + (size_t)cls * 2 * S * S;
         const T* Nt = Mt + (size_t)S * S;
@@ -860,13 +875,13 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs<T>& a, unsigned cha
           T acc0 = T(0), acc1 = T(0);
           if (k < S) {
             if (!fr.zero)
-              for (int b = p; b < S; b += 4) acc0 = fma(Mt[(size_t)b * S + k], vsrc[pos(d, b)], acc0);
-            for (int b = p; b < S; b += 4) acc1 = fma(Nt[(size_t)b * S + k], f[pos(d, b)], acc1);
+              for (int b = p; b < S; b += 4) acc0 = fma(Mt[(size_t)b * S + k], vsrc[pad_pos(b, s, mg)], acc0);
+            for (int b = p; b < S; b += 4) acc1 = fma(Nt[(size_t)b * S + k], f[pad_pos(b, s, mg)], acc1);
           }
           T acc = acc0 + acc1;
           acc += __shfl_xor_sync(0xffffffffu, acc, 1);
           acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-          if (k < S && p == 0) dst[pos(d, k)] = acc;
+          if (k < S && p == 0) dst[pad_pos(k, s, mg)] = acc;
         }
         cur ^= 1u << d;
         __syncthreads();
