@@ -122,3 +122,24 @@ def test_batch_equal_bitwise(lib):
         runs.append((out, [x.clone() for x in xs]))
     assert runs[0][0] == runs[1][0]
     assert all(torch.equal(a, b) for a, b in zip(runs[0][1], runs[1][1]))
+
+
+@pytest.mark.parametrize("nu1,nu2", [(0, 3), (3, 1), (1, 0)])
+def test_fp64_cycles_equal_bitwise_other_sweeps(lib, nu1, nu2):
+    """Pre- or post-smoothing counts other than 2 (including none) through the fused launch."""
+    import torch
+    n, levels = 255, 8
+    on, off = pair(lib, n, 1e-2, 1.2, levels, nu1, nu2)
+    f = dev(rhs_normal(n, 7))
+    v_on, v_off = torch.zeros_like(f), torch.zeros_like(f)
+    for _ in range(2):
+        on.kcycle(v_on, f, 3)
+        off.kcycle(v_off, f, 3)
+        torch.cuda.synchronize()
+        assert torch.equal(v_on, v_off)
+    f32 = dev(rhs_uniform(n, 8), "float32")
+    a, b = torch.zeros_like(f32), torch.zeros_like(f32)
+    on.kcycle_f32(a, f32, 2)
+    off.kcycle_f32(b, f32, 2)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
