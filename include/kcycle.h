@@ -93,13 +93,15 @@ typedef enum {
                               MG_OPT_COARSE_OP = 1 (rediscretized upwind operators) is the stable
                               choice. Recomputes the stencils.                                    */
   MG_OPT_FUSED_CALL = 14   /* 1 (default): with damped Jacobi and full coarsening, each call at the
-                              level just above the coarse-level kernel's runs as one launch of a
-                              thread-block cluster (pass A over that level's tiles, the coarse
-                              walk on one CTA, pass B), instead of three launches; same results
-                              bit for bit. 0: three launches (the default for the instances of a
-                              batch, whose concurrent branches need the SMs a cluster would hold
-                              while one of them walks). Ignored (three launches) where the
-                              device cannot run the cluster.                                    */
+                              level just above the coarse-level kernel's (FP64 and FP32 cycles)
+                              runs as one launch of a thread-block cluster with one CTA per tile
+                              of that level, at most 16 (pass A over the tiles, the coarse walk on
+                              one CTA, pass B), instead of three launches; same results bit for
+                              bit. 0: three launches (the default for the instances of a batch,
+                              whose concurrent branches need the SMs a cluster would hold while
+                              one of them walks). Not applied at level 0, to adjoint cycles, to
+                              levels of more than 16 tiles, or where the device cannot run the
+                              cluster (three launches then).                                    */
 } mg_option;
 
 /* Set up the hierarchy for the Section 4 problem on an n x n interior grid.
