@@ -279,6 +279,12 @@ int set_all_smem_attrs() {
     KC_CUDA(cudaFuncSetAttribute(coarse_kernel<T, nt_coarse<T>(), false, true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)coarse_smem_max<T>()));
   }
+  if constexpr (std::is_same<T, float>::value) {
+    for (auto k : {pass_a_tile32<0>, pass_a_tile32<1>, pass_a_tile32<2>})
+      KC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile32_smem_a()));
+    for (auto k : {pass_b_tile32<0>, pass_b_tile32<1>, pass_b_tile32<2>})
+      KC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile32_smem_b()));
+  }
   KC_TRY((set_line_attrs<T, 1>()));
   KC_TRY((set_line_attrs<T, 2>()));
   KC_TRY((set_line_attrs<T, 4>()));
@@ -360,7 +366,38 @@ bool stream_ok(int n, int nu, const void* p, int ld) {
 }
 int stream_rows(int n) { return n >= 4095 ? 64 : (n >= 2047 ? 32 : 16); }
 
+// FP32 passes at the stream-eligible levels: the shared-memory tile passes below side 4095, the
+// register pipelines from 4095 up. Measured in the FP32 cycle of the 4095^2 mixed solve: at 2047^2
+// the tiles take pass A 39 -> 29 us and pass B 40 -> 32 us (the pipelines' grid gives 9 warps per
+// SM there, the tiles 24); at 4095^2 pass A is equal (83 us) and pass B slower with tiles (136
+// against 107 us), whose loads are not overlapped within a CTA.
+bool f32_tile_passes(int n) { return n < 4095; }
+
+int launch_pass_a_tile32(const PassAArgs<float>& a, cudaStream_t s) {
+  dim3 grid((a.n + T32_TX - 1) / T32_TX, (a.n + T32_TY - 1) / T32_TY);
+  const size_t sm = tile32_smem_a();
+  switch (a.nu) {
+    case 0: pass_a_tile32<0><<<grid, T32_NT, sm, s>>>(a); break;
+    case 1: pass_a_tile32<1><<<grid, T32_NT, sm, s>>>(a); break;
+    default: pass_a_tile32<2><<<grid, T32_NT, sm, s>>>(a); break;
+  }
+  KC_CUDA(cudaGetLastError());
+  return MG_OK;
+}
+int launch_pass_b_tile32(const PassBArgs<float>& a, cudaStream_t s) {
+  dim3 grid((a.n + T32_TX - 1) / T32_TX, (a.n + T32_TY - 1) / T32_TY);
+  const size_t sm = tile32_smem_b();
+  switch (a.nu) {
+    case 0: pass_b_tile32<0><<<grid, T32_NT, sm, s>>>(a); break;
+    case 1: pass_b_tile32<1><<<grid, T32_NT, sm, s>>>(a); break;
+    default: pass_b_tile32<2><<<grid, T32_NT, sm, s>>>(a); break;
+  }
+  KC_CUDA(cudaGetLastError());
+  return MG_OK;
+}
+
 int launch_pass_a_stream(const PassAArgs<float>& a, cudaStream_t s) {
+  if (f32_tile_passes(a.n)) return launch_pass_a_tile32(a, s);
   const int strips = (a.n + SF_COLS - 1) / SF_COLS, R = stream_rows(a.n);
   dim3 grid((strips + SF_WARPS - 1) / SF_WARPS, (a.n + R - 1) / R);
   switch (a.nu) {
@@ -372,6 +409,7 @@ int launch_pass_a_stream(const PassAArgs<float>& a, cudaStream_t s) {
   return MG_OK;
 }
 int launch_pass_b_stream(const PassBArgs<float>& a, cudaStream_t s) {
+  if (f32_tile_passes(a.n)) return launch_pass_b_tile32(a, s);
   const int strips = (a.n + SF_COLS - 1) / SF_COLS, R = stream_rows(a.n);
   dim3 grid((strips + SF_WARPS - 1) / SF_WARPS, (a.n + R - 1) / R);
   switch (a.nu) {
@@ -1867,9 +1905,13 @@ int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas) {
     *ctas = fp32 ? call_ctas<float>(h, level) : call_ctas<double>(h, level);
     return MG_OK;
   }
-  if (fp32 && n >= 2047 && std::max(h->nu1, h->nu2) <= 2) {  // streaming passes (stream_ok)
-    const int strips = (n + SF_COLS - 1) / SF_COLS, R = stream_rows(n);
-    *ctas = ((strips + SF_WARPS - 1) / SF_WARPS) * ((n + R - 1) / R);
+  if (fp32 && n >= 2047 && std::max(h->nu1, h->nu2) <= 2) {  // the stream-eligible levels (stream_ok)
+    if (f32_tile_passes(n)) {
+      *ctas = ((n + T32_TX - 1) / T32_TX) * ((n + T32_TY - 1) / T32_TY);
+    } else {
+      const int strips = (n + SF_COLS - 1) / SF_COLS, R = stream_rows(n);
+      *ctas = ((strips + SF_WARPS - 1) / SF_WARPS) * ((n + R - 1) / R);
+    }
     return MG_OK;
   }
   const int bx = tile_edge(n), by = tile_rows(n, false);
