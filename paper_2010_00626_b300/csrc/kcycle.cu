@@ -361,16 +361,18 @@ void prof_end(mg_ctx* h, cudaStream_t s) {
 }
 
 // FP32 streaming passes: large levels, nu <= 2, 16-byte aligned rows with a pitch multiple of 4.
+constexpr int F32_FAST_MIN = 1023;  // smallest side for the FP32 pipelines or shared-memory tiles
 bool stream_ok(int n, int nu, const void* p, int ld) {
-  return n >= 2047 && nu <= 2 && (p == nullptr || ((uintptr_t)p & 15) == 0) && (ld & 3) == 0;
+  return n >= F32_FAST_MIN && nu <= 2 && (p == nullptr || ((uintptr_t)p & 15) == 0) && (ld & 3) == 0;
 }
 int stream_rows(int n) { return n >= 4095 ? 64 : (n >= 2047 ? 32 : 16); }
 
 // FP32 passes at the stream-eligible levels: the shared-memory tile passes below side 4095, the
 // register pipelines from 4095 up. Measured in the FP32 cycle of the 4095^2 mixed solve: at 2047^2
 // the tiles take pass A 39 -> 29 us and pass B 40 -> 32 us (the pipelines' grid gives 9 warps per
-// SM there, the tiles 24); at 4095^2 pass A is equal (83 us) and pass B slower with tiles (136
-// against 107 us), whose loads are not overlapped within a CTA.
+// SM there, the tiles 24), at 1023^2 17 -> 14 and 18 -> 15 us against the generic tiles; at
+// 4095^2 pass A is equal (83 us) and pass B slower with tiles (136 against 107 us), whose loads are
+// not overlapped within a CTA.
 bool f32_tile_passes(int n) { return n < 4095; }
 
 int launch_pass_a_tile32(const PassAArgs<float>& a, cudaStream_t s) {
@@ -1905,7 +1907,7 @@ int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas) {
     *ctas = fp32 ? call_ctas<float>(h, level) : call_ctas<double>(h, level);
     return MG_OK;
   }
-  if (fp32 && n >= 2047 && std::max(h->nu1, h->nu2) <= 2) {  // the stream-eligible levels (stream_ok)
+  if (fp32 && n >= F32_FAST_MIN && std::max(h->nu1, h->nu2) <= 2) {  // the stream-eligible levels (stream_ok)
     if (f32_tile_passes(n)) {
       *ctas = ((n + T32_TX - 1) / T32_TX) * ((n + T32_TY - 1) / T32_TY);
     } else {
