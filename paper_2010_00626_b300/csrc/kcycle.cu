@@ -367,13 +367,14 @@ bool stream_ok(int n, int nu, const void* p, int ld) {
 }
 int stream_rows(int n) { return n >= 4095 ? 64 : (n >= 2047 ? 32 : 16); }
 
-// FP32 passes at the stream-eligible levels: the shared-memory tile passes below side 4095, the
-// register pipelines from 4095 up. Measured in the FP32 cycle of the 4095^2 mixed solve: at 2047^2
-// the tiles take pass A 39 -> 29 us and pass B 40 -> 32 us (the pipelines' grid gives 9 warps per
-// SM there, the tiles 24), at 1023^2 17 -> 14 and 18 -> 15 us against the generic tiles; at
-// 4095^2 pass A is equal (83 us) and pass B slower with tiles (136 against 107 us), whose loads are
-// not overlapped within a CTA.
-bool f32_tile_passes(int n) { return n < 4095; }
+// FP32 passes at the stream-eligible levels: the shared-memory tile passes (112 x 16 outputs per
+// CTA) for pass A, and for pass B below side 4095; the register pipelines for pass B from 4095 up.
+// Measured in the FP32 cycle of the 4095^2 mixed solve: at 4095^2 pass A 83 -> 76 us with tiles,
+// pass B 107 us with the pipelines against 114 with tiles (whose loads are not overlapped within a
+// CTA); at 2047^2 pass A 39 -> 28 us and pass B 40 -> 32 us (the pipelines' grid gives 9 warps per
+// SM there); at 1023^2 17 -> 13 and 18 -> 14 us against the generic tiles.
+bool f32_tile_pass_a(int n) { return n >= 0; }
+bool f32_tile_pass_b(int n) { return n < 4095; }
 
 int launch_pass_a_tile32(const PassAArgs<float>& a, cudaStream_t s) {
   dim3 grid((a.n + T32_TX - 1) / T32_TX, (a.n + T32_TY - 1) / T32_TY);
@@ -399,7 +400,7 @@ int launch_pass_b_tile32(const PassBArgs<float>& a, cudaStream_t s) {
 }
 
 int launch_pass_a_stream(const PassAArgs<float>& a, cudaStream_t s) {
-  if (f32_tile_passes(a.n)) return launch_pass_a_tile32(a, s);
+  if (f32_tile_pass_a(a.n)) return launch_pass_a_tile32(a, s);
   const int strips = (a.n + SF_COLS - 1) / SF_COLS, R = stream_rows(a.n);
   dim3 grid((strips + SF_WARPS - 1) / SF_WARPS, (a.n + R - 1) / R);
   switch (a.nu) {
@@ -411,7 +412,7 @@ int launch_pass_a_stream(const PassAArgs<float>& a, cudaStream_t s) {
   return MG_OK;
 }
 int launch_pass_b_stream(const PassBArgs<float>& a, cudaStream_t s) {
-  if (f32_tile_passes(a.n)) return launch_pass_b_tile32(a, s);
+  if (f32_tile_pass_b(a.n)) return launch_pass_b_tile32(a, s);
   const int strips = (a.n + SF_COLS - 1) / SF_COLS, R = stream_rows(a.n);
   dim3 grid((strips + SF_WARPS - 1) / SF_WARPS, (a.n + R - 1) / R);
   switch (a.nu) {
@@ -1908,7 +1909,7 @@ int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas) {
     return MG_OK;
   }
   if (fp32 && n >= F32_FAST_MIN && std::max(h->nu1, h->nu2) <= 2) {  // the stream-eligible levels (stream_ok)
-    if (f32_tile_passes(n)) {
+    if (f32_tile_pass_b(n)) {  // (pass A always runs as tiles; pass B shown)
       *ctas = ((n + T32_TX - 1) / T32_TX) * ((n + T32_TY - 1) / T32_TY);
     } else {
       const int strips = (n + SF_COLS - 1) / SF_COLS, R = stream_rows(n);

@@ -365,8 +365,8 @@ namespace kc {
 
 // ---------------------------------------------------------------------------------------------
 // FP32 tile passes staged in shared memory (the large FP32 levels). A CTA owns a TX x TY tile of
-// outputs (TX = 112, TY = 32) and stages the tile with a halo of 8 columns and 4 rows on each side:
-// 128 x 40 floats per field, loaded with float4 (zeros outside the grid). A stage (a sweep, the
+// outputs (TX = 112, TY = 16) and stages the tile with a halo of 8 columns and 4 rows on each side:
+// 128 x 24 floats per field, loaded with float4 (zeros outside the grid). A stage (a sweep, the
 // residual) is computed row by row, one warp per row: lane q owns the four columns 4q..4q+3, keeps
 // the rows above and below in registers as the warp walks down its band of rows, and gets its
 // left and right neighbours from the adjacent lanes. Points near the staged border are computed
@@ -374,7 +374,7 @@ namespace kc {
 // Points outside the grid are reset to zero only in tiles that touch its edge. About half the
 // instructions per point of the register pipelines (which keep every stage's rows in registers).
 // ---------------------------------------------------------------------------------------------
-constexpr int T32_TX = 112, T32_TY = 32;       // outputs per tile
+constexpr int T32_TX = 112, T32_TY = 16;       // outputs per tile (16 rows: five CTAs per SM)
 constexpr int T32_P = 128, T32_R = T32_TY + 8;  // staged row pitch (floats) and rows
 constexpr int T32_HX = 8, T32_HY = 4;           // staged halo: columns, rows
 constexpr int T32_NT = 256;                     // 8 warps
