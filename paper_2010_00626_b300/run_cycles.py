@@ -2,6 +2,7 @@
 
     python -m paper_2010_00626_b300.run_cycles --n 4095 --levels 12 --kappa 4 --cycles 1 \
         [--smoother zebra] [--coarsening y] [--theta 1.0471975511965976] [--eps 1e-4] [--fp32] [--solve]
+        [--mixed]
 
 The right-hand side is f ~ N(0, 1) (seed 0) and the start v = 0. With --fp32 the cycles are the
 FP32 cycles of the mixed forms (mg_kcycle_f32). Prints one JSON line with the wall time; the
@@ -24,6 +25,9 @@ def main():
     ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "zebra", "xzebra"])
     ap.add_argument("--coarsening", default="full", choices=["full", "y"])
     ap.add_argument("--fp32", action="store_true")
+    ap.add_argument("--mixed", action="store_true", help="run the FP32 cycle of the mixed solve launch by launch on "
+                                                          "the handle's own FP32 arrays (16-byte pitches), as "
+                                                          "mg_profile_cycle does")
     ap.add_argument("--solve", action="store_true", help="run the launches of stand-alone solve cycles (with the "
                                                          "stopping test's norm) one by one, as mg_profile_cycle "
                                                          "does, instead of bare cycles (a solve's own graph has "
@@ -47,7 +51,9 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.cycles if args.solve else 0):
         mg.profile_cycle(v, f, args.kappa, with_norm=True)
-    for _ in range(0 if args.solve else args.cycles):
+    for _ in range(args.cycles if args.mixed else 0):
+        mg.profile_cycle(v, f, args.kappa, fp32=True)
+    for _ in range(0 if (args.solve or args.mixed) else args.cycles):
         if args.fp32:
             mg.kcycle_f32(v, f, args.kappa)
         else:
@@ -55,7 +61,7 @@ def main():
     torch.cuda.synchronize()
     print(json.dumps({"n": n, "levels": levels, "kappa": args.kappa, "cycles": args.cycles,
                       "smoother": args.smoother, "coarsening": args.coarsening, "fp32": args.fp32,
-                      "solve": args.solve,
+                      "solve": args.solve, "mixed": args.mixed,
                       "wall_ms": 1e3 * (time.perf_counter() - t0)}))
 
 
