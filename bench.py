@@ -153,6 +153,18 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks_of(x, world, device):
+    """The largest x over the ranks of the default process group (NCCL with device "cuda", gloo with
+    "cpu"): a replicated run reports its slowest rank's step time."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ------------------------------------------------------------------------------------ GPU arm
 def dp_ops_per_point(kind, nu, norm):
     """FP64 operations per fine point the method needs in one launch (no halo recomputation):
@@ -329,11 +341,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(x, world, "cuda")
 
     from paper_2010_00626_b300 import build
     build.build()
