@@ -360,20 +360,21 @@ void prof_end(mg_ctx* h, cudaStream_t s) {
   h->pev.push_back(e);
 }
 
-// FP32 streaming passes: large levels, nu <= 2, 16-byte aligned rows with a pitch multiple of 4.
+// FP32 fast passes (register pipeline, shared-memory tiles): large levels, nu <= 2, 16-byte
+// aligned rows with a pitch multiple of 4.
 constexpr int F32_FAST_MIN = 1023;  // smallest side for the FP32 pipelines or shared-memory tiles
-bool stream_ok(int n, int nu, const void* p, int ld) {
+bool fast32_ok(int n, int nu, const void* p, int ld) {
   return n >= F32_FAST_MIN && nu <= 2 && (p == nullptr || ((uintptr_t)p & 15) == 0) && (ld & 3) == 0;
 }
 int stream_rows(int n) { return n >= 4095 ? 64 : (n >= 2047 ? 32 : 16); }
 
-// FP32 passes at the stream-eligible levels: the shared-memory tile passes (112 x 16 outputs per
-// CTA) for pass A, and for pass B below side 4095; the register pipelines for pass B from 4095 up.
-// Measured in the FP32 cycle of the 4095^2 mixed solve: at 4095^2 pass A 83 -> 76 us with tiles,
-// pass B 107 us with the pipelines against 114 with tiles (whose loads are not overlapped within a
-// CTA); at 2047^2 pass A 39 -> 28 us and pass B 40 -> 32 us (the pipelines' grid gives 9 warps per
-// SM there); at 1023^2 17 -> 13 and 18 -> 14 us against the generic tiles.
-bool f32_tile_pass_a(int n) { return n >= 0; }
+// FP32 passes at the fast-eligible levels: the shared-memory tile passes (112 x 16 outputs per
+// CTA) for pass A, and for pass B below side 4095; the register pipeline for pass B from 4095 up.
+// Measured in the FP32 cycle of the 4095^2 mixed solve: at 4095^2 pass A 83 -> 76 us with tiles
+// (against the register pipeline it replaced), pass B 107 us with the pipeline against 114 with
+// tiles (whose loads are not overlapped within a CTA); at 2047^2 pass A 39 -> 28 us and pass B 40
+// -> 32 us (the pipelines' grid gives 9 warps per SM there); at 1023^2 17 -> 13 and 18 -> 14 us
+// against the generic tiles.
 bool f32_tile_pass_b(int n) { return n < 4095; }
 
 int launch_pass_a_tile32(const PassAArgs<float>& a, cudaStream_t s) {
@@ -399,19 +400,7 @@ int launch_pass_b_tile32(const PassBArgs<float>& a, cudaStream_t s) {
   return MG_OK;
 }
 
-int launch_pass_a_stream(const PassAArgs<float>& a, cudaStream_t s) {
-  if (f32_tile_pass_a(a.n)) return launch_pass_a_tile32(a, s);
-  const int strips = (a.n + SF_COLS - 1) / SF_COLS, R = stream_rows(a.n);
-  dim3 grid((strips + SF_WARPS - 1) / SF_WARPS, (a.n + R - 1) / R);
-  switch (a.nu) {
-    case 0: pass_a_stream_f32<0><<<grid, 32 * SF_WARPS, 0, s>>>(a, R); break;
-    case 1: pass_a_stream_f32<1><<<grid, 32 * SF_WARPS, 0, s>>>(a, R); break;
-    default: pass_a_stream_f32<2><<<grid, 32 * SF_WARPS, 0, s>>>(a, R); break;
-  }
-  KC_CUDA(cudaGetLastError());
-  return MG_OK;
-}
-int launch_pass_b_stream(const PassBArgs<float>& a, cudaStream_t s) {
+int launch_pass_b_fast32(const PassBArgs<float>& a, cudaStream_t s) {
   if (f32_tile_pass_b(a.n)) return launch_pass_b_tile32(a, s);
   const int strips = (a.n + SF_COLS - 1) / SF_COLS, R = stream_rows(a.n);
   dim3 grid((strips + SF_WARPS - 1) / SF_WARPS, (a.n + R - 1) / R);
@@ -592,10 +581,10 @@ int emit_pass_a(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const
   prof_begin(h, K_PASS_A, l, s);
   int st;
   if constexpr (std::is_same<T, float>::value) {
-    if (!lines && stream_ok(a.n, nu, a.vin, a.ldvin) && stream_ok(a.n, nu, a.f, a.ldf) &&
-        stream_ok(a.n, nu, a.vout, a.ldvout) &&
+    if (!lines && fast32_ok(a.n, nu, a.vin, a.ldvin) && fast32_ok(a.n, nu, a.f, a.ldf) &&
+        fast32_ok(a.n, nu, a.vout, a.ldvout) &&
         ((uintptr_t)a.fc & 7) == 0 && (a.ldc & 1) == 0) {
-      st = launch_pass_a_stream(a, s);
+      st = launch_pass_a_tile32(a, s);
       prof_end(h, s);
       return st;
     }
@@ -640,9 +629,9 @@ int emit_pass_b(mg_ctx* h, const BindingT<T>& b, int l, int nu, double* partial,
   prof_begin(h, K_PASS_B, l, s);
   int st;
   if constexpr (std::is_same<T, float>::value) {
-    if (!lines && partial == nullptr && stream_ok(a.n, nu, a.vin, a.ldvin) && stream_ok(a.n, nu, a.f, a.ldf) &&
-        stream_ok(a.n, nu, a.vout, a.ldvout) && ((uintptr_t)a.vc & 7) == 0 && (a.ldc & 1) == 0) {
-      st = launch_pass_b_stream(a, s);
+    if (!lines && partial == nullptr && fast32_ok(a.n, nu, a.vin, a.ldvin) && fast32_ok(a.n, nu, a.f, a.ldf) &&
+        fast32_ok(a.n, nu, a.vout, a.ldvout) && ((uintptr_t)a.vc & 7) == 0 && (a.ldc & 1) == 0) {
+      st = launch_pass_b_fast32(a, s);
       prof_end(h, s);
       return st;
     }
@@ -1908,8 +1897,8 @@ int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas) {
     *ctas = fp32 ? call_ctas<float>(h, level) : call_ctas<double>(h, level);
     return MG_OK;
   }
-  if (fp32 && n >= F32_FAST_MIN && std::max(h->nu1, h->nu2) <= 2) {  // the stream-eligible levels (stream_ok)
-    if (f32_tile_pass_b(n)) {  // (pass A always runs as tiles; pass B shown)
+  if (fp32 && n >= F32_FAST_MIN && std::max(h->nu1, h->nu2) <= 2) {  // the fast-eligible levels (fast32_ok)
+    if (f32_tile_pass_b(n)) {  // (pass A always runs as tiles; pass B's shape shown)
       *ctas = ((n + T32_TX - 1) / T32_TX) * ((n + T32_TY - 1) / T32_TY);
     } else {
       const int strips = (n + SF_COLS - 1) / SF_COLS, R = stream_rows(n);

@@ -1,11 +1,12 @@
-// FP32 fused level passes for the large levels of the FP32 cycle of the mixed forms: register
-// pipelines (from side 4095) and shared-memory tiles (below; at the end of this file).
+// FP32 fused level passes for the large levels of the FP32 cycle of the mixed forms: pass B as a
+// register pipeline from side 4095, pass A (all large levels) and pass B below 4095 as
+// shared-memory tiles (at the end of this file).
 //
 // FP32 level passes are bound by HBM bandwidth and instruction issue, not by arithmetic: the
-// generic shared-memory tile kernels spend their issue slots on index arithmetic and barriers. Here one
-// warp owns a vertical strip of 128 columns (4 consecutive columns per lane, read with float4 loads)
-// and streams down a chunk of rows. Every stage of the pass (Jacobi sweeps, residual, full
-// weighting; or interpolation + sweeps) keeps a window of three rows in registers and gets the
+// generic shared-memory tile kernels spend their issue slots on index arithmetic and barriers. In
+// the register pipeline one warp owns a vertical strip of 128 columns (4 consecutive columns per
+// lane, read with float4 loads) and streams down a chunk of rows. Every stage of the pass
+// (interpolation, Jacobi sweeps) keeps a window of three rows in registers and gets the
 // column to the left and right of its 4 columns from the neighbouring lanes by warp shuffles. No
 // shared memory, no barriers; the next input row is loaded while the current one is processed.
 // Each stage loses one column per side, so a strip yields 120 output columns; rows of neighbouring
@@ -20,8 +21,7 @@ namespace kc {
 
 constexpr int SF_COLS = 120;  // output columns per warp
 constexpr int SF_WARPS = 4;   // warps per CTA (independent strips)
-constexpr int SF_AHEAD = 3;   // input rows loaded ahead of use (pass A)
-constexpr int SF_AHEAD_B = 4; // same for pass B (at 4095^2: 115 -> 107 us; pass A got slower at 4)
+constexpr int SF_AHEAD_B = 4; // input rows loaded ahead of use (at 4095^2: 115 -> 107 us against 3)
 
 struct Row6 {  // 4 columns of one row plus the neighbouring column on each side
   float l, v[4], r;
@@ -65,140 +65,6 @@ __device__ __forceinline__ void load4(const float* base, int ld, int y, int x0, 
   } else {
 #pragma unroll
     for (int k = 0; k < 4; ++k) out[k] = 0.f;
-  }
-}
-
-// ---------------------------------------------------------------------------------------------
-// Pass A: nu Jacobi sweeps (nu <= 2), residual, full weighting. One warp: output columns
-// [xs, xs+120) of rows [ys, ys+R).
-// ---------------------------------------------------------------------------------------------
-template <int NU>
-__global__ void __launch_bounds__(32 * SF_WARPS) pass_a_stream_f32(const PassAArgs<float> a, int R) {
-  if (a.skip && *a.skip) return;
-  const int lane = threadIdx.x & 31;
-  const int strip = blockIdx.x * SF_WARPS + (threadIdx.x >> 5);
-  const int n = a.n, nc = (n - 1) / 2;
-  const int xs = strip * SF_COLS;
-  if (xs >= n) return;  // uniform per warp
-  const int ys = blockIdx.y * R;
-  const int x0 = xs - 4 + 4 * lane;
-  const Coef<float> c = load_coef(a.coef, a.level);
-  const bool out_lane = lane >= 1 && lane <= 30;  // owns output columns x0..x0+3
-  bool colin[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) colin[k] = (unsigned)(x0 + k) < (unsigned)n;
-
-  // stage windows (south, middle, north) and delayed right-hand sides
-  constexpr int DEPTH = NU + 1;            // stages before the restriction: NU sweeps + residual
-  Row6 w[DEPTH + 1][3];                    // w[0]: input rows; w[s]: output rows of stage s
-  float fdel[DEPTH + 1][4];                // fdel[d]: f of input row y_in - d
-#pragma unroll
-  for (int s = 0; s <= DEPTH; ++s)
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-      w[s][r].l = w[s][r].r = 0.f;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) w[s][r].v[k] = 0.f;
-    }
-#pragma unroll
-  for (int d = 0; d <= DEPTH; ++d)
-#pragma unroll
-    for (int k = 0; k < 4; ++k) fdel[d][k] = 0.f;
-
-  // residual rows kept for the restriction (vertical weights need rows yr-2, yr-1, yr)
-  float rres[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-  const int y_first = ys - DEPTH - 1;  // first input row
-  const int steps = R + 2 * DEPTH + 2;
-  // input rows are loaded SF_AHEAD rows ahead of use (bytes in flight hide HBM latency)
-  float qv[SF_AHEAD][4], qf[SF_AHEAD][4];
-#pragma unroll
-  for (int r = 0; r < SF_AHEAD; ++r) {
-    load4(a.vin, a.ldvin, y_first + r, x0, n, qv[r]);
-    load4(a.f, a.ldf, y_first + r, x0, n, qf[r]);
-  }
-  // unrolled by the period of the register windows (3) so their shifts become register renames
-#pragma unroll 3
-  for (int t = 0; t < steps; ++t) {
-    const int y_in = y_first + t;
-    float cv[4], cf[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) { cv[k] = qv[0][k]; cf[k] = qf[0][k]; }
-#pragma unroll
-    for (int r = 0; r + 1 < SF_AHEAD; ++r)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) { qv[r][k] = qv[r + 1][k]; qf[r][k] = qf[r + 1][k]; }
-    if (t + SF_AHEAD < steps) {
-      load4(a.vin, a.ldvin, y_in + SF_AHEAD, x0, n, qv[SF_AHEAD - 1]);
-      load4(a.f, a.ldf, y_in + SF_AHEAD, x0, n, qf[SF_AHEAD - 1]);
-    }
-    // input window and f delay line
-    w[0][0] = w[0][1];
-    w[0][1] = w[0][2];
-    w[0][2] = with_halo(cv);
-#pragma unroll
-    for (int d = DEPTH; d > 0; --d)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) fdel[d][k] = fdel[d - 1][k];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) fdel[0][k] = cf[k];
-    // stages: stage s produces row y_in - s from the window of stage s-1 (rows y_in-s-1 .. y_in-s+1)
-#pragma unroll
-    for (int s = 1; s <= DEPTH; ++s) {
-      const int ys_out = y_in - s;
-      const bool row_in = (unsigned)ys_out < (unsigned)n;
-      float o[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const Nb<float> nb = nb6(w[s - 1][0], w[s - 1][1], w[s - 1][2], k);
-        const float v = s <= NU ? jacobi_update(nb, fdel[s][k], c) : residual_at(nb, fdel[s][k], c);
-        o[k] = (row_in && colin[k]) ? v : 0.f;
-      }
-      w[s][0] = w[s][1];
-      w[s][1] = w[s][2];
-      w[s][2] = with_halo(o);
-    }
-    // relaxed v: output row y_in - NU (the last sweep)
-    {
-      const int yv = y_in - NU;
-      if (out_lane && yv >= ys && yv < ys + R && yv < n && x0 < n) {
-        const Row6& o = w[NU][2];
-        float* p = a.vout + (size_t)yv * a.ldvout + x0;
-        if (x0 + 3 < n) {
-          *reinterpret_cast<float4*>(p) = make_float4(o.v[0], o.v[1], o.v[2], o.v[3]);
-        } else {
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            if (colin[k]) p[k] = o.v[k];
-        }
-      }
-    }
-    // restriction: the residual row just produced is yr = y_in - DEPTH; coarse row J sits on fine
-    // row 2J+1 = yr - 1 and weighs residual rows yr-2, yr-1, yr by 1, 2, 1
-    {
-      const int yr = y_in - DEPTH;
-      const Row6& rn = w[DEPTH][2];
-      const int yc = yr - 1;
-      if ((yc & 1) && yc >= ys && yc < ys + R && yc < n) {
-        float vs[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) vs[k] = rres[0][k] + 2.f * rres[1][k] + rn.v[k];
-        const float right = __shfl_down_sync(0xffffffffu, vs[0], 1);
-        // this lane's odd columns x0+1 and x0+3 are coarse points (x0 is a multiple of 4)
-        const float c1 = 0.0625f * (vs[0] + 2.f * vs[1] + vs[2]);
-        const float c3 = 0.0625f * (vs[2] + 2.f * vs[3] + right);
-        const int J = (yc - 1) >> 1, I = x0 >> 1;
-        if (out_lane && J < nc && I < nc) {
-          float* q = a.fc + (size_t)J * a.ldc + I;
-          if (I + 1 < nc) *reinterpret_cast<float2*>(q) = make_float2(c1, c3);
-          else q[0] = c1;
-        }
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        rres[0][k] = rres[1][k];
-        rres[1][k] = rn.v[k];
-      }
-    }
   }
 }
 
