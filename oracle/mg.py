@@ -13,7 +13,7 @@ Grid convention used by every function here:
 A stencil is a 3x3 array ``st`` with ``st[1+dy, 1+dx]`` the coefficient that multiplies
 v(i+dx, j+dy) in (A v)(i, j).
 
-Readings of the paper taken here (each also listed in the design doc):
+Readings of the paper taken here:
   * The operator is A = S / h^2 with S the printed table (the table omits h^2).
   * The top row of the printed table is north (j+1); then the corner entries are
     NW = SE = +(1-eps)CS/2 and NE = SW = -(1-eps)CS/2, which is the standard
