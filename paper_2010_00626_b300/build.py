@@ -6,6 +6,7 @@ The library is written next to this file so that it travels with the source tree
 """
 from __future__ import annotations
 
+import glob
 import os
 import subprocess
 import sys
@@ -14,7 +15,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libkcycle.so")
 SOURCES = [os.path.join(HERE, "csrc", "kcycle.cu")]
-DEPS = SOURCES + [os.path.join(HERE, "csrc", "kernels.cuh"), os.path.join(ROOT, "include", "kcycle.h")]
+
+
+def deps():
+    """Every file the library is built from: all sources and headers under csrc/ and include/
+    (a glob, so that a new header can never be left out of the staleness check)."""
+    pats = [os.path.join(HERE, "csrc", "*.cu"), os.path.join(HERE, "csrc", "*.cuh"),
+            os.path.join(HERE, "csrc", "*.h"), os.path.join(ROOT, "include", "*.h")]
+    return sorted({p for pat in pats for p in glob.glob(pat)} | set(SOURCES))
 
 
 def nvcc_command(out: str = LIB, extra=()):
@@ -28,7 +36,7 @@ def up_to_date() -> bool:
     if not os.path.exists(LIB):
         return False
     t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(p) <= t for p in DEPS)
+    return all(os.path.getmtime(p) <= t for p in deps())
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
