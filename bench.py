@@ -31,10 +31,59 @@ from paper_2010_00626_b300.inputs import KAPPA_W, LARGE, rhs_normal  # noqa: E40
 
 METRIC = "ms to 1e-8 rel. residual per kappa (FP64 vs mixed/batched) and % of HBM peak"
 WORKLOAD = "large standalone 4095^2 (12 levels, theta=pi/3, eps=1e-4, FP64)"
-NOMINAL_FP64_TFLOPS = 1.25  # recipe's nominal B300 FP64 rate
-# DRAM bytes (read + write) of one level-0 pass A launch of a solve cycle at 4095^2, from the ncu
-# capture summarised in profiles/pass_a_fp64_4095_L0.md; to be retaken whenever pass_a_kernel changes
-PASS_A_L0_DRAM_BYTES = 269_017_856 + 134_404_608
+NOMINAL_FP64_TFLOPS = 1.25  # nominal B300 FP64 rate
+# Measured DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture) of one level-0
+# pass A launch of a solve cycle at 4095^2, keyed by the SHA-256 of the kernel source it was taken
+# on (kernels.cuh from its start to the pass B section: the shared helpers and pass A): when that
+# text changes the figure no longer describes the kernel and is reported as null until a new
+# capture replaces it.
+PASS_A_L0_TRAFFIC = {"source": "paper_2010_00626_b300/csrc/kernels.cuh", "until": "// Pass B: v <- v + P v_c",
+                     "sha256": "046e620f3f62b3a7b5f3e8be612719cd8261797e0b1bf25f90a78dbcaa590516",
+                     "bytes": 269_017_856 + 134_404_608}
+
+
+def source_digest(entry):
+    """SHA-256 of the kernel source text an entry's figure was measured on."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, entry["source"])) as fh:
+            text = fh.read()
+    except OSError:
+        return None
+    end = text.find(entry["until"]) if entry.get("until") else -1
+    return hashlib.sha256((text[:end] if end >= 0 else text).encode()).hexdigest()
+
+
+def measured_traffic(entry):
+    """The stored DRAM bytes of `entry` if its kernel source is unchanged since the capture, else None."""
+    if not entry.get("sha256"):
+        return None
+    return entry["bytes"] if source_digest(entry) == entry["sha256"] else None
+
+
+def host_cpu():
+    """CPU model and logical core count of the host the oracle runs on."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count()}
+
+
+def bench_config(kappa, world=1):
+    """The workload description both arms print (the same keys and values)."""
+    cfg = LARGE
+    out = {"workload": WORKLOAD, "n": cfg["n"], "levels": cfg["levels"], "theta": cfg["theta"], "eps": cfg["eps"],
+           "kappa": kname(kappa), "tol": 1e-8, "nu1": cfg["nu1"], "nu2": cfg["nu2"], "omega": cfg["omega"],
+           "l2": "inputs larger than L2 (each 4095^2 FP64 array is 134 MB)"}
+    if world > 1:
+        out["parallelism"] = f"replicas x{world}"
+    return out
 
 
 def kname(k):
@@ -120,6 +169,49 @@ def time_oracle_cycles(kappa, ncycles):
     return 1e3 * (time.perf_counter() - t0) / ncycles
 
 
+def _oracle_replica(kappa, seed, barrier, out):
+    """One oracle cycle on its own 4095^2 problem, started together with the other replicas."""
+    import oracle
+    cfg = LARGE
+    h = oracle.Hierarchy(cfg["n"], cfg["levels"], cfg["theta"], cfg["eps"])
+    f = rhs_normal(cfg["n"], seed)
+    v = np.zeros_like(f)
+    barrier.wait()
+    t0 = time.perf_counter()
+    oracle.cycle(h, v, f, kappa)
+    out.put(1e3 * (time.perf_counter() - t0))
+
+
+def oracle_all_cores(kappa, cycles):
+    """The oracle on every host core at once. It is single-threaded (numpy stencil operations),
+    so one problem cannot use more than one core; the host's cores are used by as many independent
+    replicas (one process each, spawned, each on its own f) as there are cores, bounded by memory
+    (about 2 GB per replica at 4095^2). Each replica times one kappa-cycle; reported: the median
+    per-replica ms to 1e-8 (ms per cycle x cycles) and the host's throughput in problems per hour."""
+    import multiprocessing as mp
+    nproc = os.cpu_count() or 1
+    try:
+        import psutil
+        mem_cap = max(1, int(psutil.virtual_memory().available / 2e9))
+    except Exception:
+        mem_cap = nproc
+    procs_n = max(1, min(nproc, mem_cap))
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(procs_n), ctx.SimpleQueue()
+    procs = [ctx.Process(target=_oracle_replica, args=(kappa, 1000 + i, barrier, out)) for i in range(procs_n)]
+    for p in procs:
+        p.start()
+    ms = sorted(out.get() for _ in range(procs_n))
+    for p in procs:
+        p.join()
+    med = ms[len(ms) // 2]
+    return {"value": med * cycles, "unit": "ms", "cores": procs_n, "kind": "oracle",
+            "sample": (f"{procs_n} concurrent replicas (one process per core, own f each), one kappa={kname(kappa)} "
+                       f"oracle cycle each on the 4095^2 problem; value = median ms per cycle "
+                       f"({med:.0f}) x {cycles} cycles to 1e-8; slowest replica {ms[-1]:.0f} ms per cycle"),
+            "problems_per_hour": procs_n * 3.6e6 / (ms[-1] * cycles)}
+
+
 def cpu_cores_used():
     try:
         import threadpoolctl
@@ -146,9 +238,9 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_cycle, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "kappa": kname(kappa), "tol": 1e-8},
+            "config": bench_config(kappa, world), "cycles": cycles, "ms_per_cycle": ms_cycle,
             "cpu_baseline": {"value": value, "unit": "ms", "cores": cpu_cores_used(), "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, **host_cpu()},
             "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -310,7 +402,65 @@ def zebra_tables(n, levels, tol, v0_host, f, settings, coarsening="full", mgcg_k
     return out
 
 
+def profile_run(argv):
+    """Profiler driver: a fixed number of kappa-cycles on one synthetic problem through the C ABI,
+    with no timing of its own (the numbers meant for reports come from CUDA events in the main
+    bench; this only gives ncu the launches to capture).
+
+        python bench.py --profile-run --n 4095 --kappa 4 --cycles 1 [--levels L] [--theta T] [--eps E]
+            [--smoother jacobi|zebra|xzebra] [--coarsening full|y] [--fp32 | --mixed | --solve]
+
+    f ~ N(0, 1) seed 0, v = 0. --fp32: FP32 cycles (mg_kcycle_f32); --mixed: the FP32 cycle of
+    mg_solve_mixed launch by launch on the handle's own FP32 arrays (mg_profile_cycle); --solve:
+    the launches of stand-alone solve cycles (with the stopping test's norm) one by one, as
+    mg_profile_cycle runs them (a solve's own graph has conditional nodes, whose kernels
+    profilers skip). Prints one JSON line with the wall time."""
+    ap = argparse.ArgumentParser(prog="bench.py --profile-run")
+    ap.add_argument("--n", type=int, default=4095)
+    ap.add_argument("--levels", type=int, default=0, help="0: down to 1x1")
+    ap.add_argument("--kappa", type=int, default=4)
+    ap.add_argument("--cycles", type=int, default=1)
+    ap.add_argument("--theta", type=float, default=math.pi / 3)
+    ap.add_argument("--eps", type=float, default=1e-4)
+    ap.add_argument("--smoother", default="jacobi", choices=["jacobi", "zebra", "xzebra"])
+    ap.add_argument("--coarsening", default="full", choices=["full", "y"])
+    ap.add_argument("--fp32", action="store_true")
+    ap.add_argument("--mixed", action="store_true")
+    ap.add_argument("--solve", action="store_true")
+    args = ap.parse_args(argv)
+
+    import torch
+
+    from paper_2010_00626_b300 import build
+    build.build()
+    from paper_2010_00626_b300 import kcycle
+
+    n = args.n
+    levels = args.levels or int(round(math.log2(n + 1)))
+    mg = kcycle.Multigrid(n, args.eps, args.theta, levels, smoother=args.smoother, coarsening=args.coarsening)
+    dt = torch.float32 if args.fp32 else torch.float64
+    f = torch.tensor(rhs_normal(n, 0), device="cuda").to(dt)
+    v = torch.zeros_like(f)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.cycles if args.solve else 0):
+        mg.profile_cycle(v, f, args.kappa, with_norm=True)
+    for _ in range(args.cycles if args.mixed else 0):
+        mg.profile_cycle(v, f, args.kappa, fp32=True)
+    for _ in range(0 if (args.solve or args.mixed) else args.cycles):
+        if args.fp32:
+            mg.kcycle_f32(v, f, args.kappa)
+        else:
+            mg.kcycle(v, f, args.kappa)
+    torch.cuda.synchronize()
+    print(json.dumps({"n": n, "levels": levels, "kappa": args.kappa, "cycles": args.cycles,
+                      "smoother": args.smoother, "coarsening": args.coarsening, "fp32": args.fp32,
+                      "solve": args.solve, "mixed": args.mixed, "wall_ms": 1e3 * (time.perf_counter() - t0)}))
+
+
 def main():
+    if "--profile-run" in sys.argv[1:]:
+        return profile_run([a for a in sys.argv[1:] if a != "--profile-run"])
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -414,8 +564,9 @@ def main():
                 "peak_source": "measured live: FP64 FMA throughput probe (mg_fp64_rate); add/mul/fma count as one",
                 "algorithmic_ops_per_point": ops, "ms_per_launch": dom_avg,
                 "tflops_fma2": achieved_tflops, "frac_of_nominal_1.25_tflops": achieved_tflops / NOMINAL_FP64_TFLOPS,
-                "traffic": PASS_A_L0_DRAM_BYTES if n == 4095 else None,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch",
+                "traffic": measured_traffic(PASS_A_L0_TRAFFIC) if n == 4095 else None,
+                "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, taken on the "
+                                   "kernel source with the recorded SHA-256 (null once that source changed)"),
                 "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
                         "algorithmic_bytes": bytes_alg}}
     cycle_share = {f"{kinds[k]}@L{l}": round(t / total, 4) for (k, l), t in sorted(share.items(), key=lambda x: -x[1])[:8]}
@@ -650,17 +801,14 @@ def main():
         cpu = {"value": ms_cycle_cpu * cyc_used, "unit": "ms", "cores": cpu_cores_used(), "kind": "oracle",
                "sample": (f"2 kappa={kname(kappa)} oracle cycles on the 4095^2 problem from v0=0 "
                           f"({ms_cycle_cpu:.0f} ms/cycle) x {cyc_used} cycles to 1e-8 "
-                          f"({'oracle count, tests/golden' if cyc_or else 'GPU count'})")}
+                          f"({'oracle count, tests/golden' if cyc_or else 'GPU count'})"), **host_cpu()}
+        cpu["all_cores"] = oracle_all_cores(kappa, cyc_used)
 
     if rank == 0:
         line = {"metric": METRIC, "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n": n, "levels": levels, "theta": cfg["theta"], "eps": cfg["eps"],
-                           "kappa": kname(kappa), "tol": tol, "nu1": cfg["nu1"], "nu2": cfg["nu2"],
-                           "omega": cfg["omega"], "cycles": cycles, "ms_per_cycle": ms_step / cycles,
-                           "l2": "inputs larger than L2 (each 4095^2 FP64 array is 134 MB)",
-                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "config": bench_config(kappa, world), "cycles": cycles, "ms_per_cycle": ms_step / cycles,
                 "roofline": roofline, "cycle_share": cycle_share, "per_level": per_level,
                 "per_level_fp32": per_level32, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clocks.summary(), "per_kappa": per_kappa,

@@ -2245,7 +2245,10 @@ int noalloc_scratch(double** out) {
 
 extern "C" int mg_residual_norm_noalloc(int n, double eps, double theta, const double* v, const double* f,
                                         void* cuda_stream, double* norm) {
-  if (!v || !f || !norm) return MG_ERR_ARG;
+  if (!v || !f || !norm) {
+    snprintf(g_err, sizeof(g_err), "mg_residual_norm_noalloc: v, f and norm must not be NULL");
+    return MG_ERR_ARG;
+  }
   int k = 0;
   while (k < 15 && ((1 << k) - 1) < n) ++k;
   if (n < 1 || ((1 << k) - 1) != n) {
@@ -2256,7 +2259,11 @@ extern "C" int mg_residual_norm_noalloc(int n, double eps, double theta, const d
     snprintf(g_err, sizeof(g_err), "mg_residual_norm_noalloc: n=%d exceeds the maximum grid side %d", n, NA_MAX_N);
     return MG_ERR_ARG;
   }
-  if (!(eps > 0.0) || !(eps <= 1.0) || !(std::fabs(theta) <= 1e4)) return MG_ERR_ARG;
+  if (!(eps > 0.0) || !(eps <= 1.0) || !(std::fabs(theta) <= 1e4)) {
+    snprintf(g_err, sizeof(g_err), "mg_residual_norm_noalloc: need 0 < eps <= 1 and |theta| <= 1e4 (eps=%g, theta=%g)",
+             eps, theta);
+    return MG_ERR_ARG;
+  }
   double* sc = nullptr;
   KC_TRY(noalloc_scratch(&sc));
   cudaStream_t s = (cudaStream_t)cuda_stream;

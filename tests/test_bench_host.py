@@ -66,3 +66,30 @@ def test_profile_kinds_cover_the_abi():
     assert set(bench.PROFILE_KINDS) == set(range(7))
     assert bench.PROFILE_KINDS[6] == "call"
     assert math.isclose(bench.dp_ops_per_point(0, 2, True)[0], 32.25)
+
+
+def test_stored_traffic_is_dropped_when_the_kernel_source_changes(tmp_path, monkeypatch):
+    src = tmp_path / "k.cuh"
+    src.write_text("pass A body\n// Pass B: v <- v + P v_c\npass B body\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    entry = {"source": "k.cuh", "until": "// Pass B: v <- v + P v_c", "sha256": None, "bytes": 123}
+    entry["sha256"] = bench.source_digest(entry)
+    assert bench.measured_traffic(entry) == 123
+    src.write_text("pass A body\n// Pass B: v <- v + P v_c\nchanged pass B body\n")
+    assert bench.measured_traffic(entry) == 123  # outside the hashed section
+    src.write_text("pass A body, changed\n// Pass B: v <- v + P v_c\npass B body\n")
+    assert bench.measured_traffic(entry) is None
+
+
+def test_stored_pass_a_traffic_matches_the_current_source():
+    """The committed figure is used only while the pass A source it was captured on is unchanged."""
+    got = bench.measured_traffic(bench.PASS_A_L0_TRAFFIC)
+    assert got is None or got == bench.PASS_A_L0_TRAFFIC["bytes"]
+
+
+def test_both_arms_print_the_same_config():
+    cfg = bench.bench_config(4)
+    for key in ("workload", "n", "levels", "theta", "eps", "kappa", "tol", "nu1", "nu2", "omega"):
+        assert key in cfg
+    assert "parallelism" not in cfg and bench.bench_config(4, 2)["parallelism"] == "replicas x2"
+    assert set(bench.host_cpu()) == {"cpu_model", "nproc"}

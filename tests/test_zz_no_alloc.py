@@ -18,9 +18,13 @@ pytestmark = pytest.mark.gpu
 REL_TOL = 1e-12  # the tolerance the other residual-norm test uses
 
 
-def test_noalloc_residual_norm_matches_handle_entry_point_twice(lib):
+@pytest.mark.parametrize("n", [1, 7, 511, 4095])
+def test_noalloc_residual_norm_matches_handle_entry_point_twice(lib, n):
+    """n = 1: every neighbour is a boundary zero; n = 7: almost all of the fixed 592 blocks write a
+    zero partial (49 points); 511 and 4095: every block sums points, 4095^2 over many grid strides."""
     import torch
-    n, levels, theta, eps = 511, 9, 1.3, 1e-4
+    levels = max(1, int(round(math.log2(n + 1))) - 2)
+    theta, eps = 1.3, 1e-4
     mg = lib.Multigrid(n, eps, theta, levels)
     stream = torch.cuda.current_stream().cuda_stream or lib.CUDA_STREAM_LEGACY
     for seed in (0, 1):  # two calls in a row: the second must not see the first's scratch
@@ -43,3 +47,8 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
                                            ctypes.c_void_p(v.data_ptr()), None, ctypes.byref(out))
     assert st == -1
     assert b"exceeds the maximum grid side" in lib._lib.mg_last_error()
+    for eps, theta in ((0.0, 0.5), (1.5, 0.5), (1e-2, 2e4)):
+        st = lib._lib.mg_residual_norm_noalloc(7, eps, theta, ctypes.c_void_p(v.data_ptr()),
+                                               ctypes.c_void_p(v.data_ptr()), None, ctypes.byref(out))
+        assert st == -1
+        assert b"need 0 < eps <= 1" in lib._lib.mg_last_error()
