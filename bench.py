@@ -280,6 +280,19 @@ def bytes_per_point(kind, norm):
     return 8 + 8 + 8 + 2 if kind == 0 else 8 + 8 + 2 + 8
 
 
+def error_vs_fp64(mg, x, f, x_star):
+    """Quality of a mixed-precision result x, stated per result: its relative residual recomputed
+    in FP64 on the device (mg_residual_norm, the FP64 kernel whose parity with the oracle the tests
+    pin) and its relative error against x_star, the FP64 solve of the same problem to a tighter
+    tolerance, norm-wise and element-wise."""
+    import torch
+    rr = mg.residual_norm(x, f) / float(torch.linalg.vector_norm(f))
+    d = x - x_star
+    return {"relres_fp64": rr,
+            "rel_error_l2": float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(x_star)),
+            "rel_error_max": float(d.abs().max() / x_star.abs().max())}
+
+
 # launch kinds of mg_profile_cycle
 PROFILE_KINDS = {0: "pass_a", 1: "pass_b", 2: "coarse", 3: "residual", 4: "lines_x", 5: "lines_y",
                  6: "call"}  # call: pass A, the coarse walk and pass B of one call in one cluster launch
@@ -610,6 +623,11 @@ def main():
     # ---------------------------------------------------------------- mixed precision (FP32 cycles + FP64 IR)
     per_kappa_mixed = {}
     if not args.no_sweep:
+        # the reference solution for the error statements: the FP64 solve to 1e-13
+        x_star = torch.zeros_like(f)
+        st_s, cyc_s, rel_s, _ = mg.solve(x_star, f, kappa, 1e-13, max_cycles, history=False)
+        per_kappa_mixed["reference_solution"] = {"what": f"FP64 kappa={kname(kappa)} solve", "tol": 1e-13,
+                                                 "cycles": cyc_s, "relres": rel_s, "status": st_s}
         for k in (1, 2, 3, 4, 5, KAPPA_W):
             v.zero_()
             mg.solve_mixed(v, f, k, tol, 1, history=False)  # builds the graph and the FP32 levels
@@ -622,7 +640,9 @@ def main():
             torch.cuda.synchronize()
             ms_k = a.elapsed_time(b)
             per_kappa_mixed[kname(k)] = {"ms": round(ms_k, 3), "iterations": it_k,
-                                         "ms_per_iteration": round(ms_k / it_k, 4), "relres": rel_k, "status": st_k}
+                                         "ms_per_iteration": round(ms_k / it_k, 4), "relres": rel_k, "status": st_k,
+                                         "error_vs_fp64": error_vs_fp64(mg, v, f, x_star)}
+        del x_star
 
     # ---------------------------------------------------------------- run-time model (Section 3) and kappa pre-selection
     model_report = None
@@ -734,6 +754,10 @@ def main():
                             "preconditioner B+B^T-B^TAB with plain CG"}
         runs = [("fp64", 1, 0, False), ("fp64", 2, 0, True), ("fp64", 3, 0, True), ("fp64", 4, 0, True),
                 ("fp64_symmetrised", 2, 1, False), ("fp64_symmetrised", 3, 1, False), ("mixed", 3, 0, True)]
+        x8_star = torch.zeros_like(b8)
+        st8s, it8s, rel8s, _ = m8.pcg(x8_star, b8, 3, 1e-13, 2000, flexible=True, history=False)
+        mgcg["reference_solution"] = {"what": "FP64 MGCG kappa=3, flexible beta", "tol": 1e-13, "iterations": it8s,
+                                      "relres": rel8s, "status": st8s}
         for name, k8, sym, flex in runs:
             m8.set_option(kcycle.MG_OPT_PRECOND, sym)
             mixed = name == "mixed"
@@ -747,8 +771,10 @@ def main():
             torch.cuda.synchronize()
             mgcg[f"{name}_k{k8}"] = {"ms": round(a.elapsed_time(b), 1), "iterations": it8, "relres": rel8,
                                      "status": st8, "flexible": flex}
+            if mixed:
+                mgcg[f"{name}_k{k8}"]["error_vs_fp64"] = error_vs_fp64(m8, x8, b8, x8_star)
         m8.close()
-        del b8, x8
+        del b8, x8, x8_star
 
     # ---------------------------------------------------------------- batched (256 ragged instances, one launch each)
     batched = None
@@ -775,10 +801,25 @@ def main():
             ms_b = 1e3 * (time.perf_counter() - t0)
             conv = [i for i in range(len(ns)) if rel_b[i] <= tol]
             q = sorted(it_b)
-            batched[("mixed" if mixed else "fp64") + ("_zebra" if smoother == "zebra" else "")] = {
-                "ms_one_launch": round(ms_b, 1), "converged": len(conv), "of": len(ns),
-                "iterations_quartiles": [q[0], q[len(q) // 4], q[len(q) // 2], q[3 * len(q) // 4], q[-1]],
-                "autotuned_coarse_n": {str(k): v for k, v in chosen.items()}}
+            entry = {"ms_one_launch": round(ms_b, 1), "converged": len(conv), "of": len(ns),
+                     "iterations_quartiles": [q[0], q[len(q) // 4], q[len(q) // 2], q[3 * len(q) // 4], q[-1]],
+                     "autotuned_coarse_n": {str(k): v for k, v in chosen.items()}}
+            if mixed:
+                # error against each sampled instance's FP64 solve to 1e-13 (a standalone handle)
+                errs = []
+                for i in range(0, len(ns), 16):
+                    if not rel_b[i] <= tol:
+                        continue  # a stalled instance (see the note) has no FP64 reference either
+                    d = inst[i]
+                    ms_ = kcycle.Multigrid(d["n"], d["eps"], d["theta"], int(round(math.log2(d["n"] + 1))),
+                                           smoother=smoother)
+                    xs_star = torch.zeros_like(fs_b[i])
+                    st_s = ms_.solve(xs_star, fs_b[i], 3, 1e-13, 3000, history=False)[0]
+                    e = error_vs_fp64(ms_, xs_b[i], fs_b[i], xs_star)
+                    errs.append({"instance": i, "n": d["n"], "reference_status": st_s, **e})
+                    ms_.close()
+                entry["error_vs_fp64_sample"] = errs
+            batched[("mixed" if mixed else "fp64") + ("_zebra" if smoother == "zebra" else "")] = entry
             bt.close()
         batched["note"] = ("damped-Jacobi instances that miss tol are near-grid-aligned with small eps, where "
                            "point relaxation does not smooth; the *_zebra runs use alternating zebra line "

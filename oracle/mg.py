@@ -13,6 +13,11 @@ Grid convention used by every function here:
 A stencil is a 3x3 array ``st`` with ``st[1+dy, 1+dx]`` the coefficient that multiplies
 v(i+dx, j+dy) in (A v)(i, j).
 
+Precision: FP64 (every input the tests and the bench pass is float64). Work arrays take the dtype
+of the function's input, so the same steps run unchanged on float32 data when a test wants the
+size of FP32 rounding in this algorithm (a calibration for the FP32 cycle; FP64 results are
+unaffected).
+
 Readings of the paper taken here:
   * The operator is A = S / h^2 with S the printed table (the table omits h^2).
   * The top row of the printed table is north (j+1); then the corner entries are
@@ -149,7 +154,7 @@ def fine_stencil_derivatives(theta: float, eps: float, n: int):
 def apply_stencil(st: np.ndarray, v: np.ndarray) -> np.ndarray:
     """(A v) for a constant 9-point stencil with zero Dirichlet values outside the grid."""
     ny, nx = v.shape
-    padded = np.zeros((ny + 2, nx + 2))
+    padded = np.zeros((ny + 2, nx + 2), dtype=v.dtype)
     padded[1:-1, 1:-1] = v
     out = np.zeros_like(v)
     for dy in (-1, 0, 1):
@@ -177,7 +182,7 @@ def restrict_fw(r: np.ndarray) -> np.ndarray:
     m = (nf - 1) // 2
     weights = {-1: 1.0, 0: 2.0, 1: 1.0}
     rows = 2 * np.arange(m) + 1
-    out = np.zeros((m, m))
+    out = np.zeros((m, m), dtype=r.dtype)
     for dy in (-1, 0, 1):
         for dx in (-1, 0, 1):
             out += (weights[dy] * weights[dx] / 16.0) * r[np.ix_(rows + dy, rows + dx)]
@@ -194,9 +199,9 @@ def prolong_bilinear(vc: np.ndarray) -> np.ndarray:
     """
     m = vc.shape[0]
     nf = 2 * m + 1
-    pc = np.zeros((m + 2, m + 2))      # coarse grid with its zero boundary ring
+    pc = np.zeros((m + 2, m + 2), dtype=vc.dtype)  # coarse grid with its zero boundary ring
     pc[1:-1, 1:-1] = vc                # pc[J+1, I+1] = vc[J, I]
-    out = np.zeros((nf, nf))
+    out = np.zeros((nf, nf), dtype=vc.dtype)
     out[1::2, 1::2] = vc
     out[1::2, 0::2] = 0.5 * (pc[1:-1, :-1] + pc[1:-1, 1:])
     out[0::2, 1::2] = 0.5 * (pc[:-1, 1:-1] + pc[1:, 1:-1])

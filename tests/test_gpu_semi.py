@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
+from parity import rel  # norm-wise and element-wise (tests/parity.py)
 from paper_2010_00626_b300.inputs import KAPPA_W, rhs_normal, rhs_uniform
 
 pytestmark = pytest.mark.gpu
@@ -33,8 +34,6 @@ def to_np(t):
     return t.detach().cpu().numpy()
 
 
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 def iter_tol(h):
