@@ -280,11 +280,14 @@ def bytes_per_point(kind, norm):
     return 8 + 8 + 8 + 2 if kind == 0 else 8 + 8 + 2 + 8
 
 
+REF_TOL = 1e-12  # tolerance of the FP64 reference solutions of the error statements
+
+
 def error_vs_fp64(mg, x, f, x_star):
     """Quality of a mixed-precision result x, stated per result: its relative residual recomputed
     in FP64 on the device (mg_residual_norm, the FP64 kernel whose parity with the oracle the tests
-    pin) and its relative error against x_star, the FP64 solve of the same problem to a tighter
-    tolerance, norm-wise and element-wise."""
+    pin) and its relative error against x_star, the FP64 solve of the same problem to REF_TOL,
+    norm-wise and element-wise."""
     import torch
     rr = mg.residual_norm(x, f) / float(torch.linalg.vector_norm(f))
     d = x - x_star
@@ -623,10 +626,11 @@ def main():
     # ---------------------------------------------------------------- mixed precision (FP32 cycles + FP64 IR)
     per_kappa_mixed = {}
     if not args.no_sweep:
-        # the reference solution for the error statements: the FP64 solve to 1e-13
+        # the reference solution for the error statements: the FP64 solve to 1e-12 (its residual
+        # levels off near 6e-13 at this size, so a tighter tolerance is not reachable)
         x_star = torch.zeros_like(f)
-        st_s, cyc_s, rel_s, _ = mg.solve(x_star, f, kappa, 1e-13, max_cycles, history=False)
-        per_kappa_mixed["reference_solution"] = {"what": f"FP64 kappa={kname(kappa)} solve", "tol": 1e-13,
+        st_s, cyc_s, rel_s, _ = mg.solve(x_star, f, kappa, REF_TOL, 3000, history=False)
+        per_kappa_mixed["reference_solution"] = {"what": f"FP64 kappa={kname(kappa)} solve", "tol": REF_TOL,
                                                  "cycles": cyc_s, "relres": rel_s, "status": st_s}
         for k in (1, 2, 3, 4, 5, KAPPA_W):
             v.zero_()
@@ -755,8 +759,8 @@ def main():
         runs = [("fp64", 1, 0, False), ("fp64", 2, 0, True), ("fp64", 3, 0, True), ("fp64", 4, 0, True),
                 ("fp64_symmetrised", 2, 1, False), ("fp64_symmetrised", 3, 1, False), ("mixed", 3, 0, True)]
         x8_star = torch.zeros_like(b8)
-        st8s, it8s, rel8s, _ = m8.pcg(x8_star, b8, 3, 1e-13, 2000, flexible=True, history=False)
-        mgcg["reference_solution"] = {"what": "FP64 MGCG kappa=3, flexible beta", "tol": 1e-13, "iterations": it8s,
+        st8s, it8s, rel8s, _ = m8.pcg(x8_star, b8, 3, REF_TOL, 2000, flexible=True, history=False)
+        mgcg["reference_solution"] = {"what": "FP64 MGCG kappa=3, flexible beta", "tol": REF_TOL, "iterations": it8s,
                                       "relres": rel8s, "status": st8s}
         for name, k8, sym, flex in runs:
             m8.set_option(kcycle.MG_OPT_PRECOND, sym)
@@ -805,7 +809,7 @@ def main():
                      "iterations_quartiles": [q[0], q[len(q) // 4], q[len(q) // 2], q[3 * len(q) // 4], q[-1]],
                      "autotuned_coarse_n": {str(k): v for k, v in chosen.items()}}
             if mixed:
-                # error against each sampled instance's FP64 solve to 1e-13 (a standalone handle)
+                # error against each sampled instance's FP64 solve to REF_TOL (a standalone handle)
                 errs = []
                 for i in range(0, len(ns), 16):
                     if not rel_b[i] <= tol:
@@ -814,7 +818,7 @@ def main():
                     ms_ = kcycle.Multigrid(d["n"], d["eps"], d["theta"], int(round(math.log2(d["n"] + 1))),
                                            smoother=smoother)
                     xs_star = torch.zeros_like(fs_b[i])
-                    st_s = ms_.solve(xs_star, fs_b[i], 3, 1e-13, 3000, history=False)[0]
+                    st_s = ms_.solve(xs_star, fs_b[i], 3, REF_TOL, 3000, history=False)[0]
                     e = error_vs_fp64(ms_, xs_b[i], fs_b[i], xs_star)
                     errs.append({"instance": i, "n": d["n"], "reference_status": st_s, **e})
                     ms_.close()

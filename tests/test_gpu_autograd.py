@@ -114,7 +114,7 @@ def test_adjoint_solve_entry_point(lib):
     g = rhs_normal(n, 6)
     mg = lib.Multigrid(n, eps, theta, levels)
     lam = t64(np.zeros((n, n)))
-    st, cycles, rel, hist = mg.solve(lam, t64(g), 2, 1e-10, 500, adjoint=True)
+    st, cycles, relres, hist = mg.solve(lam, t64(g), 2, 1e-10, 500, adjoint=True)
     h = oracle.Hierarchy(n, levels, theta, eps)
     lam_or, hist_or = oracle.solve(h, g, 2, 1e-10, 500, adjoint=True)
     assert st == 0 and cycles == len(hist_or)
