@@ -92,7 +92,7 @@ typedef enum {
                               lose its upwind structure on coarse grids and the cycle can diverge;
                               MG_OPT_COARSE_OP = 1 (rediscretized upwind operators) is the stable
                               choice. Recomputes the stencils.                                    */
-  MG_OPT_FUSED_CALL = 14   /* 1 (default): with damped Jacobi and full coarsening, each call at the
+  MG_OPT_FUSED_CALL = 14,  /* 1 (default): with damped Jacobi and full coarsening, each call at the
                               level just above the coarse-level kernel's (FP64 and FP32 cycles)
                               runs as one launch of a thread-block cluster with one CTA per tile
                               of that level, at most 16 (pass A over the tiles, the coarse walk on
@@ -102,6 +102,22 @@ typedef enum {
                               one of them walks). Not applied at level 0, to adjoint cycles, to
                               levels of more than 16 tiles, or where the device cannot run the
                               cluster (three launches then).                                    */
+  MG_OPT_TMA_PASSES = 15,  /* 1 (default): the FP32 cycles' passes at sides >= 1023 with nu = 2 run as
+                              persistent kernels whose input windows arrive by 2-D tensor copies
+                              (TMA), double-buffered; 0: the shared-memory tile and register-pipeline
+                              passes. Same arithmetic per point up to the order of FP32 rounding. Arrays
+                              must be 16-byte aligned with pitches that are multiples of 4 floats (the
+                              handle's own are), else the other passes run.                       */
+  MG_OPT_CONDENSED_CHILDREN = 16 /* 1 (default): the two calls that a call just above the coarse-
+                              kernel level makes there (counters k and k-1, the first from zero,
+                              Algorithm 3), with everything below them, are one linear map of the
+                              restricted residual, v = P_c f with c = min(k, levels - lc + 1);
+                              the handle computes P_c once (FP64, by the coarse kernel run on unit
+                              vectors) and applies it as one matrix-vector product over 16 CTAs
+                              (inside the fused call, or as its own launch). Same linear map as
+                              the call-by-call walk, rounded differently. Used where that level's
+                              side is <= 31 and the maps take <= 64 MB; not for adjoint cycles.
+                              0: the walk of the coarse-level kernel.                          */
 } mg_option;
 
 /* Set up the hierarchy for the Section 4 problem on an n x n interior grid.
@@ -272,10 +288,17 @@ typedef struct mg_batch_ctx* mg_batch;
 int mg_batch_create(int count, const int* n, const double* eps, const double* theta, const int* levels,
                     int nu1, int nu2, mg_batch* out);
 
-/* Autotuner: for each distinct grid side in the batch, time kappa-cycles of one instance with the
- * candidate coarse-kernel thresholds (FP64: 7, 15, 31; FP32 when mixed != 0: 15, 31, 63) and apply
- * the fastest to every instance of that side. chosen (host, nullable, 2 ints per distinct side):
- * pairs (n, threshold). Allocates and frees temporary arrays. Synchronises. */
+/* Autotuner of the batch's launch shapes, per distinct grid side (largest first), timed inside the
+ * batch's concurrency: up to 8 instances of that side are solved together as batch branches of one
+ * graph (4 iterations of the FP64 solve, or of the mixed solve when mixed != 0, on scratch arrays),
+ * and the side's options are chosen by coordinate descent over
+ *   1. the coarse-kernel threshold: FP64 7, 15, 31 (MG_OPT_COARSE_N); FP32 15, 31, 63 (COARSE_N32);
+ *   2. fused calls (MG_OPT_FUSED_CALL) x condensed child calls (MG_OPT_CONDENSED_CHILDREN), on/off;
+ *   3. for mixed solves of sides >= 1023, the FP32 passes (MG_OPT_TMA_PASSES) on/off;
+ * keeping a change only when it is faster; the winner is applied to every instance of that side.
+ * chosen (host, nullable, 2 ints per distinct side, largest side first): pairs (n, threshold); the
+ * other choices can be read per instance with mg_batch_instance + mg_get_option. Allocates and frees
+ * scratch arrays. Synchronises. */
 int mg_batch_autotune(mg_batch b, int kappa, int mixed, int* chosen);
 
 /* Solve every instance to ||f_i - A_i x_i|| / ||f_i|| <= tol from the initial guesses x_i, with
@@ -290,6 +313,13 @@ int mg_batch_solve(mg_batch b, double* const* x, const double* const* f, int kap
  * relaxation everywhere, which also smooths the near-grid-aligned instances that damped Jacobi
  * cannot). Returns the first failing status, MG_ERR_ARG for read-only keys. Synchronises. */
 int mg_batch_set_option(mg_batch b, int key, double value);
+
+/* The handle of instance `index` (0-based) of the batch, for mg_get_option (the autotuner's choices)
+ * or for solving that instance alone with mg_solve / mg_solve_mixed. The batch owns the handle: do
+ * not destroy it; it is valid until mg_batch_destroy. Options set on it apply to the batch too (the
+ * batch's graph is rebuilt on its next solve only through mg_batch_set_option or the autotuner, so
+ * set per-instance options before the first mg_batch_solve). */
+int mg_batch_instance(mg_batch b, int index, mg_handle* out);
 
 int mg_batch_size(mg_batch b, int* count);
 int mg_batch_destroy(mg_batch b);

@@ -9,6 +9,8 @@
 // replayed; stand-alone solves and MGCG put one cycle (or one PCG iteration) in the body of a
 // WHILE conditional node whose last kernel evaluates the stopping test on the device, so a whole
 // solve is a single graph launch.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,6 +27,7 @@
 #include "kernels.cuh"
 #include "lines.cuh"
 #include "stream_f32.cuh"
+#include "tma_f32.cuh"
 
 using namespace kc;
 
@@ -60,6 +63,7 @@ constexpr int MAX_NU = 8;
 constexpr int VEC_BLOCKS = 148 * 8;
 constexpr int MAX_COARSE_N = 63;
 constexpr size_t SMEM_CAP = 220 * 1024;  // dynamic shared memory per CTA (227 KB less static use)
+constexpr int TMA_TY_MAX = 64;           // largest tile height of the tensor-copy FP32 passes
 constexpr int MAP_S = 49;       // unknowns of the side-7 level
 constexpr int MAP_CLASSES = 3;  // at most two levels below it: counters 1, 2, >= 3
 
@@ -107,6 +111,8 @@ struct mg_ctx {
   int lc = 0;         // first level handled by the coarse kernel (FP64 cycles)
   int lc32 = 0;       // same for the FP32 cycles of the mixed path
   int fused = 1;         // calls just above the coarse kernel as one cluster launch (MG_OPT_FUSED_CALL)
+  int tma32 = 1;         // FP32 large-level passes fed by tensor copies (MG_OPT_TMA_PASSES)
+  int sms = 148;         // multiprocessors of the device (grid of the persistent passes)
   int coarse_n32 = 31;  // FP32 threshold: one SM does FP32 at 64x the FP64 rate, so the single-CTA
                         // kernel takes more levels (31 measured best at 4095^2 for kappa 3 and 4)
   Level lv[MAXL];
@@ -138,6 +144,13 @@ struct mg_ctx {
   double* cmap = nullptr;
   float* cmap32 = nullptr;
   bool maps_ok = false, maps32_ok = false;
+  // condensed child calls at the coarse-kernel level (children_kernel): per class c = 1..pm_cls the
+  // map P_c (pm_side^2 rows of pitch pm_ld), FP64 and FP32 cycles; valid while pm_ok / pm32_ok
+  int condense = 1;  // MG_OPT_CONDENSED_CHILDREN
+  double* pm = nullptr;
+  float* pm32 = nullptr;
+  int pm_cls = 0, pm_ld = 0, pm_side = 0, pm32_cls = 0, pm32_ld = 0, pm32_side = 0;
+  bool pm_ok = false, pm32_ok = false;
   double* ltab = nullptr;  // line-solve tables (Thomas factors and chunk products) per level/direction
   float* ltab32 = nullptr;
   double* linv = nullptr;  // dense line inverses of the levels with side <= LINV_MAX
@@ -284,6 +297,12 @@ int set_all_smem_attrs() {
       KC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile32_smem_a()));
     for (auto k : {pass_b_tile32<0>, pass_b_tile32<1>, pass_b_tile32<2>})
       KC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile32_smem_b()));
+    KC_CUDA(cudaFuncSetAttribute(pass_a_tma32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(tm_smem_a(TMA_TY_MAX, 2, true) + 1024)));
+    KC_CUDA(cudaFuncSetAttribute(pass_a_tma32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(tm_smem_a(TMA_TY_MAX, 2, false) + 1024)));
+    KC_CUDA(cudaFuncSetAttribute(pass_b_tma32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(tm_smem_b(TMA_TY_MAX, 2) + 1024)));
   }
   KC_TRY((set_line_attrs<T, 1>()));
   KC_TRY((set_line_attrs<T, 2>()));
@@ -317,6 +336,11 @@ struct Arr<double> {
   static double* cmap(mg_ctx* h) { return h->cmap; }
   static bool maps_ok(mg_ctx* h) { return h->maps_ok; }
   static int ld(mg_ctx* h, int l) { return h->lv[l].ld; }
+  static const double* pmap(const mg_ctx* h, int c, int* ld) {
+    if (!h->pm_ok || !h->condense) return nullptr;
+    *ld = h->pm_ld;
+    return h->pm + (size_t)(std::min(c, h->pm_cls) - 1) * h->pm_side * h->pm_side * h->pm_ld;
+  }
 };
 template <>
 struct Arr<float> {
@@ -328,6 +352,11 @@ struct Arr<float> {
   static float* cmap(mg_ctx* h) { return h->cmap32; }
   static bool maps_ok(mg_ctx* h) { return h->maps32_ok; }
   static int ld(mg_ctx* h, int l) { return l == 0 ? h->ld32_0 : h->lv[l].ld; }
+  static const float* pmap(const mg_ctx* h, int c, int* ld) {
+    if (!h->pm32_ok || !h->condense) return nullptr;
+    *ld = h->pm32_ld;
+    return h->pm32 + (size_t)(std::min(c, h->pm32_cls) - 1) * h->pm32_side * h->pm32_side * h->pm32_ld;
+  }
 };
 
 template <typename T>
@@ -413,6 +442,116 @@ int launch_pass_b_fast32(const PassBArgs<float>& a, cudaStream_t s) {
   return MG_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// FP32 passes fed by tensor copies (tma_f32.cuh): tensor maps and launches
+// ------------------------------------------------------------------------------------------
+// The driver's tensor-map encoder, looked up once through the runtime (no link against libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  return fn;
+}
+
+// A 2-D map of an n_cols x n_rows FP32 array (row pitch ld floats) read in box_x x box_y boxes;
+// points outside the extents read as zero.
+int make_map_f32(CUtensorMap* m, const float* base, int n_cols, int n_rows, int ld, int box_x, int box_y) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return MG_ERR_CUDA;
+  const cuuint64_t dims[2] = {(cuuint64_t)n_cols, (cuuint64_t)n_rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    snprintf(g_err, sizeof(g_err), "cuTensorMapEncodeTiled failed (%d) for a %d x %d array, pitch %d", (int)r, n_cols,
+             n_rows, ld);
+    return MG_ERR_CUDA;
+  }
+  return MG_OK;
+}
+
+// Output rows per tile: tall tiles where the level has rows to spare (less halo recomputed), lower
+// ones where the tiles would not fill the device.
+int tma_ty(int n) { return n >= 2047 ? 64 : 32; }
+
+bool aligned16(const void* p, int ld) { return ((uintptr_t)p & 15) == 0 && (ld & 3) == 0; }
+
+// Whether the tensor-copy passes take this launch: nu = 2, a large level, 16-byte aligned arrays
+// with pitches of whole 16-byte units (the tensor maps' rule), the encoder available.
+bool tma_pass_a_ok(const mg_ctx* h, const PassAArgs<float>& a) {
+  return h->tma32 && a.nu == 2 && a.n >= F32_FAST_MIN && a.vout && (a.vin == nullptr || aligned16(a.vin, a.ldvin)) &&
+         aligned16(a.f, a.ldf) && aligned16(a.vout, a.ldvout) && ((uintptr_t)a.fc & 7) == 0 && (a.ldc & 1) == 0 &&
+         tensor_map_encoder() != nullptr;
+}
+bool tma_pass_b_ok(const mg_ctx* h, const PassBArgs<float>& a) {
+  return h->tma32 && a.nu == 2 && a.n >= F32_FAST_MIN && a.partial == nullptr && aligned16(a.vin, a.ldvin) &&
+         aligned16(a.f, a.ldf) && aligned16(a.vout, a.ldvout) && aligned16(a.vc, a.ldc) &&
+         tensor_map_encoder() != nullptr;
+}
+
+TmaPassArgs tma_args(const mg_ctx* h, int n, int level, const float* coef, const int* skip, int* err) {
+  TmaPassArgs t;
+  t.n = n;
+  t.ty = tma_ty(n);
+  t.tiles_x = (n + TM_TX - 1) / TM_TX;
+  t.tiles = t.tiles_x * ((n + t.ty - 1) / t.ty);
+  t.level = level;
+  t.coef = coef;
+  t.skip = skip;
+  t.err = err;
+  t.vout = nullptr;
+  t.ldvout = 0;
+  t.fc = nullptr;
+  t.ldc = 0;
+  (void)h;
+  return t;
+}
+
+int launch_pass_a_tma32(mg_ctx* h, const PassAArgs<float>& a, cudaStream_t s) {
+  TmaPassArgs t = tma_args(h, a.n, a.level, a.coef, a.skip, h->ints + I_ERR);
+  t.vout = a.vout;
+  t.ldvout = a.ldvout;
+  t.fc = a.fc;
+  t.ldc = a.ldc;
+  const int R = tm_rows_a(t.ty, 2);
+  CUtensorMap mv, mf;
+  KC_TRY(make_map_f32(&mf, a.f, a.n, a.n, a.ldf, TM_P, R));
+  if (a.vin) KC_TRY(make_map_f32(&mv, a.vin, a.n, a.n, a.ldvin, TM_P, R));
+  else mv = mf;  // not read from a zero start
+  const int grid = std::min(t.tiles, h->sms);
+  if (a.vin)
+    pass_a_tma32<false><<<grid, TM_NT, tm_smem_a(t.ty, 2, false) + 1024, s>>>(mv, mf, t);
+  else
+    pass_a_tma32<true><<<grid, TM_NT, tm_smem_a(t.ty, 2, true) + 1024, s>>>(mv, mf, t);
+  KC_CUDA(cudaGetLastError());
+  return MG_OK;
+}
+
+int launch_pass_b_tma32(mg_ctx* h, const PassBArgs<float>& a, cudaStream_t s) {
+  TmaPassArgs t = tma_args(h, a.n, a.level, a.coef, a.skip, h->ints + I_ERR);
+  t.vout = a.vout;
+  t.ldvout = a.ldvout;
+  const int nc = (a.n - 1) / 2;
+  CUtensorMap mv, mf, mc;
+  KC_TRY(make_map_f32(&mv, a.vin, a.n, a.n, a.ldvin, TM_P, tm_rows_b(t.ty, 2)));
+  KC_TRY(make_map_f32(&mf, a.f, a.n, a.n, a.ldf, TM_P, tm_rows_b(t.ty, 2)));
+  KC_TRY(make_map_f32(&mc, a.vc, nc, nc, a.ldc, TM_CP, tm_crows_b(t.ty, 2)));
+  const int grid = std::min(t.tiles, h->sms);
+  pass_b_tma32<<<grid, TM_NT, tm_smem_b(t.ty, 2) + 1024, s>>>(mv, mf, mc, t);
+  KC_CUDA(cudaGetLastError());
+  return MG_OK;
+}
+
 // The coarse kernel variant for the handle: line relaxation (symmetric operators) or damped
 // Jacobi on the symmetric or the general stencil.
 template <typename T>
@@ -491,11 +630,28 @@ size_t coarse_walk_smem(const mg_ctx* h, CoarseArgs<T>& a) {
   return base;
 }
 
+// The condensed child-call map for calls (k1, k2) from zero at the coarse-kernel level, or nullptr
+// (adjoint cycles, a nonzero start, other counter pairs, maps not built).
+template <typename T>
+const T* child_map(const mg_ctx* h, int k1, int k2, int zero1, bool adjoint, int* ld) {
+  if (adjoint || !zero1 || lc_of<T>(h) < 1 || k2 != (k1 > 1 ? k1 - 1 : 0)) return nullptr;
+  return Arr<T>::pmap(h, k1, ld);
+}
+
 template <typename T>
 int emit_coarse(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int zero1, bool adjoint, const int* skip,
                 cudaStream_t s) {
   const int lc = lc_of<T>(h);
   CoarseArgs<T> a = coarse_args(h, b, k1, k2, zero1, adjoint, skip);
+  int pld = 0;
+  if (const T* pmap = child_map<T>(h, k1, k2, zero1, adjoint, &pld)) {
+    prof_begin(h, K_COARSE, lc, s);
+    children_kernel<T, nt_coarse<T>()><<<CHILD_PARTS, nt_coarse<T>(), (size_t)pld * sizeof(T), s>>>(pmap, pld, a);
+    prof_end(h, s);
+    KC_CUDA(cudaGetLastError());
+    ++h->launch_count;
+    return MG_OK;
+  }
   const size_t sm = coarse_walk_smem(h, a);
   prof_begin(h, K_COARSE, lc, s);
   KC_TRY(launch_coarse(h, a, 1, sm, s));
@@ -542,11 +698,76 @@ int compute_maps(mg_ctx* h) {
   return MG_OK;
 }
 
+// Largest coarse-kernel side whose child calls are condensed, and the memory cap of the maps.
+constexpr int PM_MAX_SIDE = 31;
+constexpr size_t PM_MAX_BYTES = size_t(64) << 20;
+
+// The condensed child-call maps P_c of the cycle in precision T (see children_matvec): for each
+// class c = 1 .. levels - lc + 1, one map-mode launch of the FP64 coarse kernel at level lc whose S
+// blocks run the calls (c, c - 1) from v = 0, f = e_b (FP64 arithmetic whatever T is), then a
+// conversion to row-major T. Needs a coarse level below the finest one of side <= PM_MAX_SIDE.
+template <typename T>
+int compute_pmaps(mg_ctx* h) {
+  const int lc = lc_of<T>(h);
+  if (h->semi || lc < 1 || lc >= h->levels) return MG_ERR_ARG;
+  const int side = h->lv[lc].n, S = side * side;
+  const int cls = h->levels - lc + 1;
+  const int ld = round_up(S, 16 / (int)sizeof(T));
+  const size_t bytes = (size_t)cls * S * ld * sizeof(T);
+  if (side > PM_MAX_SIDE || bytes > PM_MAX_BYTES) return MG_ERR_ARG;
+  T*& dst = std::is_same<T, double>::value ? reinterpret_cast<T*&>(h->pm) : reinterpret_cast<T*&>(h->pm32);
+  if (dst) KC_CUDA(cudaFree(dst));
+  dst = nullptr;
+  KC_CUDA(cudaMalloc(&dst, bytes));
+  double* tmp = nullptr;
+  KC_CUDA(cudaMalloc(&tmp, sizeof(double) * (size_t)S * S));
+  CoarseArgs<double> a;
+  memset(&a, 0, sizeof(a));
+  a.coef = h->coef;
+  a.coef64 = h->coef;
+  a.cinv = h->cinv;
+  a.n_lc = side;
+  a.lc = lc;
+  a.L = h->levels;
+  a.nu1 = h->nu1;
+  a.nu2 = h->nu2;
+  a.zero1 = 1;
+  a.ltab = h->smoother != 0 ? h->ltab : nullptr;
+  a.linv = h->smoother != 0 ? h->linv : nullptr;
+  a.k = h->k;
+  a.xonly = h->smoother == 2 ? 1 : 0;
+  a.basis = 2;
+  a.cmap_out = tmp;
+  const size_t sm = coarse_smem<double>(side, h->levels - lc);
+  int st = MG_OK;
+  for (int c = 1; c <= cls && st == MG_OK; ++c) {
+    a.k1 = c;
+    a.k2 = c > 1 ? c - 1 : 0;
+    st = launch_coarse(h, a, S, sm, h->own);
+    if (st == MG_OK) {
+      pmap_convert_kernel<T><<<256, 256, 0, h->own>>>(tmp, S, ld, dst + (size_t)(c - 1) * S * ld);
+      if (cudaGetLastError() != cudaSuccess) st = MG_ERR_CUDA;
+    }
+  }
+  if (cudaStreamSynchronize(h->own) != cudaSuccess && st == MG_OK) st = MG_ERR_CUDA;
+  cudaFree(tmp);
+  if (st != MG_OK) return st;
+  if (std::is_same<T, double>::value) {
+    h->pm_cls = cls; h->pm_ld = ld; h->pm_side = side;
+  } else {
+    h->pm32_cls = cls; h->pm32_ld = ld; h->pm32_side = side;
+  }
+  return MG_OK;
+}
+
 // Compute whichever maps are stale (the FP32 ones only once the FP32 hierarchy exists). A
 // failure leaves the flag clear: the coarse kernel then runs those calls step by step.
 void ensure_maps(mg_ctx* h) {
   if (!h->maps_ok && compute_maps<double>(h) == MG_OK) h->maps_ok = true;
   if (h->have32 && !h->maps32_ok && compute_maps<float>(h) == MG_OK) h->maps32_ok = true;
+  if (h->condense && !h->pm_ok && compute_pmaps<double>(h) == MG_OK) h->pm_ok = true;
+  if (h->condense && h->have32 && !h->pm32_ok && compute_pmaps<float>(h) == MG_OK) h->pm32_ok = true;
+  cudaGetLastError();  // a refused map leaves no sticky error: those calls run step by step
 }
 
 // With `lines` (zebra smoothing done in place by the line kernels) pass A only restricts the
@@ -581,6 +802,11 @@ int emit_pass_a(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const
   prof_begin(h, K_PASS_A, l, s);
   int st;
   if constexpr (std::is_same<T, float>::value) {
+    if (!lines && tma_pass_a_ok(h, a)) {
+      st = launch_pass_a_tma32(h, a, s);
+      prof_end(h, s);
+      return st;
+    }
     if (!lines && fast32_ok(a.n, nu, a.vin, a.ldvin) && fast32_ok(a.n, nu, a.f, a.ldf) &&
         fast32_ok(a.n, nu, a.vout, a.ldvout) &&
         ((uintptr_t)a.fc & 7) == 0 && (a.ldc & 1) == 0) {
@@ -629,6 +855,11 @@ int emit_pass_b(mg_ctx* h, const BindingT<T>& b, int l, int nu, double* partial,
   prof_begin(h, K_PASS_B, l, s);
   int st;
   if constexpr (std::is_same<T, float>::value) {
+    if (!lines && tma_pass_b_ok(h, a)) {
+      st = launch_pass_b_tma32(h, a, s);
+      prof_end(h, s);
+      return st;
+    }
     if (!lines && partial == nullptr && fast32_ok(a.n, nu, a.vin, a.ldvin) && fast32_ok(a.n, nu, a.f, a.ldf) &&
         fast32_ok(a.n, nu, a.vout, a.ldvout) && ((uintptr_t)a.vc & 7) == 0 && (a.ldc & 1) == 0) {
       st = launch_pass_b_fast32(a, s);
@@ -885,6 +1116,8 @@ int emit_call_fused(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero
   CoarseArgs<T> ca = coarse_args(h, b, k1, k2, 1, false, skip);
   const size_t sm_walk = coarse_walk_smem(h, ca);
   const PassBArgs<T> pb = pass_b_args(h, b, l, h->nu2, nullptr, skip, false);
+  int pld = 0;
+  const T* pmap = child_map<T>(h, k1, k2, 1, false, &pld);
   constexpr int NT = nt_coarse<T>(), TILE = call_tile<T>();
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
@@ -902,12 +1135,12 @@ int emit_call_fused(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero
   prof_begin(h, K_CALL, l, s);
   if constexpr (std::is_same<T, double>::value) {
     if (h->nonsym) {
-      KC_CUDA(cudaLaunchKernelEx(&cfg, call_cluster_kernel<T, NT, TILE, true>, pa, ca, pb));
+      KC_CUDA(cudaLaunchKernelEx(&cfg, call_cluster_kernel<T, NT, TILE, true>, pa, ca, pb, pmap, pld));
     } else {
-      KC_CUDA(cudaLaunchKernelEx(&cfg, call_cluster_kernel<T, NT, TILE, false>, pa, ca, pb));
+      KC_CUDA(cudaLaunchKernelEx(&cfg, call_cluster_kernel<T, NT, TILE, false>, pa, ca, pb, pmap, pld));
     }
   } else {
-    KC_CUDA(cudaLaunchKernelEx(&cfg, call_cluster_kernel<T, NT, TILE, false>, pa, ca, pb));
+    KC_CUDA(cudaLaunchKernelEx(&cfg, call_cluster_kernel<T, NT, TILE, false>, pa, ca, pb, pmap, pld));
   }
   prof_end(h, s);
   return MG_OK;
@@ -1131,12 +1364,23 @@ int launch_norm2(mg_ctx* h, const double* x, double* out_scalar, cudaStream_t s)
 
 bool valid_handle(mg_handle h) { return h && h->ok; }
 
+// A kernel whose bounded wait for a tensor copy ran out left code in the error slot: report it
+// once (MG_ERR_TIMEOUT) and clear the slot.
+int device_error(mg_ctx* h, int code, cudaStream_t s) {
+  if (code == 0) return MG_OK;
+  KC_CUDA(cudaMemsetAsync(h->ints + I_ERR, 0, sizeof(int), s));
+  KC_CUDA(cudaStreamSynchronize(s));
+  snprintf(g_err, sizeof(g_err), "a level kernel gave up waiting for its tensor copies (code %d)", code);
+  return MG_ERR_TIMEOUT;
+}
+
 int read_result(mg_ctx* h, cudaStream_t s, double tol, int* count_out, double* final_relres, double* history) {
   int ints[NINT];
   double scal[NSCAL];
   KC_CUDA(cudaMemcpyAsync(ints, h->ints, sizeof(ints), cudaMemcpyDeviceToHost, s));
   KC_CUDA(cudaMemcpyAsync(scal, h->scal, sizeof(scal), cudaMemcpyDeviceToHost, s));
   KC_CUDA(cudaStreamSynchronize(s));
+  KC_TRY(device_error(h, ints[I_ERR], s));
   const int count = ints[I_COUNT];
   if (history && count > 0) KC_CUDA(cudaMemcpy(history, h->hist, sizeof(double) * count, cudaMemcpyDeviceToHost));
   if (count_out) *count_out = count;
@@ -1333,11 +1577,13 @@ int free_levels(mg_ctx* h) {
     h->lv[l].tmp = nullptr;
   }
   h->have32 = false;
+  h->pm_ok = h->pm32_ok = false;  // the coarse-kernel level may move
   return MG_OK;
 }
 
 int run_setup_kernels(mg_ctx* h) {
   h->maps_ok = h->maps32_ok = false;
+  h->pm_ok = h->pm32_ok = false;
   setup_stencils_kernel<<<1, 32, 0, h->own>>>(h->theta, h->eps, h->n, h->levels, h->omega, h->coef, h->coef32,
                                              h->stencils, h->dstencil, h->rediscretized, h->semi, h->bx, h->by);
   KC_CUDA(cudaGetLastError());
@@ -1379,7 +1625,7 @@ int mg_destroy(mg_handle h) {
   if (h->own) cudaStreamSynchronize(h->own);
   drop_graphs(h);
   free_levels(h);
-  void* ptrs[] = {h->cmap, h->cmap32, h->pw, h->pz2, h->coef, h->coef32, h->stencils, h->dstencil, h->ltab, h->ltab32, h->linv, h->cinv, h->cinv32, h->work, h->partial,
+  void* ptrs[] = {h->cmap, h->cmap32, h->pm, h->pm32, h->pw, h->pz2, h->coef, h->coef32, h->stencils, h->dstencil, h->ltab, h->ltab32, h->linv, h->cinv, h->cinv32, h->work, h->partial,
                   h->partial2, h->scal, h->ints, h->hist, h->pr, h->pp, h->pq, h->pz, h->pzold, h->hv, h->hf};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -1407,6 +1653,12 @@ int mg_setup(int n, double eps, double theta, int levels, int nu1, int nu2, mg_h
     return st;
   };
   if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) return fail(MG_ERR_CUDA);
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || h->sms < 1)
+      return fail(MG_ERR_CUDA);
+  }
   int st = alloc_levels(h);
   if (st < 0) return fail(st);
   const int nc = h->lv[levels - 1].n, N = nc * nc;
@@ -1456,6 +1708,20 @@ int mg_set_option(mg_handle h, int key, double value) {
       drop_graphs(h);
       return run_setup_kernels(h);
     }
+    case MG_OPT_TMA_PASSES: {
+      if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
+      KC_CUDA(cudaStreamSynchronize(h->stream()));
+      h->tma32 = (int)value;
+      drop_graphs(h);
+      return MG_OK;
+    }
+    case MG_OPT_CONDENSED_CHILDREN: {
+      if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
+      KC_CUDA(cudaStreamSynchronize(h->stream()));
+      h->condense = (int)value;
+      drop_graphs(h);
+      return MG_OK;
+    }
     case MG_OPT_COARSE_OP: {
       if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
       if (h->semi && value != 0.0) return MG_ERR_ARG;
@@ -1477,6 +1743,7 @@ int mg_set_option(mg_handle h, int key, double value) {
       KC_CUDA(cudaStreamSynchronize(h->stream()));
       h->smoother = (int)value;
       h->maps_ok = h->maps32_ok = false;
+      h->pm_ok = h->pm32_ok = false;
       drop_graphs(h);
       return MG_OK;
     }
@@ -1546,6 +1813,8 @@ int mg_get_option(mg_handle h, int key, double* value) {
     case MG_OPT_COARSENING: *value = h->semi; return MG_OK;
     case MG_OPT_PRECOND: *value = h->precond; return MG_OK;
     case MG_OPT_FUSED_CALL: *value = h->fused; return MG_OK;
+    case MG_OPT_TMA_PASSES: *value = h->tma32; return MG_OK;
+    case MG_OPT_CONDENSED_CHILDREN: *value = h->condense; return MG_OK;
     case MG_OPT_CONV_X: *value = h->bx; return MG_OK;
     case MG_OPT_CONV_Y: *value = h->by; return MG_OK;
     case MG_OPT_LEVELS: *value = h->levels; return MG_OK;
@@ -1897,6 +2166,12 @@ int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas) {
     *ctas = fp32 ? call_ctas<float>(h, level) : call_ctas<double>(h, level);
     return MG_OK;
   }
+  if (fp32 && h->tma32 && n >= F32_FAST_MIN && h->nu1 == 2 && h->nu2 == 2 && tensor_map_encoder()) {
+    // the persistent tensor-copy passes: one CTA per SM, at most one per tile
+    const int ty = tma_ty(n);
+    *ctas = std::min(h->sms, ((n + TM_TX - 1) / TM_TX) * ((n + ty - 1) / ty));
+    return MG_OK;
+  }
   if (fp32 && n >= F32_FAST_MIN && std::max(h->nu1, h->nu2) <= 2) {  // the fast-eligible levels (fast32_ok)
     if (f32_tile_pass_b(n)) {  // (pass A always runs as tiles; pass B's shape shown)
       *ctas = ((n + T32_TX - 1) / T32_TX) * ((n + T32_TY - 1) / T32_TY);
@@ -2006,22 +2281,46 @@ void batch_drop_graph(mg_batch_ctx* b) {
 }
 
 // Time `reps` kappa-cycles of handle h in the given precision (ms per cycle) on scratch arrays.
-int time_cycles(mg_handle h, bool mixed, int kappa, int reps, double* v64, double* f64, float* v32, float* f32,
-                float* ms_out) {
-  cudaEvent_t e0, e1;
-  KC_CUDA(cudaEventCreate(&e0));
-  KC_CUDA(cudaEventCreate(&e1));
-  auto one = [&]() -> int { return mixed ? mg_kcycle_f32(h, v32, f32, kappa) : mg_kcycle(h, v64, f64, kappa); };
-  KC_TRY(one());
-  KC_CUDA(cudaEventRecord(e0, h->stream()));
-  for (int r = 0; r < reps; ++r) KC_TRY(one());
-  KC_CUDA(cudaEventRecord(e1, h->stream()));
-  KC_CUDA(cudaEventSynchronize(e1));
+// The autotuner's launch shape of one instance.
+struct TuneShape {
+  int thr, fused, condensed, tma;
+};
+constexpr size_t TUNE_MAX_INSTANCES = 8;  // instances of one side timed together
+constexpr int TUNE_ITERS = 4;             // solve iterations timed per candidate
+
+// ms per iteration of the instances `hs` solved together, as in a batch: one graph holding each
+// instance's solve branch (initialisation, then TUNE_ITERS iterations; a tolerance of 1e-300 keeps
+// every branch running), launched once to warm up and once timed.
+int time_subbatch(const std::vector<mg_handle>& hs, cudaStream_t s, int kappa, bool mixed, int iters,
+                  const std::vector<double*>& xs, const std::vector<double*>& fs, float* ms_out) {
+  for (mg_handle h : hs) {
+    KC_TRY(ensure_hist(h, iters));
+    if (mixed) KC_TRY(ensure_levels32(h));
+    trim_graphs(h);  // builds the maps the options call for
+  }
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t e = nullptr;
+  KC_CUDA(cudaGraphCreate(&g, 0));
+  int st = MG_OK;
+  for (size_t i = 0; i < hs.size() && st == MG_OK; ++i)
+    st = add_solve_branch(hs[i], g, xs[i], fs[i], kappa, 1e-300, iters, mixed);
+  if (st == MG_OK && cudaGraphInstantiate(&e, g, 0) != cudaSuccess) st = MG_ERR_CUDA;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
   float ms = 0.f;
-  KC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  *ms_out = ms / reps;
+  if (st == MG_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) st = MG_ERR_CUDA;
+  if (st == MG_OK && (cudaGraphLaunch(e, s) != cudaSuccess || cudaEventRecord(e0, s) != cudaSuccess ||
+                      cudaGraphLaunch(e, s) != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
+                      cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+    st = MG_ERR_CUDA;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e) cudaGraphExecDestroy(e);
+  if (g) cudaGraphDestroy(g);
+  if (st != MG_OK) {
+    cudaGetLastError();
+    return st;
+  }
+  *ms_out = ms / iters;
   return MG_OK;
 }
 }  // namespace
@@ -2068,45 +2367,85 @@ int mg_batch_create(int count, const int* n, const double* eps, const double* th
 
 int mg_batch_autotune(mg_batch b, int kappa, int mixed, int* chosen) {
   if (!b || kappa < 1) return MG_ERR_ARG;
-  // one representative per grid side; candidates for the coarse-kernel threshold
+  // distinct grid sides, largest first (the large instances set the batch's critical path)
   std::vector<int> sizes;
   for (mg_handle h : b->inst)
     if (std::find(sizes.begin(), sizes.end(), h->n) == sizes.end()) sizes.push_back(h->n);
-  const int cand64[] = {7, 15, 31};
-  const int cand32[] = {15, 31, 63};
+  std::sort(sizes.begin(), sizes.end(), std::greater<int>());
+  const int thr_key = mixed ? MG_OPT_COARSE_N32 : MG_OPT_COARSE_N;
+  const std::vector<int> cand_thr = mixed ? std::vector<int>{15, 31, 63} : std::vector<int>{7, 15, 31};
   int pos = 0;
   for (int n : sizes) {
-    mg_handle rep = nullptr;
+    std::vector<mg_handle> all, sub;
     for (mg_handle h : b->inst)
-      if (h->n == n) { rep = h; break; }
+      if (h->n == n) all.push_back(h);
+    for (size_t i = 0; i < all.size() && sub.size() < TUNE_MAX_INSTANCES; ++i) sub.push_back(all[i]);
     const size_t len = (size_t)n * n;
-    double *v64 = nullptr, *f64 = nullptr;
-    float *v32 = nullptr, *f32 = nullptr;
-    KC_CUDA(cudaMalloc(&v64, len * 8));
-    KC_CUDA(cudaMalloc(&f64, len * 8));
-    KC_CUDA(cudaMalloc(&v32, len * 4));
-    KC_CUDA(cudaMalloc(&f32, len * 4));
-    KC_CUDA(cudaMemset(v64, 0, len * 8));
-    KC_CUDA(cudaMemset(f64, 0, len * 8));
-    KC_CUDA(cudaMemset(v32, 0, len * 4));
-    KC_CUDA(cudaMemset(f32, 0, len * 4));
-    const int key = mixed ? MG_OPT_COARSE_N32 : MG_OPT_COARSE_N;
-    int best = -1;
-    float best_ms = 1e30f;
-    for (int c : (mixed ? cand32 : cand64)) {
-      if (mg_set_option(rep, key, c) < 0) continue;
-      float ms;
-      if (time_cycles(rep, mixed != 0, kappa, 3, v64, f64, v32, f32, &ms) < 0) continue;
-      if (ms < best_ms) { best_ms = ms; best = c; }
+    std::vector<double*> xs(sub.size(), nullptr), fs(sub.size(), nullptr);
+    int st = MG_OK;
+    for (size_t i = 0; i < sub.size() && st == MG_OK; ++i) {
+      if (cudaMalloc(&xs[i], len * 8) != cudaSuccess || cudaMalloc(&fs[i], len * 8) != cudaSuccess) st = MG_ERR_NOMEM;
+      else if (cudaMemset(fs[i], 0x3f, len * 8) != cudaSuccess) st = MG_ERR_CUDA;  // a positive constant
     }
-    cudaFree(v64); cudaFree(f64); cudaFree(v32); cudaFree(f32);
-    if (best < 0) return MG_ERR_CUDA;
-    for (mg_handle h : b->inst)
-      if (h->n == n) KC_TRY(mg_set_option(h, key, best));
-    if (chosen) { chosen[2 * pos] = n; chosen[2 * pos + 1] = best; }
+    auto apply = [&](const std::vector<mg_handle>& hs, const TuneShape& t) -> int {
+      for (mg_handle h : hs) {
+        KC_TRY(mg_set_option(h, thr_key, t.thr));
+        KC_TRY(mg_set_option(h, MG_OPT_FUSED_CALL, t.fused));
+        KC_TRY(mg_set_option(h, MG_OPT_CONDENSED_CHILDREN, t.condensed));
+        KC_TRY(mg_set_option(h, MG_OPT_TMA_PASSES, t.tma));
+      }
+      return MG_OK;
+    };
+    auto measure = [&](const TuneShape& t, float* ms) -> int {
+      KC_TRY(apply(sub, t));
+      return time_subbatch(sub, b->stream, kappa, mixed != 0, TUNE_ITERS, xs, fs, ms);
+    };
+    TuneShape best{thr_key == MG_OPT_COARSE_N ? sub[0]->coarse_n : sub[0]->coarse_n32, sub[0]->fused,
+                   sub[0]->condense, sub[0]->tma32};
+    float best_ms = 1e30f;
+    // coordinate descent: the threshold, then fused call x condensed children, then the FP32
+    // large-level passes (sides >= 1023 only)
+    if (st == MG_OK) {
+      for (int c : cand_thr) {
+        TuneShape t = best;
+        t.thr = c;
+        float ms;
+        if (measure(t, &ms) == MG_OK && ms < best_ms) { best_ms = ms; best.thr = c; }
+      }
+      const TuneShape base = best;
+      for (int fc = 0; fc < 4; ++fc) {
+        TuneShape t = base;
+        t.fused = fc & 1;
+        t.condensed = (fc >> 1) & 1;
+        if (t.fused == base.fused && t.condensed == base.condensed) continue;
+        float ms;
+        if (measure(t, &ms) == MG_OK && ms < best_ms) { best_ms = ms; best = t; }
+      }
+      if (mixed && n >= F32_FAST_MIN) {
+        TuneShape t = best;
+        t.tma = 1 - best.tma;
+        float ms;
+        if (measure(t, &ms) == MG_OK && ms < best_ms) { best_ms = ms; best = t; }
+      }
+    }
+    for (size_t i = 0; i < sub.size(); ++i) {
+      if (xs[i]) cudaFree(xs[i]);
+      if (fs[i]) cudaFree(fs[i]);
+    }
+    cudaGetLastError();
+    if (st < 0) return st;
+    if (best_ms >= 1e30f) return MG_ERR_CUDA;
+    KC_TRY(apply(all, best));
+    if (chosen) { chosen[2 * pos] = n; chosen[2 * pos + 1] = best.thr; }
     ++pos;
   }
   batch_drop_graph(b);
+  return MG_OK;
+}
+
+int mg_batch_instance(mg_batch b, int index, mg_handle* out) {
+  if (!b || !out || index < 0 || index >= (int)b->inst.size()) return MG_ERR_ARG;
+  *out = b->inst[index];
   return MG_OK;
 }
 

@@ -497,8 +497,9 @@ struct CoarseArgs {
   const T* cmap;
   int dcond, ncls;
   int map_smem;    // copy the maps into shared memory (after the levels) at the start of the walk
-  // basis != 0: map mode. Block b runs one call of counter k1 at the top level from v = e_b
-  // (b < S) or f = e_(b-S) and writes the result to cmap_out + b * S.
+  // basis != 0: map mode. basis = 1: block b runs one call of counter k1 at the top level from
+  // v = e_b (b < S) or f = e_(b-S); basis = 2: block b runs the calls k1, k2 from v = 0 with
+  // f = e_b. Each block writes its result to cmap_out + b * S.
   int basis;
   T* cmap_out;
 };
@@ -643,9 +644,10 @@ __device__ __forceinline__ void coarse_body(const CoarseArgs<T>& a, unsigned cha
     T* vv = vbuf(0, 0);
     if (a.basis) {
       const int S = s * s, b = blockIdx.x;
+      const int bv = a.basis == 2 ? -1 : b, bf = a.basis == 2 ? b : b - S;
       for (int k = threadIdx.x; k < S; k += NT) {
-        vv[pos(0, k)] = (b < S && k == b) ? T(1) : T(0);
-        fv[pos(0, k)] = (b >= S && k == b - S) ? T(1) : T(0);
+        vv[pos(0, k)] = (k == bv) ? T(1) : T(0);
+        fv[pos(0, k)] = (k == bf) ? T(1) : T(0);
       }
     } else {
       for (int k = threadIdx.x; k < s * s; k += NT) {
@@ -932,6 +934,85 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// Condensed child calls. The two calls that a call at level lc-1 makes at level lc (counters k and
+// k-1, the first from v = 0, Algorithm 3) together with everything below them are one linear map of
+// the restricted residual: v_lc = P_c f_lc, c = min(k, levels - lc + 1) (a call's subtree depends on
+// its counter only up to the number of levels below it). P_c is computed once per handle by the
+// FP64 coarse kernel in map mode (f = e_b, basis = 2) and stored row by row (pitch pld, rows padded
+// with zeros to 16 bytes) in the cycle's precision. Applying it is one matrix-vector product
+// instead of the walk's dozens of barrier-separated phases on one SM; it is the same linear map,
+// rounded once per entry and once per dot product instead of along the walk.
+//
+// One warp per row: lane l accumulates the 16-byte chunks l, l + 32, ... of the row in order, then
+// a fixed shuffle tree sums the lanes, so a row's result does not depend on which CTA computes it.
+// Rows are dealt to warps round-robin over `parts` CTAs (the fused call's cluster, or the grid of
+// children_kernel).
+// ---------------------------------------------------------------------------------------------
+template <typename T, int NT>
+__device__ __forceinline__ void children_matvec(const T* __restrict__ pmap, int pld, const CoarseArgs<T>& a,
+                                                int part, int parts, T* fs) {
+  const int s = a.n_lc, S = s * s;
+  for (int b = threadIdx.x; b < pld; b += NT) {
+    T val = T(0);
+    if (b < S) {
+      const int j = b / s, i = b - j * s;
+      val = a.f[(size_t)j * a.ldf + i];
+    }
+    fs[b] = val;
+  }
+  __syncthreads();
+  constexpr int NW = NT / 32;
+  constexpr int VW = 16 / sizeof(T);  // elements per 16-byte chunk
+  const int lane = threadIdx.x & 31;
+  for (int k = part * NW + (threadIdx.x >> 5); k < S; k += parts * NW) {
+    const T* row = pmap + (size_t)k * pld;
+    T acc = T(0);
+    for (int b = VW * lane; b < pld; b += 32 * VW) {
+      if constexpr (VW == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(row + b);
+        const float4 x = *reinterpret_cast<const float4*>(fs + b);
+        acc = fma(q.x, x.x, acc);
+        acc = fma(q.y, x.y, acc);
+        acc = fma(q.z, x.z, acc);
+        acc = fma(q.w, x.w, acc);
+      } else {
+        const double2 q = *reinterpret_cast<const double2*>(row + b);
+        const double2 x = *reinterpret_cast<const double2*>(fs + b);
+        acc = fma(q.x, x.x, acc);
+        acc = fma(q.y, x.y, acc);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      const int j = k / s, i = k - j * s;
+      a.v[(size_t)j * a.ldv + i] = acc;
+    }
+  }
+}
+
+constexpr int CHILD_PARTS = 16;  // CTAs of children_kernel (the fused call's cluster size)
+
+// The condensed child calls as their own launch (calls not fused with their parent's passes).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) children_kernel(const T* __restrict__ pmap, int pld, const CoarseArgs<T> a) {
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  children_matvec<T, NT>(pmap, pld, a, blockIdx.x, gridDim.x, reinterpret_cast<T*>(smem_raw));
+}
+
+// Column-major FP64 maps (entry (k, b) at b * S + k, as map mode writes them) to row-major maps in
+// T with row pitch pld and zero padding.
+template <typename T>
+__global__ void pmap_convert_kernel(const double* __restrict__ src, int S, int pld, T* __restrict__ dst) {
+  const size_t tot = (size_t)S * pld;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e / pld), b = (int)(e - (size_t)k * pld);
+    dst[e] = b < S ? (T)src[(size_t)b * S + k] : T(0);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // One call at the level just above the coarse kernel's, in one launch: a cluster with one CTA per
 // TILE x TILE tile of that level runs pass A, then its CTA of rank 0 walks the coarse calls below
 // it (the coarse kernel's work), then the cluster runs pass B. The two hand-offs go through global
@@ -952,7 +1033,8 @@ __host__ __device__ constexpr size_t call_cluster_smem_tiles(int nu1, int nu2) {
 
 template <typename T, int NT, int TILE, bool NS = false>
 __global__ void __launch_bounds__(NT)
-    call_cluster_kernel(const PassAArgs<T> pa, const CoarseArgs<T> ca, const PassBArgs<T> pb) {
+    call_cluster_kernel(const PassAArgs<T> pa, const CoarseArgs<T> ca, const PassBArgs<T> pb, const T* pmap,
+                        int pld) {
   if (pa.skip && *pa.skip) return;  // the same flag for every CTA: the whole cluster returns
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
@@ -963,7 +1045,11 @@ __global__ void __launch_bounds__(NT)
     __syncthreads();  // the next tile reuses the shared memory
   }
   cluster.sync();
-  if (rank == 0) coarse_body<T, NT, false, NS>(ca, smem_raw);
+  if (pmap) {  // the child calls condensed: every CTA computes its share of v_lc = P_c f_lc
+    children_matvec<T, NT>(pmap, pld, ca, rank, size, reinterpret_cast<T*>(smem_raw));
+  } else if (rank == 0) {
+    coarse_body<T, NT, false, NS>(ca, smem_raw);
+  }
   cluster.sync();
   for (int t = rank; t < ntiles; t += size) {
     pass_b_tile<T, TILE, TILE, NT, NS>(pb, t % tx, t / tx, 0, smem_raw);
@@ -1328,7 +1414,7 @@ enum {
   NSCAL = 8
 };
 // Integer slots
-enum { I_DONE = 0, I_COUNT, I_MAX, NINT = 4 };
+enum { I_DONE = 0, I_COUNT, I_MAX, I_ERR, NINT = 4 };  // I_ERR: set by a kernel whose bounded wait ran out
 
 template <int NT>
 __global__ void __launch_bounds__(NT) sum_to_scalar_kernel(const double* partial, int np, double* out) {

@@ -21,7 +21,7 @@ MG_KAPPA_W = 0x7FFFFFFF
 CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
 MG_OPT_OMEGA, MG_OPT_COARSE_N, MG_OPT_LEVELS, MG_OPT_N, MG_OPT_LAUNCHES, MG_OPT_COARSE_N32 = 1, 2, 3, 4, 5, 6
 MG_OPT_COARSE_OP, MG_OPT_STOP, MG_OPT_SMOOTHER, MG_OPT_COARSENING, MG_OPT_PRECOND = 7, 8, 9, 10, 11
-MG_OPT_CONV_X, MG_OPT_CONV_Y, MG_OPT_FUSED_CALL = 12, 13, 14
+MG_OPT_CONV_X, MG_OPT_CONV_Y, MG_OPT_FUSED_CALL, MG_OPT_TMA_PASSES, MG_OPT_CONDENSED_CHILDREN = 12, 13, 14, 15, 16
 SMOOTHERS = {"jacobi": 0, "zebra": 1, "xzebra": 2}
 COARSENINGS = {"full": 0, "y": 1}
 
@@ -65,6 +65,7 @@ SIGNATURES = {
     "mg_batch_autotune": (_i, [_h, _i, _i, _ip]),
     "mg_batch_solve": (_i, [_h, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, _d, _i, _i, _ip, _dp]),
     "mg_batch_set_option": (_i, [_h, _i, _d]),
+    "mg_batch_instance": (_i, [_h, _i, ctypes.POINTER(_h)]),
     "mg_batch_size": (_i, [_h, _ip]),
     "mg_batch_destroy": (_i, [_h]),
     "mg_fp64_rate": (_i, [_dp]),
@@ -141,7 +142,22 @@ class Multigrid:
             self.set_option(MG_OPT_CONV_X, convection[0])
             self.set_option(MG_OPT_CONV_Y, convection[1])
 
+    @classmethod
+    def _borrow(cls, handle, n, owner):
+        """A Multigrid over a handle another object owns (a batch instance): close() releases nothing."""
+        m = cls.__new__(cls)
+        m._h, m._owner = handle, owner
+        m.n = int(n)
+        lv = ctypes.c_double()
+        _check(_lib.mg_get_option(handle, MG_OPT_LEVELS, ctypes.byref(lv)), "mg_get_option")
+        m.levels = int(lv.value)
+        m.smoother, m.coarsening = None, "full"
+        return m
+
     def close(self):
+        if getattr(self, "_owner", None) is not None:
+            self._h, self._owner = None, None
+            return
         if getattr(self, "_h", None):
             _lib.mg_destroy(self._h)
             self._h = None
@@ -316,10 +332,30 @@ class Batch:
             pass
 
     def autotune(self, kappa, mixed=False):
-        """Returns {n: chosen coarse-kernel threshold}."""
+        """Returns {n: chosen coarse-kernel threshold}; shapes() gives every tuned option."""
         out = (ctypes.c_int * (2 * len(set(self.ns))))()
         _check(_lib.mg_batch_autotune(self._h, int(kappa), int(bool(mixed)), out), "mg_batch_autotune")
         return {out[2 * i]: out[2 * i + 1] for i in range(len(set(self.ns)))}
+
+    def instance(self, index):
+        """Instance `index` as a Multigrid that borrows the batch's handle (not destroyed by it)."""
+        h = _h()
+        _check(_lib.mg_batch_instance(self._h, int(index), ctypes.byref(h)), "mg_batch_instance")
+        return Multigrid._borrow(h, self.ns[index], self)
+
+    def shapes(self):
+        """{n: {option: value}} of the first instance of each grid side (the autotuner sets every
+        instance of a side alike)."""
+        out = {}
+        for i, n in enumerate(self.ns):
+            if n in out:
+                continue
+            m = self.instance(i)
+            out[n] = {"coarse_n": int(m.get_option(MG_OPT_COARSE_N)), "coarse_n32": int(m.get_option(MG_OPT_COARSE_N32)),
+                      "fused_call": int(m.get_option(MG_OPT_FUSED_CALL)),
+                      "condensed_children": int(m.get_option(MG_OPT_CONDENSED_CHILDREN)),
+                      "tma_passes": int(m.get_option(MG_OPT_TMA_PASSES))}
+        return out
 
     def solve(self, xs, fs, kappa, tol, max_iters, mixed=False):
         """xs, fs: lists of float64 CUDA tensors (n_i, n_i). Returns (status, iters list, relres list)."""

@@ -86,6 +86,34 @@ def test_fp32_cycle_close_to_fp64_oracle(lib, n, levels, theta, eps, kappa):
         assert rel(got, ref) <= F32_CYCLE_TOL
 
 
+@pytest.mark.parametrize("n,levels,kappa", [(1023, 10, 3), (2047, 11, 1), (4095, 12, 4)])
+def test_fp32_cycle_tensor_copy_passes_and_tile_passes_agree(lib, n, levels, kappa):
+    """The large-level FP32 passes exist twice: persistent kernels fed by tensor copies (default)
+    and the shared-memory tile / register-pipeline kernels (MG_OPT_TMA_PASSES = 0). Both must meet
+    the calibrated FP32 bound against the FP64 oracle, and a few cycles of each stay together
+    (a wrong tile edge in either would separate them element-wise)."""
+    from parity import rel_elem, rel_l2
+    theta, eps = 2.4, 3e-4
+    h = oracle.Hierarchy(n, levels, theta, eps)
+    f = rhs_uniform(n, 5)
+    ref = oracle.cycle(h, np.zeros((n, n)), f, kappa)
+    cal = oracle_fp32_cycle(h, f, kappa)
+    mg = lib.Multigrid(n, eps, theta, levels)
+    out = {}
+    for tma in (1, 0):
+        mg.set_option(lib.MG_OPT_TMA_PASSES, tma)
+        v32 = dev(np.zeros((n, n)), "float32")
+        mg.kcycle_f32(v32, dev(f, "float32"), kappa)
+        got = host(v32)
+        assert rel_l2(got, ref) <= CAL_FACTOR * rel_l2(cal, ref) + 16 * U32, tma
+        assert rel_elem(got, ref) <= CAL_FACTOR * rel_elem(cal, ref) + 16 * U32, tma
+        out[tma] = got
+    assert mg.get_option(lib.MG_OPT_TMA_PASSES) == 0
+    d = rel(out[1], out[0])
+    print(f"n={n} kappa={kappa}: tensor-copy vs tile passes {d:.2e}")
+    assert d <= 2 * CAL_FACTOR * rel_l2(cal, ref) + 16 * U32
+
+
 @pytest.mark.parametrize("kappa", [1, 2, 3, KAPPA_W])
 def test_mixed_solve_small_meets_tolerance_and_error(lib, kappa):
     n, levels, theta, eps = 127, 7, math.pi / 6, 1e-2

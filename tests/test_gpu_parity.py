@@ -231,17 +231,23 @@ def test_counters_match_closed_forms(lib, kappa):
 def test_level_grid_reports_the_launch_shapes(lib):
     """CTAs per pass launch at 4095^2: 64x32 tiles at 4095 and 2047 (about two waves), 32^2 at 1023
     and 511, 16^2 at 255, 8^2 below (about one wave), one coarse-kernel CTA at 15^2 and below. FP32:
-    pass B as the register pipelines at 4095 (35 strips of 120 columns, 4 per CTA, chunks of 64
-    rows), the shared-memory tiles of 112 x 16 at 2047, the FP32 coarse kernel from 31^2. The level
-    just above the coarse kernel runs its calls as one cluster launch: 16 CTAs of 8^2 tiles at 31^2
-    (FP64), of 16^2 tiles at 63^2 (FP32); without the fused calls 64 CTAs at 63^2 (FP32)."""
+    the persistent tensor-copy passes at 4095, 2047 and 1023 (one CTA per SM: 2240, 576 and 288
+    tiles of 120 columns), the FP32 coarse kernel from 31^2; with MG_OPT_TMA_PASSES = 0 pass B as
+    the register pipelines at 4095 (35 strips of 120 columns, 4 per CTA, chunks of 64 rows) and the
+    shared-memory tiles of 112 x 16 at 2047. The level just above the coarse kernel runs its calls
+    as one cluster launch: 16 CTAs of 8^2 tiles at 31^2 (FP64), of 16^2 tiles at 63^2 (FP32);
+    without the fused calls 64 CTAs at 63^2 (FP32)."""
     mg = lib.Multigrid(4095, 1e-4, math.pi / 3, 12)
     fp64 = [mg.level_grid(l) for l in range(12)]
     assert [c for _, c in fp64] == [64 * 128, 32 * 64, 32 * 32, 16 * 16, 16 * 16, 16 * 16, 8 * 8, 4 * 4,
                                      1, 1, 1, 1]
     assert [m for m, _ in fp64] == [2 ** (12 - l) - 1 for l in range(12)]
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
     fp32 = [mg.level_grid(l, fp32=True)[1] for l in range(12)]
-    assert fp32[:2] == [9 * 64, 19 * 128] and fp32[6] == 16 and fp32[7:] == [1] * 5
+    assert fp32[:3] == [min(sms, 2240), min(sms, 576), min(sms, 288)] and fp32[6] == 16 and fp32[7:] == [1] * 5
+    mg.set_option(lib.MG_OPT_TMA_PASSES, 0)
+    assert [mg.level_grid(l, fp32=True)[1] for l in range(2)] == [9 * 64, 19 * 128]
     mg.set_option(lib.MG_OPT_FUSED_CALL, 0)
     assert mg.level_grid(6, fp32=True)[1] == 64 and mg.level_grid(7)[1] == 16
     zebra = lib.Multigrid(127, 1e-4, math.pi / 3, 7, smoother="zebra")
