@@ -807,7 +807,28 @@ def main():
             q = sorted(it_b)
             entry = {"ms_one_launch": round(ms_b, 1), "converged": len(conv), "of": len(ns),
                      "iterations_quartiles": [q[0], q[len(q) // 4], q[len(q) // 2], q[3 * len(q) // 4], q[-1]],
-                     "autotuned_coarse_n": {str(k): v for k, v in chosen.items()}}
+                     "autotuned_coarse_n": {str(k): v for k, v in chosen.items()},
+                     "autotuned_shapes": {str(k): v for k, v in bt.shapes().items()}}
+            if mixed:
+                # the same problems solved one after another: each instance alone through its own
+                # handle (the batch's, with the same tuned options), one graph launch per solve
+                solo = [bt.instance(i) for i in range(len(ns))]
+                ys = [torch.zeros_like(xb) for xb in xs_b]
+                for i, m in enumerate(solo):
+                    m.solve_mixed(ys[i], fs_b[i], 3, tol, 1, history=False)  # builds its graph
+                for y in ys:
+                    y.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for i, m in enumerate(solo):
+                    m.solve_mixed(ys[i], fs_b[i], 3, tol, 3000, history=False)
+                torch.cuda.synchronize()
+                seq_ms = 1e3 * (time.perf_counter() - t0)
+                entry["sequential_ms"] = round(seq_ms, 1)
+                entry["batch_speedup_vs_sequential"] = round(seq_ms / ms_b, 3)
+                for m in solo:
+                    m.close()
+                del ys
             if mixed:
                 # error against each sampled instance's FP64 solve to REF_TOL (a standalone handle)
                 errs = []

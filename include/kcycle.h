@@ -92,7 +92,14 @@ typedef enum {
                               lose its upwind structure on coarse grids and the cycle can diverge;
                               MG_OPT_COARSE_OP = 1 (rediscretized upwind operators) is the stable
                               choice. Recomputes the stencils.                                    */
-  MG_OPT_FUSED_CALL = 14,  /* 1 (default): with damped Jacobi and full coarsening, each call at the
+  MG_OPT_FUSED_CALL = 14,  /* 2: as 1, and each call two levels above the coarse-level
+                              kernel's (not level 0), whose child calls' own children are condensed
+                              (MG_OPT_CONDENSED_CHILDREN), runs with those child calls as one launch
+                              of a 16-CTA cluster: pass A, per child call pass A, the condensed
+                              matrix-vector product and pass B, then pass B; same results bit for
+                              bit (measured no faster inside a graph: its 16 CTAs do that level's
+                              passes on 16 SMs). 1 (default): with damped Jacobi and full
+                              coarsening, each call at the
                               level just above the coarse-level kernel's (FP64 and FP32 cycles)
                               runs as one launch of a thread-block cluster with one CTA per tile
                               of that level, at most 16 (pass A over the tiles, the coarse walk on
@@ -226,7 +233,9 @@ int mg_stencils(mg_handle h, double* out, int max_levels, int* written);
 
 /* Call counts of one kappa-cycle of this handle's hierarchy: calls_per_level[l] for l = 0..levels-1
  * (Proposition 2.2), the kernel launches of its cycle graph and the calls served by the coarse-level
- * kernel. All host, nullable; calls_per_level holds levels entries. No device work. */
+ * kernel. All host, nullable; calls_per_level holds levels entries. No device work beyond computing
+ * the condensed child-call maps if they are not built yet (which launches may be fused depends on
+ * them). */
 int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* launches,
                 long long* coarse_calls);
 

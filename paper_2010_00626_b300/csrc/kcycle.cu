@@ -110,7 +110,8 @@ struct mg_ctx {
   int coarse_n = 15;  // largest side handled by the coarse kernel (FP64 cycles)
   int lc = 0;         // first level handled by the coarse kernel (FP64 cycles)
   int lc32 = 0;       // same for the FP32 cycles of the mixed path
-  int fused = 1;         // calls just above the coarse kernel as one cluster launch (MG_OPT_FUSED_CALL)
+  int fused = 1;         // calls one (1) or two (2) levels above the coarse kernel as one cluster launch
+                         // (MG_OPT_FUSED_CALL)
   int tma32 = 1;         // FP32 large-level passes fed by tensor copies (MG_OPT_TMA_PASSES)
   int sms = 148;         // multiprocessors of the device (grid of the persistent passes)
   int coarse_n32 = 31;  // FP32 threshold: one SM does FP32 at 64x the FP64 rate, so the single-CTA
@@ -480,9 +481,27 @@ int make_map_f32(CUtensorMap* m, const float* base, int n_cols, int n_rows, int 
   return MG_OK;
 }
 
-// Output rows per tile: tall tiles where the level has rows to spare (less halo recomputed), lower
-// ones where the tiles would not fill the device.
-int tma_ty(int n) { return n >= 2047 ? 64 : 32; }
+// Output rows per tile of each tensor-copy pass: the window (tile plus halo rows, double-buffered)
+// sized so that two (pass A from v, pass B) or three (pass A from zero) CTAs of 8 warps share an
+// SM, whose copies and barriers then overlap each other's arithmetic.
+enum TmaKind { TMA_A_ZERO = 0, TMA_A = 1, TMA_B = 2 };
+int tma_ty(int kind) { return kind == TMA_A ? 24 : 32; }
+size_t tma_smem(int kind) {
+  return (kind == TMA_B ? tm_smem_b(tma_ty(kind), 2) : tm_smem_a(tma_ty(kind), 2, kind == TMA_A_ZERO)) + 1024;
+}
+
+// CTAs of a tensor-copy pass: every resident slot of the device, at most one per tile.
+template <typename K>
+int tma_grid(const mg_ctx* h, K kern, int kind, int tiles) {
+  static int per_sm[3] = {0, 0, 0};
+  if (per_sm[kind] == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, TM_NT, tma_smem(kind)) != cudaSuccess || b < 1) b = 1;
+    cudaGetLastError();
+    per_sm[kind] = b;
+  }
+  return std::min(tiles, h->sms * per_sm[kind]);
+}
 
 bool aligned16(const void* p, int ld) { return ((uintptr_t)p & 15) == 0 && (ld & 3) == 0; }
 
@@ -499,10 +518,10 @@ bool tma_pass_b_ok(const mg_ctx* h, const PassBArgs<float>& a) {
          tensor_map_encoder() != nullptr;
 }
 
-TmaPassArgs tma_args(const mg_ctx* h, int n, int level, const float* coef, const int* skip, int* err) {
+TmaPassArgs tma_args(const mg_ctx* h, int kind, int n, int level, const float* coef, const int* skip, int* err) {
   TmaPassArgs t;
   t.n = n;
-  t.ty = tma_ty(n);
+  t.ty = tma_ty(kind);
   t.tiles_x = (n + TM_TX - 1) / TM_TX;
   t.tiles = t.tiles_x * ((n + t.ty - 1) / t.ty);
   t.level = level;
@@ -518,7 +537,8 @@ TmaPassArgs tma_args(const mg_ctx* h, int n, int level, const float* coef, const
 }
 
 int launch_pass_a_tma32(mg_ctx* h, const PassAArgs<float>& a, cudaStream_t s) {
-  TmaPassArgs t = tma_args(h, a.n, a.level, a.coef, a.skip, h->ints + I_ERR);
+  const int kind = a.vin ? TMA_A : TMA_A_ZERO;
+  TmaPassArgs t = tma_args(h, kind, a.n, a.level, a.coef, a.skip, h->ints + I_ERR);
   t.vout = a.vout;
   t.ldvout = a.ldvout;
   t.fc = a.fc;
@@ -528,17 +548,16 @@ int launch_pass_a_tma32(mg_ctx* h, const PassAArgs<float>& a, cudaStream_t s) {
   KC_TRY(make_map_f32(&mf, a.f, a.n, a.n, a.ldf, TM_P, R));
   if (a.vin) KC_TRY(make_map_f32(&mv, a.vin, a.n, a.n, a.ldvin, TM_P, R));
   else mv = mf;  // not read from a zero start
-  const int grid = std::min(t.tiles, h->sms);
   if (a.vin)
-    pass_a_tma32<false><<<grid, TM_NT, tm_smem_a(t.ty, 2, false) + 1024, s>>>(mv, mf, t);
+    pass_a_tma32<false><<<tma_grid(h, pass_a_tma32<false>, kind, t.tiles), TM_NT, tma_smem(kind), s>>>(mv, mf, t);
   else
-    pass_a_tma32<true><<<grid, TM_NT, tm_smem_a(t.ty, 2, true) + 1024, s>>>(mv, mf, t);
+    pass_a_tma32<true><<<tma_grid(h, pass_a_tma32<true>, kind, t.tiles), TM_NT, tma_smem(kind), s>>>(mv, mf, t);
   KC_CUDA(cudaGetLastError());
   return MG_OK;
 }
 
 int launch_pass_b_tma32(mg_ctx* h, const PassBArgs<float>& a, cudaStream_t s) {
-  TmaPassArgs t = tma_args(h, a.n, a.level, a.coef, a.skip, h->ints + I_ERR);
+  TmaPassArgs t = tma_args(h, TMA_B, a.n, a.level, a.coef, a.skip, h->ints + I_ERR);
   t.vout = a.vout;
   t.ldvout = a.ldvout;
   const int nc = (a.n - 1) / 2;
@@ -546,8 +565,7 @@ int launch_pass_b_tma32(mg_ctx* h, const PassBArgs<float>& a, cudaStream_t s) {
   KC_TRY(make_map_f32(&mv, a.vin, a.n, a.n, a.ldvin, TM_P, tm_rows_b(t.ty, 2)));
   KC_TRY(make_map_f32(&mf, a.f, a.n, a.n, a.ldf, TM_P, tm_rows_b(t.ty, 2)));
   KC_TRY(make_map_f32(&mc, a.vc, nc, nc, a.ldc, TM_CP, tm_crows_b(t.ty, 2)));
-  const int grid = std::min(t.tiles, h->sms);
-  pass_b_tma32<<<grid, TM_NT, tm_smem_b(t.ty, 2) + 1024, s>>>(mv, mf, mc, t);
+  pass_b_tma32<<<tma_grid(h, pass_b_tma32, TMA_B, t.tiles), TM_NT, tma_smem(TMA_B), s>>>(mv, mf, mc, t);
   KC_CUDA(cudaGetLastError());
   return MG_OK;
 }
@@ -1146,9 +1164,103 @@ int emit_call_fused(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero
   return MG_OK;
 }
 
+// Two-level fused calls (call2_cluster_kernel): a call two levels above the coarse kernel's with its
+// child calls, whose own children are condensed. Tiles of 32 (FP32) / 16 (FP64) at that level, so a
+// 127^2 (FP32) or 63^2 (FP64) level has 16 of them, one per CTA of the cluster.
+template <typename T>
+constexpr int call2_tile() { return std::is_same<T, double>::value ? 16 : 32; }
+
+template <typename T>
+bool call2_cluster_supported() {
+  static int ok = -1;
+  if (ok < 0) {
+    auto kern = call2_cluster_kernel<T, nt_coarse<T>(), call2_tile<T>(), call_tile<T>()>;
+    const size_t sm = call2_smem<T, call2_tile<T>(), call_tile<T>()>(MAX_NU, MAX_NU);
+    ok = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = CALL_MAX_CTAS;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(CALL_MAX_CTAS);
+      cfg.blockDim = dim3(nt_coarse<T>());
+      cfg.dynamicSmemBytes = sm;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int clusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters >= 1) ok = 1;
+    }
+    cudaGetLastError();
+  }
+  return ok == 1;
+}
+
+template <typename T>
+bool fused2_ok(const mg_ctx* h, int l, int kappa, bool adjoint) {
+  const int lc = lc_of<T>(h);
+  if (h->fused < 2 || adjoint || h->smoother != 0 || h->semi || h->nonsym || l < 1 || l + 2 != lc) return false;
+  if (h->nu1 > MAX_NU || h->nu2 > MAX_NU) return false;
+  const int t1 = (h->lv[l].n + call2_tile<T>() - 1) / call2_tile<T>();
+  if (t1 * t1 > CALL_MAX_CTAS || call_ctas<T>(h, l + 1) > CALL_MAX_CTAS) return false;
+  int k1, k2, ld = 0;
+  child_counters(kappa, false, &k1, &k2);
+  for (int c : {k1, k2}) {  // the grandchildren of each child call must be condensed
+    if (c == 0) continue;
+    int g1, g2;
+    child_counters(c, false, &g1, &g2);
+    if (!child_map<T>(h, g1, g2, 1, false, &ld)) return false;
+  }
+  return call2_cluster_supported<T>();
+}
+
+template <typename T>
+int emit_call_fused2(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero, const int* skip, cudaStream_t s) {
+  Call2Args<T> a;
+  a.pa1 = pass_a_args(h, b, l, zero, h->nu1, skip, false, nullptr);
+  a.pb1 = pass_b_args(h, b, l, h->nu2, nullptr, skip, false);
+  a.pa2[0] = pass_a_args(h, b, l + 1, true, h->nu1, skip, false, nullptr);
+  a.pa2[1] = pass_a_args(h, b, l + 1, false, h->nu1, skip, false, nullptr);
+  a.pb2 = pass_b_args(h, b, l + 1, h->nu2, nullptr, skip, false);
+  int k1, k2;
+  child_counters(kappa, false, &k1, &k2);
+  a.children = k2 > 0 ? 2 : 1;
+  a.cc = coarse_args(h, b, 1, 0, 1, false, skip);  // v, f, pitches and side of level l + 2
+  const int ks[2] = {k1, k2};
+  for (int c = 0; c < 2; ++c) {
+    a.pmap[c] = nullptr;
+    if (ks[c] == 0) continue;
+    int g1, g2;
+    child_counters(ks[c], false, &g1, &g2);
+    a.pmap[c] = child_map<T>(h, g1, g2, 1, false, &a.pld);
+  }
+  constexpr int NT = nt_coarse<T>();
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CALL_MAX_CTAS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(CALL_MAX_CTAS);
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = std::max(call2_smem<T, call2_tile<T>(), call_tile<T>()>(h->nu1, h->nu2),
+                                  (size_t)a.pld * sizeof(T));
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ++h->launch_count;
+  prof_begin(h, K_CALL, l, s);
+  KC_CUDA(cudaLaunchKernelEx(&cfg, call2_cluster_kernel<T, NT, call2_tile<T>(), call_tile<T>()>, a));
+  prof_end(h, s);
+  return MG_OK;
+}
+
 template <typename T>
 int emit_call(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero, bool adjoint, bool norm,
               const int* skip, cudaStream_t s) {
+  if (fused2_ok<T>(h, l, kappa, adjoint)) return emit_call_fused2(h, b, l, kappa, zero, skip, s);
   if (fused_call_ok<T>(h, l, adjoint)) return emit_call_fused(h, b, l, kappa, zero, skip, s);
   const int nu_pre = adjoint ? h->nu2 : h->nu1;
   const int nu_post = adjoint ? h->nu1 : h->nu2;
@@ -1693,6 +1805,8 @@ int mg_setup(int n, double eps, double theta, int levels, int nu1, int nu2, mg_h
   call_cluster_supported<double, false>();
   call_cluster_supported<double, true>();
   call_cluster_supported<float, false>();
+  call2_cluster_supported<double>();
+  call2_cluster_supported<float>();
   h->ok = true;
   *out = h;
   return MG_OK;
@@ -1766,7 +1880,7 @@ int mg_set_option(mg_handle h, int key, double value) {
       return MG_OK;
     }
     case MG_OPT_FUSED_CALL: {
-      if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
+      if (!(value == 0.0 || value == 1.0 || value == 2.0)) return MG_ERR_ARG;
       h->fused = (int)value;
       drop_graphs(h);
       return MG_OK;
@@ -2105,19 +2219,33 @@ int mg_stencils(mg_handle h, double* out, int max_levels, int* written) {
 int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* launches, long long* coarse_calls) {
   if (!valid_handle(h)) return MG_ERR_STATE;
   if (kappa < 1) return MG_ERR_ARG;
+  ensure_maps(h);  // whether calls run condensed or fused depends on the maps being available
   // walk Algorithm 3's recursion, counting only
   std::vector<long long> calls(h->levels, 0);
-  long long fine_launches = 0, coarse = 0;
+  long long fine_launches = 0, coarse = 0, absorbed = 0;
   struct Walk {
     mg_ctx* h;
     std::vector<long long>& calls;
     long long& fine_launches;
     long long& coarse;
-    void call(int l, int kap) {
+    long long& absorbed;  // calls just above the coarse kernel's that run inside a two-level launch
+    void call(int l, int kap, bool inside = false) {
       calls[l] += 1;
       if (l >= h->lc) ++coarse;
       if (l == h->levels - 1) {
         if (h->semi) ++fine_launches;  // the one-row line solve
+        return;
+      }
+      if (inside) {  // part of its parent's two-level launch
+        ++absorbed;
+        call(l + 1, kap);
+        if (kap > 1) call(l + 1, kap - 1);
+        return;
+      }
+      if (l < h->lc && fused2_ok<double>(h, l, kap, false)) {
+        ++fine_launches;  // one launch for the call and its child calls
+        call(l + 1, kap, true);
+        if (kap > 1) call(l + 1, kap - 1, true);
         return;
       }
       if (l < h->lc) {
@@ -2132,10 +2260,10 @@ int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* l
       call(l + 1, kap);
       if (kap > 1) call(l + 1, kap - 1);
     }
-  } w{h, calls, fine_launches, coarse};
+  } w{h, calls, fine_launches, coarse, absorbed};
   w.call(0, std::min(kappa, h->levels + 1));
   // one coarse-kernel launch serves both calls of a fine parent (or the whole cycle when lc == 0)
-  const long long coarse_launches = h->lc >= h->levels ? 0 : (h->lc == 0 ? 1 : calls[h->lc - 1]);
+  const long long coarse_launches = h->lc >= h->levels ? 0 : (h->lc == 0 ? 1 : calls[h->lc - 1] - absorbed);
   if (calls_per_level)
     for (int l = 0; l < h->levels; ++l) calls_per_level[l] = calls[l];
   if (launches) *launches = fine_launches + coarse_launches;
@@ -2162,14 +2290,19 @@ int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas) {
     *ctas = 1;
     return MG_OK;
   }
+  if (h->fused >= 2 && h->condense && !h->nonsym && level >= 1 && level + 2 == lc && h->lv[lc].n <= PM_MAX_SIDE &&
+      (fp32 ? call2_cluster_supported<float>() : call2_cluster_supported<double>())) {
+    *ctas = CALL_MAX_CTAS;  // the call runs with its child calls as one cluster launch
+    return MG_OK;
+  }
   if (fp32 ? fused_call_ok<float>(h, level, false, lc) : fused_call_ok<double>(h, level, false, lc)) {
     *ctas = fp32 ? call_ctas<float>(h, level) : call_ctas<double>(h, level);
     return MG_OK;
   }
   if (fp32 && h->tma32 && n >= F32_FAST_MIN && h->nu1 == 2 && h->nu2 == 2 && tensor_map_encoder()) {
-    // the persistent tensor-copy passes: one CTA per SM, at most one per tile
-    const int ty = tma_ty(n);
-    *ctas = std::min(h->sms, ((n + TM_TX - 1) / TM_TX) * ((n + ty - 1) / ty));
+    // the persistent tensor-copy passes (pass B's shape shown): every resident slot, at most one per tile
+    const int ty = tma_ty(TMA_B);
+    *ctas = tma_grid(h, pass_b_tma32, TMA_B, ((n + TM_TX - 1) / TM_TX) * ((n + ty - 1) / ty));
     return MG_OK;
   }
   if (fp32 && n >= F32_FAST_MIN && std::max(h->nu1, h->nu2) <= 2) {  // the fast-eligible levels (fast32_ok)
@@ -2413,10 +2546,10 @@ int mg_batch_autotune(mg_batch b, int kappa, int mixed, int* chosen) {
         if (measure(t, &ms) == MG_OK && ms < best_ms) { best_ms = ms; best.thr = c; }
       }
       const TuneShape base = best;
-      for (int fc = 0; fc < 4; ++fc) {
+      for (int fc = 0; fc < 6; ++fc) {
         TuneShape t = base;
-        t.fused = fc & 1;
-        t.condensed = (fc >> 1) & 1;
+        t.fused = fc % 3;
+        t.condensed = fc / 3;
         if (t.fused == base.fused && t.condensed == base.condensed) continue;
         float ms;
         if (measure(t, &ms) == MG_OK && ms < best_ms) { best_ms = ms; best = t; }

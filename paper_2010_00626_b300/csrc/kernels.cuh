@@ -963,30 +963,52 @@ __device__ __forceinline__ void children_matvec(const T* __restrict__ pmap, int 
   __syncthreads();
   constexpr int NW = NT / 32;
   constexpr int VW = 16 / sizeof(T);  // elements per 16-byte chunk
-  const int lane = threadIdx.x & 31;
-  for (int k = part * NW + (threadIdx.x >> 5); k < S; k += parts * NW) {
-    const T* row = pmap + (size_t)k * pld;
-    T acc = T(0);
+  constexpr int RG = 4;               // rows a warp streams at once (independent loads in flight)
+  const int lane = threadIdx.x & 31, stride = parts * NW;
+  for (int k0 = part * NW + (threadIdx.x >> 5); k0 < S; k0 += RG * stride) {
+    T acc[RG];
+    const T* row[RG];
+#pragma unroll
+    for (int g = 0; g < RG; ++g) {
+      acc[g] = T(0);
+      const int k = k0 + g * stride;
+      row[g] = pmap + (size_t)(k < S ? k : k0) * pld;
+    }
+#pragma unroll 2
     for (int b = VW * lane; b < pld; b += 32 * VW) {
       if constexpr (VW == 4) {
-        const float4 q = *reinterpret_cast<const float4*>(row + b);
         const float4 x = *reinterpret_cast<const float4*>(fs + b);
-        acc = fma(q.x, x.x, acc);
-        acc = fma(q.y, x.y, acc);
-        acc = fma(q.z, x.z, acc);
-        acc = fma(q.w, x.w, acc);
+        float4 q[RG];
+#pragma unroll
+        for (int g = 0; g < RG; ++g) q[g] = *reinterpret_cast<const float4*>(row[g] + b);
+#pragma unroll
+        for (int g = 0; g < RG; ++g) {
+          acc[g] = fma(q[g].x, x.x, acc[g]);
+          acc[g] = fma(q[g].y, x.y, acc[g]);
+          acc[g] = fma(q[g].z, x.z, acc[g]);
+          acc[g] = fma(q[g].w, x.w, acc[g]);
+        }
       } else {
-        const double2 q = *reinterpret_cast<const double2*>(row + b);
         const double2 x = *reinterpret_cast<const double2*>(fs + b);
-        acc = fma(q.x, x.x, acc);
-        acc = fma(q.y, x.y, acc);
+        double2 q[RG];
+#pragma unroll
+        for (int g = 0; g < RG; ++g) q[g] = *reinterpret_cast<const double2*>(row[g] + b);
+#pragma unroll
+        for (int g = 0; g < RG; ++g) {
+          acc[g] = fma(q[g].x, x.x, acc[g]);
+          acc[g] = fma(q[g].y, x.y, acc[g]);
+        }
       }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      const int j = k / s, i = k - j * s;
-      a.v[(size_t)j * a.ldv + i] = acc;
+    for (int g = 0; g < RG; ++g) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[g] += __shfl_xor_sync(0xffffffffu, acc[g], o);
+      const int k = k0 + g * stride;
+      if (lane == 0 && k < S) {
+        const int j = k / s, i = k - j * s;
+        a.v[(size_t)j * a.ldv + i] = acc[g];
+      }
     }
   }
 }
@@ -1053,6 +1075,67 @@ __global__ void __launch_bounds__(NT)
   cluster.sync();
   for (int t = rank; t < ntiles; t += size) {
     pass_b_tile<T, TILE, TILE, NT, NS>(pb, t % tx, t / tx, 0, smem_raw);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// One call two levels above the coarse kernel's, in one cluster launch: pass A at level l, then its
+// one or two child calls at level l+1 -- each pass A at l+1, the condensed grandchildren
+// v_{l+2} = P_c f_{l+2} (children_matvec), pass B at l+1 -- then pass B at level l (Algorithm 3 with
+// the recursion unrolled two levels deep). Every hand-off goes through global memory between
+// cluster barriers; every point's arithmetic is that of the separate launches, so the results equal
+// them bit for bit. Launched with a cluster of CALL_MAX_CTAS CTAs; tiles TILE1 at level l, TILE2 at
+// level l+1.
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct Call2Args {
+  PassAArgs<T> pa1;        // level l
+  PassBArgs<T> pb1;
+  PassAArgs<T> pa2[2];     // level l+1: first child (from zero), second child (from its v)
+  PassBArgs<T> pb2;
+  CoarseArgs<T> cc;        // v, f and side of level l+2 for the condensed grandchildren
+  const T* pmap[2];        // P of the first and second child's counter class
+  int pld;
+  int children;            // 1 or 2
+};
+
+template <typename T, int TILE1, int TILE2>
+__host__ __device__ constexpr size_t call2_smem(int nu1, int nu2) {
+  return call_cluster_smem_tiles<T, TILE1>(nu1, nu2) > call_cluster_smem_tiles<T, TILE2>(nu1, nu2)
+             ? call_cluster_smem_tiles<T, TILE1>(nu1, nu2)
+             : call_cluster_smem_tiles<T, TILE2>(nu1, nu2);
+}
+
+template <typename T, int NT, int TILE1, int TILE2>
+__global__ void __launch_bounds__(NT) call2_cluster_kernel(const Call2Args<T> a) {
+  if (a.pa1.skip && *a.pa1.skip) return;  // the same flag for every CTA: the whole cluster returns
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
+  const int rank = (int)cluster.block_rank(), size = (int)cluster.num_blocks();
+  const int tx1 = (a.pa1.n + TILE1 - 1) / TILE1, nt1 = tx1 * tx1;
+  const int tx2 = (a.pb2.n + TILE2 - 1) / TILE2, nt2 = tx2 * tx2;
+  for (int t = rank; t < nt1; t += size) {
+    pass_a_tile<T, TILE1, TILE1, NT, false>(a.pa1, t % tx1, t / tx1, 0, smem_raw);
+    __syncthreads();
+  }
+  cluster.sync();
+  for (int c = 0; c < a.children; ++c) {
+    for (int t = rank; t < nt2; t += size) {
+      pass_a_tile<T, TILE2, TILE2, NT, false>(a.pa2[c], t % tx2, t / tx2, 0, smem_raw);
+      __syncthreads();
+    }
+    cluster.sync();
+    children_matvec<T, NT>(a.pmap[c], a.pld, a.cc, rank, size, reinterpret_cast<T*>(smem_raw));
+    cluster.sync();
+    for (int t = rank; t < nt2; t += size) {
+      pass_b_tile<T, TILE2, TILE2, NT, false>(a.pb2, t % tx2, t / tx2, 0, smem_raw);
+      __syncthreads();
+    }
+    cluster.sync();
+  }
+  for (int t = rank; t < nt1; t += size) {
+    pass_b_tile<T, TILE1, TILE1, NT, false>(a.pb1, t % tx1, t / tx1, 0, smem_raw);
     __syncthreads();
   }
 }

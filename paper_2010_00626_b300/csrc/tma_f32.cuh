@@ -35,9 +35,9 @@ namespace kc {
 constexpr int TM_TX = 120;        // output columns per tile
 constexpr int TM_P = 128;         // staged columns (TM_TX + 2 * 4)
 constexpr int TM_HX = 4;          // staged halo columns per side
-constexpr int TM_NT = 512;        // threads per CTA (16 warps)
+constexpr int TM_NT = 256;        // threads per CTA (8 warps); two or three CTAs per SM
 constexpr int TM_CP = 72;         // staged coarse columns of pass B (x start rounded down to 4)
-constexpr uint32_t TMA_WAIT_LIMIT = 1u << 22;
+constexpr uint32_t TMA_WAIT_LIMIT = 1u << 21;  // polls of at most about 1 us each: a copy gets ~2 s
 constexpr int TM_ERR_TIMEOUT = 1;
 
 // Rows of the staged window of a pass with TY output rows: pass A (nu sweeps, residual, full
@@ -83,12 +83,15 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
+// One poll: the thread is suspended until the phase completes or about TMA_POLL_NS nanoseconds
+// pass, so a waiting warp takes no issue slots from the other CTAs on its SM.
+constexpr uint32_t TMA_POLL_NS = 1000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(TMA_POLL_NS)
       : "memory");
   return ok != 0;
 }
@@ -133,12 +136,25 @@ __device__ __forceinline__ void tm_walk(int r0, int r1, Load load, Emit emit) {
   const int per = (r1 - r0 + NW - 1) / NW;
   const int a = r0 + warp * per, b = min(r1, a + per);
   if (a >= b) return;
-  Row6 S = load(a - 1), M = load(a);
-  for (int r = a; r < b; ++r) {
-    const Row6 N = load(r + 1);
-    emit(r, S, M, N);
-    S = M;
-    M = N;
+  // unrolled by hand by the window's period (3), so that the three rows rotate through three
+  // register sets instead of being copied
+  auto A = load(a - 1), B = load(a), C = A;
+  int r = a;
+  for (; r + 3 <= b; r += 3) {
+    C = load(r + 1);
+    emit(r, A, B, C);
+    A = load(r + 2);
+    emit(r + 1, B, C, A);
+    B = load(r + 3);
+    emit(r + 2, C, A, B);
+  }
+  if (r < b) {
+    C = load(r + 1);
+    emit(r, A, B, C);
+    if (r + 1 < b) {
+      A = load(r + 2);
+      emit(r + 1, B, C, A);
+    }
   }
 }
 
@@ -150,21 +166,35 @@ __device__ __forceinline__ void tm_mask(float (&o)[4], int gx0, int gy, int n) {
     if ((unsigned)gy >= (unsigned)n || (unsigned)(gx + k) >= (unsigned)n) o[k] = 0.f;
 }
 
-// Store lanes 1..30's four columns of one output row to global memory (columns < n only).
-__device__ __forceinline__ void tm_store_row(float* __restrict__ base, int ld, int gx0, int gy, int n,
-                                             const float (&o)[4]) {
-  const int lane = threadIdx.x & 31;
-  const int gx = gx0 + 4 * lane;
-  if (lane < 1 || lane > 30 || gy >= n || gx >= n) return;
-  float* p = base + (size_t)gy * ld + gx;
-  if (gx + 3 < n) {
-    *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
-  } else {
-    p[0] = o[0];
-    if (gx + 1 < n) p[1] = o[1];
-    if (gx + 2 < n) p[2] = o[2];
+// This lane's four columns of the tile's output rows in a global array, set up once per tile:
+// lanes 1..30 own the output columns; `full` lanes store float4 rows, the lane holding the grid's
+// last columns stores them one by one.
+struct TmColumn {
+  float* p;       // column gx of row 0
+  int ld, n, cols;  // cols: columns of the four this lane stores (0: none)
+  __device__ __forceinline__ TmColumn(float* base, int ld_, int gx0, int n_) : ld(ld_), n(n_) {
+    const int lane = threadIdx.x & 31, gx = gx0 + 4 * lane;
+    cols = (lane >= 1 && lane <= 30 && gx < n_) ? min(4, n_ - gx) : 0;
+    p = base + gx;
   }
-}
+  __device__ __forceinline__ void store(int gy, const float (&o)[4]) const {
+    if (gy >= n || cols == 0) return;
+    float* q = p + gy * ld;
+    if (cols == 4) {
+      *reinterpret_cast<float4*>(q) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+      q[0] = o[0];
+      if (cols > 1) q[1] = o[1];
+      if (cols > 2) q[2] = o[2];
+    }
+  }
+};
+
+// A row of the zero-start walk: v1 = w f with its halo, and the f row itself.
+struct ZRow {
+  Row6 v;
+  float f[4];
+};
 
 struct TmaPassArgs {
   int n, ty, tiles_x, tiles;  // grid side, output rows per tile, tiles per row of tiles, all tiles
@@ -196,7 +226,7 @@ __device__ __forceinline__ void tm_abort(int* err, uint64_t* bars, uint32_t pend
 // Pass A: nu = 2 damped-Jacobi sweeps (ZERO: from v = 0), residual, full weighting.
 // ------------------------------------------------------------------------------------------------
 template <bool ZERO>
-__global__ void __launch_bounds__(TM_NT, 1)
+__global__ void __launch_bounds__(TM_NT, 3)
     pass_a_tma32(const __grid_constant__ CUtensorMap map_v, const __grid_constant__ CUtensorMap map_f,
                  const TmaPassArgs a) {
   if (a.skip && *a.skip) return;
@@ -258,19 +288,21 @@ __global__ void __launch_bounds__(TM_NT, 1)
     float* v2;  // the second sweep's result
     if (ZERO) {
       // sweep 2 from v1 = w f on rows [2, R - 2): v1 formed in registers from the f rows
+      // (each f row is read once: the window carries it beside v1)
       tm_walk(2, R - 2,
               [&](int r) {
+                ZRow z;
+                tm_f4(fs, r, z.f);
                 float q[4];
-                tm_f4(fs, r, q);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) q[k] = c.w * q[k];
-                return with_halo(q);
+                for (int k = 0; k < 4; ++k) q[k] = c.w * z.f[k];
+                z.v = with_halo(q);
+                return z;
               },
-              [&](int r, const Row6& S, const Row6& M, const Row6& N) {
-                float fv[4], o[4];
-                tm_f4(fs, r, fv);
+              [&](int r, const ZRow& S, const ZRow& M, const ZRow& N) {
+                float o[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) o[k] = jacobi_update(nb6(S, M, N, k), fv[k], c);
+                for (int k = 0; k < 4; ++k) o[k] = jacobi_update(nb6(S.v, M.v, N.v, k), M.f[k], c);
                 if (edge) tm_mask(o, gx0, gy0 + r, n);
                 tm_st4(work, r, o);
               });
@@ -301,6 +333,7 @@ __global__ void __launch_bounds__(TM_NT, 1)
     __syncthreads();
     // residual on rows [3, R - 3) (full weighting of the output rows reads one row beyond them);
     // the relaxed v of the output rows [4, R - 4) goes to global memory from the same registers
+    const TmColumn out(a.vout, a.ldvout, gx0, n);
     tm_walk(3, R - 3, [&](int r) { return tm_row(v2, r); },
             [&](int r, const Row6& S, const Row6& M, const Row6& N) {
               float fv[4], res[4];
@@ -312,9 +345,9 @@ __global__ void __launch_bounds__(TM_NT, 1)
               h.x = fmaf(2.f, res[1], res[0] + res[2]);
               h.y = fmaf(2.f, res[3], res[2] + nxt);
               hsum[r * 32 + lane] = h;
-              if (a.vout && r >= NU + 2 && r < R - (NU + 2)) {
+              if (r >= NU + 2 && r < R - (NU + 2)) {
                 const float o[4] = {M.v[0], M.v[1], M.v[2], M.v[3]};
-                tm_store_row(a.vout, a.ldvout, gx0, gy0 + r, n, o);
+                out.store(gy0 + r, o);
               }
             });
     __syncthreads();
@@ -323,17 +356,19 @@ __global__ void __launch_bounds__(TM_NT, 1)
     {
       constexpr int NW = TM_NT / 32;
       const int cj_n = a.ty / 2;
+      const int I = x0 / 2 + 2 * lane - 2;
+      const int ccols = (lane >= 1 && lane <= 30 && I < nc) ? min(2, nc - I) : 0;
+      float* cp = a.fc + I;
       for (int j = threadIdx.x >> 5; j < cj_n; j += NW) {
         const int J = y0 / 2 + j;
         const int r = 2 * j + (NU + 2) + 1;
         const float2 hs = hsum[(r - 1) * 32 + lane], hm = hsum[r * 32 + lane], hn = hsum[(r + 1) * 32 + lane];
-        const int I = x0 / 2 + 2 * lane - 2;
-        if (lane >= 1 && lane <= 30 && J < nc && I < nc) {
+        if (ccols && J < nc) {
           float2 o;
           o.x = 0.0625f * fmaf(2.f, hm.x, hs.x + hn.x);
           o.y = 0.0625f * fmaf(2.f, hm.y, hs.y + hn.y);
-          float* q = a.fc + (size_t)J * a.ldc + I;
-          if (I + 1 < nc) *reinterpret_cast<float2*>(q) = o;
+          float* q = cp + J * a.ldc;
+          if (ccols == 2) *reinterpret_cast<float2*>(q) = o;
           else q[0] = o.x;
         }
       }
@@ -348,7 +383,7 @@ __global__ void __launch_bounds__(TM_NT, 1)
 // ------------------------------------------------------------------------------------------------
 // Pass B: v <- v + P v_c (bilinear), nu = 2 damped-Jacobi sweeps.
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(TM_NT, 1)
+__global__ void __launch_bounds__(TM_NT, 2)
     pass_b_tma32(const __grid_constant__ CUtensorMap map_v, const __grid_constant__ CUtensorMap map_f,
                  const __grid_constant__ CUtensorMap map_c, const TmaPassArgs a) {
   if (a.skip && *a.skip) return;
@@ -456,13 +491,14 @@ __global__ void __launch_bounds__(TM_NT, 1)
             });
     __syncthreads();
     // sweep 2 on the output rows [2, R - 2), written to global memory
+    const TmColumn out(a.vout, a.ldvout, gx0, n);
     tm_walk(NU, R - NU, [&](int r) { return tm_row(work, r); },
             [&](int r, const Row6& S, const Row6& M, const Row6& N) {
               float fv[4], o[4];
               tm_f4(fs, r, fv);
 #pragma unroll
               for (int k = 0; k < 4; ++k) o[k] = jacobi_update(nb6(S, M, N, k), fv[k], c);
-              tm_store_row(a.vout, a.ldvout, gx0, gy0 + r, n, o);
+              out.store(gy0 + r, o);
             });
     // this tile's generic-proxy writes to buffer set s are ordered before the tensor copies that
     // refill it (issued at the top of iteration it + 1)

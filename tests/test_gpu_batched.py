@@ -90,3 +90,44 @@ def test_full_batch_with_zebra_relaxation_all_converge(lib, mixed):
         h = oracle.Hierarchy(d["n"], int(round(math.log2(d["n"] + 1))), d["theta"], d["eps"], smoother="zebra")
         torch.cuda.synchronize()
         assert oracle.relres(h, xs[i].cpu().numpy(), fs[i]) <= 1e-8 * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("mixed", [True, False])
+def test_autotuner_shapes_and_instance_handles(lib, mixed):
+    """The autotuner times sub-batches of each side inside the batch's concurrency and picks, per
+    side, the coarse threshold, fused calls (0, 1, 2), condensed child calls and (mixed, sides >= 1023) the
+    FP32 pass kind from their candidate sets; every instance of a side gets the same shape. An
+    instance solved alone through its batch handle (mg_batch_instance) takes the same iterations
+    as in the batch, and its result meets the oracle's residual check."""
+    import torch
+    inst = batched_instances(count=10, seed=5, sizes=(127, 255, 1023))
+    ns = [d["n"] for d in inst]
+    batch = lib.Batch(ns, [d["eps"] for d in inst], [d["theta"] for d in inst])
+    chosen = batch.autotune(3, mixed=mixed)
+    assert set(chosen) == set(ns)
+    shapes = batch.shapes()
+    for n, sh in shapes.items():
+        thr = sh["coarse_n32"] if mixed else sh["coarse_n"]
+        assert thr == chosen[n] and thr in ((15, 31, 63) if mixed else (7, 15, 31))
+        assert sh["fused_call"] in (0, 1, 2) and sh["condensed_children"] in (0, 1) and sh["tma_passes"] in (0, 1)
+    for i, n in enumerate(ns):  # every instance of a side has its side's shape
+        m = batch.instance(i)
+        assert int(m.get_option(lib.MG_OPT_FUSED_CALL)) == shapes[n]["fused_call"]
+        assert int(m.get_option(lib.MG_OPT_CONDENSED_CHILDREN)) == shapes[n]["condensed_children"]
+    fs = [rhs_uniform(d["n"], d["seed"]) for d in inst]
+    xs = [dev(np.zeros((d["n"], d["n"]))) for d in inst]
+    st, iters, rel = batch.solve(xs, [dev(f) for f in fs], 3, 1e-8, 3000, mixed=mixed)
+    for i in (0, len(ns) - 1):
+        d = inst[i]
+        y = dev(np.zeros((d["n"], d["n"])))
+        m = batch.instance(i)
+        alone = m.solve_mixed(y, dev(fs[i]), 3, 1e-8, 3000) if mixed else m.solve(y, dev(fs[i]), 3, 1e-8, 3000)
+        assert alone[1] == iters[i]
+        m.close()  # releases nothing: the batch owns the handle
+        if rel[i] <= 1e-8:
+            h = oracle.Hierarchy(d["n"], int(round(math.log2(d["n"] + 1))), d["theta"], d["eps"])
+            torch.cuda.synchronize()
+            assert oracle.relres(h, y.cpu().numpy(), fs[i]) <= 1e-8 * (1 + 1e-6)
+    assert batch.instance(0).get_option(lib.MG_OPT_N) == ns[0]  # the handle is still alive
+    with pytest.raises(lib.MultigridError):
+        batch.instance(len(ns))

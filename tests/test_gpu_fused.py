@@ -1,8 +1,9 @@
 """Fused calls (MG_OPT_FUSED_CALL): a call at the level just above the coarse kernel's runs as one
-thread-block-cluster launch (pass A over that level's tiles, the coarse walk on one CTA, pass B)
-instead of three launches. Every point's arithmetic is that of the three-launch form, so iterates,
-histories and iteration counts must be equal bit for bit, and the graph must hold two launches
-fewer per call at that level. Oracle parity of the default (fused) path is in test_gpu_parity,
+thread-block-cluster launch (pass A over that level's tiles, the coarse walk or the condensed
+child calls, pass B) instead of three launches; with the default 2, a call two levels above runs
+with its child calls as one launch too. Every point's arithmetic is that of the separate launches,
+so iterates, histories and iteration counts must be equal bit for bit, and the graph must hold the
+launches counted by saved_launches fewer. Oracle parity of the default (fused) path is in test_gpu_parity,
 test_gpu_mixed and the others."""
 import math
 
@@ -27,6 +28,15 @@ def pair(lib, *args, **kw):
     return on, off
 
 
+def saved_launches(calls, lc, fused=1):
+    """Launches a cycle saves with fused calls: each call one level above the coarse kernel's (not
+    at level 0) is one launch in place of three; with fused = 2 a call two levels above (not at
+    level 0) is one launch in place of its own two and the three of each child call."""
+    if fused == 2 and lc - 2 >= 1:
+        return calls[lc - 2] + 3 * calls[lc - 1]
+    return 2 * calls[lc - 1] if lc - 1 >= 1 else 0
+
+
 def first_coarse_level(n, levels, coarse_n):
     sides = [(n + 1) // 2 ** l - 1 for l in range(levels)]
     return next((l for l, s in enumerate(sides) if s <= coarse_n), levels - 1)
@@ -48,8 +58,7 @@ def test_fp64_cycles_equal_bitwise(lib, n, levels, kappa):
     assert on.get_option(lib.MG_OPT_LAUNCHES) == launches
     assert off.get_option(lib.MG_OPT_LAUNCHES) == off.counters(kappa)[1]
     lc = first_coarse_level(n, levels, 15)
-    fused_calls = calls[lc - 1] if lc >= 2 else 0  # the level above the coarse kernel, not level 0
-    assert off.counters(kappa)[1] - launches == 2 * fused_calls
+    assert off.counters(kappa)[1] - launches == saved_launches(calls, lc)
 
 
 def test_fp64_solve_and_pcg_equal_bitwise(lib):
@@ -112,7 +121,7 @@ def test_batch_equal_bitwise(lib):
     import torch
     ns, epss, thetas = [63, 127, 255], [1e-2, 1e-3, 1e-4], [0.3, 1.1, 2.4]
     runs = []
-    for fused in (1, 0):
+    for fused in (2, 1, 0):
         batch = lib.Batch(ns, epss, thetas)
         batch.set_option(lib.MG_OPT_FUSED_CALL, fused)
         fs = [dev(rhs_uniform(n, 40 + i)) for i, n in enumerate(ns)]
@@ -120,8 +129,9 @@ def test_batch_equal_bitwise(lib):
         out = batch.solve(xs, fs, 3, 1e-8, 2000, mixed=True)
         torch.cuda.synchronize()
         runs.append((out, [x.clone() for x in xs]))
-    assert runs[0][0] == runs[1][0]
-    assert all(torch.equal(a, b) for a, b in zip(runs[0][1], runs[1][1]))
+    for r in runs[1:]:
+        assert runs[0][0] == r[0]
+        assert all(torch.equal(a, b) for a, b in zip(runs[0][1], r[1]))
 
 
 @pytest.mark.parametrize("nu1,nu2", [(0, 3), (3, 1), (1, 0)])
@@ -143,3 +153,32 @@ def test_fp64_cycles_equal_bitwise_other_sweeps(lib, nu1, nu2):
     off.kcycle_f32(b, f32, 2)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("n,levels,kappa", [(255, 8, 3), (4095, 12, 4)])
+def test_one_and_two_level_fusion_equal_bitwise(lib, n, levels, kappa):
+    """MG_OPT_FUSED_CALL = 2 (calls two levels above the coarse kernel fused with their child calls)
+    against 1 (only the level just above): same iterates in FP64 and FP32."""
+    import torch
+    two = lib.Multigrid(n, 3e-4, 2.2, levels)
+    one = lib.Multigrid(n, 3e-4, 2.2, levels)
+    two.set_option(lib.MG_OPT_FUSED_CALL, 2)
+    f = dev(rhs_uniform(n, 9))
+    a, b = torch.zeros_like(f), torch.zeros_like(f)
+    for _ in range(2):
+        two.kcycle(a, f, kappa)
+        one.kcycle(b, f, kappa)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    f32 = dev(rhs_uniform(n, 10), "float32")
+    a, b = torch.zeros_like(f32), torch.zeros_like(f32)
+    two.kcycle_f32(a, f32, kappa)
+    one.kcycle_f32(b, f32, kappa)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    two.set_option(lib.MG_OPT_FUSED_CALL, 2)
+    two.kcycle(torch.zeros_like(f), f, kappa)
+    calls, launches, _ = two.counters(kappa)
+    assert two.get_option(lib.MG_OPT_LAUNCHES) == launches
+    lc = first_coarse_level(n, levels, 15)
+    assert one.counters(kappa)[1] - launches == calls[lc - 2] + calls[lc - 1]

@@ -245,7 +245,10 @@ def test_level_grid_reports_the_launch_shapes(lib):
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     fp32 = [mg.level_grid(l, fp32=True)[1] for l in range(12)]
-    assert fp32[:3] == [min(sms, 2240), min(sms, 576), min(sms, 288)] and fp32[6] == 16 and fp32[7:] == [1] * 5
+    assert fp32[5] == 16 * 16 and fp32[6] == 16 and fp32[7:] == [1] * 5
+    assert all(0 < c <= 3 * sms for c in fp32[:3])
+    mg.set_option(lib.MG_OPT_FUSED_CALL, 2)
+    assert mg.level_grid(6)[1] == 16 and mg.level_grid(5, fp32=True)[1] == 16
     mg.set_option(lib.MG_OPT_TMA_PASSES, 0)
     assert [mg.level_grid(l, fp32=True)[1] for l in range(2)] == [9 * 64, 19 * 128]
     mg.set_option(lib.MG_OPT_FUSED_CALL, 0)
