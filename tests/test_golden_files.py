@@ -30,6 +30,18 @@ def test_golden_run_is_consistent(path):
     assert 0.1 < h[0] < 1.0
 
 
+def test_first_cycles_run_is_consistent():
+    """The oracle's first 200 V-cycles of the same solve (oracle/full_size_cycles.py --first 200):
+    no tolerance applied, every cycle reduces the residual, and it has not reached 1e-8 (the full
+    V-cycle solve needs about 4100 cycles)."""
+    d = load(os.path.join(HERE, "golden", "large_standalone_first200_k1.json"))
+    h = d["history"]
+    assert d["written_by"] == "oracle/full_size_cycles.py" and d["tol"] is None and d["kappa"] == 1
+    assert (d["n"], d["levels"], d["cycles"], len(h)) == (4095, 12, 200, 200)
+    assert all(b < a for a, b in zip(h, h[1:]))
+    assert 1e-8 < h[-1] < h[0] < 1.0
+
+
 def test_counts_do_not_grow_with_kappa():
     counts = sorted((load(p)["kappa"], load(p)["cycles"]) for p in FILES)
     assert len(counts) >= 2

@@ -318,6 +318,22 @@ def test_large_solve_matches_oracle_cycle_counts(lib, kappa):
         assert abs(a - b) <= HIST_TOL * b + 1e-12 * g["history"][0], (a, b)
 
 
+def test_large_vcycle_history_matches_oracle_first_200_cycles(lib):
+    """4095^2 V-cycles (kappa = 1, the slowest counter: 4115 cycles to 1e-8, Table 4's first row)
+    against the oracle's own first 200 cycles of the same solve (tests/golden, written by
+    oracle/full_size_cycles.py --first 200): the residual history cycle by cycle."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "large_standalone_first200_k1.json")))
+    n, levels = g["n"], g["levels"]
+    mg = lib.Multigrid(n, g["eps"], g["theta"], levels)
+    vd = torch_dev(np.zeros((n, n)))
+    st, cycles, relres, hist = mg.solve(vd, torch_dev(rhs_normal(n, 0)), 1, 1e-300, g["cycles"])
+    assert st == 1 and cycles == g["cycles"] == 200
+    for a, b in zip(hist, g["history"]):
+        assert abs(a - b) <= HIST_TOL * b + 1e-12 * g["history"][0], (a, b)
+
+
 def test_largest_grid_solve(lib):
     """16383^2 (14 levels, the paper's largest): kappa=3 solve to 1e-8; the oracle recomputes the
     residual of the result (a property that holds at any size)."""
