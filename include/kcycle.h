@@ -298,7 +298,7 @@ int mg_batch_create(int count, const int* n, const double* eps, const double* th
                     int nu1, int nu2, mg_batch* out);
 
 /* Autotuner of the batch's launch shapes, per distinct grid side (largest first), timed inside the
- * batch's concurrency: up to 8 instances of that side are solved together as batch branches of one
+ * batch's concurrency: up to 64 instances of that side are solved together as batch branches of one
  * graph (4 iterations of the FP64 solve, or of the mixed solve when mixed != 0, on scratch arrays),
  * and the side's options are chosen by coordinate descent over
  *   1. the coarse-kernel threshold: FP64 7, 15, 31 (MG_OPT_COARSE_N); FP32 15, 31, 63 (COARSE_N32);

@@ -2418,7 +2418,7 @@ void batch_drop_graph(mg_batch_ctx* b) {
 struct TuneShape {
   int thr, fused, condensed, tma;
 };
-constexpr size_t TUNE_MAX_INSTANCES = 8;  // instances of one side timed together
+constexpr size_t TUNE_MAX_INSTANCES = 64;  // instances of one side timed together (the memory pressure of the batch)
 constexpr int TUNE_ITERS = 4;             // solve iterations timed per candidate
 
 // ms per iteration of the instances `hs` solved together, as in a batch: one graph holding each
