@@ -63,7 +63,12 @@ constexpr int MAX_NU = 8;
 constexpr int VEC_BLOCKS = 148 * 8;
 constexpr int MAX_COARSE_N = 63;
 constexpr size_t SMEM_CAP = 220 * 1024;  // dynamic shared memory per CTA (227 KB less static use)
-constexpr int TMA_TY_MAX = 64;           // largest tile height of the tensor-copy FP32 passes
+// Output rows per tile of the tensor-copy FP32 passes (pass A from zero, pass A from v, pass B): the
+// window (tile plus halo rows, double-buffered) sized so that three, two and two CTAs of 8 warps
+// share an SM, whose copies and barriers then overlap each other's arithmetic.
+constexpr int TMA_TY_A0 = 32, TMA_TY_A = 24, TMA_TY_B = 32;
+constexpr int TMA_TY_S = 8, TMA_SMALL_MAX = 511;  // tile height at the small sides (255, 511)
+constexpr int TMA_MIN_N = 255;                     // smallest side for the tensor-copy passes
 constexpr int MAP_S = 49;       // unknowns of the side-7 level
 constexpr int MAP_CLASSES = 3;  // at most two levels below it: counters 1, 2, >= 3
 
@@ -298,12 +303,18 @@ int set_all_smem_attrs() {
       KC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile32_smem_a()));
     for (auto k : {pass_b_tile32<0>, pass_b_tile32<1>, pass_b_tile32<2>})
       KC_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile32_smem_b()));
-    KC_CUDA(cudaFuncSetAttribute(pass_a_tma32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(tm_smem_a(TMA_TY_MAX, 2, true) + 1024)));
-    KC_CUDA(cudaFuncSetAttribute(pass_a_tma32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(tm_smem_a(TMA_TY_MAX, 2, false) + 1024)));
-    KC_CUDA(cudaFuncSetAttribute(pass_b_tma32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(tm_smem_b(TMA_TY_MAX, 2) + 1024)));
+    KC_CUDA(cudaFuncSetAttribute(pass_a_tma32<true, TMA_TY_A0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(tm_smem_a(TMA_TY_A0, 2, true) + 1024)));
+    KC_CUDA(cudaFuncSetAttribute(pass_a_tma32<false, TMA_TY_A>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(tm_smem_a(TMA_TY_A, 2, false) + 1024)));
+    KC_CUDA(cudaFuncSetAttribute(pass_b_tma32<TMA_TY_B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(tm_smem_b(TMA_TY_B, 2) + 1024)));
+    KC_CUDA(cudaFuncSetAttribute(pass_a_tma32<true, TMA_TY_S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(tm_smem_a(TMA_TY_S, 2, true) + 1024)));
+    KC_CUDA(cudaFuncSetAttribute(pass_a_tma32<false, TMA_TY_S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(tm_smem_a(TMA_TY_S, 2, false) + 1024)));
+    KC_CUDA(cudaFuncSetAttribute(pass_b_tma32<TMA_TY_S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(tm_smem_b(TMA_TY_S, 2) + 1024)));
   }
   KC_TRY((set_line_attrs<T, 1>()));
   KC_TRY((set_line_attrs<T, 2>()));
@@ -481,19 +492,23 @@ int make_map_f32(CUtensorMap* m, const float* base, int n_cols, int n_rows, int 
   return MG_OK;
 }
 
-// Output rows per tile of each tensor-copy pass: the window (tile plus halo rows, double-buffered)
-// sized so that two (pass A from v, pass B) or three (pass A from zero) CTAs of 8 warps share an
-// SM, whose copies and barriers then overlap each other's arithmetic.
-enum TmaKind { TMA_A_ZERO = 0, TMA_A = 1, TMA_B = 2 };
-int tma_ty(int kind) { return kind == TMA_A ? 24 : 32; }
+// Kinds of tensor-copy pass; TMA_SMALL + kind: the same pass with tiles of TMA_TY_S rows, used at the
+// sides up to TMA_SMALL_MAX, where tall tiles would leave most SMs without a tile.
+enum TmaKind { TMA_A_ZERO = 0, TMA_A = 1, TMA_B = 2, TMA_SMALL = 3 };
+int tma_kind(int base, int n) { return n <= TMA_SMALL_MAX ? TMA_SMALL + base : base; }
+int tma_ty(int kind) {
+  if (kind >= TMA_SMALL) return TMA_TY_S;
+  return kind == TMA_A ? TMA_TY_A : (kind == TMA_B ? TMA_TY_B : TMA_TY_A0);
+}
 size_t tma_smem(int kind) {
-  return (kind == TMA_B ? tm_smem_b(tma_ty(kind), 2) : tm_smem_a(tma_ty(kind), 2, kind == TMA_A_ZERO)) + 1024;
+  const int base = kind % TMA_SMALL;
+  return (base == TMA_B ? tm_smem_b(tma_ty(kind), 2) : tm_smem_a(tma_ty(kind), 2, base == TMA_A_ZERO)) + 1024;
 }
 
 // CTAs of a tensor-copy pass: every resident slot of the device, at most one per tile.
 template <typename K>
 int tma_grid(const mg_ctx* h, K kern, int kind, int tiles) {
-  static int per_sm[3] = {0, 0, 0};
+  static int per_sm[6] = {0, 0, 0, 0, 0, 0};
   if (per_sm[kind] == 0) {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, TM_NT, tma_smem(kind)) != cudaSuccess || b < 1) b = 1;
@@ -508,12 +523,12 @@ bool aligned16(const void* p, int ld) { return ((uintptr_t)p & 15) == 0 && (ld &
 // Whether the tensor-copy passes take this launch: nu = 2, a large level, 16-byte aligned arrays
 // with pitches of whole 16-byte units (the tensor maps' rule), the encoder available.
 bool tma_pass_a_ok(const mg_ctx* h, const PassAArgs<float>& a) {
-  return h->tma32 && a.nu == 2 && a.n >= F32_FAST_MIN && a.vout && (a.vin == nullptr || aligned16(a.vin, a.ldvin)) &&
+  return h->tma32 && a.nu == 2 && a.n >= TMA_MIN_N && a.vout && (a.vin == nullptr || aligned16(a.vin, a.ldvin)) &&
          aligned16(a.f, a.ldf) && aligned16(a.vout, a.ldvout) && ((uintptr_t)a.fc & 7) == 0 && (a.ldc & 1) == 0 &&
          tensor_map_encoder() != nullptr;
 }
 bool tma_pass_b_ok(const mg_ctx* h, const PassBArgs<float>& a) {
-  return h->tma32 && a.nu == 2 && a.n >= F32_FAST_MIN && a.partial == nullptr && aligned16(a.vin, a.ldvin) &&
+  return h->tma32 && a.nu == 2 && a.n >= TMA_MIN_N && a.partial == nullptr && aligned16(a.vin, a.ldvin) &&
          aligned16(a.f, a.ldf) && aligned16(a.vout, a.ldvout) && aligned16(a.vc, a.ldc) &&
          tensor_map_encoder() != nullptr;
 }
@@ -537,7 +552,7 @@ TmaPassArgs tma_args(const mg_ctx* h, int kind, int n, int level, const float* c
 }
 
 int launch_pass_a_tma32(mg_ctx* h, const PassAArgs<float>& a, cudaStream_t s) {
-  const int kind = a.vin ? TMA_A : TMA_A_ZERO;
+  const int kind = tma_kind(a.vin ? TMA_A : TMA_A_ZERO, a.n);
   TmaPassArgs t = tma_args(h, kind, a.n, a.level, a.coef, a.skip, h->ints + I_ERR);
   t.vout = a.vout;
   t.ldvout = a.ldvout;
@@ -548,16 +563,20 @@ int launch_pass_a_tma32(mg_ctx* h, const PassAArgs<float>& a, cudaStream_t s) {
   KC_TRY(make_map_f32(&mf, a.f, a.n, a.n, a.ldf, TM_P, R));
   if (a.vin) KC_TRY(make_map_f32(&mv, a.vin, a.n, a.n, a.ldvin, TM_P, R));
   else mv = mf;  // not read from a zero start
-  if (a.vin)
-    pass_a_tma32<false><<<tma_grid(h, pass_a_tma32<false>, kind, t.tiles), TM_NT, tma_smem(kind), s>>>(mv, mf, t);
-  else
-    pass_a_tma32<true><<<tma_grid(h, pass_a_tma32<true>, kind, t.tiles), TM_NT, tma_smem(kind), s>>>(mv, mf, t);
+  auto go = [&](auto k) { k<<<tma_grid(h, k, kind, t.tiles), TM_NT, tma_smem(kind), s>>>(mv, mf, t); };
+  switch (kind) {
+    case TMA_A: go(pass_a_tma32<false, TMA_TY_A>); break;
+    case TMA_A_ZERO: go(pass_a_tma32<true, TMA_TY_A0>); break;
+    case TMA_SMALL + TMA_A: go(pass_a_tma32<false, TMA_TY_S>); break;
+    default: go(pass_a_tma32<true, TMA_TY_S>); break;
+  }
   KC_CUDA(cudaGetLastError());
   return MG_OK;
 }
 
 int launch_pass_b_tma32(mg_ctx* h, const PassBArgs<float>& a, cudaStream_t s) {
-  TmaPassArgs t = tma_args(h, TMA_B, a.n, a.level, a.coef, a.skip, h->ints + I_ERR);
+  const int kind = tma_kind(TMA_B, a.n);
+  TmaPassArgs t = tma_args(h, kind, a.n, a.level, a.coef, a.skip, h->ints + I_ERR);
   t.vout = a.vout;
   t.ldvout = a.ldvout;
   const int nc = (a.n - 1) / 2;
@@ -565,7 +584,9 @@ int launch_pass_b_tma32(mg_ctx* h, const PassBArgs<float>& a, cudaStream_t s) {
   KC_TRY(make_map_f32(&mv, a.vin, a.n, a.n, a.ldvin, TM_P, tm_rows_b(t.ty, 2)));
   KC_TRY(make_map_f32(&mf, a.f, a.n, a.n, a.ldf, TM_P, tm_rows_b(t.ty, 2)));
   KC_TRY(make_map_f32(&mc, a.vc, nc, nc, a.ldc, TM_CP, tm_crows_b(t.ty, 2)));
-  pass_b_tma32<<<tma_grid(h, pass_b_tma32, TMA_B, t.tiles), TM_NT, tma_smem(TMA_B), s>>>(mv, mf, mc, t);
+  auto go = [&](auto k) { k<<<tma_grid(h, k, kind, t.tiles), TM_NT, tma_smem(kind), s>>>(mv, mf, mc, t); };
+  if (kind == TMA_B) go(pass_b_tma32<TMA_TY_B>);
+  else go(pass_b_tma32<TMA_TY_S>);
   KC_CUDA(cudaGetLastError());
   return MG_OK;
 }
@@ -2299,10 +2320,10 @@ int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas) {
     *ctas = fp32 ? call_ctas<float>(h, level) : call_ctas<double>(h, level);
     return MG_OK;
   }
-  if (fp32 && h->tma32 && n >= F32_FAST_MIN && h->nu1 == 2 && h->nu2 == 2 && tensor_map_encoder()) {
+  if (fp32 && h->tma32 && n >= TMA_MIN_N && h->nu1 == 2 && h->nu2 == 2 && tensor_map_encoder()) {
     // the persistent tensor-copy passes (pass B's shape shown): every resident slot, at most one per tile
-    const int ty = tma_ty(TMA_B);
-    *ctas = tma_grid(h, pass_b_tma32, TMA_B, ((n + TM_TX - 1) / TM_TX) * ((n + ty - 1) / ty));
+    const int kind = tma_kind(TMA_B, n), ty = tma_ty(kind), tiles = ((n + TM_TX - 1) / TM_TX) * ((n + ty - 1) / ty);
+    *ctas = kind == TMA_B ? tma_grid(h, pass_b_tma32<TMA_TY_B>, kind, tiles) : tma_grid(h, pass_b_tma32<TMA_TY_S>, kind, tiles);
     return MG_OK;
   }
   if (fp32 && n >= F32_FAST_MIN && std::max(h->nu1, h->nu2) <= 2) {  // the fast-eligible levels (fast32_ok)

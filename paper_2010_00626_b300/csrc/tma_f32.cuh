@@ -127,34 +127,30 @@ __device__ __forceinline__ void tm_st4(float* __restrict__ s, int r, const float
   *reinterpret_cast<float4*>(s + r * TM_P + 4 * (threadIdx.x & 31)) = make_float4(o[0], o[1], o[2], o[3]);
 }
 
-// Rows [r0, r1) split into contiguous bands, one per warp; for each row r of its band the warp
-// calls emit(r, S, M, N) with rows r-1, r, r+1 as produced by load().
-template <class Load, class Emit>
-__device__ __forceinline__ void tm_walk(int r0, int r1, Load load, Emit emit) {
+// Rows [R0, R0 + NROWS) split into contiguous bands, one per warp (NROWS / 8 rows each, one more for
+// the first NROWS % 8 warps); for each row r of its band the warp calls emit(r, S, M, N) with rows
+// r-1, r, r+1 as produced by load(). The band length is a compile-time constant, so the loop is
+// unrolled: the three rows rotate through registers without copies and every row's shared-memory
+// address is the band's base plus a constant.
+template <int R0, int NROWS, class Load, class Emit>
+__device__ __forceinline__ void tm_walk(Load load, Emit emit) {
   constexpr int NW = TM_NT / 32;
+  constexpr int PER = NROWS / NW, EXTRA = NROWS % NW;
+  static_assert(PER >= 1, "every warp walks at least one row");
   const int warp = threadIdx.x >> 5;
-  const int per = (r1 - r0 + NW - 1) / NW;
-  const int a = r0 + warp * per, b = min(r1, a + per);
-  if (a >= b) return;
-  // unrolled by hand by the window's period (3), so that the three rows rotate through three
-  // register sets instead of being copied
-  auto A = load(a - 1), B = load(a), C = A;
-  int r = a;
-  for (; r + 3 <= b; r += 3) {
-    C = load(r + 1);
-    emit(r, A, B, C);
-    A = load(r + 2);
-    emit(r + 1, B, C, A);
-    B = load(r + 3);
-    emit(r + 2, C, A, B);
+  const int a = R0 + warp * PER + min(warp, EXTRA);
+  auto S = load(a - 1);
+  auto M = load(a);
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const auto N = load(a + i + 1);
+    emit(a + i, S, M, N);
+    S = M;
+    M = N;
   }
-  if (r < b) {
-    C = load(r + 1);
-    emit(r, A, B, C);
-    if (r + 1 < b) {
-      A = load(r + 2);
-      emit(r + 1, B, C, A);
-    }
+  if (EXTRA > 0 && warp < EXTRA) {
+    const auto N = load(a + PER + 1);
+    emit(a + PER, S, M, N);
   }
 }
 
@@ -186,6 +182,23 @@ struct TmColumn {
       q[0] = o[0];
       if (cols > 1) q[1] = o[1];
       if (cols > 2) q[2] = o[2];
+    }
+  }
+};
+
+// The tiles a persistent CTA visits: tile blockIdx.x, then every gridDim.x-th one, in row-major
+// order of tiles_x tiles per row; coordinates advance incrementally (no division per tile).
+struct TmTiles {
+  int nx, ny, x0, y0, dx, dy;
+  __device__ __forceinline__ TmTiles(int tiles_x, int tiles)
+      : nx(tiles_x), ny(tiles / tiles_x), x0((int)blockIdx.x % tiles_x), y0((int)blockIdx.x / tiles_x),
+        dx((int)gridDim.x % tiles_x), dy((int)gridDim.x / tiles_x) {}
+  __device__ __forceinline__ void advance(int& x, int& y) const {
+    x += dx;
+    y += dy;
+    if (x >= nx) {
+      x -= nx;
+      ++y;
     }
   }
 };
@@ -225,7 +238,7 @@ __device__ __forceinline__ void tm_abort(int* err, uint64_t* bars, uint32_t pend
 // ------------------------------------------------------------------------------------------------
 // Pass A: nu = 2 damped-Jacobi sweeps (ZERO: from v = 0), residual, full weighting.
 // ------------------------------------------------------------------------------------------------
-template <bool ZERO>
+template <bool ZERO, int TY>
 __global__ void __launch_bounds__(TM_NT, 3)
     pass_a_tma32(const __grid_constant__ CUtensorMap map_v, const __grid_constant__ CUtensorMap map_f,
                  const TmaPassArgs a) {
@@ -233,8 +246,8 @@ __global__ void __launch_bounds__(TM_NT, 3)
   constexpr int NU = 2;
   extern __shared__ __align__(1024) unsigned char smem_dyn[];
   unsigned char* smem_raw = tm_base(smem_dyn);
-  const int R = tm_rows_a(a.ty, NU);
-  const size_t FB = tm_field_a(a.ty, NU);
+  constexpr int R = tm_rows_a(TY, NU);
+  constexpr size_t FB = tm_field_a(TY, NU);
   // buffer set s: f at set(s), v (not from zero) one field after it
   const size_t SET = (ZERO ? 1 : 2) * FB;
   auto fin = [&](int s) { return reinterpret_cast<float*>(smem_raw + s * SET); };
@@ -256,10 +269,9 @@ __global__ void __launch_bounds__(TM_NT, 3)
   }
   __syncthreads();
   uint32_t pending = 0u, pend_par = 0u;  // bit s: copies into set s in flight, and their phase parity
-  auto issue = [&](int t, int s, uint32_t parity) {
+  auto issue = [&](int bx, int by, int s, uint32_t parity) {
     if (threadIdx.x == 0) {
-      const int bx = t % a.tiles_x, by = t / a.tiles_x;
-      const int gx0 = bx * TM_TX - TM_HX, gy0 = by * a.ty - (NU + 2);
+      const int gx0 = bx * TM_TX - TM_HX, gy0 = by * TY - (NU + 2);
       mbar_expect_tx(bars + s, box_bytes);
       tma_load_2d(fin(s), &map_f, bars + s, gx0, gy0);
       if (!ZERO) tma_load_2d(vin(s), &map_v, bars + s, gx0, gy0);
@@ -267,21 +279,22 @@ __global__ void __launch_bounds__(TM_NT, 3)
     pending |= 1u << s;
     pend_par = (pend_par & ~(1u << s)) | (parity << s);
   };
-  int it = 0;
-  int t = blockIdx.x;
-  if (t < a.tiles) issue(t, 0, 0u);
-  for (; t < a.tiles; t += gridDim.x, ++it) {
+  TmTiles tl(a.tiles_x, a.tiles);
+  int bx = tl.x0, by = tl.y0, px = bx, py = by;  // this CTA's current tile, and the next to fetch
+  if (by < tl.ny) issue(px, py, 0, 0u);
+  tl.advance(px, py);
+  for (int it = 0; by < tl.ny; ++it, tl.advance(bx, by)) {
     const int s = it & 1;
-    const uint32_t parity = (uint32_t)(it >> 1) & 1u;
-    const int tn = t + gridDim.x;
-    if (tn < a.tiles) issue(tn, s ^ 1, (uint32_t)((it + 1) >> 1) & 1u);
-    if (!tm_wait_all(bars + s, parity)) {
+    if (!tm_wait_all(bars + s, (uint32_t)(it >> 1) & 1u)) {
       tm_abort(a.err, bars, pend_par, pending);
       return;
     }
     pending &= ~(1u << s);
-    const int bx = t % a.tiles_x, by = t / a.tiles_x;
-    const int x0 = bx * TM_TX, y0 = by * a.ty;
+    // past this barrier every thread has finished the previous tile, whose buffer set the copies of
+    // the next tile refill
+    if (py < tl.ny) issue(px, py, s ^ 1, (uint32_t)((it + 1) >> 1) & 1u);
+    tl.advance(px, py);
+    const int x0 = bx * TM_TX, y0 = by * TY;
     const int gx0 = x0 - TM_HX, gy0 = y0 - (NU + 2);
     const bool edge = gx0 < 0 || gy0 < 0 || gx0 + TM_P > n || gy0 + R > n;
     const float* fs = fin(s);
@@ -289,7 +302,7 @@ __global__ void __launch_bounds__(TM_NT, 3)
     if (ZERO) {
       // sweep 2 from v1 = w f on rows [2, R - 2): v1 formed in registers from the f rows
       // (each f row is read once: the window carries it beside v1)
-      tm_walk(2, R - 2,
+      tm_walk<2, R - 4>(
               [&](int r) {
                 ZRow z;
                 tm_f4(fs, r, z.f);
@@ -309,7 +322,7 @@ __global__ void __launch_bounds__(TM_NT, 3)
       v2 = work;
     } else {
       float* vs = vin(s);
-      tm_walk(1, R - 1, [&](int r) { return tm_row(vs, r); },
+      tm_walk<1, R - 2>([&](int r) { return tm_row(vs, r); },
               [&](int r, const Row6& S, const Row6& M, const Row6& N) {
                 float fv[4], o[4];
                 tm_f4(fs, r, fv);
@@ -319,7 +332,7 @@ __global__ void __launch_bounds__(TM_NT, 3)
                 tm_st4(work, r, o);
               });
       __syncthreads();
-      tm_walk(2, R - 2, [&](int r) { return tm_row(work, r); },
+      tm_walk<2, R - 4>([&](int r) { return tm_row(work, r); },
               [&](int r, const Row6& S, const Row6& M, const Row6& N) {
                 float fv[4], o[4];
                 tm_f4(fs, r, fv);
@@ -334,7 +347,7 @@ __global__ void __launch_bounds__(TM_NT, 3)
     // residual on rows [3, R - 3) (full weighting of the output rows reads one row beyond them);
     // the relaxed v of the output rows [4, R - 4) goes to global memory from the same registers
     const TmColumn out(a.vout, a.ldvout, gx0, n);
-    tm_walk(3, R - 3, [&](int r) { return tm_row(v2, r); },
+    tm_walk<3, R - 6>([&](int r) { return tm_row(v2, r); },
             [&](int r, const Row6& S, const Row6& M, const Row6& N) {
               float fv[4], res[4];
               tm_f4(fs, r, fv);
@@ -355,7 +368,7 @@ __global__ void __launch_bounds__(TM_NT, 3)
     // 4q + 1 and 4q + 3 of lane q (I = x0/2 + 2q - 2 and the next)
     {
       constexpr int NW = TM_NT / 32;
-      const int cj_n = a.ty / 2;
+      constexpr int cj_n = TY / 2;
       const int I = x0 / 2 + 2 * lane - 2;
       const int ccols = (lane >= 1 && lane <= 30 && I < nc) ? min(2, nc - I) : 0;
       float* cp = a.fc + I;
@@ -374,15 +387,15 @@ __global__ void __launch_bounds__(TM_NT, 3)
       }
     }
     // this tile's generic-proxy writes to buffer set s are ordered before the tensor copies that
-    // refill it (issued at the top of iteration it + 1)
+    // refill it (issued after the next tile's wait, whose barrier every thread passes first)
     fence_proxy_async_smem();
-    __syncthreads();
   }
 }
 
 // ------------------------------------------------------------------------------------------------
 // Pass B: v <- v + P v_c (bilinear), nu = 2 damped-Jacobi sweeps.
 // ------------------------------------------------------------------------------------------------
+template <int TY>
 __global__ void __launch_bounds__(TM_NT, 2)
     pass_b_tma32(const __grid_constant__ CUtensorMap map_v, const __grid_constant__ CUtensorMap map_f,
                  const __grid_constant__ CUtensorMap map_c, const TmaPassArgs a) {
@@ -390,8 +403,8 @@ __global__ void __launch_bounds__(TM_NT, 2)
   constexpr int NU = 2;
   extern __shared__ __align__(1024) unsigned char smem_dyn[];
   unsigned char* smem_raw = tm_base(smem_dyn);
-  const int R = tm_rows_b(a.ty, NU), CR = tm_crows_b(a.ty, NU);
-  const size_t FB = tm_field_b(a.ty, NU), CB = tm_cfield_b(a.ty, NU);
+  constexpr int R = tm_rows_b(TY, NU), CR = tm_crows_b(TY, NU);
+  constexpr size_t FB = tm_field_b(TY, NU), CB = tm_cfield_b(TY, NU);
   // buffer set s: v, f, then the coarse window
   const size_t SET = 2 * FB + CB;
   auto vin = [&](int s) { return reinterpret_cast<float*>(smem_raw + s * SET); };
@@ -416,10 +429,9 @@ __global__ void __launch_bounds__(TM_NT, 2)
   uint32_t pending = 0u, pend_par = 0u;  // bit s: copies into set s in flight, and their phase parity
   // window origin: fine (gx0, gy0) = (x0 - 4, y0 - NU); coarse (cx0, cy0) with cx0 = x0/2 - 4
   // (x0/2 - 3 rounded down to a multiple of 4, the tensor copy's alignment) and cy0 = gy0/2 - 1
-  auto issue = [&](int t, int s, uint32_t parity) {
+  auto issue = [&](int bx, int by, int s, uint32_t parity) {
     if (threadIdx.x == 0) {
-      const int bx = t % a.tiles_x, by = t / a.tiles_x;
-      const int x0 = bx * TM_TX, y0 = by * a.ty;
+      const int x0 = bx * TM_TX, y0 = by * TY;
       const int gy0 = y0 - NU;
       mbar_expect_tx(bars + s, box_bytes);
       tma_load_2d(vin(s), &map_v, bars + s, x0 - TM_HX, gy0);
@@ -429,21 +441,20 @@ __global__ void __launch_bounds__(TM_NT, 2)
     pending |= 1u << s;
     pend_par = (pend_par & ~(1u << s)) | (parity << s);
   };
-  int it = 0;
-  int t = blockIdx.x;
-  if (t < a.tiles) issue(t, 0, 0u);
-  for (; t < a.tiles; t += gridDim.x, ++it) {
+  TmTiles tl(a.tiles_x, a.tiles);
+  int bx = tl.x0, by = tl.y0, px = bx, py = by;  // this CTA's current tile, and the next to fetch
+  if (by < tl.ny) issue(px, py, 0, 0u);
+  tl.advance(px, py);
+  for (int it = 0; by < tl.ny; ++it, tl.advance(bx, by)) {
     const int s = it & 1;
-    const uint32_t parity = (uint32_t)(it >> 1) & 1u;
-    const int tn = t + gridDim.x;
-    if (tn < a.tiles) issue(tn, s ^ 1, (uint32_t)((it + 1) >> 1) & 1u);
-    if (!tm_wait_all(bars + s, parity)) {
+    if (!tm_wait_all(bars + s, (uint32_t)(it >> 1) & 1u)) {
       tm_abort(a.err, bars, pend_par, pending);
       return;
     }
     pending &= ~(1u << s);
-    const int bx = t % a.tiles_x, by = t / a.tiles_x;
-    const int x0 = bx * TM_TX, y0 = by * a.ty;
+    if (py < tl.ny) issue(px, py, s ^ 1, (uint32_t)((it + 1) >> 1) & 1u);
+    tl.advance(px, py);
+    const int x0 = bx * TM_TX, y0 = by * TY;
     const int gx0 = x0 - TM_HX, gy0 = y0 - NU;
     const int cy0 = (gy0 >> 1) - 1;
     const bool edge = gx0 < 0 || gy0 < 0 || gx0 + TM_P > n || gy0 + R > n;
@@ -462,7 +473,7 @@ __global__ void __launch_bounds__(TM_NT, 2)
       o[3] = q.y;
     };
     // sweep 1 on rows [1, R - 1) from the corrected v = v + P v_c, formed as rows enter the window
-    tm_walk(1, R - 1,
+    tm_walk<1, R - 2>(
             [&](int r) {
               float v[4], ca[4];
               tm_f4(vs, r, v);
@@ -492,7 +503,7 @@ __global__ void __launch_bounds__(TM_NT, 2)
     __syncthreads();
     // sweep 2 on the output rows [2, R - 2), written to global memory
     const TmColumn out(a.vout, a.ldvout, gx0, n);
-    tm_walk(NU, R - NU, [&](int r) { return tm_row(work, r); },
+    tm_walk<NU, R - 2 * NU>([&](int r) { return tm_row(work, r); },
             [&](int r, const Row6& S, const Row6& M, const Row6& N) {
               float fv[4], o[4];
               tm_f4(fs, r, fv);
@@ -501,9 +512,8 @@ __global__ void __launch_bounds__(TM_NT, 2)
               out.store(gy0 + r, o);
             });
     // this tile's generic-proxy writes to buffer set s are ordered before the tensor copies that
-    // refill it (issued at the top of iteration it + 1)
+    // refill it (issued after the next tile's wait, whose barrier every thread passes first)
     fence_proxy_async_smem();
-    __syncthreads();
   }
 }
 
