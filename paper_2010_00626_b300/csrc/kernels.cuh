@@ -948,33 +948,48 @@ __global__ void __launch_bounds__(NT) coarse_kernel(const CoarseArgs<T> a) {
 // Rows are dealt to warps round-robin over `parts` CTAs (the fused call's cluster, or the grid of
 // children_kernel).
 // ---------------------------------------------------------------------------------------------
+// Rows of P that part `part` of `parts` computes: a contiguous block [lo(part), lo(part + 1)).
+__host__ __device__ inline int child_rows_lo(int S, int part, int parts) { return (int)((long long)S * part / parts); }
+
+// Ask L2 for part `part`'s rows of P ahead of the matrix-vector product (one bulk prefetch by one
+// thread; the rows are contiguous and 16-byte aligned, pld being a whole number of 16-byte units).
+template <typename T>
+__device__ __forceinline__ void children_prefetch(const T* pmap, int pld, int S, int part, int parts) {
+  if (threadIdx.x != 0 || pmap == nullptr) return;
+  const int lo = child_rows_lo(S, part, parts), hi = child_rows_lo(S, part + 1, parts);
+  if (hi <= lo) return;
+  const T* p = pmap + (size_t)lo * pld;
+  const unsigned bytes = (unsigned)((size_t)(hi - lo) * pld * sizeof(T));
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <typename T, int NT>
 __device__ __forceinline__ void children_matvec(const T* __restrict__ pmap, int pld, const CoarseArgs<T>& a,
                                                 int part, int parts, T* fs) {
   const int s = a.n_lc, S = s * s;
-  for (int b = threadIdx.x; b < pld; b += NT) {
-    T val = T(0);
-    if (b < S) {
-      const int j = b / s, i = b - j * s;
-      val = a.f[(size_t)j * a.ldf + i];
-    }
-    fs[b] = val;
-  }
+  // f of level lc into shared memory, row by row (no division), zero padding up to pld
+  for (int j = threadIdx.x / 32; j < s; j += NT / 32)
+    for (int i = threadIdx.x & 31; i < s; i += 32) fs[j * s + i] = a.f[(size_t)j * a.ldf + i];
+  for (int b = S + (int)threadIdx.x; b < pld; b += NT) fs[b] = T(0);
   __syncthreads();
   constexpr int NW = NT / 32;
   constexpr int VW = 16 / sizeof(T);  // elements per 16-byte chunk
-  constexpr int RG = 4;               // rows a warp streams at once (independent loads in flight)
-  const int lane = threadIdx.x & 31, stride = parts * NW;
-  for (int k0 = part * NW + (threadIdx.x >> 5); k0 < S; k0 += RG * stride) {
+  // rows a warp streams at once, and 16-byte chunks per lane and row issued together: FP64 rows (up
+  // to 512 entries) take one round trip for two rows; FP32 rows (up to 1024) two for four rows
+  constexpr int RG = sizeof(T) == 8 ? 2 : 4;
+  constexpr int CH = 4;
+  const int lane = threadIdx.x & 31, stride = NW;
+  const int lo = child_rows_lo(S, part, parts), hi = child_rows_lo(S, part + 1, parts);
+  for (int k0 = lo + (threadIdx.x >> 5); k0 < hi; k0 += RG * stride) {
     T acc[RG];
     const T* row[RG];
 #pragma unroll
     for (int g = 0; g < RG; ++g) {
       acc[g] = T(0);
       const int k = k0 + g * stride;
-      row[g] = pmap + (size_t)(k < S ? k : k0) * pld;
+      row[g] = pmap + (size_t)(k < hi ? k : k0) * pld;
     }
-#pragma unroll 2
+#pragma unroll CH
     for (int b = VW * lane; b < pld; b += 32 * VW) {
       if constexpr (VW == 4) {
         const float4 x = *reinterpret_cast<const float4*>(fs + b);
@@ -1005,7 +1020,7 @@ __device__ __forceinline__ void children_matvec(const T* __restrict__ pmap, int 
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) acc[g] += __shfl_xor_sync(0xffffffffu, acc[g], o);
       const int k = k0 + g * stride;
-      if (lane == 0 && k < S) {
+      if (lane == 0 && k < hi) {
         const int j = k / s, i = k - j * s;
         a.v[(size_t)j * a.ldv + i] = acc[g];
       }
@@ -1062,6 +1077,7 @@ __global__ void __launch_bounds__(NT)
   cooperative_groups::cluster_group cluster = cooperative_groups::this_cluster();
   const int rank = (int)cluster.block_rank(), size = (int)cluster.num_blocks();
   const int tx = (pa.n + TILE - 1) / TILE, ntiles = tx * tx;
+  children_prefetch(pmap, pld, ca.n_lc * ca.n_lc, rank, size);  // lands in L2 while pass A runs
   for (int t = rank; t < ntiles; t += size) {
     pass_a_tile<T, TILE, TILE, NT, NS>(pa, t % tx, t / tx, 0, smem_raw);
     __syncthreads();  // the next tile reuses the shared memory
@@ -1115,6 +1131,8 @@ __global__ void __launch_bounds__(NT) call2_cluster_kernel(const Call2Args<T> a)
   const int rank = (int)cluster.block_rank(), size = (int)cluster.num_blocks();
   const int tx1 = (a.pa1.n + TILE1 - 1) / TILE1, nt1 = tx1 * tx1;
   const int tx2 = (a.pb2.n + TILE2 - 1) / TILE2, nt2 = tx2 * tx2;
+  children_prefetch(a.pmap[0], a.pld, a.cc.n_lc * a.cc.n_lc, rank, size);
+  if (a.children > 1) children_prefetch(a.pmap[1], a.pld, a.cc.n_lc * a.cc.n_lc, rank, size);
   for (int t = rank; t < nt1; t += size) {
     pass_a_tile<T, TILE1, TILE1, NT, false>(a.pa1, t % tx1, t / tx1, 0, smem_raw);
     __syncthreads();
