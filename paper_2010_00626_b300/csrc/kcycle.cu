@@ -2348,6 +2348,7 @@ int mg_profile_cycle(mg_handle h, double* v, const double* f, int kappa, int wit
   Binding b{v, f, h->n};
   const bool fp32 = (with_norm & 2) != 0;
   if (fp32) KC_TRY(ensure_levels32(h));
+  ensure_maps(h);  // the same condensed calls as the graphs of a cycle or a solve
   h->pev.clear();
   h->pkind.clear();
   h->plevel.clear();
