@@ -42,6 +42,16 @@ PASS_A_L0_TRAFFIC = {"source": "paper_2010_00626_b300/csrc/kernels.cuh", "until"
                      "bytes": 269_017_856 + 134_404_608}
 
 
+# The same for the FP32 tensor-copy passes at level 0 of the mixed solve's FP32 cycle (4095^2), keyed
+# by the whole of tma_f32.cuh.
+TMA_L0_TRAFFIC = {
+    "pass_a": {"source": "paper_2010_00626_b300/csrc/tma_f32.cuh", "sha256": "cab407984472104888ed2ac66e28f5fe6dcbc74e2bbe09fe864cd88a1cfc2f13",
+               "bytes": 67_183_616 + 33_107_712},
+    "pass_b": {"source": "paper_2010_00626_b300/csrc/tma_f32.cuh", "sha256": "cab407984472104888ed2ac66e28f5fe6dcbc74e2bbe09fe864cd88a1cfc2f13",
+               "bytes": 151_067_136 + 37_790_464},
+}
+
+
 def source_digest(entry):
     """SHA-256 of the kernel source text an entry's figure was measured on."""
     import hashlib
@@ -851,12 +861,23 @@ def main():
                            "relaxation (Section 4) on every instance")
 
     # ---------------------------------------------------------------- FP32 cycle of the mixed solve, per level
-    per_level32 = None
+    per_level32 = roofline_fp32 = None
     if not args.no_sweep:
         for _ in range(3):
             prof32 = mg.profile_cycle(v, f, kappa, fp32=True)
         per_level32 = per_level_report(mg, prof32, True, fp64_peak_ops, hbm_peak, False, sms, kappa, True)
         per_level32["cycle"] = f"FP32 kappa={kname(kappa)} cycle of the mixed solve (from zero)"
+        # the bandwidth roofline of the FP32 fused passes at level 0 (tensor-copy kernels)
+        roofline_fp32 = {}
+        for e in per_level32["levels"]:
+            if e["level"] == 0 and e["kind"] in ("pass_a", "pass_b"):
+                roofline_fp32[e["kind"]] = {
+                    "bound": "hbm", "achieved": e["gb_s"], "peak": hbm_peak, "unit": "GB/s", "frac": e["hbm_frac"],
+                    "us_per_launch": e["us_per_launch"],
+                    "traffic": measured_traffic(TMA_L0_TRAFFIC[e["kind"]]) if n == 4095 else None,
+                    "note": "algorithmic bytes (pass A from zero: f read, v and coarse f written, 9 B per point; "
+                            "pass B: v, f, coarse v read, v written, 13 B per point) over the launch's CUDA-event "
+                            "time in the FP32 cycle, eager"}
 
     # ---------------------------------------------------------------- oracle on the host cores
     cpu = None
@@ -875,7 +896,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": bench_config(kappa, world), "cycles": cycles, "ms_per_cycle": ms_step / cycles,
-                "roofline": roofline, "cycle_share": cycle_share, "per_level": per_level,
+                "roofline": roofline, "roofline_fp32_passes": roofline_fp32, "cycle_share": cycle_share,
+                "per_level": per_level,
                 "per_level_fp32": per_level32, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clocks.summary(), "per_kappa": per_kappa,
                 "per_kappa_mixed": per_kappa_mixed, "batched": batched, "model": model_report,

@@ -93,3 +93,14 @@ def test_both_arms_print_the_same_config():
         assert key in cfg
     assert "parallelism" not in cfg and bench.bench_config(4, 2)["parallelism"] == "replicas x2"
     assert set(bench.host_cpu()) == {"cpu_model", "nproc"}
+
+
+def test_stored_fp32_pass_traffic_matches_the_current_source():
+    """The FP32 tensor-copy passes' DRAM bytes are used only while tma_f32.cuh is the source the
+    capture ran on; the stored figures are near the algorithmic bytes (4095^2: 151 MB for pass A from
+    zero, 218 MB for pass B, writes partly still in L2 when the kernel ends)."""
+    for kind, alg in (("pass_a", 9 * 4095 ** 2), ("pass_b", 13 * 4095 ** 2)):
+        entry = bench.TMA_L0_TRAFFIC[kind]
+        got = bench.measured_traffic(entry)
+        assert got is None or got == entry["bytes"]
+        assert 0.5 * alg < entry["bytes"] < 1.2 * alg
