@@ -203,6 +203,49 @@ struct TmTiles {
   }
 };
 
+// The four points of a lane at once, with the Blackwell paired FP32 instructions (two lanes of
+// arithmetic per instruction, each element rounded as the scalar operation would be, so the results
+// equal jacobi_update / residual_at bit for bit): the neighbour pair sums are scalar additions, the
+// multiply-add chain runs on the pairs (points 0,1 and 2,3).
+struct Coef2 {
+  float2 w, b0, bwe, bns, bnw, bne, c0, cwe, cns, cnw, cne;  // both halves the same coefficient
+  __device__ __forceinline__ explicit Coef2(const Coef<float>& c)
+      : w(make_float2(c.w, c.w)), b0(make_float2(c.b0, c.b0)), bwe(make_float2(c.bwe, c.bwe)),
+        bns(make_float2(c.bns, c.bns)), bnw(make_float2(c.bnw, c.bnw)), bne(make_float2(c.bne, c.bne)),
+        c0(make_float2(-c.c0, -c.c0)), cwe(make_float2(-c.cwe, -c.cwe)), cns(make_float2(-c.cns, -c.cns)),
+        cnw(make_float2(-c.cnw, -c.cnw)), cne(make_float2(-c.cne, -c.cne)) {}
+};
+
+template <bool RES>
+__device__ __forceinline__ void stencil4(const Row6& S, const Row6& M, const Row6& N, const float (&f)[4],
+                                         const Coef2& c, float (&o)[4]) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int k = 2 * h;
+    const Nb<float> a = nb6(S, M, N, k), b = nb6(S, M, N, k + 1);
+    const float2 cc = make_float2(a.c, b.c), ff = make_float2(f[k], f[k + 1]);
+    const float2 we = make_float2(a.we, b.we), ns = make_float2(a.ns, b.ns);
+    const float2 d1 = make_float2(a.d1, b.d1), d2 = make_float2(a.d2, b.d2);
+    float2 t;
+    if (RES) {  // f - A v, in residual_at's order
+      t = __ffma2_rn(c.c0, cc, ff);
+      t = __ffma2_rn(c.cwe, we, t);
+      t = __ffma2_rn(c.cns, ns, t);
+      t = __ffma2_rn(c.cnw, d1, t);
+      t = __ffma2_rn(c.cne, d2, t);
+    } else {    // damped Jacobi, in jacobi_update's order
+      t = __fmul2_rn(c.b0, cc);
+      t = __ffma2_rn(c.w, ff, t);
+      t = __ffma2_rn(c.bwe, we, t);
+      t = __ffma2_rn(c.bns, ns, t);
+      t = __ffma2_rn(c.bnw, d1, t);
+      t = __ffma2_rn(c.bne, d2, t);
+    }
+    o[k] = t.x;
+    o[k + 1] = t.y;
+  }
+}
+
 // A row of the zero-start walk: v1 = w f with its halo, and the f row itself.
 struct ZRow {
   Row6 v;
@@ -260,6 +303,7 @@ __global__ void __launch_bounds__(TM_NT, 3)
   const int n = a.n, nc = (n - 1) / 2, lane = threadIdx.x & 31;
   const uint32_t box_bytes = (uint32_t)(TM_P * R * 4) * (ZERO ? 1u : 2u);
   const Coef<float> c = load_coef(a.coef, a.level);
+  const Coef2 c2(c);
   if (threadIdx.x == 0) {
     prefetch_tensormap(&map_f);
     if (!ZERO) prefetch_tensormap(&map_v);
@@ -314,8 +358,7 @@ __global__ void __launch_bounds__(TM_NT, 3)
               },
               [&](int r, const ZRow& S, const ZRow& M, const ZRow& N) {
                 float o[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) o[k] = jacobi_update(nb6(S.v, M.v, N.v, k), M.f[k], c);
+                stencil4<false>(S.v, M.v, N.v, M.f, c2, o);
                 if (edge) tm_mask(o, gx0, gy0 + r, n);
                 tm_st4(work, r, o);
               });
@@ -326,8 +369,7 @@ __global__ void __launch_bounds__(TM_NT, 3)
               [&](int r, const Row6& S, const Row6& M, const Row6& N) {
                 float fv[4], o[4];
                 tm_f4(fs, r, fv);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) o[k] = jacobi_update(nb6(S, M, N, k), fv[k], c);
+                stencil4<false>(S, M, N, fv, c2, o);
                 if (edge) tm_mask(o, gx0, gy0 + r, n);
                 tm_st4(work, r, o);
               });
@@ -336,8 +378,7 @@ __global__ void __launch_bounds__(TM_NT, 3)
               [&](int r, const Row6& S, const Row6& M, const Row6& N) {
                 float fv[4], o[4];
                 tm_f4(fs, r, fv);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) o[k] = jacobi_update(nb6(S, M, N, k), fv[k], c);
+                stencil4<false>(S, M, N, fv, c2, o);
                 if (edge) tm_mask(o, gx0, gy0 + r, n);
                 tm_st4(vs, r, o);
               });
@@ -351,8 +392,7 @@ __global__ void __launch_bounds__(TM_NT, 3)
             [&](int r, const Row6& S, const Row6& M, const Row6& N) {
               float fv[4], res[4];
               tm_f4(fs, r, fv);
-#pragma unroll
-              for (int k = 0; k < 4; ++k) res[k] = residual_at(nb6(S, M, N, k), fv[k], c);
+              stencil4<true>(S, M, N, fv, c2, res);
               const float nxt = __shfl_down_sync(0xffffffffu, res[0], 1);
               float2 h;
               h.x = fmaf(2.f, res[1], res[0] + res[2]);
@@ -417,6 +457,7 @@ __global__ void __launch_bounds__(TM_NT, 2)
   const int n = a.n, lane = threadIdx.x & 31;
   const uint32_t box_bytes = (uint32_t)(2 * TM_P * R * 4 + TM_CP * CR * 4);
   const Coef<float> c = load_coef(a.coef, a.level);
+  const Coef2 c2(c);
   if (threadIdx.x == 0) {
     prefetch_tensormap(&map_v);
     prefetch_tensormap(&map_f);
@@ -495,8 +536,7 @@ __global__ void __launch_bounds__(TM_NT, 2)
             [&](int r, const Row6& S, const Row6& M, const Row6& N) {
               float fv[4], o[4];
               tm_f4(fs, r, fv);
-#pragma unroll
-              for (int k = 0; k < 4; ++k) o[k] = jacobi_update(nb6(S, M, N, k), fv[k], c);
+              stencil4<false>(S, M, N, fv, c2, o);
               if (edge) tm_mask(o, gx0, gy0 + r, n);
               tm_st4(work, r, o);
             });
@@ -507,8 +547,7 @@ __global__ void __launch_bounds__(TM_NT, 2)
             [&](int r, const Row6& S, const Row6& M, const Row6& N) {
               float fv[4], o[4];
               tm_f4(fs, r, fv);
-#pragma unroll
-              for (int k = 0; k < 4; ++k) o[k] = jacobi_update(nb6(S, M, N, k), fv[k], c);
+              stencil4<false>(S, M, N, fv, c2, o);
               out.store(gy0 + r, o);
             });
     // this tile's generic-proxy writes to buffer set s are ordered before the tensor copies that
