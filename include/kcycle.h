@@ -109,13 +109,13 @@ typedef enum {
                               one of them walks). Not applied at level 0, to adjoint cycles, to
                               levels of more than 16 tiles, or where the device cannot run the
                               cluster (three launches then).                                    */
-  MG_OPT_TMA_PASSES = 15,  /* 1 (default): the FP32 cycles' passes at sides >= 1023 with nu = 2 run as
+  MG_OPT_TMA_PASSES = 15,  /* 1 (default): the FP32 cycles' passes at sides >= 255 with nu = 2 run as
                               persistent kernels whose input windows arrive by 2-D tensor copies
                               (TMA), double-buffered; 0: the shared-memory tile and register-pipeline
                               passes. Same arithmetic per point up to the order of FP32 rounding. Arrays
                               must be 16-byte aligned with pitches that are multiples of 4 floats (the
                               handle's own are), else the other passes run.                       */
-  MG_OPT_CONDENSED_CHILDREN = 16 /* 1 (default): the two calls that a call just above the coarse-
+  MG_OPT_CONDENSED_CHILDREN = 16, /* 1 (default): the two calls that a call just above the coarse-
                               kernel level makes there (counters k and k-1, the first from zero,
                               Algorithm 3), with everything below them, are one linear map of the
                               restricted residual, v = P_c f with c = min(k, levels - lc + 1);
@@ -125,6 +125,13 @@ typedef enum {
                               the call-by-call walk, rounded differently. Used where that level's
                               side is <= 31 and the maps take <= 64 MB; not for adjoint cycles.
                               0: the walk of the coarse-level kernel.                          */
+  MG_OPT_TEST_STALL_COPY = 17 /* Test hook for the bounded waits. t >= 0: the FP32 tensor-copy pass A
+                              at level 0 arms the copy barrier of tile t (row-major tile index) but
+                              issues no copy, so that CTA's wait runs out after its limit (0.5 s,
+                              twice); the CTA records the timeout and returns, the launch and the
+                              rest of the cycle complete, and the next call that reads the solve's
+                              result returns MG_ERR_TIMEOUT once. -1 (default): off. Makes no
+                              fault: every copy that is issued completes.                      */
 } mg_option;
 
 /* Set up the hierarchy for the Section 4 problem on an n x n interior grid.

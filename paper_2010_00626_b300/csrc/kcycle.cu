@@ -153,6 +153,7 @@ struct mg_ctx {
   // condensed child calls at the coarse-kernel level (children_kernel): per class c = 1..pm_cls the
   // map P_c (pm_side^2 rows of pitch pm_ld), FP64 and FP32 cycles; valid while pm_ok / pm32_ok
   int condense = 1;  // MG_OPT_CONDENSED_CHILDREN
+  int stall_tile = -1;  // MG_OPT_TEST_STALL_COPY
   double* pm = nullptr;
   float* pm32 = nullptr;
   int pm_cls = 0, pm_ld = 0, pm_side = 0, pm32_cls = 0, pm32_ld = 0, pm32_side = 0;
@@ -543,6 +544,7 @@ TmaPassArgs tma_args(const mg_ctx* h, int kind, int n, int level, const float* c
   t.coef = coef;
   t.skip = skip;
   t.err = err;
+  t.stall_tile = -1;
   t.vout = nullptr;
   t.ldvout = 0;
   t.fc = nullptr;
@@ -554,6 +556,7 @@ TmaPassArgs tma_args(const mg_ctx* h, int kind, int n, int level, const float* c
 int launch_pass_a_tma32(mg_ctx* h, const PassAArgs<float>& a, cudaStream_t s) {
   const int kind = tma_kind(a.vin ? TMA_A : TMA_A_ZERO, a.n);
   TmaPassArgs t = tma_args(h, kind, a.n, a.level, a.coef, a.skip, h->ints + I_ERR);
+  if (a.level == 0) t.stall_tile = h->stall_tile;
   t.vout = a.vout;
   t.ldvout = a.ldvout;
   t.fc = a.fc;
@@ -1857,6 +1860,13 @@ int mg_set_option(mg_handle h, int key, double value) {
       drop_graphs(h);
       return MG_OK;
     }
+    case MG_OPT_TEST_STALL_COPY: {
+      if (!(value >= -1.0 && value <= 1e9 && value == (double)(int)value)) return MG_ERR_ARG;
+      KC_CUDA(cudaStreamSynchronize(h->stream()));
+      h->stall_tile = (int)value;
+      drop_graphs(h);
+      return MG_OK;
+    }
     case MG_OPT_COARSE_OP: {
       if (!(value == 0.0 || value == 1.0)) return MG_ERR_ARG;
       if (h->semi && value != 0.0) return MG_ERR_ARG;
@@ -1950,6 +1960,7 @@ int mg_get_option(mg_handle h, int key, double* value) {
     case MG_OPT_FUSED_CALL: *value = h->fused; return MG_OK;
     case MG_OPT_TMA_PASSES: *value = h->tma32; return MG_OK;
     case MG_OPT_CONDENSED_CHILDREN: *value = h->condense; return MG_OK;
+    case MG_OPT_TEST_STALL_COPY: *value = h->stall_tile; return MG_OK;
     case MG_OPT_CONV_X: *value = h->bx; return MG_OK;
     case MG_OPT_CONV_Y: *value = h->by; return MG_OK;
     case MG_OPT_LEVELS: *value = h->levels; return MG_OK;

@@ -22,8 +22,9 @@
 // Outputs (the relaxed v, the coarse right-hand side, pass B's corrected and relaxed v) are written
 // from registers with coalesced vector stores.
 //
-// Waits are bounded: a copy that has not completed after TMA_WAIT_LIMIT polls sets *err, every CTA
-// waits (bounded again) for the copies it has issued and returns; the host reports MG_ERR_TIMEOUT.
+// Waits are bounded: a copy that has not completed after TMA_WAIT_NS nanoseconds of the global timer
+// (or TMA_WAIT_LIMIT polls, whichever comes first) sets *err, the CTA waits (bounded again) for the
+// copies it has issued and returns; the host reports MG_ERR_TIMEOUT.
 #pragma once
 #include <cuda.h>
 #include <stdint.h>
@@ -37,7 +38,8 @@ constexpr int TM_P = 128;         // staged columns (TM_TX + 2 * 4)
 constexpr int TM_HX = 4;          // staged halo columns per side
 constexpr int TM_NT = 256;        // threads per CTA (8 warps); two or three CTAs per SM
 constexpr int TM_CP = 72;         // staged coarse columns of pass B (x start rounded down to 4)
-constexpr uint32_t TMA_WAIT_LIMIT = 1u << 21;  // polls of at most about 1 us each: a copy gets ~2 s
+constexpr uint64_t TMA_WAIT_NS = 500000000ull;  // a copy gets half a second (it takes microseconds)
+constexpr uint32_t TMA_WAIT_LIMIT = 1u << 21;    // and at most this many polls (a poll lasts ~4 us)
 constexpr int TM_ERR_TIMEOUT = 1;
 
 // Rows of the staged window of a pass with TY output rows: pass A (nu sweeps, residual, full
@@ -95,10 +97,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 // Bounded wait for the phase with the given parity; false when the limit ran out.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < TMA_WAIT_LIMIT; ++it)
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < TMA_WAIT_LIMIT; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > TMA_WAIT_NS) break;
+  }
   return false;
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -258,6 +269,7 @@ struct TmaPassArgs {
   const float* coef;
   const int* skip;
   int* err;                   // set to TM_ERR_TIMEOUT when a copy never completes
+  int stall_tile;             // pass A test hook: this tile's copies are never issued (-1: none)
   float* vout;                // pass A: relaxed v (nullable); pass B: corrected and relaxed v
   int ldvout;
   float* fc;                  // pass A: coarse right-hand side
@@ -317,8 +329,10 @@ __global__ void __launch_bounds__(TM_NT, 3)
     if (threadIdx.x == 0) {
       const int gx0 = bx * TM_TX - TM_HX, gy0 = by * TY - (NU + 2);
       mbar_expect_tx(bars + s, box_bytes);
-      tma_load_2d(fin(s), &map_f, bars + s, gx0, gy0);
-      if (!ZERO) tma_load_2d(vin(s), &map_v, bars + s, gx0, gy0);
+      if (by * a.tiles_x + bx != a.stall_tile) {
+        tma_load_2d(fin(s), &map_f, bars + s, gx0, gy0);
+        if (!ZERO) tma_load_2d(vin(s), &map_v, bars + s, gx0, gy0);
+      }
     }
     pending |= 1u << s;
     pend_par = (pend_par & ~(1u << s)) | (parity << s);

@@ -146,6 +146,34 @@ def test_mixed_solve_large(lib):
     assert oracle.relres(h, host(xd), f) <= 1e-8 * (1 + 1e-6)
 
 
+def test_tensor_copy_wait_runs_out_and_reports_timeout(lib):
+    """Bounded waits: with the test hook, one CTA of the FP32 tensor-copy pass A at level 0 arms its
+    copy barrier for a tile whose copy is never issued. Its wait runs out after the limit, it
+    records the timeout and returns; the solve reports MG_ERR_TIMEOUT (-4) once, and the same handle
+    then solves as a fresh handle does, bit for bit (the context stays usable)."""
+    import time
+    n, levels, theta, eps = 1023, 10, math.pi / 3, 1e-4
+    f = rhs_normal(n, 0)
+    mg = lib.Multigrid(n, eps, theta, levels)
+    mg.set_option(lib.MG_OPT_TEST_STALL_COPY, 3)
+    assert mg.get_option(lib.MG_OPT_TEST_STALL_COPY) == 3
+    t0 = time.perf_counter()
+    with pytest.raises(lib.MultigridError, match=r"\(-4\)"):
+        mg.solve_mixed(dev(np.zeros((n, n))), dev(f), 1, 1e-8, 1)
+    waited = time.perf_counter() - t0
+    mg.set_option(lib.MG_OPT_TEST_STALL_COPY, -1)
+    xd = dev(np.zeros((n, n)))
+    st, iters, relres, _ = mg.solve_mixed(xd, dev(f), 3, 1e-8, 300)
+    fresh = lib.Multigrid(n, eps, theta, levels)
+    xe = dev(np.zeros((n, n)))
+    st2, iters2, relres2, _ = fresh.solve_mixed(xe, dev(f), 3, 1e-8, 300)
+    print(f"timed-out solve took {waited:.2f} s; then {iters} iterations")
+    assert st == 0 and st2 == 0 and iters == iters2 and relres == relres2
+    assert np.array_equal(host(xd), host(xe))
+    with pytest.raises(lib.MultigridError):
+        mg.set_option(lib.MG_OPT_TEST_STALL_COPY, -2)
+
+
 def test_mixed_solve_not_converged_and_bad_args(lib):
     n = 63
     mg = lib.Multigrid(n, 1e-4, 1.0, 6)
