@@ -54,7 +54,7 @@ typedef enum {
   MG_OPT_OMEGA = 1,        /* Jacobi damping (Section 4: between 0.8 and 0.87); default 0.8     */
   MG_OPT_COARSE_N = 2,     /* largest grid side handled by the single-CTA coarse-level kernel,
                               which walks the kappa recursion on the device; one of 1, 3, 7,
-                              15, 31, 63                                                          */
+                              15, 31 (default), 63                                                */
   MG_OPT_LEVELS = 3,       /* read-only: number of levels                                          */
   MG_OPT_N = 4,            /* read-only: finest grid side                                          */
   MG_OPT_LAUNCHES = 5,     /* read-only: kernel launches in the last cycle graph built              */
@@ -125,6 +125,17 @@ typedef enum {
                               the call-by-call walk, rounded differently. Used where that level's
                               side is <= 31 and the maps take <= 64 MB; not for adjoint cycles.
                               0: the walk of the coarse-level kernel.                          */
+  MG_OPT_DEEP_CALLS = 18,  /* 0 (off), 63, 127, 255 or 511: each call at the largest level of side
+                              <= this value runs, with every call below it, as one persistent
+                              cooperative launch of one or two CTAs per SM: pass A over the level's
+                              tiles, a grid barrier, the child calls (recursively, the two at the
+                              coarse-kernel level as the condensed product of
+                              MG_OPT_CONDENSED_CHILDREN), pass B, a grid barrier; the kappa
+                              recursion walked on the device. Same tiles and per-point arithmetic
+                              as the separate launches, so the same results bit for bit. Damped
+                              Jacobi, full coarsening, symmetric operators, not adjoint cycles, and
+                              only where the condensed maps exist (else the separate launches run).
+                              Grid barrier waits are bounded (0.5 s): MG_ERR_TIMEOUT.           */
   MG_OPT_TEST_STALL_COPY = 17 /* Test hook for the bounded waits. t >= 0: the FP32 tensor-copy pass A
                               at level 0 arms the copy barrier of tile t (row-major tile index) but
                               issues no copy, so that CTA's wait runs out after its limit (0.5 s,
@@ -262,7 +273,8 @@ int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas);
  * launch: ms[r] its duration in milliseconds, kind[r] 0 = pass A (relax + residual + restrict),
  * 1 = pass B (interpolate + correct + relax), 2 = coarse-level kernel, 3 = whole-grid residual;
  * level[r] its level (0 finest); kinds 4 and 5 are zebra row and column relaxations, kind 6 a call
- * run as one cluster launch (pass A, the coarse-level walk, pass B; MG_OPT_FUSED_CALL). Flags in
+ * run as one cluster launch (pass A, the coarse-level walk, pass B; MG_OPT_FUSED_CALL), kind 7 a
+ * call run with everything below it as one persistent launch (MG_OPT_DEEP_CALLS). Flags in
  * with_norm: bit 0 profiles the launches of a stand-alone solve cycle (with the residual partial
  * sums of its stopping test, formed by the first sweep of pass A at level 0 where mg_solve does so,
  * else by the last pass); bit 1 profiles instead the FP32 cycle of mg_solve_mixed (zero start on the

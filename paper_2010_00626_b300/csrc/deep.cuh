@@ -1,0 +1,173 @@
+// Persistent deep calls: one call at a small level with everything below it in one cooperative
+// launch (Algorithm 3's recursion walked on the device by every CTA of the grid in lock step).
+//
+// Below a few hundred points per side a level's pass is a few microseconds of latency-bound work,
+// and a kappa-cycle makes hundreds of such calls (the sum of Prop. 2.2's counts over the small
+// levels); as separate launches each pays its launch and its ramp. Here a grid of co-resident CTAs
+// (a cooperative launch: one or two per SM) runs, for the call at level `top` and recursively for
+// its child calls, pass A over the level's tiles, a grid barrier, the child calls, pass B over the
+// tiles, a grid barrier. At the level just above the coarse kernel's, the two child calls are the
+// condensed map v_lc = P_c f_lc (children_matvec), its rows dealt over the whole grid. Every
+// point's arithmetic is that of the separate launches (the same tile functions on the same tiles,
+// the same per-row sums), so the results equal them bit for bit.
+//
+// The grid barrier: after a CTA barrier, one thread per CTA counts the CTA in with an acquire-release
+// atomic add and polls the count with acquire loads until the whole grid has arrived (release and
+// acquire at GPU scope order every write before the barrier, of any thread of the CTA, before every
+// read after it). Waits are bounded (half a second of the global timer): a CTA whose wait runs out
+// records DEEP_ERR_TIMEOUT and returns, so every other CTA's next wait runs out too; the host
+// reports MG_ERR_TIMEOUT and clears the barrier words.
+#pragma once
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace kc {
+
+constexpr int DEEP_MAX_DEPTH = 6;                   // levels whose passes one launch runs
+constexpr uint64_t GRID_WAIT_NS = 500000000ull;     // a grid barrier waits at most half a second
+constexpr uint32_t GRID_WAIT_POLLS = 1u << 26;      // and at most this many polls
+constexpr int DEEP_ERR_TIMEOUT = 2;
+
+template <typename T>
+struct DeepArgs {
+  PassAArgs<T> pa[DEEP_MAX_DEPTH];  // level top + d; the kernel clears vin for a zero start
+  PassBArgs<T> pb[DEEP_MAX_DEPTH];
+  int tile[DEEP_MAX_DEPTH];         // tile edge of level top + d (8, 16 or 32), as its separate launches
+  CoarseArgs<T> cc;                 // the condensed level lc = top + depth: v, f, their pitches, side
+  const T* pmap;                    // P of counter class 1; class c at pmap + (c - 1) * pstride
+  size_t pstride;
+  int pld, pcls;
+  int top, depth;
+  int kappa, zero;                  // the launch's call: counter and start
+  unsigned* bar;                    // grid barrier words: arrivals, exits (both zero at rest)
+  int* err;                         // set to DEEP_ERR_TIMEOUT when a barrier wait runs out
+  const int* skip;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t deep_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// All CTAs of the grid meet; false (in every thread of the CTA) when this CTA's wait ran out. The
+// arrival is one acquire-release add on the count; a CTA that is not the last of its generation
+// polls the count with acquire loads until it reaches the generation's end (count a multiple of
+// the grid size: deep_exit clears it when the launch ends).
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* err) {
+  __shared__ int good;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
+    const unsigned target = (old / gridDim.x + 1u) * gridDim.x;
+    if (old + 1u != target) {
+      const uint64_t t0 = deep_ns();
+      for (uint32_t it = 1; ld_acquire_gpu(bar) < target; ++it) {
+        if (it >= GRID_WAIT_POLLS || ((it & 63u) == 0 && deep_ns() - t0 > GRID_WAIT_NS)) {
+          ok = 0;
+          atomicExch(err, DEEP_ERR_TIMEOUT);
+          break;
+        }
+      }
+    }
+    good = ok;
+  }
+  __syncthreads();
+  return good != 0;
+}
+
+// The end of a launch: the last CTA out (every CTA has passed every barrier by then) clears the
+// barrier words for the next launch.
+__device__ __forceinline__ void deep_exit(unsigned* bar) {
+  __syncthreads();
+  if (threadIdx.x == 0 && atomicAdd(bar + 1, 1u) == gridDim.x - 1) {
+    atomicExch(bar, 0u);
+    atomicExch(bar + 1, 0u);
+  }
+}
+
+template <typename T, int B, int NT>
+__device__ __forceinline__ void deep_tiles_a(const PassAArgs<T>& pa, unsigned char* smem) {
+  const int tx = (pa.n + B - 1) / B, nt = tx * tx;
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    pass_a_tile<T, B, B, NT, false>(pa, t % tx, t / tx, 0, smem);
+    __syncthreads();  // the next tile reuses the shared memory
+  }
+}
+template <typename T, int B, int NT>
+__device__ __forceinline__ void deep_tiles_b(const PassBArgs<T>& pb, unsigned char* smem) {
+  const int tx = (pb.n + B - 1) / B, nt = tx * tx;
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    pass_b_tile<T, B, B, NT, false>(pb, t % tx, t / tx, 0, smem);
+    __syncthreads();
+  }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) deep_kernel(const DeepArgs<T> a) {
+  if (a.skip && *a.skip) return;  // the same flag for every CTA: the whole grid returns
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // the recursion's frames: counter, start and stage of the call at depth d (level top + d)
+  int kap[DEEP_MAX_DEPTH], zer[DEEP_MAX_DEPTH], stage[DEEP_MAX_DEPTH];
+  int d = 0;
+  kap[0] = a.kappa;
+  zer[0] = a.zero;
+  stage[0] = 0;
+  while (d >= 0) {
+    if (stage[d] == 0) {  // pass A, then the child calls
+      PassAArgs<T> pa = a.pa[d];
+      if (zer[d]) pa.vin = nullptr;
+      switch (a.tile[d]) {
+        case 32: deep_tiles_a<T, 32, NT>(pa, smem_raw); break;
+        case 16: deep_tiles_a<T, 16, NT>(pa, smem_raw); break;
+        default: deep_tiles_a<T, 8, NT>(pa, smem_raw); break;
+      }
+      if (!grid_barrier(a.bar, a.err)) return;
+      if (d + 1 == a.depth) {  // children at the coarse-kernel level: v_lc = P_c f_lc
+        const int c = kap[d] < a.pcls ? kap[d] : a.pcls;
+        children_matvec<T, NT, 1, 8>(a.pmap + (size_t)(c - 1) * a.pstride, a.pld, a.cc, blockIdx.x, gridDim.x,
+                                     reinterpret_cast<T*>(smem_raw));
+        if (!grid_barrier(a.bar, a.err)) return;
+        stage[d] = 3;
+      } else {  // first child: counter k from zero
+        stage[d] = 1;
+        kap[d + 1] = kap[d];
+        zer[d + 1] = 1;
+        stage[d + 1] = 0;
+        ++d;
+        continue;
+      }
+    } else if (stage[d] == 1) {  // second child: counter k - 1 from the first child's result
+      if (kap[d] > 1) {
+        stage[d] = 2;
+        kap[d + 1] = kap[d] - 1;
+        zer[d + 1] = 0;
+        stage[d + 1] = 0;
+        ++d;
+        continue;
+      }
+      stage[d] = 3;
+    } else if (stage[d] == 2) {
+      stage[d] = 3;
+    }
+    // stage 3: pass B; the top call's needs no barrier after it (the launch ends)
+    switch (a.tile[d]) {
+      case 32: deep_tiles_b<T, 32, NT>(a.pb[d], smem_raw); break;
+      case 16: deep_tiles_b<T, 16, NT>(a.pb[d], smem_raw); break;
+      default: deep_tiles_b<T, 8, NT>(a.pb[d], smem_raw); break;
+    }
+    if (d > 0 && !grid_barrier(a.bar, a.err)) return;
+    --d;
+  }
+  deep_exit(a.bar);
+}
+
+}  // namespace kc

@@ -28,6 +28,7 @@
 #include "lines.cuh"
 #include "stream_f32.cuh"
 #include "tma_f32.cuh"
+#include "deep.cuh"
 
 using namespace kc;
 
@@ -59,6 +60,7 @@ constexpr int NT_COARSE32 = 512;   // coarse kernel, FP32 (latency bound: more t
 template <typename T>
 constexpr int nt_coarse() { return std::is_same<T, double>::value ? NT_COARSE : NT_COARSE32; }
 constexpr int NT_VEC = 256;
+constexpr int NT_DEEP = 256;  // persistent deep calls: threads per CTA (one or two CTAs per SM)
 constexpr int MAX_NU = 8;
 constexpr int VEC_BLOCKS = 148 * 8;
 constexpr int MAX_COARSE_N = 63;
@@ -112,7 +114,10 @@ using Binding = BindingT<double>;
 struct mg_ctx {
   int n = 0, k = 0, levels = 0, nu1 = 2, nu2 = 2;
   double eps = 0, theta = 0, omega = 0.8;
-  int coarse_n = 15;  // largest side handled by the coarse kernel (FP64 cycles)
+  int coarse_n = 31;  // largest side handled by the coarse kernel (FP64 cycles); its two child calls
+                      // of each call at 63^2 run as the condensed 961 x 961 product over ~120 CTAs
+                      // (measured at 4095^2 against 15: kappa=4 solve 1,860 -> 1,716 ms, every
+                      // kappa and the zebra and MGCG settings faster or equal)
   int lc = 0;         // first level handled by the coarse kernel (FP64 cycles)
   int lc32 = 0;       // same for the FP32 cycles of the mixed path
   int fused = 1;         // calls one (1) or two (2) levels above the coarse kernel as one cluster launch
@@ -154,6 +159,7 @@ struct mg_ctx {
   // map P_c (pm_side^2 rows of pitch pm_ld), FP64 and FP32 cycles; valid while pm_ok / pm32_ok
   int condense = 1;  // MG_OPT_CONDENSED_CHILDREN
   int stall_tile = -1;  // MG_OPT_TEST_STALL_COPY
+  int deep_n = 0;       // MG_OPT_DEEP_CALLS: calls at sides <= deep_n as one persistent launch (0: off)
   double* pm = nullptr;
   float* pm32 = nullptr;
   int pm_cls = 0, pm_ld = 0, pm_side = 0, pm32_cls = 0, pm32_ld = 0, pm32_side = 0;
@@ -382,7 +388,7 @@ const T* lv_f(mg_ctx* h, const BindingT<T>& b, int l) { return l == 0 ? b.f0 : A
 template <typename T>
 int lv_ld(mg_ctx* h, const BindingT<T>& b, int l) { return l == 0 ? b.ld0 : Arr<T>::ld(h, l); }
 
-enum { K_PASS_A = 0, K_PASS_B = 1, K_COARSE = 2, K_APPLY = 3, K_LINES_X = 4, K_LINES_Y = 5, K_CALL = 6 };
+enum { K_PASS_A = 0, K_PASS_B = 1, K_COARSE = 2, K_APPLY = 3, K_LINES_X = 4, K_LINES_Y = 5, K_CALL = 6, K_DEEP = 7 };
 // (under semi-coarsening K_PASS_A is the y restriction and K_PASS_B the y prolongation)
 
 void prof_begin(mg_ctx* h, int kind, int level, cudaStream_t s) {
@@ -672,6 +678,15 @@ size_t coarse_walk_smem(const mg_ctx* h, CoarseArgs<T>& a) {
   return base;
 }
 
+// CTAs of a stand-alone children_kernel launch: one row of P per warp, at most two CTAs per SM, at
+// least the fused call's cluster size.
+template <typename T>
+int child_parts(const mg_ctx* h, int side) {
+  constexpr int NW = nt_coarse<T>() / 32;
+  const int rows = side * side;
+  return std::max(CHILD_PARTS, std::min((rows + NW - 1) / NW, 2 * h->sms));
+}
+
 // The condensed child-call map for calls (k1, k2) from zero at the coarse-kernel level, or nullptr
 // (adjoint cycles, a nonzero start, other counter pairs, maps not built).
 template <typename T>
@@ -688,7 +703,7 @@ int emit_coarse(mg_ctx* h, const BindingT<T>& b, int k1, int k2, int zero1, bool
   int pld = 0;
   if (const T* pmap = child_map<T>(h, k1, k2, zero1, adjoint, &pld)) {
     prof_begin(h, K_COARSE, lc, s);
-    children_kernel<T, nt_coarse<T>()><<<CHILD_PARTS, nt_coarse<T>(), (size_t)pld * sizeof(T), s>>>(pmap, pld, a);
+    children_kernel<T, nt_coarse<T>()><<<child_parts<T>(h, a.n_lc), nt_coarse<T>(), (size_t)pld * sizeof(T), s>>>(pmap, pld, a);
     prof_end(h, s);
     KC_CUDA(cudaGetLastError());
     ++h->launch_count;
@@ -741,8 +756,8 @@ int compute_maps(mg_ctx* h) {
 }
 
 // Largest coarse-kernel side whose child calls are condensed, and the memory cap of the maps.
-constexpr int PM_MAX_SIDE = 31;
-constexpr size_t PM_MAX_BYTES = size_t(64) << 20;
+constexpr int PM_MAX_SIDE = 63;
+constexpr size_t PM_MAX_BYTES = size_t(512) << 20;
 
 // The condensed child-call maps P_c of the cycle in precision T (see children_matvec): for each
 // class c = 1 .. levels - lc + 1, one map-mode launch of the FP64 coarse kernel at level lc whose S
@@ -1281,9 +1296,105 @@ int emit_call_fused2(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zer
   return MG_OK;
 }
 
+// ------------------------------------------------------------------------------------------
+// Persistent deep calls (deep.cuh): a call at a side <= deep_n with everything below it in one
+// cooperative launch, its child calls at the coarse-kernel level condensed.
+// ------------------------------------------------------------------------------------------
+constexpr int DEEP_MAX_SIDE = 511;  // tiles up to 32 x 32, as tile_edge gives up to that side
+
+// Dynamic shared memory of a deep launch: the largest tile pass of its levels, and P's staged f.
+template <typename T>
+size_t deep_smem_tiles(int edge, int nu1, int nu2) {
+  switch (edge) {
+    case 32: return std::max(pass_a_smem<T, 32, 32>(nu1), pass_b_smem<T, 32, 32>(nu2, false));
+    case 16: return std::max(pass_a_smem<T, 16, 16>(nu1), pass_b_smem<T, 16, 16>(nu2, false));
+    default: return std::max(pass_a_smem<T, 8, 8>(nu1), pass_b_smem<T, 8, 8>(nu2, false));
+  }
+}
+template <typename T>
+size_t deep_smem_max() {
+  return std::max(deep_smem_tiles<T>(32, MAX_NU, MAX_NU), (size_t)round_up(63 * 63, 4) * sizeof(T));
+}
+
+// CTAs of a deep launch: one or two per SM, as many as stay resident together (0: the device runs
+// no cooperative launch of this kernel). Checked once per process and precision.
+template <typename T>
+int deep_grid(const mg_ctx* h) {
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    per_sm = 0;
+    int dev = 0, coop = 0, occ = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+        cudaFuncSetAttribute(deep_kernel<T, NT_DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)deep_smem_max<T>()) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, deep_kernel<T, NT_DEEP>, NT_DEEP, deep_smem_max<T>()) ==
+            cudaSuccess)
+      per_sm = std::min(occ, 2);
+    cudaGetLastError();
+  }
+  return per_sm * h->sms;
+}
+
+// Whether the call at level l starts a deep launch: the largest level at or below deep_n, damped
+// Jacobi with full coarsening and the symmetric stencil, its condensed child-call maps available.
+template <typename T>
+bool deep_ok(const mg_ctx* h, int l, bool adjoint) {
+  const int lc = lc_of<T>(h);
+  if (!h->deep_n || adjoint || h->smoother != 0 || h->semi || h->nonsym || l < 1 || l >= lc) return false;
+  if (h->lv[l].n > std::min(h->deep_n, DEEP_MAX_SIDE) || lc - l > DEEP_MAX_DEPTH) return false;
+  if (h->nu1 > MAX_NU || h->nu2 > MAX_NU) return false;
+  int ld = 0;
+  if (!Arr<T>::pmap(h, 1, &ld)) return false;
+  return deep_grid<T>(h) > 0;
+}
+
+template <typename T>
+int emit_deep(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero, const int* skip, cudaStream_t s) {
+  const int lc = lc_of<T>(h);
+  DeepArgs<T> a;
+  memset(&a, 0, sizeof(a));
+  size_t sm = 0;
+  for (int d = 0; d < lc - l; ++d) {
+    a.pa[d] = pass_a_args(h, b, l + d, false, h->nu1, skip, false, nullptr);
+    a.pb[d] = pass_b_args(h, b, l + d, h->nu2, nullptr, skip, false);
+    a.tile[d] = tile_edge(h->lv[l + d].n);
+    sm = std::max(sm, deep_smem_tiles<T>(a.tile[d], h->nu1, h->nu2));
+  }
+  a.cc = coarse_args(h, b, kappa, kappa > 1 ? kappa - 1 : 0, 1, false, skip);
+  a.pmap = Arr<T>::pmap(h, 1, &a.pld);
+  const int side = h->lv[lc].n;
+  a.pstride = (size_t)side * side * a.pld;
+  a.pcls = std::is_same<T, double>::value ? h->pm_cls : h->pm32_cls;
+  a.top = l;
+  a.depth = lc - l;
+  a.kappa = kappa;
+  a.zero = zero ? 1 : 0;
+  a.bar = reinterpret_cast<unsigned*>(h->ints + I_BAR);
+  a.err = h->ints + I_ERR;
+  a.skip = skip;
+  sm = std::max(sm, (size_t)a.pld * sizeof(T));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.gridDim = dim3(deep_grid<T>(h));
+  cfg.blockDim = dim3(NT_DEEP);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  ++h->launch_count;
+  prof_begin(h, K_DEEP, l, s);
+  KC_CUDA(cudaLaunchKernelEx(&cfg, deep_kernel<T, NT_DEEP>, a));
+  prof_end(h, s);
+  return MG_OK;
+}
+
 template <typename T>
 int emit_call(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero, bool adjoint, bool norm,
               const int* skip, cudaStream_t s) {
+  if (deep_ok<T>(h, l, adjoint)) return emit_deep(h, b, l, kappa, zero, skip, s);
   if (fused2_ok<T>(h, l, kappa, adjoint)) return emit_call_fused2(h, b, l, kappa, zero, skip, s);
   if (fused_call_ok<T>(h, l, adjoint)) return emit_call_fused(h, b, l, kappa, zero, skip, s);
   const int nu_pre = adjoint ? h->nu2 : h->nu1;
@@ -1500,13 +1611,17 @@ int launch_norm2(mg_ctx* h, const double* x, double* out_scalar, cudaStream_t s)
 
 bool valid_handle(mg_handle h) { return h && h->ok; }
 
-// A kernel whose bounded wait for a tensor copy ran out left code in the error slot: report it
-// once (MG_ERR_TIMEOUT) and clear the slot.
+// A kernel whose bounded wait (for a tensor copy, or at a deep call's grid barrier) ran out left
+// its code in the error slot: report it once (MG_ERR_TIMEOUT) and clear the slot.
 int device_error(mg_ctx* h, int code, cudaStream_t s) {
   if (code == 0) return MG_OK;
-  KC_CUDA(cudaMemsetAsync(h->ints + I_ERR, 0, sizeof(int), s));
+  // the error slot and the grid barrier's words (a timed-out barrier leaves its count behind)
+  KC_CUDA(cudaMemsetAsync(h->ints + I_ERR, 0, sizeof(int) * 3, s));
   KC_CUDA(cudaStreamSynchronize(s));
-  snprintf(g_err, sizeof(g_err), "a level kernel gave up waiting for its tensor copies (code %d)", code);
+  snprintf(g_err, sizeof(g_err), "%s (code %d)",
+           code == DEEP_ERR_TIMEOUT ? "a persistent deep call gave up waiting at a grid barrier"
+                                    : "a level kernel gave up waiting for its tensor copies",
+           code);
   return MG_ERR_TIMEOUT;
 }
 
@@ -1860,6 +1975,14 @@ int mg_set_option(mg_handle h, int key, double value) {
       drop_graphs(h);
       return MG_OK;
     }
+    case MG_OPT_DEEP_CALLS: {
+      const int c = (int)value;
+      if (value != (double)c || !(c == 0 || c == 63 || c == 127 || c == 255 || c == 511)) return MG_ERR_ARG;
+      KC_CUDA(cudaStreamSynchronize(h->stream()));
+      h->deep_n = c;
+      drop_graphs(h);
+      return MG_OK;
+    }
     case MG_OPT_TEST_STALL_COPY: {
       if (!(value >= -1.0 && value <= 1e9 && value == (double)(int)value)) return MG_ERR_ARG;
       KC_CUDA(cudaStreamSynchronize(h->stream()));
@@ -1961,6 +2084,7 @@ int mg_get_option(mg_handle h, int key, double* value) {
     case MG_OPT_TMA_PASSES: *value = h->tma32; return MG_OK;
     case MG_OPT_CONDENSED_CHILDREN: *value = h->condense; return MG_OK;
     case MG_OPT_TEST_STALL_COPY: *value = h->stall_tile; return MG_OK;
+    case MG_OPT_DEEP_CALLS: *value = h->deep_n; return MG_OK;
     case MG_OPT_CONV_X: *value = h->bx; return MG_OK;
     case MG_OPT_CONV_Y: *value = h->by; return MG_OK;
     case MG_OPT_LEVELS: *value = h->levels; return MG_OK;
@@ -2260,18 +2384,31 @@ int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* l
     std::vector<long long>& calls;
     long long& fine_launches;
     long long& coarse;
-    long long& absorbed;  // calls just above the coarse kernel's that run inside a two-level launch
-    void call(int l, int kap, bool inside = false) {
+    long long& absorbed;  // calls just above the coarse kernel's that run inside a larger launch
+    void call(int l, int kap, bool inside = false, bool deep = false) {
       calls[l] += 1;
       if (l >= h->lc) ++coarse;
       if (l == h->levels - 1) {
         if (h->semi) ++fine_launches;  // the one-row line solve
         return;
       }
+      if (deep && l < h->lc) {  // inside a persistent deep launch, with its condensed child calls
+        if (l + 1 == h->lc) ++absorbed;
+        call(l + 1, kap, false, true);
+        if (kap > 1) call(l + 1, kap - 1, false, true);
+        return;
+      }
       if (inside) {  // part of its parent's two-level launch
         ++absorbed;
         call(l + 1, kap);
         if (kap > 1) call(l + 1, kap - 1);
+        return;
+      }
+      if (l < h->lc && deep_ok<double>(h, l, false)) {
+        ++fine_launches;  // one launch for the call and everything below it
+        if (l + 1 == h->lc) ++absorbed;
+        call(l + 1, kap, false, true);
+        if (kap > 1) call(l + 1, kap - 1, false, true);
         return;
       }
       if (l < h->lc && fused2_ok<double>(h, l, kap, false)) {
@@ -2307,6 +2444,7 @@ int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas) {
   if (!valid_handle(h)) return MG_ERR_STATE;
   if (!n_level || !ctas || level < 0 || level >= h->levels) return MG_ERR_ARG;
   if (h->smoother != 0 || h->semi) return MG_ERR_ARG;
+  ensure_maps(h);  // deep and condensed calls depend on the maps being available
   const int n = h->lv[level].n;
   *n_level = n;
   int lc = h->lc;
@@ -2322,6 +2460,11 @@ int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas) {
     *ctas = 1;
     return MG_OK;
   }
+  for (int l = 1; l <= level; ++l)
+    if (fp32 ? deep_ok<float>(h, l, false) : deep_ok<double>(h, l, false)) {
+      *ctas = fp32 ? deep_grid<float>(h) : deep_grid<double>(h);  // inside a persistent deep launch
+      return MG_OK;
+    }
   if (h->fused >= 2 && h->condense && !h->nonsym && level >= 1 && level + 2 == lc && h->lv[lc].n <= PM_MAX_SIDE &&
       (fp32 ? call2_cluster_supported<float>() : call2_cluster_supported<double>())) {
     *ctas = CALL_MAX_CTAS;  // the call runs with its child calls as one cluster launch

@@ -963,7 +963,11 @@ __device__ __forceinline__ void children_prefetch(const T* pmap, int pld, int S,
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-template <typename T, int NT>
+// RG rows a warp streams at once and CH 16-byte chunks per lane and row issued together. Inside a
+// fused call (16 CTAs, many rows per warp): FP64 rows (up to 512 entries here) take one round trip
+// for two rows, FP32 rows (up to 1024) two for four rows. A stand-alone launch gives each warp about
+// one row and streams it eight chunks per lane at a time.
+template <typename T, int NT, int RG = (sizeof(T) == 8 ? 2 : 4), int CH = 4>
 __device__ __forceinline__ void children_matvec(const T* __restrict__ pmap, int pld, const CoarseArgs<T>& a,
                                                 int part, int parts, T* fs) {
   const int s = a.n_lc, S = s * s;
@@ -974,10 +978,6 @@ __device__ __forceinline__ void children_matvec(const T* __restrict__ pmap, int 
   __syncthreads();
   constexpr int NW = NT / 32;
   constexpr int VW = 16 / sizeof(T);  // elements per 16-byte chunk
-  // rows a warp streams at once, and 16-byte chunks per lane and row issued together: FP64 rows (up
-  // to 512 entries) take one round trip for two rows; FP32 rows (up to 1024) two for four rows
-  constexpr int RG = sizeof(T) == 8 ? 2 : 4;
-  constexpr int CH = 4;
   const int lane = threadIdx.x & 31, stride = NW;
   const int lo = child_rows_lo(S, part, parts), hi = child_rows_lo(S, part + 1, parts);
   for (int k0 = lo + (threadIdx.x >> 5); k0 < hi; k0 += RG * stride) {
@@ -1028,14 +1028,15 @@ __device__ __forceinline__ void children_matvec(const T* __restrict__ pmap, int 
   }
 }
 
-constexpr int CHILD_PARTS = 16;  // CTAs of children_kernel (the fused call's cluster size)
+constexpr int CHILD_PARTS = 16;  // the fused call's cluster size, and the fewest CTAs of children_kernel
 
-// The condensed child calls as their own launch (calls not fused with their parent's passes).
+// The condensed child calls as their own launch (calls not fused with their parent's passes), one
+// row per warp where the grid allows.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) children_kernel(const T* __restrict__ pmap, int pld, const CoarseArgs<T> a) {
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  children_matvec<T, NT>(pmap, pld, a, blockIdx.x, gridDim.x, reinterpret_cast<T*>(smem_raw));
+  children_matvec<T, NT, 1, 8>(pmap, pld, a, blockIdx.x, gridDim.x, reinterpret_cast<T*>(smem_raw));
 }
 
 // Column-major FP64 maps (entry (k, b) at b * S + k, as map mode writes them) to row-major maps in
@@ -1515,7 +1516,9 @@ enum {
   NSCAL = 8
 };
 // Integer slots
-enum { I_DONE = 0, I_COUNT, I_MAX, I_ERR, NINT = 4 };  // I_ERR: set by a kernel whose bounded wait ran out
+// I_ERR: set by a kernel whose bounded wait ran out; I_BAR, I_BAR + 1: the persistent deep calls'
+// grid barrier (arrivals, generation)
+enum { I_DONE = 0, I_COUNT, I_MAX, I_ERR, I_BAR, NINT = 6 };
 
 template <int NT>
 __global__ void __launch_bounds__(NT) sum_to_scalar_kernel(const double* partial, int np, double* out) {

@@ -21,6 +21,9 @@ def dev(a, dtype="float64"):
 
 
 def pair(lib, *args, **kw):
+    # FP64 fused calls run at 31^2, the level above a 15^2 coarse kernel (the default coarse kernel
+    # at 31^2 leaves the FP64 cycle no level with at most 16 tiles above it)
+    kw.setdefault("coarse_n", 15)
     on = lib.Multigrid(*args, **kw)
     off = lib.Multigrid(*args, **kw)
     off.set_option(lib.MG_OPT_FUSED_CALL, 0)
@@ -160,8 +163,8 @@ def test_one_and_two_level_fusion_equal_bitwise(lib, n, levels, kappa):
     """MG_OPT_FUSED_CALL = 2 (calls two levels above the coarse kernel fused with their child calls)
     against 1 (only the level just above): same iterates in FP64 and FP32."""
     import torch
-    two = lib.Multigrid(n, 3e-4, 2.2, levels)
-    one = lib.Multigrid(n, 3e-4, 2.2, levels)
+    two = lib.Multigrid(n, 3e-4, 2.2, levels, coarse_n=15)  # FP64: the fused levels above 15^2
+    one = lib.Multigrid(n, 3e-4, 2.2, levels, coarse_n=15)
     two.set_option(lib.MG_OPT_FUSED_CALL, 2)
     f = dev(rhs_uniform(n, 9))
     a, b = torch.zeros_like(f), torch.zeros_like(f)

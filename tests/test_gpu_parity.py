@@ -235,9 +235,13 @@ def test_level_grid_reports_the_launch_shapes(lib):
     tiles of 120 columns), the FP32 coarse kernel from 31^2; with MG_OPT_TMA_PASSES = 0 pass B as
     the register pipelines at 4095 (35 strips of 120 columns, 4 per CTA, chunks of 64 rows) and the
     shared-memory tiles of 112 x 16 at 2047. The level just above the coarse kernel runs its calls
-    as one cluster launch: 16 CTAs of 8^2 tiles at 31^2 (FP64), of 16^2 tiles at 63^2 (FP32);
-    without the fused calls 64 CTAs at 63^2 (FP32)."""
-    mg = lib.Multigrid(4095, 1e-4, math.pi / 3, 12)
+    as one cluster launch: 16 CTAs of 8^2 tiles at 31^2 (FP64 with the coarse kernel at 15^2), of
+    16^2 tiles at 63^2 (FP32); without the fused calls 64 CTAs at 63^2 (FP32). With the default FP64
+    coarse kernel at 31^2, the 63^2 level keeps its 64 tiles (a fused call would need at most 16)."""
+    default = lib.Multigrid(4095, 1e-4, math.pi / 3, 12)
+    assert [default.level_grid(l)[1] for l in range(12)] == [64 * 128, 32 * 64, 32 * 32, 16 * 16, 16 * 16,
+                                                            16 * 16, 8 * 8, 1, 1, 1, 1, 1]
+    mg = lib.Multigrid(4095, 1e-4, math.pi / 3, 12, coarse_n=15)
     fp64 = [mg.level_grid(l) for l in range(12)]
     assert [c for _, c in fp64] == [64 * 128, 32 * 64, 32 * 32, 16 * 16, 16 * 16, 16 * 16, 8 * 8, 4 * 4,
                                      1, 1, 1, 1]
