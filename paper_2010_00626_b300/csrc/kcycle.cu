@@ -160,6 +160,7 @@ struct mg_ctx {
   int condense = 1;  // MG_OPT_CONDENSED_CHILDREN
   int stall_tile = -1;  // MG_OPT_TEST_STALL_COPY
   int deep_n = 0;       // MG_OPT_DEEP_CALLS: calls at sides <= deep_n as one persistent launch (0: off)
+  bool batched = false;  // an instance of a batch: its graph branch runs beside the others'
   double* pm = nullptr;
   float* pm32 = nullptr;
   int pm_cls = 0, pm_ld = 0, pm_side = 0, pm32_cls = 0, pm32_ld = 0, pm32_side = 0;
@@ -679,9 +680,11 @@ size_t coarse_walk_smem(const mg_ctx* h, CoarseArgs<T>& a) {
 }
 
 // CTAs of a stand-alone children_kernel launch: one row of P per warp, at most two CTAs per SM, at
-// least the fused call's cluster size.
+// least the fused call's cluster size; the cluster size in a batch, whose concurrent branches share
+// the SMs.
 template <typename T>
 int child_parts(const mg_ctx* h, int side) {
+  if (h->batched) return CHILD_PARTS;
   constexpr int NW = nt_coarse<T>() / 32;
   const int rows = side * side;
   return std::max(CHILD_PARTS, std::min((rows + NW - 1) / NW, 2 * h->sms));
@@ -1341,7 +1344,8 @@ int deep_grid(const mg_ctx* h) {
 template <typename T>
 bool deep_ok(const mg_ctx* h, int l, bool adjoint) {
   const int lc = lc_of<T>(h);
-  if (!h->deep_n || adjoint || h->smoother != 0 || h->semi || h->nonsym || l < 1 || l >= lc) return false;
+  if (!h->deep_n || h->batched || adjoint || h->smoother != 0 || h->semi || h->nonsym || l < 1 || l >= lc)
+    return false;
   if (h->lv[l].n > std::min(h->deep_n, DEEP_MAX_SIDE) || lc - l > DEEP_MAX_DEPTH) return false;
   if (h->nu1 > MAX_NU || h->nu2 > MAX_NU) return false;
   int ld = 0;
@@ -1978,6 +1982,7 @@ int mg_set_option(mg_handle h, int key, double value) {
     case MG_OPT_DEEP_CALLS: {
       const int c = (int)value;
       if (value != (double)c || !(c == 0 || c == 63 || c == 127 || c == 255 || c == 511)) return MG_ERR_ARG;
+      if (c && h->batched) return MG_ERR_ARG;  // cooperative launches in concurrent graph branches
       KC_CUDA(cudaStreamSynchronize(h->stream()));
       h->deep_n = c;
       drop_graphs(h);
@@ -2664,6 +2669,7 @@ int mg_batch_create(int count, const int* n, const double* eps, const double* th
     // levels, SMs the other instances' concurrent branches would use (measured: 256-instance mixed
     // batch 4.2 s without, 4.7 s with)
     h->fused = 0;
+    h->batched = true;
     b->inst.push_back(h);
   }
   if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {

@@ -29,6 +29,8 @@
 #include <cuda.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "stream_f32.cuh"
 
 namespace kc {
@@ -184,6 +186,11 @@ struct TmColumn {
     cols = (lane >= 1 && lane <= 30 && gx < n_) ? min(4, n_ - gx) : 0;
     p = base + gx;
   }
+  // A tile away from the grid's edges: lanes 1..30 store whole float4 rows (pred folds in the row
+  // and lane conditions, so the store is one predicated instruction)
+  __device__ __forceinline__ void store_inner(int gy, const float (&o)[4], bool pred) const {
+    if (pred) *reinterpret_cast<float4*>(p + gy * ld) = make_float4(o[0], o[1], o[2], o[3]);
+  }
   __device__ __forceinline__ void store(int gy, const float (&o)[4]) const {
     if (gy >= n || cols == 0) return;
     float* q = p + gy * ld;
@@ -313,6 +320,7 @@ __global__ void __launch_bounds__(TM_NT, 3)
   uint64_t* bars = reinterpret_cast<uint64_t*>(p);
 
   const int n = a.n, nc = (n - 1) / 2, lane = threadIdx.x & 31;
+  const bool inner = (unsigned)(lane - 1) < 30u;  // lanes holding output columns
   const uint32_t box_bytes = (uint32_t)(TM_P * R * 4) * (ZERO ? 1u : 2u);
   const Coef<float> c = load_coef(a.coef, a.level);
   const Coef2 c2(c);
@@ -355,6 +363,10 @@ __global__ void __launch_bounds__(TM_NT, 3)
     const int x0 = bx * TM_TX, y0 = by * TY;
     const int gx0 = x0 - TM_HX, gy0 = y0 - (NU + 2);
     const bool edge = gx0 < 0 || gy0 < 0 || gx0 + TM_P > n || gy0 + R > n;
+    // tiles away from the grid's edges (all but a few percent) run without masks and with
+    // predicated whole-row stores; the edge tiles take the general code
+    auto tile = [&](auto edge_c) {
+    constexpr bool EDGE = decltype(edge_c)::value;
     const float* fs = fin(s);
     float* v2;  // the second sweep's result
     if (ZERO) {
@@ -373,7 +385,7 @@ __global__ void __launch_bounds__(TM_NT, 3)
               [&](int r, const ZRow& S, const ZRow& M, const ZRow& N) {
                 float o[4];
                 stencil4<false>(S.v, M.v, N.v, M.f, c2, o);
-                if (edge) tm_mask(o, gx0, gy0 + r, n);
+                if constexpr (EDGE) tm_mask(o, gx0, gy0 + r, n);
                 tm_st4(work, r, o);
               });
       v2 = work;
@@ -384,7 +396,7 @@ __global__ void __launch_bounds__(TM_NT, 3)
                 float fv[4], o[4];
                 tm_f4(fs, r, fv);
                 stencil4<false>(S, M, N, fv, c2, o);
-                if (edge) tm_mask(o, gx0, gy0 + r, n);
+                if constexpr (EDGE) tm_mask(o, gx0, gy0 + r, n);
                 tm_st4(work, r, o);
               });
       __syncthreads();
@@ -393,7 +405,7 @@ __global__ void __launch_bounds__(TM_NT, 3)
                 float fv[4], o[4];
                 tm_f4(fs, r, fv);
                 stencil4<false>(S, M, N, fv, c2, o);
-                if (edge) tm_mask(o, gx0, gy0 + r, n);
+                if constexpr (EDGE) tm_mask(o, gx0, gy0 + r, n);
                 tm_st4(vs, r, o);
               });
       v2 = vs;
@@ -412,9 +424,11 @@ __global__ void __launch_bounds__(TM_NT, 3)
               h.x = fmaf(2.f, res[1], res[0] + res[2]);
               h.y = fmaf(2.f, res[3], res[2] + nxt);
               hsum[r * 32 + lane] = h;
-              if (r >= NU + 2 && r < R - (NU + 2)) {
-                const float o[4] = {M.v[0], M.v[1], M.v[2], M.v[3]};
-                out.store(gy0 + r, o);
+              const float o[4] = {M.v[0], M.v[1], M.v[2], M.v[3]};
+              if constexpr (EDGE) {
+                if (r >= NU + 2 && r < R - (NU + 2)) out.store(gy0 + r, o);
+              } else {
+                out.store_inner(gy0 + r, o, inner && r >= NU + 2 && r < R - (NU + 2));
               }
             });
     __syncthreads();
@@ -424,13 +438,13 @@ __global__ void __launch_bounds__(TM_NT, 3)
       constexpr int NW = TM_NT / 32;
       constexpr int cj_n = TY / 2;
       const int I = x0 / 2 + 2 * lane - 2;
-      const int ccols = (lane >= 1 && lane <= 30 && I < nc) ? min(2, nc - I) : 0;
+      const int ccols = EDGE ? ((lane >= 1 && lane <= 30 && I < nc) ? min(2, nc - I) : 0) : (inner ? 2 : 0);
       float* cp = a.fc + I;
       for (int j = threadIdx.x >> 5; j < cj_n; j += NW) {
         const int J = y0 / 2 + j;
         const int r = 2 * j + (NU + 2) + 1;
         const float2 hs = hsum[(r - 1) * 32 + lane], hm = hsum[r * 32 + lane], hn = hsum[(r + 1) * 32 + lane];
-        if (ccols && J < nc) {
+        if (ccols && (!EDGE || J < nc)) {
           float2 o;
           o.x = 0.0625f * fmaf(2.f, hm.x, hs.x + hn.x);
           o.y = 0.0625f * fmaf(2.f, hm.y, hs.y + hn.y);
@@ -440,6 +454,9 @@ __global__ void __launch_bounds__(TM_NT, 3)
         }
       }
     }
+    };
+    if (edge) tile(std::true_type{});
+    else tile(std::false_type{});
     // this tile's generic-proxy writes to buffer set s are ordered before the tensor copies that
     // refill it (issued after the next tile's wait, whose barrier every thread passes first)
     fence_proxy_async_smem();
@@ -469,6 +486,7 @@ __global__ void __launch_bounds__(TM_NT, 2)
   uint64_t* bars = reinterpret_cast<uint64_t*>(p);
 
   const int n = a.n, lane = threadIdx.x & 31;
+  const bool inner = (unsigned)(lane - 1) < 30u;  // lanes holding output columns
   const uint32_t box_bytes = (uint32_t)(2 * TM_P * R * 4 + TM_CP * CR * 4);
   const Coef<float> c = load_coef(a.coef, a.level);
   const Coef2 c2(c);
@@ -513,6 +531,8 @@ __global__ void __launch_bounds__(TM_NT, 2)
     const int gx0 = x0 - TM_HX, gy0 = y0 - NU;
     const int cy0 = (gy0 >> 1) - 1;
     const bool edge = gx0 < 0 || gy0 < 0 || gx0 + TM_P > n || gy0 + R > n;
+    auto tile = [&](auto edge_c) {  // interior tiles: no masks, predicated whole-row stores
+    constexpr bool EDGE = decltype(edge_c)::value;
     const float* vs = vin(s);
     const float* fs = fin(s);
     const float* cs = cin(s);
@@ -544,14 +564,14 @@ __global__ void __launch_bounds__(TM_NT, 2)
 #pragma unroll
                 for (int k = 0; k < 4; ++k) v[k] += 0.5f * (ca[k] + cb[k]);
               }
-              if (edge) tm_mask(v, gx0, gy, n);
+              if constexpr (EDGE) tm_mask(v, gx0, gy, n);
               return with_halo(v);
             },
             [&](int r, const Row6& S, const Row6& M, const Row6& N) {
               float fv[4], o[4];
               tm_f4(fs, r, fv);
               stencil4<false>(S, M, N, fv, c2, o);
-              if (edge) tm_mask(o, gx0, gy0 + r, n);
+              if constexpr (EDGE) tm_mask(o, gx0, gy0 + r, n);
               tm_st4(work, r, o);
             });
     __syncthreads();
@@ -562,8 +582,12 @@ __global__ void __launch_bounds__(TM_NT, 2)
               float fv[4], o[4];
               tm_f4(fs, r, fv);
               stencil4<false>(S, M, N, fv, c2, o);
-              out.store(gy0 + r, o);
+              if constexpr (EDGE) out.store(gy0 + r, o);
+              else out.store_inner(gy0 + r, o, inner);
             });
+    };
+    if (edge) tile(std::true_type{});
+    else tile(std::false_type{});
     // this tile's generic-proxy writes to buffer set s are ordered before the tensor copies that
     // refill it (issued after the next tile's wait, whose barrier every thread passes first)
     fence_proxy_async_smem();
