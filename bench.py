@@ -45,10 +45,10 @@ PASS_A_L0_TRAFFIC = {"source": "paper_2010_00626_b300/csrc/kernels.cuh", "until"
 # The same for the FP32 tensor-copy passes at level 0 of the mixed solve's FP32 cycle (4095^2), keyed
 # by the whole of tma_f32.cuh.
 TMA_L0_TRAFFIC = {
-    "pass_a": {"source": "paper_2010_00626_b300/csrc/tma_f32.cuh", "sha256": "cab407984472104888ed2ac66e28f5fe6dcbc74e2bbe09fe864cd88a1cfc2f13",
-               "bytes": 67_183_616 + 33_107_712},
-    "pass_b": {"source": "paper_2010_00626_b300/csrc/tma_f32.cuh", "sha256": "cab407984472104888ed2ac66e28f5fe6dcbc74e2bbe09fe864cd88a1cfc2f13",
-               "bytes": 151_067_136 + 37_790_464},
+    "pass_a": {"source": "paper_2010_00626_b300/csrc/tma_f32.cuh", "sha256": "aedf126f506700bace586c5478c5e794744bdcbc7feb452e929347050a973443",
+               "bytes": 67_187_200 + 33_016_064},
+    "pass_b": {"source": "paper_2010_00626_b300/csrc/tma_f32.cuh", "sha256": "aedf126f506700bace586c5478c5e794744bdcbc7feb452e929347050a973443",
+               "bytes": 151_072_512 + 37_347_072},
 }
 
 
@@ -308,7 +308,8 @@ def error_vs_fp64(mg, x, f, x_star):
 
 # launch kinds of mg_profile_cycle
 PROFILE_KINDS = {0: "pass_a", 1: "pass_b", 2: "coarse", 3: "residual", 4: "lines_x", 5: "lines_y",
-                 6: "call"}  # call: pass A, the coarse walk and pass B of one call in one cluster launch
+                 6: "call",  # call: pass A, the coarse walk and pass B of one call in one cluster launch
+                 7: "deep"}  # deep: a call with every call below it in one persistent cooperative launch
 
 
 def per_level_report(mg, prof, fp32, fp64_peak_ops, hbm_peak, norm_l0, sms, kappa, l0_zero):

@@ -125,7 +125,8 @@ typedef enum {
                               the call-by-call walk, rounded differently. Used where that level's
                               side is <= 31 and the maps take <= 64 MB; not for adjoint cycles.
                               0: the walk of the coarse-level kernel.                          */
-  MG_OPT_DEEP_CALLS = 18,  /* 0 (off), 63, 127, 255 or 511: each call at the largest level of side
+  MG_OPT_DEEP_CALLS = 18,  /* 0 (off), 63, 127 (default), 255 or 511 (batch instances: 0 only): each
+                              call at the largest level of side
                               <= this value runs, with every call below it, as one persistent
                               cooperative launch of one or two CTAs per SM: pass A over the level's
                               tiles, a grid barrier, the child calls (recursively, the two at the

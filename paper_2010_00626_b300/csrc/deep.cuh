@@ -7,7 +7,9 @@
 // (a cooperative launch: one or two per SM) runs, for the call at level `top` and recursively for
 // its child calls, pass A over the level's tiles, a grid barrier, the child calls, pass B over the
 // tiles, a grid barrier. At the level just above the coarse kernel's, the two child calls are the
-// condensed map v_lc = P_c f_lc (children_matvec), its rows dealt over the whole grid. Every
+// condensed map v_lc = P_c f_lc (children_matvec), its rows dealt over the whole grid; each CTA's
+// rows of P_c arrive in its shared memory by one bulk copy issued before the parent's pass A, so the
+// product waits only for f_lc. Every
 // point's arithmetic is that of the separate launches (the same tile functions on the same tiles,
 // the same per-row sums), so the results equal them bit for bit.
 //
@@ -21,6 +23,7 @@
 #include <stdint.h>
 
 #include "kernels.cuh"
+#include "tma_f32.cuh"  // mbarrier helpers and bounded waits
 
 namespace kc {
 
@@ -40,6 +43,7 @@ struct DeepArgs {
   int pld, pcls;
   int top, depth;
   int kappa, zero;                  // the launch's call: counter and start
+  int prow_off;                     // shared-memory offset of the staged rows of P (16-byte aligned)
   unsigned* bar;                    // grid barrier words: arrivals, exits (both zero at rest)
   int* err;                         // set to DEEP_ERR_TIMEOUT when a barrier wait runs out
   const int* skip;
@@ -115,6 +119,19 @@ template <typename T, int NT>
 __global__ void __launch_bounds__(NT) deep_kernel(const DeepArgs<T> a) {
   if (a.skip && *a.skip) return;  // the same flag for every CTA: the whole grid returns
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // this CTA's rows of P (a contiguous block, see child_rows_lo) and the copy's barrier after them
+  const int S = a.cc.n_lc * a.cc.n_lc;
+  const int rlo = child_rows_lo(S, blockIdx.x, gridDim.x), rhi = child_rows_lo(S, blockIdx.x + 1, gridDim.x);
+  T* prow = reinterpret_cast<T*>(smem_raw + a.prow_off);
+  const uint32_t pbytes = (uint32_t)((size_t)(rhi - rlo) * a.pld * sizeof(T));
+  uint64_t* pbar = reinterpret_cast<uint64_t*>(smem_raw + a.prow_off + (((size_t)pbytes + 15) & ~(size_t)15));
+  uint32_t pphase = 0;
+  bool pinflight = false;
+  if (threadIdx.x == 0 && pbytes) {
+    mbar_init(pbar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
   // the recursion's frames: counter, start and stage of the call at depth d (level top + d)
   int kap[DEEP_MAX_DEPTH], zer[DEEP_MAX_DEPTH], stage[DEEP_MAX_DEPTH];
   int d = 0;
@@ -123,6 +140,19 @@ __global__ void __launch_bounds__(NT) deep_kernel(const DeepArgs<T> a) {
   stage[0] = 0;
   while (d >= 0) {
     if (stage[d] == 0) {  // pass A, then the child calls
+      if (d + 1 == a.depth && pbytes) {  // fetch this CTA's rows of P_c while pass A runs
+        const int c = kap[d] < a.pcls ? kap[d] : a.pcls;
+        if (threadIdx.x == 0) {
+          // the previous product's reads of the rows (before a CTA barrier) precede this refill
+          fence_proxy_async_smem();
+          mbar_expect_tx(pbar, pbytes);
+          const T* src = a.pmap + (size_t)(c - 1) * a.pstride + (size_t)rlo * a.pld;
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                       ::"r"(smem_u32(prow)), "l"(src), "r"(pbytes), "r"(smem_u32(pbar))
+                       : "memory");
+        }
+        pinflight = true;
+      }
       PassAArgs<T> pa = a.pa[d];
       if (zer[d]) pa.vin = nullptr;
       switch (a.tile[d]) {
@@ -132,9 +162,17 @@ __global__ void __launch_bounds__(NT) deep_kernel(const DeepArgs<T> a) {
       }
       if (!grid_barrier(a.bar, a.err)) return;
       if (d + 1 == a.depth) {  // children at the coarse-kernel level: v_lc = P_c f_lc
-        const int c = kap[d] < a.pcls ? kap[d] : a.pcls;
-        children_matvec<T, NT, 1, 8>(a.pmap + (size_t)(c - 1) * a.pstride, a.pld, a.cc, blockIdx.x, gridDim.x,
-                                     reinterpret_cast<T*>(smem_raw));
+        if (pinflight) {
+          if (!tm_wait_all(pbar, pphase)) {
+            if (threadIdx.x == 0) atomicExch(a.err, DEEP_ERR_TIMEOUT);
+            (void)mbar_wait_bounded(pbar, pphase);  // let the copy land before the CTA leaves
+            return;
+          }
+          pphase ^= 1u;
+          pinflight = false;
+        }
+        children_matvec<T, NT, 1, 8, true>(nullptr, a.pld, a.cc, blockIdx.x, gridDim.x,
+                                           reinterpret_cast<T*>(smem_raw), prow);
         if (!grid_barrier(a.bar, a.err)) return;
         stage[d] = 3;
       } else {  // first child: counter k from zero

@@ -967,9 +967,10 @@ __device__ __forceinline__ void children_prefetch(const T* pmap, int pld, int S,
 // fused call (16 CTAs, many rows per warp): FP64 rows (up to 512 entries here) take one round trip
 // for two rows, FP32 rows (up to 1024) two for four rows. A stand-alone launch gives each warp about
 // one row and streams it eight chunks per lane at a time.
-template <typename T, int NT, int RG = (sizeof(T) == 8 ? 2 : 4), int CH = 4>
+// STAGED: this part's rows of P were copied to shared memory beforehand (`staged`, row lo first).
+template <typename T, int NT, int RG = (sizeof(T) == 8 ? 2 : 4), int CH = 4, bool STAGED = false>
 __device__ __forceinline__ void children_matvec(const T* __restrict__ pmap, int pld, const CoarseArgs<T>& a,
-                                                int part, int parts, T* fs) {
+                                                int part, int parts, T* fs, const T* staged = nullptr) {
   const int s = a.n_lc, S = s * s;
   // f of level lc into shared memory, row by row (no division), zero padding up to pld
   for (int j = threadIdx.x / 32; j < s; j += NT / 32)
@@ -987,7 +988,8 @@ __device__ __forceinline__ void children_matvec(const T* __restrict__ pmap, int 
     for (int g = 0; g < RG; ++g) {
       acc[g] = T(0);
       const int k = k0 + g * stride;
-      row[g] = pmap + (size_t)(k < hi ? k : k0) * pld;
+      if constexpr (STAGED) row[g] = staged + (size_t)((k < hi ? k : k0) - lo) * pld;
+      else row[g] = pmap + (size_t)(k < hi ? k : k0) * pld;
     }
 #pragma unroll CH
     for (int b = VW * lane; b < pld; b += 32 * VW) {

@@ -35,6 +35,7 @@ def measure(max_levels=13, reps=3, kappas=KAPPAS, theta=math.pi / 4, eps=1e-4):
     for L in range(4, max_levels + 1):
         n = 2 ** L - 1
         mg = kcycle.Multigrid(n, eps, theta, L)
+        mg.set_option(kcycle.MG_OPT_DEEP_CALLS, 0)  # the launch-by-launch form whose launches the model counts
         f = torch.tensor(rhs_normal(n, 0), device="cuda")
         v = torch.zeros_like(f)
         lc = None

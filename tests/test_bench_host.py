@@ -63,8 +63,8 @@ def test_per_level_fp32_from_zero():
 
 def test_profile_kinds_cover_the_abi():
     """Every launch kind mg_profile_cycle documents has a name."""
-    assert set(bench.PROFILE_KINDS) == set(range(7))
-    assert bench.PROFILE_KINDS[6] == "call"
+    assert set(bench.PROFILE_KINDS) == set(range(8))
+    assert bench.PROFILE_KINDS[6] == "call" and bench.PROFILE_KINDS[7] == "deep"
     assert math.isclose(bench.dp_ops_per_point(0, 2, True)[0], 32.25)
 
 

@@ -34,7 +34,9 @@ def test_fp64_deep_cycles_equal_separate_launches(lib, n, levels, kappa, deep):
     import torch
     on = lib.Multigrid(n, 2e-4, 1.9, levels)
     off = lib.Multigrid(n, 2e-4, 1.9, levels)
+    assert on.get_option(lib.MG_OPT_DEEP_CALLS) == 127  # the default
     on.set_option(lib.MG_OPT_DEEP_CALLS, deep)
+    off.set_option(lib.MG_OPT_DEEP_CALLS, 0)
     assert on.get_option(lib.MG_OPT_DEEP_CALLS) == deep and off.get_option(lib.MG_OPT_DEEP_CALLS) == 0
     f = dev(rhs_uniform(n, 21))
     a, b = torch.zeros_like(f), torch.zeros_like(f)
@@ -127,6 +129,7 @@ def test_deep_calls_fall_back_where_they_do_not_apply(lib):
         on = lib.Multigrid(n, 1e-2, 0.6, levels, **kw)
         off = lib.Multigrid(n, 1e-2, 0.6, levels, **kw)
         on.set_option(lib.MG_OPT_DEEP_CALLS, 255)
+        off.set_option(lib.MG_OPT_DEEP_CALLS, 0)
         f = dev(rhs_uniform(n, 8))
         a, b = torch.zeros_like(f), torch.zeros_like(f)
         if not kw:

@@ -26,6 +26,8 @@ def pair(lib, *args, **kw):
     kw.setdefault("coarse_n", 15)
     on = lib.Multigrid(*args, **kw)
     off = lib.Multigrid(*args, **kw)
+    for mg in (on, off):  # the fused calls, not the persistent deep launches that would contain them
+        mg.set_option(lib.MG_OPT_DEEP_CALLS, 0)
     off.set_option(lib.MG_OPT_FUSED_CALL, 0)
     assert on.get_option(lib.MG_OPT_FUSED_CALL) == 1 and off.get_option(lib.MG_OPT_FUSED_CALL) == 0
     return on, off
@@ -165,6 +167,8 @@ def test_one_and_two_level_fusion_equal_bitwise(lib, n, levels, kappa):
     import torch
     two = lib.Multigrid(n, 3e-4, 2.2, levels, coarse_n=15)  # FP64: the fused levels above 15^2
     one = lib.Multigrid(n, 3e-4, 2.2, levels, coarse_n=15)
+    for mg in (two, one):
+        mg.set_option(lib.MG_OPT_DEEP_CALLS, 0)
     two.set_option(lib.MG_OPT_FUSED_CALL, 2)
     f = dev(rhs_uniform(n, 9))
     a, b = torch.zeros_like(f), torch.zeros_like(f)

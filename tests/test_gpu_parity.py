@@ -238,10 +238,17 @@ def test_level_grid_reports_the_launch_shapes(lib):
     as one cluster launch: 16 CTAs of 8^2 tiles at 31^2 (FP64 with the coarse kernel at 15^2), of
     16^2 tiles at 63^2 (FP32); without the fused calls 64 CTAs at 63^2 (FP32). With the default FP64
     coarse kernel at 31^2, the 63^2 level keeps its 64 tiles (a fused call would need at most 16)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
     default = lib.Multigrid(4095, 1e-4, math.pi / 3, 12)
-    assert [default.level_grid(l)[1] for l in range(12)] == [64 * 128, 32 * 64, 32 * 32, 16 * 16, 16 * 16,
-                                                            16 * 16, 8 * 8, 1, 1, 1, 1, 1]
+    grid = [default.level_grid(l)[1] for l in range(12)]
+    # the 127^2 and 63^2 levels inside the persistent deep launches (one or two CTAs per SM)
+    assert grid[:5] == [64 * 128, 32 * 64, 32 * 32, 16 * 16, 16 * 16] and grid[7:] == [1] * 5
+    assert grid[5] == grid[6] and grid[5] in (sms, 2 * sms)
+    default.set_option(lib.MG_OPT_DEEP_CALLS, 0)
+    assert [default.level_grid(l)[1] for l in range(5, 8)] == [16 * 16, 8 * 8, 1]
     mg = lib.Multigrid(4095, 1e-4, math.pi / 3, 12, coarse_n=15)
+    mg.set_option(lib.MG_OPT_DEEP_CALLS, 0)
     fp64 = [mg.level_grid(l) for l in range(12)]
     assert [c for _, c in fp64] == [64 * 128, 32 * 64, 32 * 32, 16 * 16, 16 * 16, 16 * 16, 8 * 8, 4 * 4,
                                      1, 1, 1, 1]
