@@ -137,6 +137,12 @@ typedef enum {
                               Jacobi, full coarsening, symmetric operators, not adjoint cycles, and
                               only where the condensed maps exist (else the separate launches run).
                               Grid barrier waits are bounded (0.5 s): MG_ERR_TIMEOUT.           */
+  MG_OPT_TEST_STALL_BARRIER = 19, /* Test hook for the deep calls' grid barriers. c >= 0: CTA c of
+                              every persistent deep launch leaves as it starts, so the other CTAs'
+                              first barrier wait runs out after its limit (0.5 s); they record the
+                              timeout and leave, the cycle completes, and the next call that reads
+                              the solve's result returns MG_ERR_TIMEOUT once (and clears the
+                              barrier words). -1 (default): off. Makes no fault.                */
   MG_OPT_TEST_STALL_COPY = 17 /* Test hook for the bounded waits. t >= 0: the FP32 tensor-copy pass A
                               at level 0 arms the copy barrier of tile t (row-major tile index) but
                               issues no copy, so that CTA's wait runs out after its limit (0.5 s,

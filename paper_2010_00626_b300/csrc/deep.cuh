@@ -44,6 +44,7 @@ struct DeepArgs {
   int top, depth;
   int kappa, zero;                  // the launch's call: counter and start
   int prow_off;                     // shared-memory offset of the staged rows of P (16-byte aligned)
+  int stall_cta;                    // test hook: this CTA leaves at once (-1: none)
   unsigned* bar;                    // grid barrier words: arrivals, exits (both zero at rest)
   int* err;                         // set to DEEP_ERR_TIMEOUT when a barrier wait runs out
   const int* skip;
@@ -132,6 +133,11 @@ __global__ void __launch_bounds__(NT) deep_kernel(const DeepArgs<T> a) {
     fence_barrier_init();
   }
   __syncthreads();
+  if ((int)blockIdx.x == a.stall_cta) return;  // the others' first barrier wait runs out
+  // a CTA whose barrier wait ran out lets its copy of P's rows land (bounded) before it leaves
+  auto bail = [&]() {
+    if (pinflight) (void)mbar_wait_bounded(pbar, pphase);
+  };
   // the recursion's frames: counter, start and stage of the call at depth d (level top + d)
   int kap[DEEP_MAX_DEPTH], zer[DEEP_MAX_DEPTH], stage[DEEP_MAX_DEPTH];
   int d = 0;
@@ -160,7 +166,7 @@ __global__ void __launch_bounds__(NT) deep_kernel(const DeepArgs<T> a) {
         case 16: deep_tiles_a<T, 16, NT>(pa, smem_raw); break;
         default: deep_tiles_a<T, 8, NT>(pa, smem_raw); break;
       }
-      if (!grid_barrier(a.bar, a.err)) return;
+      if (!grid_barrier(a.bar, a.err)) return bail();
       if (d + 1 == a.depth) {  // children at the coarse-kernel level: v_lc = P_c f_lc
         if (pinflight) {
           if (!tm_wait_all(pbar, pphase)) {
@@ -173,7 +179,7 @@ __global__ void __launch_bounds__(NT) deep_kernel(const DeepArgs<T> a) {
         }
         children_matvec<T, NT, 1, 8, true>(nullptr, a.pld, a.cc, blockIdx.x, gridDim.x,
                                            reinterpret_cast<T*>(smem_raw), prow);
-        if (!grid_barrier(a.bar, a.err)) return;
+        if (!grid_barrier(a.bar, a.err)) return bail();
         stage[d] = 3;
       } else {  // first child: counter k from zero
         stage[d] = 1;
@@ -202,7 +208,7 @@ __global__ void __launch_bounds__(NT) deep_kernel(const DeepArgs<T> a) {
       case 16: deep_tiles_b<T, 16, NT>(a.pb[d], smem_raw); break;
       default: deep_tiles_b<T, 8, NT>(a.pb[d], smem_raw); break;
     }
-    if (d > 0 && !grid_barrier(a.bar, a.err)) return;
+    if (d > 0 && !grid_barrier(a.bar, a.err)) return bail();
     --d;
   }
   deep_exit(a.bar);

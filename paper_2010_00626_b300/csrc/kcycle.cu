@@ -159,6 +159,7 @@ struct mg_ctx {
   // map P_c (pm_side^2 rows of pitch pm_ld), FP64 and FP32 cycles; valid while pm_ok / pm32_ok
   int condense = 1;  // MG_OPT_CONDENSED_CHILDREN
   int stall_tile = -1;  // MG_OPT_TEST_STALL_COPY
+  int stall_cta = -1;   // MG_OPT_TEST_STALL_BARRIER
   int deep_n = 127;     // MG_OPT_DEEP_CALLS: calls at sides <= deep_n as one persistent launch (0: off);
                         // measured at 4095^2: mixed solves 2-6% faster, FP64 solves unchanged
   bool batched = false;  // an instance of a batch: its graph branch runs beside the others'
@@ -1399,6 +1400,7 @@ int emit_deep(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero, cons
   a.err = h->ints + I_ERR;
   a.skip = skip;
   a.prow_off = (int)sh.prow_off;
+  a.stall_cta = h->stall_cta;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -2009,6 +2011,13 @@ int mg_set_option(mg_handle h, int key, double value) {
       drop_graphs(h);
       return MG_OK;
     }
+    case MG_OPT_TEST_STALL_BARRIER: {
+      if (!(value >= -1.0 && value <= 1e6 && value == (double)(int)value)) return MG_ERR_ARG;
+      KC_CUDA(cudaStreamSynchronize(h->stream()));
+      h->stall_cta = (int)value;
+      drop_graphs(h);
+      return MG_OK;
+    }
     case MG_OPT_TEST_STALL_COPY: {
       if (!(value >= -1.0 && value <= 1e9 && value == (double)(int)value)) return MG_ERR_ARG;
       KC_CUDA(cudaStreamSynchronize(h->stream()));
@@ -2110,6 +2119,7 @@ int mg_get_option(mg_handle h, int key, double* value) {
     case MG_OPT_TMA_PASSES: *value = h->tma32; return MG_OK;
     case MG_OPT_CONDENSED_CHILDREN: *value = h->condense; return MG_OK;
     case MG_OPT_TEST_STALL_COPY: *value = h->stall_tile; return MG_OK;
+    case MG_OPT_TEST_STALL_BARRIER: *value = h->stall_cta; return MG_OK;
     case MG_OPT_DEEP_CALLS: *value = h->deep_n; return MG_OK;
     case MG_OPT_CONV_X: *value = h->bx; return MG_OK;
     case MG_OPT_CONV_Y: *value = h->by; return MG_OK;

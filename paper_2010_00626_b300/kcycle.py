@@ -22,7 +22,7 @@ CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
 MG_OPT_OMEGA, MG_OPT_COARSE_N, MG_OPT_LEVELS, MG_OPT_N, MG_OPT_LAUNCHES, MG_OPT_COARSE_N32 = 1, 2, 3, 4, 5, 6
 MG_OPT_COARSE_OP, MG_OPT_STOP, MG_OPT_SMOOTHER, MG_OPT_COARSENING, MG_OPT_PRECOND = 7, 8, 9, 10, 11
 MG_OPT_CONV_X, MG_OPT_CONV_Y, MG_OPT_FUSED_CALL, MG_OPT_TMA_PASSES, MG_OPT_CONDENSED_CHILDREN = 12, 13, 14, 15, 16
-MG_OPT_TEST_STALL_COPY, MG_OPT_DEEP_CALLS = 17, 18
+MG_OPT_TEST_STALL_COPY, MG_OPT_DEEP_CALLS, MG_OPT_TEST_STALL_BARRIER = 17, 18, 19
 SMOOTHERS = {"jacobi": 0, "zebra": 1, "xzebra": 2}
 COARSENINGS = {"full": 0, "y": 1}
 

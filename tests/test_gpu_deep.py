@@ -145,3 +145,31 @@ def test_deep_calls_fall_back_where_they_do_not_apply(lib):
     for bad in (1, 100, 1023, -1):
         with pytest.raises(lib.MultigridError):
             on.set_option(lib.MG_OPT_DEEP_CALLS, bad)
+
+
+def test_grid_barrier_wait_runs_out_and_reports_timeout(lib):
+    """Bounded grid-barrier waits: with the test hook one CTA of each deep launch leaves as it
+    starts; the others' first barrier wait runs out (0.5 s), they record the timeout and leave, the
+    solve reports MG_ERR_TIMEOUT (-4), and the same handle then solves as a fresh one does, bit for
+    bit (the barrier words were cleared and the context stays usable)."""
+    import time
+    import torch
+    n, levels = 1023, 10
+    f = dev(rhs_normal(n, 0))
+    mg = lib.Multigrid(n, 1e-4, math.pi / 3, levels)
+    mg.set_option(lib.MG_OPT_TEST_STALL_BARRIER, 5)
+    assert mg.get_option(lib.MG_OPT_TEST_STALL_BARRIER) == 5
+    t0 = time.perf_counter()
+    with pytest.raises(lib.MultigridError, match=r"\(-4\)"):
+        mg.solve(torch.zeros_like(f), f, 1, 1e-8, 1)  # a V-cycle: one deep launch
+    waited = time.perf_counter() - t0
+    mg.set_option(lib.MG_OPT_TEST_STALL_BARRIER, -1)
+    v = torch.zeros_like(f)
+    st = mg.solve(v, f, 4, 1e-8, 500)
+    fresh = lib.Multigrid(n, 1e-4, math.pi / 3, levels)
+    w = torch.zeros_like(f)
+    st2 = fresh.solve(w, f, 4, 1e-8, 500)
+    print(f"timed-out solve took {waited:.2f} s")
+    assert st[0] == 0 and st == st2 and torch.equal(v, w)
+    with pytest.raises(lib.MultigridError):
+        mg.set_option(lib.MG_OPT_TEST_STALL_BARRIER, -3)
