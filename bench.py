@@ -313,7 +313,8 @@ PROFILE_KINDS = {0: "pass_a", 1: "pass_b", 2: "coarse", 3: "residual", 4: "lines
 
 
 def per_level_report(mg, prof, fp32, fp64_peak_ops, hbm_peak, norm_l0, sms, kappa, l0_zero):
-    """Per level of one profiled cycle (launch-by-launch CUDA events, eager launches): launches,
+    """Per level of one profiled cycle (a CUDA event pair around every launch, replayed from a graph
+    as a solve runs it): launches,
     microseconds per launch, CTAs per launch (mg_level_grid), algorithmic bytes and FP64 operations
     per launch (each field read or written once; no halo recomputation; a pass A that starts from
     zero reads no v and its first sweep is one operation: the first call below each parent call, and
@@ -365,7 +366,7 @@ def per_level_report(mg, prof, fp32, fp64_peak_ops, hbm_peak, norm_l0, sms, kapp
             "sm_idle": {"ms_per_cycle": round(idle_ms, 4), "frac_of_cycle": round(idle_ms / total_ms, 4),
                         "launches_below_one_wave_ms": round(coarse_ms, 4),
                         "idle_within_those_ms": round(coarse_idle, 4),
-                        "note": "eager launches timed with CUDA events; an SM idles while a launch has fewer "
+                        "note": "launches timed with CUDA event pairs inside a graph replay; an SM idles while a launch has fewer "
                                 "CTAs than SMs (the coarse levels and the one-CTA coarse kernel)"}}
 
 
@@ -555,7 +556,7 @@ def main():
     # ---------------------------------------------------------------- per-launch profile
     prof_ms, prof_kind, prof_level = None, None, None
     for _ in range(3):
-        prof_ms, prof_kind, prof_level = mg.profile_cycle(v, f, kappa, with_norm=True)
+        prof_ms, prof_kind, prof_level = mg.profile_cycle(v, f, kappa, with_norm=True, graph=True)
     share = {}
     for t, k, l in zip(prof_ms, prof_kind, prof_level):
         key = (int(k), int(l))
@@ -865,7 +866,7 @@ def main():
     per_level32 = roofline_fp32 = None
     if not args.no_sweep:
         for _ in range(3):
-            prof32 = mg.profile_cycle(v, f, kappa, fp32=True)
+            prof32 = mg.profile_cycle(v, f, kappa, fp32=True, graph=True)
         per_level32 = per_level_report(mg, prof32, True, fp64_peak_ops, hbm_peak, False, sms, kappa, True)
         per_level32["cycle"] = f"FP32 kappa={kname(kappa)} cycle of the mixed solve (from zero)"
         # the bandwidth roofline of the FP32 fused passes at level 0 (tensor-copy kernels)
@@ -878,7 +879,7 @@ def main():
                     "traffic": measured_traffic(TMA_L0_TRAFFIC[e["kind"]]) if n == 4095 else None,
                     "note": "algorithmic bytes (pass A from zero: f read, v and coarse f written, 9 B per point; "
                             "pass B: v, f, coarse v read, v written, 13 B per point) over the launch's CUDA-event "
-                            "time in the FP32 cycle, eager"}
+                            "time in the FP32 cycle, replayed from a graph as the solve runs it"}
 
     # ---------------------------------------------------------------- oracle on the host cores
     cpu = None

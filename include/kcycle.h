@@ -285,7 +285,9 @@ int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas);
  * with_norm: bit 0 profiles the launches of a stand-alone solve cycle (with the residual partial
  * sums of its stopping test, formed by the first sweep of pass A at level 0 where mg_solve does so,
  * else by the last pass); bit 1 profiles instead the FP32 cycle of mg_solve_mixed (zero start on the
- * handle's FP32 level-0 arrays; v and f are then not used).
+ * handle's FP32 level-0 arrays; v and f are then not used); bit 2 captures the launches with their
+ * event pairs into a graph and replays it once (the pairs then hold no host launch latency, as in a
+ * solve's graph).
  * ms, kind, level: host, nullable, max_records entries; *count: number of launches (may exceed
  * max_records). Measurement hook with no counterpart in the paper. Synchronises. */
 int mg_profile_cycle(mg_handle h, double* v, const double* f, int kappa, int with_norm, int max_records,

@@ -182,6 +182,7 @@ struct mg_ctx {
   bool ok = false;
   // per-launch timing (mg_profile_cycle): an event pair around each launch while `prof` is set
   bool prof = false;
+  bool prof_graph = false;  // profiling inside a stream capture (external event records)
   std::vector<cudaEvent_t> pev;
   std::vector<int> pkind, plevel;
 
@@ -394,11 +395,17 @@ int lv_ld(mg_ctx* h, const BindingT<T>& b, int l) { return l == 0 ? b.ld0 : Arr<
 enum { K_PASS_A = 0, K_PASS_B = 1, K_COARSE = 2, K_APPLY = 3, K_LINES_X = 4, K_LINES_Y = 5, K_CALL = 6, K_DEEP = 7 };
 // (under semi-coarsening K_PASS_A is the y restriction and K_PASS_B the y prolongation)
 
+// Inside a stream capture an event record must be an external one to become a graph node whose
+// time cudaEventElapsedTime reads.
+void prof_record(mg_ctx* h, cudaEvent_t e, cudaStream_t s) {
+  if (h->prof_graph) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else cudaEventRecord(e, s);
+}
 void prof_begin(mg_ctx* h, int kind, int level, cudaStream_t s) {
   if (!h->prof) return;
   cudaEvent_t e;
   cudaEventCreate(&e);
-  cudaEventRecord(e, s);
+  prof_record(h, e, s);
   h->pev.push_back(e);
   h->pkind.push_back(kind);
   h->plevel.push_back(level);
@@ -407,7 +414,7 @@ void prof_end(mg_ctx* h, cudaStream_t s) {
   if (!h->prof) return;
   cudaEvent_t e;
   cudaEventCreate(&e);
-  cudaEventRecord(e, s);
+  prof_record(h, e, s);
   h->pev.push_back(e);
 }
 
@@ -2544,16 +2551,39 @@ int mg_profile_cycle(mg_handle h, double* v, const double* f, int kappa, int wit
   h->pkind.clear();
   h->plevel.clear();
   h->prof = true;
+  // bit 2: the launches and their event pairs captured into a graph and replayed once, as a
+  // solve's graph runs them (no host launch latency inside a pair)
+  const bool in_graph = (with_norm & 4) != 0;
+  h->prof_graph = in_graph;
+  cudaStream_t es = in_graph ? h->own : s;
+  if (in_graph) {
+    KC_CUDA(cudaStreamSynchronize(s));
+    KC_CUDA(cudaStreamBeginCapture(es, cudaStreamCaptureModeThreadLocal));
+  }
   int st;
   if (fp32) {  // the FP32 cycle of the mixed path: d = B32 r from zero on the handle's FP32 arrays
     BindingT<float> b32{h->lv[0].v32, h->lv[0].f32, h->ld32_0};
-    st = emit_cycle(h, b32, kappa, true, false, false, nullptr, s);
+    st = emit_cycle(h, b32, kappa, true, false, false, nullptr, es);
   } else if ((with_norm & 1) && prenorm_ok(h)) {  // the launches of a stand-alone solve cycle
-    st = emit_solve_cycle_prenorm(h, b, kappa, cudaGraphConditionalHandle{}, nullptr, s, false);
+    st = emit_solve_cycle_prenorm(h, b, kappa, cudaGraphConditionalHandle{}, nullptr, es, false);
   } else {
-    st = emit_cycle(h, b, kappa, false, false, (with_norm & 1) != 0, nullptr, s);
+    st = emit_cycle(h, b, kappa, false, false, (with_norm & 1) != 0, nullptr, es);
   }
   h->prof = false;
+  h->prof_graph = false;
+  if (in_graph) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(es, &g);
+    if (st >= 0 && ce != cudaSuccess) st = MG_ERR_CUDA;
+    if (st >= 0 && cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) st = MG_ERR_CUDA;
+    if (st >= 0 && cudaGraphLaunch(ge, s) != cudaSuccess) st = MG_ERR_CUDA;
+    if (st >= 0 && cudaStreamSynchronize(s) != cudaSuccess) st = MG_ERR_CUDA;
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    if (st == MG_ERR_CUDA) snprintf(g_err, sizeof(g_err), "mg_profile_cycle: graph replay failed");
+    cudaGetLastError();
+  }
   int result = st;
   if (st >= 0) {
     const cudaError_t se = cudaStreamSynchronize(s);

@@ -269,11 +269,12 @@ class Multigrid:
         _check(_lib.mg_stencils(self._h, out.ctypes.data_as(_dp), self.levels, ctypes.byref(w)), "mg_stencils")
         return out[: w.value * 9].reshape(w.value, 3, 3)
 
-    def profile_cycle(self, v, f, kappa, with_norm=False, max_records=8192, fp32=False):
+    def profile_cycle(self, v, f, kappa, with_norm=False, max_records=8192, fp32=False, graph=False):
         """Per-launch (ms, kind, level) of one cycle run launch by launch with CUDA events
-        (fp32: the FP32 cycle of the mixed solve)."""
+        (fp32: the FP32 cycle of the mixed solve; graph: the launches and events replayed from a
+        graph, as a solve runs them)."""
         self._stream()
-        with_norm = int(bool(with_norm)) | (2 if fp32 else 0)
+        with_norm = int(bool(with_norm)) | (2 if fp32 else 0) | (4 if graph else 0)
         ms = np.zeros(max_records)
         kind = np.zeros(max_records, dtype=np.int32)
         level = np.zeros(max_records, dtype=np.int32)
