@@ -173,3 +173,29 @@ def test_grid_barrier_wait_runs_out_and_reports_timeout(lib):
     assert st[0] == 0 and st == st2 and torch.equal(v, w)
     with pytest.raises(lib.MultigridError):
         mg.set_option(lib.MG_OPT_TEST_STALL_BARRIER, -3)
+
+
+@pytest.mark.parametrize("n,levels,coarse_n,deep,nu1,nu2,kappa", [
+    (1023, 10, 7, 511, 2, 2, 3),    # six levels in one launch (511^2 down to 15^2), P at 7^2
+    (1023, 10, 3, 511, 2, 2, 2),    # seven would be too many: the launches start at 255^2
+    (511, 9, 15, 255, 1, 3, 4),     # other sweep counts
+    (511, 9, 31, 127, 0, 2, KAPPA_W),  # no pre-smoothing
+    (255, 8, 31, 63, 3, 1, 1),
+])
+def test_fp64_deep_shapes_equal_separate_launches(lib, n, levels, coarse_n, deep, nu1, nu2, kappa):
+    """Depths, coarse thresholds and sweep counts: bit for bit the separate launches, and the
+    launch count that mg_counters gives."""
+    import torch
+    on = lib.Multigrid(n, 1e-3, 0.4, levels, nu1=nu1, nu2=nu2, coarse_n=coarse_n)
+    off = lib.Multigrid(n, 1e-3, 0.4, levels, nu1=nu1, nu2=nu2, coarse_n=coarse_n)
+    on.set_option(lib.MG_OPT_DEEP_CALLS, deep)
+    off.set_option(lib.MG_OPT_DEEP_CALLS, 0)
+    f = dev(rhs_normal(n, 31))
+    a, b = torch.zeros_like(f), torch.zeros_like(f)
+    for _ in range(2):
+        on.kcycle(a, f, kappa)
+        off.kcycle(b, f, kappa)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    launches = on.counters(kappa)[1]
+    assert on.get_option(lib.MG_OPT_LAUNCHES) == launches < off.counters(kappa)[1]
