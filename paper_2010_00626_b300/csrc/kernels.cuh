@@ -177,6 +177,49 @@ __device__ __forceinline__ void for_region(int Rw, int Rh, F fn) {
   }
 }
 
+// Visit every point of an Rw x Rh region as for_region does, K points per thread at a time: a
+// round issues all K loads before any of their stores. (A store waits for its load, so visiting
+// one point at a time pays one memory round trip per point a thread visits; the small tiles of the
+// latency-bound levels give a thread several.)
+template <int NT, int K, typename Load, typename Store>
+__device__ __forceinline__ void stage_region(int Rw, int Rh, Load load, Store store) {
+  const int q = NT / Rw, r = NT - q * Rw;
+  int ly = threadIdx.x / Rw, lx = threadIdx.x - ly * Rw;
+  while (ly < Rh) {
+    int xs[K], ys[K];
+    decltype(load(0, 0)) vals[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      xs[u] = lx;
+      ys[u] = ly;
+      if (ly < Rh) vals[u] = load(lx, ly);
+      lx += r;
+      ly += q;
+      if (lx >= Rw) {
+        lx -= Rw;
+        ++ly;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < K; ++u)
+      if (ys[u] < Rh) store(xs[u], ys[u], vals[u]);
+  }
+}
+
+// Points per thread and round of a tile's staging: the region of a BX x BY tile with nu = 2 over
+// NT threads, at most 8, for tiles up to 16 wide; the 32- and 64-wide tiles of the larger levels
+// keep one (more registers would cost them CTAs per SM, and their many warps per SM hide the
+// loads: measured, 32-wide FP64 pass B at 1023^2 71.0 -> 72.2 us with four).
+template <int BX, int BY, int NT>
+constexpr int stage_k() {
+  return BX > 16 ? 1 : (((BX + 7) * (BY + 7) + NT - 1) / NT > 8 ? 8 : ((BX + 7) * (BY + 7) + NT - 1) / NT);
+}
+
+template <typename T>
+struct TwoVals {
+  T a, b;
+};
+
 __device__ __forceinline__ bool inside(int gx, int gy, int n) {
   return (unsigned)gx < (unsigned)n && (unsigned)gy < (unsigned)n;
 }
@@ -237,12 +280,19 @@ __device__ __forceinline__ void pass_a_tile(const PassAArgs<T>& a, int bx, int b
   op.load(a.coef, a.level);
 
   // local (lx, ly) <-> global (gx0 + lx, gy0 + ly)
-  for_region<NT>(W, Hh, [&](int lx, int ly) {
-    const int gx = gx0 + lx, gy = gy0 + ly, k = ly * W + lx;
-    const bool in = inside(gx, gy, n);
-    s0[k] = (in && a.vin) ? a.vin[(size_t)gy * a.ldvin + gx] : T(0);
-    fs[k] = in ? a.f[(size_t)gy * a.ldf + gx] : T(0);
-  });
+  stage_region<NT, stage_k<BX, BY, NT>()>(
+      W, Hh,
+      [&](int lx, int ly) {
+        const int gx = gx0 + lx, gy = gy0 + ly;
+        const bool in = inside(gx, gy, n);
+        return TwoVals<T>{(in && a.vin) ? a.vin[(size_t)gy * a.ldvin + gx] : T(0),
+                          in ? a.f[(size_t)gy * a.ldf + gx] : T(0)};
+      },
+      [&](int lx, int ly, const TwoVals<T>& x) {
+        const int k = ly * W + lx;
+        s0[k] = x.a;
+        fs[k] = x.b;
+      });
   __syncthreads();
 
   T* src = s0;
@@ -359,14 +409,17 @@ __device__ __forceinline__ void pass_b_tile(const PassBArgs<T>& a, int bx, int b
   StencilOp<T, NS> op;
   op.load(a.coef, a.level);
 
-  for_region<NT>(CW, CH, [&](int lx, int ly) {
-    const int cx = cx0 + lx, cy = cy0 + ly;
-    cs[ly * CW + lx] = inside(cx, cy, nc) ? a.vc[(size_t)cy * a.ldc + cx] : T(0);
-  });
+  stage_region<NT, stage_k<BX, BY, NT>()>(
+      CW, CH,
+      [&](int lx, int ly) {
+        const int cx = cx0 + lx, cy = cy0 + ly;
+        return inside(cx, cy, nc) ? a.vc[(size_t)cy * a.ldc + cx] : T(0);
+      },
+      [&](int lx, int ly, T x) { cs[ly * CW + lx] = x; });
   __syncthreads();
   auto cv = [&](int cx, int cy) { return cs[(cy - cy0) * CW + (cx - cx0)]; };
-  for_region<NT>(W, Hh, [&](int lx, int ly) {
-    const int gx = gx0 + lx, gy = gy0 + ly, k = ly * W + lx;
+  stage_region<NT, stage_k<BX, BY, NT>()>(W, Hh, [&](int lx, int ly) {
+    const int gx = gx0 + lx, gy = gy0 + ly;
     T v = T(0), fv = T(0);
     if (inside(gx, gy, n)) {
       fv = a.f[(size_t)gy * a.ldf + gx];
@@ -385,8 +438,11 @@ __device__ __forceinline__ void pass_b_tile(const PassBArgs<T>& a, int bx, int b
       }
       v = a.vin[(size_t)gy * a.ldvin + gx] + p;
     }
-    s0[k] = v;
-    fs[k] = fv;
+    return TwoVals<T>{v, fv};
+  }, [&](int lx, int ly, const TwoVals<T>& x) {
+    const int k = ly * W + lx;
+    s0[k] = x.a;
+    fs[k] = x.b;
   });
   __syncthreads();
 
@@ -972,9 +1028,10 @@ template <typename T, int NT, int RG = (sizeof(T) == 8 ? 2 : 4), int CH = 4, boo
 __device__ __forceinline__ void children_matvec(const T* __restrict__ pmap, int pld, const CoarseArgs<T>& a,
                                                 int part, int parts, T* fs, const T* staged = nullptr) {
   const int s = a.n_lc, S = s * s;
-  // f of level lc into shared memory, row by row (no division), zero padding up to pld
-  for (int j = threadIdx.x / 32; j < s; j += NT / 32)
-    for (int i = threadIdx.x & 31; i < s; i += 32) fs[j * s + i] = a.f[(size_t)j * a.ldf + i];
+  // f of level lc into shared memory (four loads per thread in flight), zero padding up to pld
+  stage_region<NT, 4>(
+      s, s, [&](int i, int j) { return a.f[(size_t)j * a.ldf + i]; },
+      [&](int i, int j, T x) { fs[j * s + i] = x; });
   for (int b = S + (int)threadIdx.x; b < pld; b += NT) fs[b] = T(0);
   __syncthreads();
   constexpr int NW = NT / 32;
