@@ -99,11 +99,13 @@ __device__ __forceinline__ void deep_exit(unsigned* bar) {
   }
 }
 
+// one point per thread and staging round (fewer registers for the whole kernel; an 8 x 8 tile's
+// window fits the CTA in one round anyway)
 template <typename T, int B, int NT>
 __device__ __forceinline__ void deep_tiles_a(const PassAArgs<T>& pa, unsigned char* smem) {
   const int tx = (pa.n + B - 1) / B, nt = tx * tx;
   for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-    pass_a_tile<T, B, B, NT, false>(pa, t % tx, t / tx, 0, smem);
+    pass_a_tile<T, B, B, NT, false, 1>(pa, t % tx, t / tx, 0, smem);
     __syncthreads();  // the next tile reuses the shared memory
   }
 }
@@ -111,7 +113,7 @@ template <typename T, int B, int NT>
 __device__ __forceinline__ void deep_tiles_b(const PassBArgs<T>& pb, unsigned char* smem) {
   const int tx = (pb.n + B - 1) / B, nt = tx * tx;
   for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-    pass_b_tile<T, B, B, NT, false>(pb, t % tx, t / tx, 0, smem);
+    pass_b_tile<T, B, B, NT, false, 1>(pb, t % tx, t / tx, 0, smem);
     __syncthreads();
   }
 }

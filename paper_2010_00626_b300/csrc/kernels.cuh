@@ -264,7 +264,8 @@ __host__ __device__ constexpr size_t pass_a_smem(int nu) {
 }
 
 // One BX x BY tile of pass A: tile column bx, tile row by; pidx is the tile's slot in a.partial.
-template <typename T, int BX, int BY, int NT, bool NS>
+// KS: points per thread and round of the staging (0: stage_k's choice).
+template <typename T, int BX, int BY, int NT, bool NS, int KS = 0>
 __device__ __forceinline__ void pass_a_tile(const PassAArgs<T>& a, int bx, int by, int pidx,
                                             unsigned char* smem_raw) {
   static_assert(BX % 2 == 0 && BY % 2 == 0, "tiles start on even fine indices");
@@ -280,7 +281,7 @@ __device__ __forceinline__ void pass_a_tile(const PassAArgs<T>& a, int bx, int b
   op.load(a.coef, a.level);
 
   // local (lx, ly) <-> global (gx0 + lx, gy0 + ly)
-  stage_region<NT, stage_k<BX, BY, NT>()>(
+  stage_region<NT, KS ? KS : stage_k<BX, BY, NT>()>(
       W, Hh,
       [&](int lx, int ly) {
         const int gx = gx0 + lx, gy = gy0 + ly;
@@ -389,7 +390,7 @@ __host__ __device__ constexpr size_t pass_b_smem(int nu, bool norm) {
 }
 
 // One BX x BY tile of pass B (tile column bx, row by; pidx: the tile's slot in a.partial).
-template <typename T, int BX, int BY, int NT, bool NS>
+template <typename T, int BX, int BY, int NT, bool NS, int KS = 0>
 __device__ __forceinline__ void pass_b_tile(const PassBArgs<T>& a, int bx, int by, int pidx,
                                             unsigned char* smem_raw) {
   const int E = a.partial ? 1 : 0;
@@ -409,41 +410,81 @@ __device__ __forceinline__ void pass_b_tile(const PassBArgs<T>& a, int bx, int b
   StencilOp<T, NS> op;
   op.load(a.coef, a.level);
 
-  stage_region<NT, stage_k<BX, BY, NT>()>(
-      CW, CH,
-      [&](int lx, int ly) {
-        const int cx = cx0 + lx, cy = cy0 + ly;
-        return inside(cx, cy, nc) ? a.vc[(size_t)cy * a.ldc + cx] : T(0);
-      },
-      [&](int lx, int ly, T x) { cs[ly * CW + lx] = x; });
-  __syncthreads();
+  constexpr int K = KS ? KS : stage_k<BX, BY, NT>();
+  auto stage_coarse = [&]() {
+    stage_region<NT, K>(
+        CW, CH,
+        [&](int lx, int ly) {
+          const int cx = cx0 + lx, cy = cy0 + ly;
+          return inside(cx, cy, nc) ? a.vc[(size_t)cy * a.ldc + cx] : T(0);
+        },
+        [&](int lx, int ly, T x) { cs[ly * CW + lx] = x; });
+  };
   auto cv = [&](int cx, int cy) { return cs[(cy - cy0) * CW + (cx - cx0)]; };
-  stage_region<NT, stage_k<BX, BY, NT>()>(W, Hh, [&](int lx, int ly) {
-    const int gx = gx0 + lx, gy = gy0 + ly;
-    T v = T(0), fv = T(0);
-    if (inside(gx, gy, n)) {
-      fv = a.f[(size_t)gy * a.ldf + gx];
-      // fine (gx, gy): odd index = coarse point (gx-1)/2; even index between gx/2-1 and gx/2
-      T p;
-      const bool xo = gx & 1, yo = gy & 1;
-      const int hx = gx >> 1, hy = gy >> 1;
-      if (xo && yo) {
-        p = cv(hx, hy);
-      } else if (yo) {
-        p = T(0.5) * (cv(hx - 1, hy) + cv(hx, hy));
-      } else if (xo) {
-        p = T(0.5) * (cv(hx, hy - 1) + cv(hx, hy));
-      } else {
-        p = T(0.25) * ((cv(hx - 1, hy - 1) + cv(hx, hy - 1)) + (cv(hx - 1, hy) + cv(hx, hy)));
-      }
-      v = a.vin[(size_t)gy * a.ldvin + gx] + p;
+  // the bilinear interpolation P v_c at fine (gx, gy), from the staged coarse window
+  auto interp = [&](int gx, int gy) {
+    // fine (gx, gy): odd index = coarse point (gx-1)/2; even index between gx/2-1 and gx/2
+    T p;
+    const bool xo = gx & 1, yo = gy & 1;
+    const int hx = gx >> 1, hy = gy >> 1;
+    if (xo && yo) {
+      p = cv(hx, hy);
+    } else if (yo) {
+      p = T(0.5) * (cv(hx - 1, hy) + cv(hx, hy));
+    } else if (xo) {
+      p = T(0.5) * (cv(hx, hy - 1) + cv(hx, hy));
+    } else {
+      p = T(0.25) * ((cv(hx - 1, hy - 1) + cv(hx, hy - 1)) + (cv(hx - 1, hy) + cv(hx, hy)));
     }
-    return TwoVals<T>{v, fv};
-  }, [&](int lx, int ly, const TwoVals<T>& x) {
-    const int k = ly * W + lx;
-    s0[k] = x.a;
-    fs[k] = x.b;
-  });
+    return p;
+  };
+  if (W * Hh <= K * NT) {
+    // one round: this thread's loads of v and f are in flight while the coarse window is staged
+    const int q = NT / W, r = NT - q * W;
+    int ly = threadIdx.x / W, lx = threadIdx.x - ly * W;
+    int xs[K], ys[K];
+    T vr[K], fr[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      xs[u] = lx;
+      ys[u] = ly;
+      const int gx = gx0 + lx, gy = gy0 + ly;
+      const bool in = ly < Hh && inside(gx, gy, n);
+      vr[u] = in ? a.vin[(size_t)gy * a.ldvin + gx] : T(0);
+      fr[u] = in ? a.f[(size_t)gy * a.ldf + gx] : T(0);
+      lx += r;
+      ly += q;
+      if (lx >= W) {
+        lx -= W;
+        ++ly;
+      }
+    }
+    stage_coarse();
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      if (ys[u] >= Hh) continue;
+      const int gx = gx0 + xs[u], gy = gy0 + ys[u], k = ys[u] * W + xs[u];
+      s0[k] = inside(gx, gy, n) ? vr[u] + interp(gx, gy) : T(0);
+      fs[k] = fr[u];
+    }
+  } else {
+    stage_coarse();
+    __syncthreads();
+    stage_region<NT, K>(W, Hh, [&](int lx, int ly) {
+      const int gx = gx0 + lx, gy = gy0 + ly;
+      T v = T(0), fv = T(0);
+      if (inside(gx, gy, n)) {
+        fv = a.f[(size_t)gy * a.ldf + gx];
+        v = a.vin[(size_t)gy * a.ldvin + gx] + interp(gx, gy);
+      }
+      return TwoVals<T>{v, fv};
+    }, [&](int lx, int ly, const TwoVals<T>& x) {
+      const int k = ly * W + lx;
+      s0[k] = x.a;
+      fs[k] = x.b;
+    });
+  }
   __syncthreads();
 
   T* src = s0;
