@@ -44,6 +44,8 @@ struct DeepArgs {
   int top, depth;
   int kappa, zero;                  // the launch's call: counter and start
   int prow_off;                     // shared-memory offset of the staged rows of P (16-byte aligned)
+  int staged;                       // 1: P's rows staged in shared memory; 0: read from global memory
+                                    // (asked of L2 ahead), for maps too large to stage
   int stall_cta;                    // test hook: this CTA leaves at once (-1: none)
   unsigned* bar;                    // grid barrier words: arrivals, exits (both zero at rest)
   int* err;                         // set to DEEP_ERR_TIMEOUT when a barrier wait runs out
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(NT) deep_kernel(const DeepArgs<T> a) {
   const int S = a.cc.n_lc * a.cc.n_lc;
   const int rlo = child_rows_lo(S, blockIdx.x, gridDim.x), rhi = child_rows_lo(S, blockIdx.x + 1, gridDim.x);
   T* prow = reinterpret_cast<T*>(smem_raw + a.prow_off);
-  const uint32_t pbytes = (uint32_t)((size_t)(rhi - rlo) * a.pld * sizeof(T));
+  const uint32_t pbytes = a.staged ? (uint32_t)((size_t)(rhi - rlo) * a.pld * sizeof(T)) : 0u;
   uint64_t* pbar = reinterpret_cast<uint64_t*>(smem_raw + a.prow_off + (((size_t)pbytes + 15) & ~(size_t)15));
   uint32_t pphase = 0;
   bool pinflight = false;
@@ -148,6 +150,10 @@ __global__ void __launch_bounds__(NT) deep_kernel(const DeepArgs<T> a) {
   stage[0] = 0;
   while (d >= 0) {
     if (stage[d] == 0) {  // pass A, then the child calls
+      if (d + 1 == a.depth && !a.staged) {  // ask L2 for this CTA's rows of P_c while pass A runs
+        const int c = kap[d] < a.pcls ? kap[d] : a.pcls;
+        children_prefetch(a.pmap + (size_t)(c - 1) * a.pstride, a.pld, S, blockIdx.x, gridDim.x);
+      }
       if (d + 1 == a.depth && pbytes) {  // fetch this CTA's rows of P_c while pass A runs
         const int c = kap[d] < a.pcls ? kap[d] : a.pcls;
         if (threadIdx.x == 0) {
@@ -179,8 +185,14 @@ __global__ void __launch_bounds__(NT) deep_kernel(const DeepArgs<T> a) {
           pphase ^= 1u;
           pinflight = false;
         }
-        children_matvec<T, NT, 1, 8, true>(nullptr, a.pld, a.cc, blockIdx.x, gridDim.x,
-                                           reinterpret_cast<T*>(smem_raw), prow);
+        if (a.staged) {
+          children_matvec<T, NT, 1, 8, true>(nullptr, a.pld, a.cc, blockIdx.x, gridDim.x,
+                                             reinterpret_cast<T*>(smem_raw), prow);
+        } else {
+          const int c = kap[d] < a.pcls ? kap[d] : a.pcls;
+          children_matvec<T, NT, 1, 8>(a.pmap + (size_t)(c - 1) * a.pstride, a.pld, a.cc, blockIdx.x, gridDim.x,
+                                       reinterpret_cast<T*>(smem_raw));
+        }
         if (!grid_barrier(a.bar, a.err)) return bail();
         stage[d] = 3;
       } else {  // first child: counter k from zero

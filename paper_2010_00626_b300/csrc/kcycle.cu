@@ -1330,6 +1330,7 @@ size_t deep_smem_tiles(int edge, int nu1, int nu2) {
 struct DeepShape {
   int grid;
   size_t smem, prow_off;
+  int staged;  // 0: P's rows too many for shared memory, read from global memory
 };
 template <typename T>
 bool deep_shape(const mg_ctx* h, int l, DeepShape* out) {
@@ -1350,22 +1351,23 @@ bool deep_shape(const mg_ctx* h, int l, DeepShape* out) {
   size_t base = (size_t)pld * sizeof(T);
   for (int q = l; q < lc; ++q) base = std::max(base, deep_smem_tiles<T>(tile_edge(h->lv[q].n), h->nu1, h->nu2));
   const int S = h->lv[lc].n * h->lv[lc].n;
-  for (int per_sm = 2; per_sm >= 1; --per_sm) {
-    const int grid = per_sm * h->sms;
-    const size_t rows = (size_t)(S + grid - 1) / grid;
-    const size_t off = (base + 15) & ~(size_t)15;
-    const size_t sm = off + ((rows * pld * sizeof(T) + 15) & ~(size_t)15) + 16;
-    int occ = 0;
-    if (sm > SMEM_CAP ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, deep_kernel<T, NT_DEEP>, NT_DEEP, sm) != cudaSuccess) {
-      cudaGetLastError();
-      continue;
+  for (int staged = 1; staged >= 0; --staged)
+    for (int per_sm = 2; per_sm >= 1; --per_sm) {
+      const int grid = per_sm * h->sms;
+      const size_t rows = (size_t)(S + grid - 1) / grid;
+      const size_t off = (base + 15) & ~(size_t)15;
+      const size_t sm = staged ? off + ((rows * pld * sizeof(T) + 15) & ~(size_t)15) + 16 : off;
+      int occ = 0;
+      if (sm > SMEM_CAP ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, deep_kernel<T, NT_DEEP>, NT_DEEP, sm) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      if (occ >= per_sm) {
+        *out = DeepShape{grid, sm, off, staged};
+        return true;
+      }
     }
-    if (occ >= per_sm) {
-      *out = DeepShape{grid, sm, off};
-      return true;
-    }
-  }
   return false;
 }
 
@@ -1407,6 +1409,7 @@ int emit_deep(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero, cons
   a.err = h->ints + I_ERR;
   a.skip = skip;
   a.prow_off = (int)sh.prow_off;
+  a.staged = sh.staged;
   a.stall_cta = h->stall_cta;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];

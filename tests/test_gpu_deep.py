@@ -199,3 +199,27 @@ def test_fp64_deep_shapes_equal_separate_launches(lib, n, levels, coarse_n, deep
     assert torch.equal(a, b)
     launches = on.counters(kappa)[1]
     assert on.get_option(lib.MG_OPT_LAUNCHES) == launches < off.counters(kappa)[1]
+
+
+def test_fp32_deep_with_maps_too_large_to_stage(lib):
+    """With the FP32 coarse kernel at 63^2 the condensed maps (3969 x 3969) have more rows per CTA
+    than shared memory holds: the deep launch reads them from global memory (asked of L2 ahead),
+    bit for bit the separate launches."""
+    import torch
+    n, levels = 1023, 10
+    f32 = dev(rhs_uniform(n, 12), "float32")
+    outs = {}
+    for deep in (127, 0):
+        mg = lib.Multigrid(n, 1e-3, 0.7, levels)
+        mg.set_option(lib.MG_OPT_COARSE_N32, 63)
+        mg.set_option(lib.MG_OPT_DEEP_CALLS, deep)
+        v = torch.zeros_like(f32)
+        for _ in range(2):
+            mg.kcycle_f32(v, f32, 3)
+        torch.cuda.synchronize()
+        outs[deep] = v.clone()
+        if deep:  # the 127^2 level (3) runs inside deep launches
+            sms = torch.cuda.get_device_properties(0).multi_processor_count
+            assert mg.level_grid(3, fp32=True)[1] in (sms, 2 * sms)
+        mg.close()
+    assert torch.equal(outs[127], outs[0])
