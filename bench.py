@@ -38,8 +38,8 @@ NOMINAL_FP64_TFLOPS = 1.25  # nominal B300 FP64 rate
 # text changes the figure no longer describes the kernel and is reported as null until a new
 # capture replaces it.
 PASS_A_L0_TRAFFIC = {"source": "paper_2010_00626_b300/csrc/kernels.cuh", "until": "// Pass B: v <- v + P v_c",
-                     "sha256": "046e620f3f62b3a7b5f3e8be612719cd8261797e0b1bf25f90a78dbcaa590516",
-                     "bytes": 269_017_856 + 134_404_608}
+                     "sha256": "f3c59394bdf93f802bfca3cd9f2ee6f75e824cfdf47e26c34f2a8b107b0166a9",
+                     "bytes": 268_376_320 + 133_515_520}
 
 
 # The same for the FP32 tensor-copy passes at level 0 of the mixed solve's FP32 cycle (4095^2), keyed
