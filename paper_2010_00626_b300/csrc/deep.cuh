@@ -9,9 +9,10 @@
 // tiles, a grid barrier. At the level just above the coarse kernel's, the two child calls are the
 // condensed map v_lc = P_c f_lc (children_matvec), its rows dealt over the whole grid; each CTA's
 // rows of P_c arrive in its shared memory by one bulk copy issued before the parent's pass A, so the
-// product waits only for f_lc. Every
-// point's arithmetic is that of the separate launches (the same tile functions on the same tiles,
-// the same per-row sums), so the results equal them bit for bit.
+// product waits only for f_lc (maps with more rows per CTA than shared memory holds are read from
+// global memory instead, asked of L2 at the same point). Every point's arithmetic is that of the
+// separate launches (the same tile functions on the same tiles, the same per-row sums), so the
+// results equal them bit for bit.
 //
 // The grid barrier: after a CTA barrier, one thread per CTA counts the CTA in with an acquire-release
 // atomic add and polls the count with acquire loads until the whole grid has arrived (release and
