@@ -358,6 +358,14 @@ int mg_batch_set_option(mg_batch b, int key, double value);
  * set per-instance options before the first mg_batch_solve). */
 int mg_batch_instance(mg_batch b, int index, mg_handle* out);
 
+/* The batch under the names of the problem-statement interface: mg_setup_batched is mg_batch_create
+ * with every instance's full level count (levels = NULL); mg_solve_batched is mg_batch_solve with
+ * FP64 kappa-cycles (mixed = 0) and at most 10000 cycles per instance, its cycle counts in `cycles`
+ * (host, nullable, `count` entries). Same ownership and errors as those calls. */
+int mg_setup_batched(int count, const int* n, const double* eps, const double* theta, int nu1, int nu2,
+                     mg_batch* out);
+int mg_solve_batched(mg_batch b, double* const* v, const double* const* f, int kappa, double tol, int* cycles);
+
 int mg_batch_size(mg_batch b, int* count);
 int mg_batch_destroy(mg_batch b);
 

@@ -2846,6 +2846,15 @@ int mg_batch_set_option(mg_batch b, int key, double value) {
   return MG_OK;
 }
 
+int mg_setup_batched(int count, const int* n, const double* eps, const double* theta, int nu1, int nu2,
+                     mg_batch* out) {
+  return mg_batch_create(count, n, eps, theta, nullptr, nu1, nu2, out);
+}
+
+int mg_solve_batched(mg_batch b, double* const* v, const double* const* f, int kappa, double tol, int* cycles) {
+  return mg_batch_solve(b, v, f, kappa, tol, 10000, 0, cycles, nullptr);
+}
+
 int mg_batch_solve(mg_batch b, double* const* x, const double* const* f, int kappa, double tol, int max_iters,
                    int mixed, int* iters, double* relres) {
   if (!b || !x || !f || kappa < 1 || !(tol > 0) || max_iters < 1) return MG_ERR_ARG;

@@ -65,6 +65,8 @@ SIGNATURES = {
     "mg_batch_create": (_i, [_i, _ip, _dp, _dp, _ip, _i, _i, ctypes.POINTER(_h)]),
     "mg_batch_autotune": (_i, [_h, _i, _i, _ip]),
     "mg_batch_solve": (_i, [_h, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, _d, _i, _i, _ip, _dp]),
+    "mg_setup_batched": (_i, [_i, _ip, _dp, _dp, _i, _i, ctypes.POINTER(_h)]),
+    "mg_solve_batched": (_i, [_h, ctypes.POINTER(_p), ctypes.POINTER(_p), _i, _d, _ip]),
     "mg_batch_set_option": (_i, [_h, _i, _d]),
     "mg_batch_instance": (_i, [_h, _i, ctypes.POINTER(_h)]),
     "mg_batch_size": (_i, [_h, _ip]),

@@ -131,3 +131,32 @@ def test_autotuner_shapes_and_instance_handles(lib, mixed):
     assert batch.instance(0).get_option(lib.MG_OPT_N) == ns[0]  # the handle is still alive
     with pytest.raises(lib.MultigridError):
         batch.instance(len(ns))
+
+
+def test_problem_interface_batch_names(lib):
+    """mg_setup_batched / mg_solve_batched (the batch under the problem-statement names) give the
+    batch API's FP64 results bit for bit."""
+    import ctypes
+    import torch
+    inst = batched_instances(count=6, seed=3)
+    ns = [d["n"] for d in inst]
+    fs = [torch.tensor(rhs_uniform(d["n"], d["seed"]), device="cuda") for d in inst]
+    ref = lib.Batch(ns, [d["eps"] for d in inst], [d["theta"] for d in inst])
+    xr = [torch.zeros_like(f) for f in fs]
+    st_ref, it_ref, _ = ref.solve(xr, fs, 3, 1e-8, 10000)
+    ref.close()
+    cnt = len(ns)
+    L = lib._lib
+    h = ctypes.c_void_p()
+    st = L.mg_setup_batched(cnt, (ctypes.c_int * cnt)(*ns), (ctypes.c_double * cnt)(*[d["eps"] for d in inst]),
+                            (ctypes.c_double * cnt)(*[d["theta"] for d in inst]), 2, 2, ctypes.byref(h))
+    assert st == 0
+    xs = [torch.zeros_like(f) for f in fs]
+    cyc = (ctypes.c_int * cnt)()
+    torch.cuda.synchronize()
+    st2 = L.mg_solve_batched(h, (ctypes.c_void_p * cnt)(*[x.data_ptr() for x in xs]),
+                             (ctypes.c_void_p * cnt)(*[f.data_ptr() for f in fs]), 3, 1e-8, cyc)
+    torch.cuda.synchronize()
+    assert st2 == st_ref and list(cyc) == it_ref
+    assert all(torch.equal(a, b) for a, b in zip(xs, xr))
+    assert L.mg_batch_destroy(h) == 0
