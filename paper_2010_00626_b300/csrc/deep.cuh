@@ -48,6 +48,8 @@ struct DeepArgs {
   int staged;                       // 1: P's rows staged in shared memory; 0: read from global memory
                                     // (asked of L2 ahead), for maps too large to stage
   int stall_cta;                    // test hook: this CTA leaves at once (-1: none)
+  int merge_b;                      // 1: the last child call's pass B at the level above the condensed one
+                                    // runs inside its parent's pass B (8 x 8 parent tiles, nu2 = 2)
   unsigned* bar;                    // grid barrier words: arrivals, exits (both zero at rest)
   int* err;                         // set to DEEP_ERR_TIMEOUT when a barrier wait runs out
   const int* skip;
@@ -117,6 +119,36 @@ __device__ __forceinline__ void deep_tiles_b(const PassBArgs<T>& pb, unsigned ch
   const int tx = (pb.n + B - 1) / B, nt = tx * tx;
   for (int t = blockIdx.x; t < nt; t += gridDim.x) {
     pass_b_tile<T, B, B, NT, false, 1>(pb, t % tx, t / tx, 0, smem);
+    __syncthreads();
+  }
+}
+
+// Shared memory of deep_tiles_b2: the parent tile's pass B, then the child window's.
+template <typename T>
+__host__ __device__ constexpr size_t deep_b2_smem() {
+  return ((pass_b_smem<T, 8, 8>(2, false) + 15) / 16) * 16 + pass_b_smem<T, 7, 7>(2, false);
+}
+
+// The last child call's pass B (level l+1, args `child`) and its parent's pass B (level l) as one
+// phase: for each 8 x 8 parent tile, the child's pass B over the 7 x 7 coarse window that the
+// parent's interpolation reads (nu = 2), written straight into the parent's coarse staging buffer
+// (zero outside the grid, as the parent would load it), then the parent's pass B from there. The
+// child's points are computed by the formula of its own pass, from the same inputs, so the parent
+// sees the values a separate child pass would have stored; the child's own result is not needed
+// after this point (the next calls at its level start from zero), so it is not stored.
+template <typename T, int NT>
+__device__ __forceinline__ void deep_tiles_b2(const PassBArgs<T>& child, const PassBArgs<T>& parent,
+                                              unsigned char* smem) {
+  constexpr int B = 8, CR = 7;
+  const int tx = (parent.n + B - 1) / B, nt = tx * tx;
+  unsigned char* child_smem = smem + ((pass_b_smem<T, B, B>(2, false) + 15) / 16) * 16;
+  T* cs = pass_b_cs<T, B, B>(smem, 2);
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    const int x0 = (t % tx) * B, y0 = (t / tx) * B;
+    // the parent's coarse window starts at (x0 - 2) / 2 - 1 (x0 is even)
+    pass_b_core<T, CR, CR, NT, false, 1, PB_TO_SMEM>(child, x0 / 2 - 2, y0 / 2 - 2, 0, child_smem, cs, CR);
+    __syncthreads();
+    pass_b_core<T, B, B, NT, false, 1, PB_CS_READY>(parent, x0, y0, 0, smem);
     __syncthreads();
   }
 }
@@ -218,6 +250,13 @@ __global__ void __launch_bounds__(NT) deep_kernel(const DeepArgs<T> a) {
       stage[d] = 3;
     }
     // stage 3: pass B; the top call's needs no barrier after it (the launch ends)
+    if (a.merge_b && d + 1 == a.depth && d >= 1 && (stage[d - 1] == 2 || (stage[d - 1] == 1 && kap[d - 1] <= 1))) {
+      // the last child of its parent: both pass B in one phase, and the parent's call is done
+      deep_tiles_b2<T, NT>(a.pb[d], a.pb[d - 1], smem_raw);
+      if (d > 1 && !grid_barrier(a.bar, a.err)) return bail();
+      d -= 2;
+      continue;
+    }
     switch (a.tile[d]) {
       case 32: deep_tiles_b<T, 32, NT>(a.pb[d], smem_raw); break;
       case 16: deep_tiles_b<T, 16, NT>(a.pb[d], smem_raw); break;

@@ -1323,6 +1323,14 @@ size_t deep_smem_tiles(int edge, int nu1, int nu2) {
     default: return std::max(pass_a_smem<T, 8, 8>(nu1), pass_b_smem<T, 8, 8>(nu2, false));
   }
 }
+// Whether a deep launch from level l runs the last child's pass B inside its parent's: at least
+// two levels of passes, the parent level's tiles 8 x 8, two post-sweeps, no residual sums.
+template <typename T>
+bool deep_merge_b(const mg_ctx* h, int l) {
+  const int lc = lc_of<T>(h);
+  return lc - l >= 2 && h->nu2 == 2 && tile_edge(h->lv[lc - 2].n) == 8;
+}
+
 // Launch shape of a deep launch whose top call is at level l: CTAs (two per SM where they fit,
 // else one), dynamic shared memory (the tile passes and P's staged f, then each CTA's rows of P
 // and their copy barrier) and the offset of those rows; false where no shape fits (a device
@@ -1350,6 +1358,7 @@ bool deep_shape(const mg_ctx* h, int l, DeepShape* out) {
   if (!coop || l < 1 || l >= lc || !Arr<T>::pmap(h, 1, &pld)) return false;
   size_t base = (size_t)pld * sizeof(T);
   for (int q = l; q < lc; ++q) base = std::max(base, deep_smem_tiles<T>(tile_edge(h->lv[q].n), h->nu1, h->nu2));
+  if (deep_merge_b<T>(h, l)) base = std::max(base, deep_b2_smem<T>());
   const int S = h->lv[lc].n * h->lv[lc].n;
   for (int staged = 1; staged >= 0; --staged)
     for (int per_sm = 2; per_sm >= 1; --per_sm) {
@@ -1411,6 +1420,7 @@ int emit_deep(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero, cons
   a.prow_off = (int)sh.prow_off;
   a.staged = sh.staged;
   a.stall_cta = h->stall_cta;
+  a.merge_b = deep_merge_b<T>(h, l) ? 1 : 0;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

@@ -389,15 +389,24 @@ __host__ __device__ constexpr size_t pass_b_smem(int nu, bool norm) {
          size_t(BX / 2 + nu + (norm ? 1 : 0) + 3) * (BY / 2 + nu + (norm ? 1 : 0) + 3) * sizeof(T);
 }
 
-// One BX x BY tile of pass B (tile column bx, row by; pidx: the tile's slot in a.partial).
-template <typename T, int BX, int BY, int NT, bool NS, int KS = 0>
-__device__ __forceinline__ void pass_b_tile(const PassBArgs<T>& a, int bx, int by, int pidx,
-                                            unsigned char* smem_raw) {
+// Pass B over the BX x BY points from (x0, y0) (pidx: the slot in a.partial). PB_CS_READY: the
+// caller has already written the coarse window into this call's staging buffer (pass_b_cs);
+// PB_TO_SMEM: the results go to out_s (pitch out_ld, zero outside the grid) instead of a.vout.
+constexpr int PB_CS_READY = 1, PB_TO_SMEM = 2;
+
+// This call's coarse staging buffer in its shared memory (BX x BY points, halo H).
+template <typename T, int BX, int BY>
+__device__ __forceinline__ T* pass_b_cs(unsigned char* smem_raw, int H) {
+  return reinterpret_cast<T*>(smem_raw + 64 * sizeof(double)) + 3 * (BX + 2 * H) * (BY + 2 * H);
+}
+
+template <typename T, int BX, int BY, int NT, bool NS, int KS = 0, int MODE = 0>
+__device__ __forceinline__ void pass_b_core(const PassBArgs<T>& a, int x0, int y0, int pidx,
+                                            unsigned char* smem_raw, T* out_s = nullptr, int out_ld = 0) {
   const int E = a.partial ? 1 : 0;
   const int H = a.nu + E;
   const int W = BX + 2 * H, Hh = BY + 2 * H;
   const int n = a.n, nc = (n - 1) / 2;
-  const int x0 = bx * BX, y0 = by * BY;
   const int gx0 = x0 - H, gy0 = y0 - H;
   // coarse indices that bilinear interpolation reads for fine x in [gx0, gx0 + W)
   const int cx0 = (gx0 >> 1) - 1, cy0 = (gy0 >> 1) - 1;
@@ -412,6 +421,7 @@ __device__ __forceinline__ void pass_b_tile(const PassBArgs<T>& a, int bx, int b
 
   constexpr int K = KS ? KS : stage_k<BX, BY, NT>();
   auto stage_coarse = [&]() {
+    if (MODE & PB_CS_READY) return;
     stage_region<NT, K>(
         CW, CH,
         [&](int lx, int ly) {
@@ -502,8 +512,10 @@ __device__ __forceinline__ void pass_b_tile(const PassBArgs<T>& a, int bx, int b
   double ss = 0.0;
   for_region<NT>(BX, BY, [&](int tx, int ty) {
     const int gx = x0 + tx, gy = y0 + ty;
-    if (inside(gx, gy, n)) {
-      const int k = (ty + H) * W + tx + H;
+    const int k = (ty + H) * W + tx + H;
+    if (MODE & PB_TO_SMEM) {
+      out_s[ty * out_ld + tx] = inside(gx, gy, n) ? src[k] : T(0);
+    } else if (inside(gx, gy, n)) {
       a.vout[(size_t)gy * a.ldvout + gx] = src[k];
       if (E) {
         const double r = (double)op.res(src, k, W, fs[k]);
@@ -515,6 +527,13 @@ __device__ __forceinline__ void pass_b_tile(const PassBArgs<T>& a, int bx, int b
     const double tot = block_sum<NT>(ss, red);
     if (threadIdx.x == 0) a.partial[pidx] = tot;
   }
+}
+
+// One BX x BY tile of pass B (tile column bx, row by; pidx: the tile's slot in a.partial).
+template <typename T, int BX, int BY, int NT, bool NS, int KS = 0>
+__device__ __forceinline__ void pass_b_tile(const PassBArgs<T>& a, int bx, int by, int pidx,
+                                            unsigned char* smem_raw) {
+  pass_b_core<T, BX, BY, NT, NS, KS>(a, bx * BX, by * BY, pidx, smem_raw);
 }
 
 template <typename T, int BX, int BY, int NT, bool NS = false>
