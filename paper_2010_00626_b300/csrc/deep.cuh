@@ -10,9 +10,10 @@
 // condensed map v_lc = P_c f_lc (children_matvec), its rows dealt over the whole grid; each CTA's
 // rows of P_c arrive in its shared memory by one bulk copy issued before the parent's pass A, so the
 // product waits only for f_lc (maps with more rows per CTA than shared memory holds are read from
-// global memory instead, asked of L2 at the same point). Every point's arithmetic is that of the
-// separate launches (the same tile functions on the same tiles, the same per-row sums), so the
-// results equal them bit for bit.
+// global memory instead, asked of L2 at the same point). The last child call's pass B there runs
+// inside its parent's pass B (deep_tiles_b2), one phase and grid barrier fewer. Every point's
+// arithmetic is that of the separate launches (the same tile functions on the same tiles, the same
+// per-row sums), so the results equal them bit for bit.
 //
 // The grid barrier: after a CTA barrier, one thread per CTA counts the CTA in with an acquire-release
 // atomic add and polls the count with acquire loads until the whole grid has arrived (release and
