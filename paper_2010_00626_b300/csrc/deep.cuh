@@ -11,7 +11,8 @@
 // rows of P_c arrive in its shared memory by one bulk copy issued before the parent's pass A, so the
 // product waits only for f_lc (maps with more rows per CTA than shared memory holds are read from
 // global memory instead, asked of L2 at the same point). The last child call's pass B there runs
-// inside its parent's pass B (deep_tiles_b2), one phase and grid barrier fewer. Every point's
+// inside its parent's pass B (deep_tiles_b2), and in FP32 a first child's pass B with the second
+// child's pass A (deep_tiles_ba): one phase and grid barrier fewer each. Every point's
 // arithmetic is that of the separate launches (the same tile functions on the same tiles, the same
 // per-row sums), so the results equal them bit for bit.
 //
@@ -51,6 +52,8 @@ struct DeepArgs {
   int stall_cta;                    // test hook: this CTA leaves at once (-1: none)
   int merge_b;                      // 1: the last child call's pass B at the level above the condensed one
                                     // runs inside its parent's pass B (8 x 8 parent tiles, nu2 = 2)
+  int merge_ba;                     // 1: there, a first child's pass B and the second child's pass A run
+                                    // as one phase (8 x 8 tiles, nu1 = nu2 = 2)
   unsigned* bar;                    // grid barrier words: arrivals, exits (both zero at rest)
   int* err;                         // set to DEEP_ERR_TIMEOUT when a barrier wait runs out
   const int* skip;
@@ -154,6 +157,32 @@ __device__ __forceinline__ void deep_tiles_b2(const PassBArgs<T>& child, const P
   }
 }
 
+// Shared memory of deep_tiles_ba: the tile's pass A, then the first child's window pass B.
+template <typename T>
+__host__ __device__ constexpr size_t deep_ba_smem() {
+  return ((pass_a_smem<T, 8, 8>(2) + 15) / 16) * 16 + pass_b_smem<T, 15, 15>(2, false);
+}
+
+// A first child call's pass B (args `pb`) and the second child call's pass A (args `pa`, the same
+// level, from that result) as one phase: for each 8 x 8 tile, the first child's pass B over the
+// 15 x 15 window that pass A stages for v (nu1 = 2: halo 3), written straight into pass A's v
+// buffer (zero outside the grid), then pass A from there. Same formulas on the same inputs as the
+// two separate passes; the first child's result is needed only by this pass A, so it is not stored.
+template <typename T, int NT>
+__device__ __forceinline__ void deep_tiles_ba(const PassBArgs<T>& pb, const PassAArgs<T>& pa, unsigned char* smem) {
+  constexpr int B = 8, VR = 15;
+  const int tx = (pa.n + B - 1) / B, nt = tx * tx;
+  unsigned char* b_smem = smem + ((pass_a_smem<T, B, B>(2) + 15) / 16) * 16;
+  T* vwin = reinterpret_cast<T*>(smem);  // pass A's first buffer: v's window, pitch 15
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    const int x0 = (t % tx) * B, y0 = (t / tx) * B;
+    pass_b_core<T, VR, VR, NT, false, 1, PB_TO_SMEM>(pb, x0 - 3, y0 - 3, 0, b_smem, vwin, VR);
+    __syncthreads();
+    pass_a_tile<T, B, B, NT, false, 1, true>(pa, t % tx, t / tx, 0, smem);
+    __syncthreads();
+  }
+}
+
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) deep_kernel(const DeepArgs<T> a) {
   if (a.skip && *a.skip) return;  // the same flag for every CTA: the whole grid returns
@@ -176,6 +205,25 @@ __global__ void __launch_bounds__(NT) deep_kernel(const DeepArgs<T> a) {
   auto bail = [&]() {
     if (pinflight) (void)mbar_wait_bounded(pbar, pphase);
   };
+  // before the pass A of a call whose children are condensed (counter k): this CTA's rows of P_c
+  // into shared memory by one bulk copy, or (unstaged maps) asked of L2
+  auto fetch_p = [&](int k) {
+    const int c = k < a.pcls ? k : a.pcls;
+    const T* rows = a.pmap + (size_t)(c - 1) * a.pstride;
+    if (!a.staged) {
+      children_prefetch(rows, a.pld, S, blockIdx.x, gridDim.x);
+    } else if (pbytes) {
+      if (threadIdx.x == 0) {
+        // the previous product's reads of the rows (before a CTA barrier) precede this refill
+        fence_proxy_async_smem();
+        mbar_expect_tx(pbar, pbytes);
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(smem_u32(prow)), "l"(rows + (size_t)rlo * a.pld), "r"(pbytes), "r"(smem_u32(pbar))
+                     : "memory");
+      }
+      pinflight = true;
+    }
+  };
   // the recursion's frames: counter, start and stage of the call at depth d (level top + d)
   int kap[DEEP_MAX_DEPTH], zer[DEEP_MAX_DEPTH], stage[DEEP_MAX_DEPTH];
   int d = 0;
@@ -183,32 +231,18 @@ __global__ void __launch_bounds__(NT) deep_kernel(const DeepArgs<T> a) {
   zer[0] = a.zero;
   stage[0] = 0;
   while (d >= 0) {
-    if (stage[d] == 0) {  // pass A, then the child calls
-      if (d + 1 == a.depth && !a.staged) {  // ask L2 for this CTA's rows of P_c while pass A runs
-        const int c = kap[d] < a.pcls ? kap[d] : a.pcls;
-        children_prefetch(a.pmap + (size_t)(c - 1) * a.pstride, a.pld, S, blockIdx.x, gridDim.x);
-      }
-      if (d + 1 == a.depth && pbytes) {  // fetch this CTA's rows of P_c while pass A runs
-        const int c = kap[d] < a.pcls ? kap[d] : a.pcls;
-        if (threadIdx.x == 0) {
-          // the previous product's reads of the rows (before a CTA barrier) precede this refill
-          fence_proxy_async_smem();
-          mbar_expect_tx(pbar, pbytes);
-          const T* src = a.pmap + (size_t)(c - 1) * a.pstride + (size_t)rlo * a.pld;
-          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                       ::"r"(smem_u32(prow)), "l"(src), "r"(pbytes), "r"(smem_u32(pbar))
-                       : "memory");
+    if (stage[d] == 0 || stage[d] == 4) {  // pass A (stage 4: already run), then the child calls
+      if (stage[d] == 0) {
+        if (d + 1 == a.depth) fetch_p(kap[d]);
+        PassAArgs<T> pa = a.pa[d];
+        if (zer[d]) pa.vin = nullptr;
+        switch (a.tile[d]) {
+          case 32: deep_tiles_a<T, 32, NT>(pa, smem_raw); break;
+          case 16: deep_tiles_a<T, 16, NT>(pa, smem_raw); break;
+          default: deep_tiles_a<T, 8, NT>(pa, smem_raw); break;
         }
-        pinflight = true;
+        if (!grid_barrier(a.bar, a.err)) return bail();
       }
-      PassAArgs<T> pa = a.pa[d];
-      if (zer[d]) pa.vin = nullptr;
-      switch (a.tile[d]) {
-        case 32: deep_tiles_a<T, 32, NT>(pa, smem_raw); break;
-        case 16: deep_tiles_a<T, 16, NT>(pa, smem_raw); break;
-        default: deep_tiles_a<T, 8, NT>(pa, smem_raw); break;
-      }
-      if (!grid_barrier(a.bar, a.err)) return bail();
       if (d + 1 == a.depth) {  // children at the coarse-kernel level: v_lc = P_c f_lc
         if (pinflight) {
           if (!tm_wait_all(pbar, pphase)) {
@@ -251,6 +285,18 @@ __global__ void __launch_bounds__(NT) deep_kernel(const DeepArgs<T> a) {
       stage[d] = 3;
     }
     // stage 3: pass B; the top call's needs no barrier after it (the launch ends)
+    if (a.merge_ba && d + 1 == a.depth && d >= 1 && stage[d - 1] == 1 && kap[d - 1] > 1) {
+      // a first child with a second to come: its pass B and the second child's pass A in one phase;
+      // the second child then continues after its pass A (stage 4) in the same frame
+      fetch_p(kap[d - 1] - 1);
+      deep_tiles_ba<T, NT>(a.pb[d], a.pa[d], smem_raw);
+      if (!grid_barrier(a.bar, a.err)) return bail();
+      stage[d - 1] = 2;
+      kap[d] = kap[d - 1] - 1;
+      zer[d] = 0;
+      stage[d] = 4;
+      continue;
+    }
     if (a.merge_b && d + 1 == a.depth && d >= 1 && (stage[d - 1] == 2 || (stage[d - 1] == 1 && kap[d - 1] <= 1))) {
       // the last child of its parent: both pass B in one phase, and the parent's call is done
       deep_tiles_b2<T, NT>(a.pb[d], a.pb[d - 1], smem_raw);

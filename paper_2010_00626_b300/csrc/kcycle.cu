@@ -1331,6 +1331,17 @@ bool deep_merge_b(const mg_ctx* h, int l) {
   return lc - l >= 2 && h->nu2 == 2 && tile_edge(h->lv[lc - 2].n) == 8;
 }
 
+// Whether a deep launch from level l runs a first child's pass B and the second child's pass A
+// (the level above the condensed one) as one phase: that level's tiles 8 x 8, two sweeps each way,
+// FP32 only (measured at 4095^2: mixed kappa=4 solve 510 -> 506 ms; in FP64 the 15 x 15 window's
+// redundant FP64 work costs more than the phase it saves, 1,704 -> 1,727 ms).
+template <typename T>
+bool deep_merge_ba(const mg_ctx* h, int l) {
+  const int lc = lc_of<T>(h);
+  return std::is_same<T, float>::value && lc - l >= 2 && h->nu1 == 2 && h->nu2 == 2 &&
+         tile_edge(h->lv[lc - 1].n) == 8;
+}
+
 // Launch shape of a deep launch whose top call is at level l: CTAs (two per SM where they fit,
 // else one), dynamic shared memory (the tile passes and P's staged f, then each CTA's rows of P
 // and their copy barrier) and the offset of those rows; false where no shape fits (a device
@@ -1359,6 +1370,7 @@ bool deep_shape(const mg_ctx* h, int l, DeepShape* out) {
   size_t base = (size_t)pld * sizeof(T);
   for (int q = l; q < lc; ++q) base = std::max(base, deep_smem_tiles<T>(tile_edge(h->lv[q].n), h->nu1, h->nu2));
   if (deep_merge_b<T>(h, l)) base = std::max(base, deep_b2_smem<T>());
+  if (deep_merge_ba<T>(h, l)) base = std::max(base, deep_ba_smem<T>());
   const int S = h->lv[lc].n * h->lv[lc].n;
   for (int staged = 1; staged >= 0; --staged)
     for (int per_sm = 2; per_sm >= 1; --per_sm) {
@@ -1421,6 +1433,7 @@ int emit_deep(mg_ctx* h, const BindingT<T>& b, int l, int kappa, bool zero, cons
   a.staged = sh.staged;
   a.stall_cta = h->stall_cta;
   a.merge_b = deep_merge_b<T>(h, l) ? 1 : 0;
+  a.merge_ba = deep_merge_ba<T>(h, l) ? 1 : 0;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

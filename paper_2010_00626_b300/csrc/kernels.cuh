@@ -264,8 +264,10 @@ __host__ __device__ constexpr size_t pass_a_smem(int nu) {
 }
 
 // One BX x BY tile of pass A: tile column bx, tile row by; pidx is the tile's slot in a.partial.
-// KS: points per thread and round of the staging (0: stage_k's choice).
-template <typename T, int BX, int BY, int NT, bool NS, int KS = 0>
+// KS: points per thread and round of the staging (0: stage_k's choice). VIN_READY: the caller has
+// already written v's window (BX + 2H + 1 square from (x0 - H, y0 - H), zero outside the grid)
+// into the first buffer (pass_a_vin), so only f is loaded.
+template <typename T, int BX, int BY, int NT, bool NS, int KS = 0, bool VIN_READY = false>
 __device__ __forceinline__ void pass_a_tile(const PassAArgs<T>& a, int bx, int by, int pidx,
                                             unsigned char* smem_raw) {
   static_assert(BX % 2 == 0 && BY % 2 == 0, "tiles start on even fine indices");
@@ -281,19 +283,29 @@ __device__ __forceinline__ void pass_a_tile(const PassAArgs<T>& a, int bx, int b
   op.load(a.coef, a.level);
 
   // local (lx, ly) <-> global (gx0 + lx, gy0 + ly)
-  stage_region<NT, KS ? KS : stage_k<BX, BY, NT>()>(
-      W, Hh,
-      [&](int lx, int ly) {
-        const int gx = gx0 + lx, gy = gy0 + ly;
-        const bool in = inside(gx, gy, n);
-        return TwoVals<T>{(in && a.vin) ? a.vin[(size_t)gy * a.ldvin + gx] : T(0),
-                          in ? a.f[(size_t)gy * a.ldf + gx] : T(0)};
-      },
-      [&](int lx, int ly, const TwoVals<T>& x) {
-        const int k = ly * W + lx;
-        s0[k] = x.a;
-        fs[k] = x.b;
-      });
+  if constexpr (VIN_READY) {
+    stage_region<NT, KS ? KS : stage_k<BX, BY, NT>()>(
+        W, Hh,
+        [&](int lx, int ly) {
+          const int gx = gx0 + lx, gy = gy0 + ly;
+          return inside(gx, gy, n) ? a.f[(size_t)gy * a.ldf + gx] : T(0);
+        },
+        [&](int lx, int ly, T x) { fs[ly * W + lx] = x; });
+  } else {
+    stage_region<NT, KS ? KS : stage_k<BX, BY, NT>()>(
+        W, Hh,
+        [&](int lx, int ly) {
+          const int gx = gx0 + lx, gy = gy0 + ly;
+          const bool in = inside(gx, gy, n);
+          return TwoVals<T>{(in && a.vin) ? a.vin[(size_t)gy * a.ldvin + gx] : T(0),
+                            in ? a.f[(size_t)gy * a.ldf + gx] : T(0)};
+        },
+        [&](int lx, int ly, const TwoVals<T>& x) {
+          const int k = ly * W + lx;
+          s0[k] = x.a;
+          fs[k] = x.b;
+        });
+  }
   __syncthreads();
 
   T* src = s0;
