@@ -808,7 +808,7 @@ def main():
             chosen = bt.autotune(3, mixed=mixed)
             for xb in xs_b:
                 xb.zero_()
-            bt.solve(xs_b, fs_b, 3, tol, 1)  # builds the graph
+            bt.solve(xs_b, fs_b, 3, tol, 1, mixed=mixed)  # builds the graph the timed solve runs
             for xb in xs_b:
                 xb.zero_()
             torch.cuda.synchronize()
