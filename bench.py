@@ -808,7 +808,9 @@ def main():
             chosen = bt.autotune(3, mixed=mixed)
             for xb in xs_b:
                 xb.zero_()
-            bt.solve(xs_b, fs_b, 3, tol, 1, mixed=mixed)  # builds the graph the timed solve runs
+            # builds the graph the timed solve runs (its key holds the tolerance and the cap, so
+            # the warm-up is the same solve)
+            bt.solve(xs_b, fs_b, 3, tol, 3000, mixed=mixed)
             for xb in xs_b:
                 xb.zero_()
             torch.cuda.synchronize()
@@ -826,8 +828,8 @@ def main():
                 # handle (the batch's, with the same tuned options), one graph launch per solve
                 solo = [bt.instance(i) for i in range(len(ns))]
                 ys = [torch.zeros_like(xb) for xb in xs_b]
-                for i, m in enumerate(solo):
-                    m.solve_mixed(ys[i], fs_b[i], 3, tol, 1, history=False)  # builds its graph
+                for i, m in enumerate(solo):  # builds its graph and a history for the cap; stops at once
+                    m.solve_mixed(ys[i], fs_b[i], 3, 1.0, 3000, history=False)
                 for y in ys:
                     y.zero_()
                 torch.cuda.synchronize()
