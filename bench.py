@@ -658,6 +658,12 @@ def main():
             per_kappa_mixed[kname(k)] = {"ms": round(ms_k, 3), "iterations": it_k,
                                          "ms_per_iteration": round(ms_k / it_k, 4), "relres": rel_k, "status": st_k,
                                          "error_vs_fp64": error_vs_fp64(mg, v, f, x_star)}
+        # the same statement for the FP64 solve to the same tolerance: a relative residual of tol
+        # bounds the error only through cond(A), for either form
+        v.zero_()
+        mg.solve(v, f, kappa, tol, max_cycles, history=False)
+        per_kappa_mixed["fp64_solve_same_tol"] = {"kappa": kname(kappa), "tol": tol,
+                                                  "error_vs_fp64": error_vs_fp64(mg, v, f, x_star)}
         del x_star
 
     # ---------------------------------------------------------------- run-time model (Section 3) and kappa pre-selection
