@@ -223,3 +223,31 @@ def test_fp32_deep_with_maps_too_large_to_stage(lib):
             assert mg.level_grid(3, fp32=True)[1] in (sms, 2 * sms)
         mg.close()
     assert torch.equal(outs[127], outs[0])
+
+
+@pytest.mark.parametrize("n,levels,deep,nu1,nu2,kappa", [
+    (1023, 10, 511, 2, 2, 3),         # four levels of passes (511^2 down to 63^2) in one launch
+    (1023, 10, 255, 2, 2, KAPPA_W),
+    (511, 9, 255, 2, 3, 2),           # three post-sweeps: no merged phases
+    (511, 9, 255, 1, 2, 4),           # one pre-sweep: the pass B phases merged, not B with A
+    (255, 8, 127, 2, 2, 1),           # a V-cycle: no second child
+])
+def test_fp32_deep_merged_phases_equal_separate_launches(lib, n, levels, deep, nu1, nu2, kappa):
+    """FP32 deep launches from 511^2, 255^2 and 127^2 with the tensor-copy passes off (the separate
+    launches then use the tile passes at every level): the merged phases (a first child's pass B
+    with the second child's pass A, the last child's pass B with its parent's) give the separate
+    launches' cycles bit for bit."""
+    import torch
+    f32 = dev(rhs_normal(n, 17), "float32")
+    outs = {}
+    for d in (deep, 0):
+        mg = lib.Multigrid(n, 1e-3, 0.9, levels, nu1=nu1, nu2=nu2)
+        mg.set_option(lib.MG_OPT_TMA_PASSES, 0)
+        mg.set_option(lib.MG_OPT_DEEP_CALLS, d)
+        v = torch.zeros_like(f32)
+        for _ in range(2):
+            mg.kcycle_f32(v, f32, kappa)
+        torch.cuda.synchronize()
+        outs[d] = v.clone()
+        mg.close()
+    assert torch.equal(outs[deep], outs[0])
