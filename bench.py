@@ -38,8 +38,8 @@ NOMINAL_FP64_TFLOPS = 1.25  # nominal B300 FP64 rate
 # text changes the figure no longer describes the kernel and is reported as null until a new
 # capture replaces it.
 PASS_A_L0_TRAFFIC = {"source": "paper_2010_00626_b300/csrc/kernels.cuh", "until": "// Pass B: v <- v + P v_c",
-                     "sha256": "612a8af4a105f135d1ff9c3be1118abd99b8e6ed404c6d685c3ce7d6f438a09d",
-                     "bytes": 268_396_288 + 133_620_736}
+                     "sha256": "4bc1574b89893c8218c12cfb6e265967970d9dfc870582efd8c56923a292db58",
+                     "bytes": 268_414_976 + 133_147_136}
 
 
 # The same for the FP32 tensor-copy passes at level 0 of the mixed solve's FP32 cycle (4095^2), keyed

@@ -223,6 +223,20 @@ int tile_edge(int n) {
 // rows of the tile of a pass at side n: `sums` for the passes that write residual sums
 int tile_rows(int n, bool sums = true) { return tile_edge(n) == 64 ? (sums ? 48 : 32) : tile_edge(n); }
 
+// FP64 levels below level 0 that one tile per SM covers: the smallest even tile edge whose tiles
+// number at most the SMs, where that edge is an instantiated one (on 148 SMs: 511^2 in 12 x 12
+// tiles of 44^2, 255^2 in 12 x 12 tiles of 22^2), instead of tile_edge's 256 tiles, of which most
+// SMs would run two on their FP64 pipe. 0: none.
+using Tile44 = TileCfg<44, 44, NT_BIG>;
+using Tile22 = TileCfg<22, 22, NT_SMALL>;
+int wide_edge(int n, int sms) {
+  for (int b = 2; b <= 64; b += 2) {
+    const int g = (n + b - 1) / b;
+    if (g * g <= sms) return (b == 44 || b == 22) ? b : 0;
+  }
+  return 0;
+}
+
 // ns: the general (non-symmetric) stencil variant, FP64 only.
 template <typename Cfg, typename T>
 int launch_pass_a(const PassAArgs<T>& a, cudaStream_t s, bool ns = false) {
@@ -301,6 +315,10 @@ int set_all_smem_attrs() {
   KC_TRY((set_smem_attrs<Tile32, T>()));
   KC_TRY((set_smem_attrs<Tile16, T>()));
   KC_TRY((set_smem_attrs<Tile8, T>()));
+  if constexpr (std::is_same<T, double>::value) {
+    KC_TRY((set_smem_attrs<Tile44, T>()));
+    KC_TRY((set_smem_attrs<Tile22, T>()));
+  }
   KC_CUDA(cudaFuncSetAttribute(coarse_kernel<T, nt_coarse<T>(), false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)coarse_smem_max<T>()));
   KC_CUDA(cudaFuncSetAttribute(coarse_kernel<T, nt_coarse<T>(), true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -884,6 +902,14 @@ int emit_pass_a(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const
       return st;
     }
   }
+  if constexpr (std::is_same<T, double>::value) {
+    const int w = (!lines && l >= 1 && !a.partial && !h->nonsym) ? wide_edge(a.n, h->sms) : 0;
+    if (w) {
+      st = w == 44 ? launch_pass_a<Tile44>(a, s) : launch_pass_a<Tile22>(a, s);
+      prof_end(h, s);
+      return st;
+    }
+  }
   switch (tile_edge(a.n)) {
     case 64: st = a.partial ? launch_pass_a<Tile64>(a, s, h->nonsym) : launch_pass_a<Tile64N>(a, s, h->nonsym); break;
     case 32: st = launch_pass_a<Tile32>(a, s, h->nonsym); break;
@@ -932,6 +958,14 @@ int emit_pass_b(mg_ctx* h, const BindingT<T>& b, int l, int nu, double* partial,
     if (!lines && partial == nullptr && fast32_ok(a.n, nu, a.vin, a.ldvin) && fast32_ok(a.n, nu, a.f, a.ldf) &&
         fast32_ok(a.n, nu, a.vout, a.ldvout) && ((uintptr_t)a.vc & 7) == 0 && (a.ldc & 1) == 0) {
       st = launch_pass_b_fast32(a, s);
+      prof_end(h, s);
+      return st;
+    }
+  }
+  if constexpr (std::is_same<T, double>::value) {
+    const int w = (!lines && l >= 1 && !a.partial && !h->nonsym) ? wide_edge(a.n, h->sms) : 0;
+    if (w) {
+      st = w == 44 ? launch_pass_b<Tile44>(a, s) : launch_pass_b<Tile22>(a, s);
       prof_end(h, s);
       return st;
     }
@@ -2559,7 +2593,8 @@ int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas) {
     }
     return MG_OK;
   }
-  const int bx = tile_edge(n), by = tile_rows(n, false);
+  const int w = (!fp32 && level >= 1 && !h->nonsym) ? wide_edge(n, h->sms) : 0;
+  const int bx = w ? w : tile_edge(n), by = w ? w : tile_rows(n, false);
   *ctas = ((n + bx - 1) / bx) * ((n + by - 1) / by);
   return MG_OK;
 }

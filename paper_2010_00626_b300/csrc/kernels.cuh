@@ -207,12 +207,13 @@ __device__ __forceinline__ void stage_region(int Rw, int Rh, Load load, Store st
 }
 
 // Points per thread and round of a tile's staging: the region of a BX x BY tile with nu = 2 over
-// NT threads, at most 8, for tiles up to 16 wide; the 32- and 64-wide tiles of the larger levels
-// keep one (more registers would cost them CTAs per SM, and their many warps per SM hide the
-// loads: measured, 32-wide FP64 pass B at 1023^2 71.0 -> 72.2 us with four).
+// NT threads, at most 8; the 32- and 64-wide tiles of the larger levels keep one (more registers
+// would cost them CTAs per SM, and their many warps per SM hide the loads: measured, 32-wide FP64
+// pass B at 1023^2 71.0 -> 72.2 us with four).
 template <int BX, int BY, int NT>
 constexpr int stage_k() {
-  return BX > 16 ? 1 : (((BX + 7) * (BY + 7) + NT - 1) / NT > 8 ? 8 : ((BX + 7) * (BY + 7) + NT - 1) / NT);
+  return BX == 32 || BX == 64 ? 1
+                              : (((BX + 7) * (BY + 7) + NT - 1) / NT > 8 ? 8 : ((BX + 7) * (BY + 7) + NT - 1) / NT);
 }
 
 template <typename T>

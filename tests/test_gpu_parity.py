@@ -229,8 +229,9 @@ def test_counters_match_closed_forms(lib, kappa):
 
 
 def test_level_grid_reports_the_launch_shapes(lib):
-    """CTAs per pass launch at 4095^2: 64x32 tiles at 4095 and 2047 (about two waves), 32^2 at 1023
-    and 511, 16^2 at 255, 8^2 below (about one wave), one coarse-kernel CTA at 15^2 and below. FP32:
+    """CTAs per pass launch at 4095^2: 64x32 tiles at 4095 and 2047 (about two waves), 32^2 at 1023,
+    one tile per SM at 511 and 255 (FP64: 12^2 tiles of 44^2 and 22^2 on 148 SMs), 8^2 below, one
+    coarse-kernel CTA at 15^2 and below. FP32:
     the persistent tensor-copy passes at 4095, 2047 and 1023 (one CTA per SM: 2240, 576 and 288
     tiles of 120 columns), the FP32 coarse kernel from 31^2; with MG_OPT_TMA_PASSES = 0 pass B as
     the register pipelines at 4095 (35 strips of 120 columns, 4 per CTA, chunks of 64 rows) and the
@@ -240,18 +241,25 @@ def test_level_grid_reports_the_launch_shapes(lib):
     coarse kernel at 31^2, the 63^2 level keeps its 64 tiles (a fused call would need at most 16)."""
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
+
+    def one_per_sm(n, old):  # the smallest even edge with at most one tile per SM, where built
+        tiles = lambda b: ((n + b - 1) // b) ** 2
+        b = next(b for b in range(2, 66, 2) if tiles(b) <= sms or b == 64)
+        return tiles(b) if b in (44, 22) and tiles(b) <= sms else old
+
+    wide = [one_per_sm(511, 16 * 16), one_per_sm(255, 16 * 16)]
+    assert sms != 148 or wide == [144, 144]
     default = lib.Multigrid(4095, 1e-4, math.pi / 3, 12)
     grid = [default.level_grid(l)[1] for l in range(12)]
     # the 127^2 and 63^2 levels inside the persistent deep launches (one or two CTAs per SM)
-    assert grid[:5] == [64 * 128, 32 * 64, 32 * 32, 16 * 16, 16 * 16] and grid[7:] == [1] * 5
+    assert grid[:5] == [64 * 128, 32 * 64, 32 * 32] + wide and grid[7:] == [1] * 5
     assert grid[5] == grid[6] and grid[5] in (sms, 2 * sms)
     default.set_option(lib.MG_OPT_DEEP_CALLS, 0)
     assert [default.level_grid(l)[1] for l in range(5, 8)] == [16 * 16, 8 * 8, 1]
     mg = lib.Multigrid(4095, 1e-4, math.pi / 3, 12, coarse_n=15)
     mg.set_option(lib.MG_OPT_DEEP_CALLS, 0)
     fp64 = [mg.level_grid(l) for l in range(12)]
-    assert [c for _, c in fp64] == [64 * 128, 32 * 64, 32 * 32, 16 * 16, 16 * 16, 16 * 16, 8 * 8, 4 * 4,
-                                     1, 1, 1, 1]
+    assert [c for _, c in fp64] == [64 * 128, 32 * 64, 32 * 32] + wide + [16 * 16, 8 * 8, 4 * 4, 1, 1, 1, 1]
     assert [m for m, _ in fp64] == [2 ** (12 - l) - 1 for l in range(12)]
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
