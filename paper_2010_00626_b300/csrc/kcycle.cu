@@ -226,7 +226,9 @@ int tile_rows(int n, bool sums = true) { return tile_edge(n) == 64 ? (sums ? 48 
 // FP64 levels below level 0 that one tile per SM covers: the smallest even tile edge whose tiles
 // number at most the SMs, where that edge is an instantiated one (on 148 SMs: 511^2 in 12 x 12
 // tiles of 44^2, 255^2 in 12 x 12 tiles of 22^2), instead of tile_edge's 256 tiles, of which most
-// SMs would run two on their FP64 pipe. 0: none.
+// SMs would run two on their FP64 pipe. 0: none. Not for the instances of a batch: their passes
+// share the SMs with the other instances' (the 44^2 pass B's 512 threads take an SM's whole
+// register file; measured, the FP64 batch 10.52 -> 10.75 s with them).
 using Tile44 = TileCfg<44, 44, NT_BIG>;
 using Tile22 = TileCfg<22, 22, NT_SMALL>;
 int wide_edge(int n, int sms) {
@@ -903,7 +905,7 @@ int emit_pass_a(mg_ctx* h, const BindingT<T>& b, int l, bool zero, int nu, const
     }
   }
   if constexpr (std::is_same<T, double>::value) {
-    const int w = (!lines && l >= 1 && !a.partial && !h->nonsym) ? wide_edge(a.n, h->sms) : 0;
+    const int w = (!lines && l >= 1 && !a.partial && !h->nonsym && !h->batched) ? wide_edge(a.n, h->sms) : 0;
     if (w) {
       st = w == 44 ? launch_pass_a<Tile44>(a, s) : launch_pass_a<Tile22>(a, s);
       prof_end(h, s);
@@ -963,7 +965,7 @@ int emit_pass_b(mg_ctx* h, const BindingT<T>& b, int l, int nu, double* partial,
     }
   }
   if constexpr (std::is_same<T, double>::value) {
-    const int w = (!lines && l >= 1 && !a.partial && !h->nonsym) ? wide_edge(a.n, h->sms) : 0;
+    const int w = (!lines && l >= 1 && !a.partial && !h->nonsym && !h->batched) ? wide_edge(a.n, h->sms) : 0;
     if (w) {
       st = w == 44 ? launch_pass_b<Tile44>(a, s) : launch_pass_b<Tile22>(a, s);
       prof_end(h, s);
@@ -2593,7 +2595,7 @@ int mg_level_grid(mg_handle h, int level, int fp32, int* n_level, int* ctas) {
     }
     return MG_OK;
   }
-  const int w = (!fp32 && level >= 1 && !h->nonsym) ? wide_edge(n, h->sms) : 0;
+  const int w = (!fp32 && level >= 1 && !h->nonsym && !h->batched) ? wide_edge(n, h->sms) : 0;
   const int bx = w ? w : tile_edge(n), by = w ? w : tile_rows(n, false);
   *ctas = ((n + bx - 1) / bx) * ((n + by - 1) / by);
   return MG_OK;
