@@ -270,7 +270,8 @@ int mg_counters(mg_handle h, int kappa, long long* calls_per_level, long long* l
  * arrays aligned to 16 bytes, as mg_solve_mixed's own are). A pass that also writes residual sums
  * (the level-0 pass A of a stand-alone FP64 solve) uses 64 x 48 tiles where the others use 64 x 32;
  * FP64 levels below level 0 that one tile per SM covers run one such tile per CTA (on 148 SMs: 511
- * in 12 x 12 tiles of 44^2, 255 in 12 x 12 tiles of 22^2); in the FP32 cycle at sides of 4095 and more the value is pass B's, pass A running as 112 x 16
+ * in 12 x 12 tiles of 44^2, 255 in 12 x 12 tiles of 22^2; not in the instances of a batch); in the
+ * FP32 cycle at sides of 4095 and more the value is pass B's, pass A running as 112 x 16
  * tiles there. For a level handled inside the coarse-level kernel *ctas = 1, that kernel's one
  * CTA; for the level whose calls run as one cluster launch (MG_OPT_FUSED_CALL), the cluster's CTAs. Damped-Jacobi smoother with full coarsening only (else
  * MG_ERR_ARG). Host pointers, both required. No device work. */
